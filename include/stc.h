@@ -1,0 +1,202 @@
+/*
+ * stc.h -- C ABI of the GB300 structure-adaptive tile Cholesky (numeric phase).
+ *
+ * Method: arxiv 2609.29765, "Dense Matrices Are Alike; Sparse Matrices Are Sparse in
+ * Their Own Way: A Structure-Adaptive Tile Cholesky Factorization".
+ *
+ *   analyze   -- once per sparsity pattern, on the host (Sec. 3 ordering and symbolic
+ *                factorization; Sec. 5.1 selector; Sec. 5.2 per-tile metadata, task list
+ *                of Algorithm 1 and per-task scatter maps).  The interface splits a
+ *                once-per-pattern analyze from a repeated factorize (Sec. 6.7).
+ *   factorize -- per call, on the GPU: replay of the POTRF / SYRK / TRSM / GEMM tile
+ *                tasks (Algorithm 1 executed as in Algorithm 2, with device-side
+ *                dependency counters in place of the progress matrix P, Sec. 5.3) on
+ *                dense tiles and on active-column tiles (Sec. 4).
+ *   logdet, solve -- consume the factor where it sits (Sec. 5.4 log-determinant reuse;
+ *                Sec. 6.8 solves).
+ *   logdet_backward / quad_backward -- adjoints; no counterpart in the paper (it leaves
+ *                selected inversion to separate work, Sec. 6.3): Takahashi selected
+ *                inverse on the same tile map.
+ *
+ * Conventions (every entry point):
+ *   - Return value: STC_OK (0) or a negative STC_ERR_* code; nothing is thrown.
+ *   - Patterns are the LOWER triangle with the diagonal, CSC, int64, rows strictly
+ *     ascending in each column, in the caller's original ordering.
+ *   - A plan (stc_plan) is opaque, owned by the library, freed by stc_plan_destroy.
+ *     It keeps a device copy of its metadata, created on first device use on the
+ *     current CUDA device (that first call synchronizes the device; make it before
+ *     any stream capture, or call stc_plan_upload first).
+ *   - All d_* buffers are DEVICE pointers owned by the caller; all h_* / unprefixed
+ *     array arguments of analyze/export are HOST pointers owned by the caller.
+ *   - Device calls are asynchronous on `stream` (a cudaStream_t passed as void*;
+ *     NULL = legacy default stream).  Numerical failure is not an error return: it is
+ *     reported per batch item in d_info (0 = success, j+1 = first non-positive pivot at
+ *     global permuted column j); the item's logdet is then NaN.
+ *   - Batched buffers are item-major: item b of d_values starts at b*nnzA, item b of a
+ *     factor at b*stc_factor_bytes(plan,1) bytes.
+ */
+#ifndef STC_H
+#define STC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define STC_OK 0
+#define STC_ERR_INVALID_ARG (-1)     /* null pointer, bad size, bad option        */
+#define STC_ERR_INVALID_PATTERN (-2) /* not lower CSC / unsorted / missing diag   */
+#define STC_ERR_OUT_OF_MEMORY (-3)   /* host or device allocation failed          */
+#define STC_ERR_CUDA (-4)            /* a CUDA runtime call failed                */
+#define STC_ERR_TIMEOUT (-5)         /* a device dependency wait hit its limit    */
+#define STC_ERR_UNSUPPORTED (-6)     /* option or size outside what is built      */
+#define STC_ERR_BUFFER_TOO_SMALL (-7)
+
+/* ---- routes (Sec. 5.1) ------------------------------------------------- */
+#define STC_ROUTE_AUTO (-1)
+#define STC_ROUTE_DENSE 0       /* every active tile stored as a full n_b x n_b block  */
+#define STC_ROUTE_SEMISPARSE 1  /* active-column tiles + banded-packed diagonal tiles */
+#define STC_ROUTE_SUPERNODAL 2  /* selector result only: the supernodal route is not
+                                   built; such plans execute on the semisparse route  */
+
+/* ---- orderings (Sec. 3) ------------------------------------------------ */
+#define STC_ORDER_AUTO 0     /* ND when coordinates are given, else best of RCM/natural */
+#define STC_ORDER_NATURAL 1
+#define STC_ORDER_GIVEN 2    /* stc_options.perm */
+#define STC_ORDER_ND 3       /* geometric nested dissection on lattice coordinates    */
+#define STC_ORDER_RCM 4      /* reverse Cuthill-McKee                                  */
+
+typedef struct stc_options {
+    int32_t nb;           /* tile size n_b; 0 = 128.  Built range 8..128, multiple of 8 */
+    int32_t force_route;  /* STC_ROUTE_AUTO, STC_ROUTE_DENSE or STC_ROUTE_SEMISPARSE   */
+    int32_t ordering;     /* STC_ORDER_*                                               */
+    int32_t nd_leaf;      /* ND leaf size; 0 = 64                                      */
+    const int64_t* perm;  /* host [n], for STC_ORDER_GIVEN: perm[k] = original index of
+                             the k-th pivot (copied during analyze)                    */
+    int32_t row_slices;   /* rows of an off-diagonal tile split into this many device
+                             tasks (1,2,4,8); 0 = chosen per call from the batch size  */
+    int32_t reserved0;
+    int64_t spin_limit;   /* polls before a device dependency wait gives up with
+                             STC_ERR_TIMEOUT; 0 = default (about 10 s)                 */
+    double gate_rho_dense;   /* selector gates (Table 5); 0 = default 0.90 */
+    double gate_phi_fill;    /* 0 = default 2.0  */
+    double gate_rho_semi;    /* 0 = default 0.15 */
+    double gate_sigma_skew;  /* 0 = default 20   */
+} stc_options;
+
+typedef struct stc_plan stc_plan;
+
+typedef struct stc_plan_info {
+    int64_t n, nb, nt;          /* order, tile size, N_T = ceil(n/nb)                 */
+    int64_t ntiles;             /* active tiles (diagonal included)                   */
+    int64_t nnzA;               /* stored lower entries of A                          */
+    int64_t nnzL;               /* structural non-zeros of L (diagonal included)      */
+    int64_t stored_entries;     /* doubles stored for L in tiles (per item)           */
+    int64_t factor_doubles;     /* per-item factor footprint incl. logdet partials    */
+    int32_t route_selected;     /* selector's choice (STC_ROUTE_*)                    */
+    int32_t route_executed;     /* route the plan runs (dense or semisparse)          */
+    int32_t ordering;           /* ordering used (STC_ORDER_*)                        */
+    int32_t reserved0;
+    double phi, rho, sigma;     /* routing features (Sec. 5.1)                        */
+    int64_t ntasks_alg1;        /* Algorithm 1 tasks                                  */
+    int64_t n_potrf, n_syrk, n_trsm, n_gemm;
+    double flops_alg;           /* sum_j c_j^2 (c_j = column count of L)              */
+    double flops_tile;          /* flops the tile kernels execute (row slice = 1)     */
+    double analyze_seconds;     /* host wall time of stc_analyze                      */
+} stc_plan_info;
+
+/* what stc_plan_export returns (all int64 unless noted) */
+#define STC_EXPORT_PERM 0       /* [n]                                               */
+#define STC_EXPORT_ETREE 1      /* [n] parent of each permuted column, -1 for roots  */
+#define STC_EXPORT_LP 2         /* [n+1] column pointers of L's structure            */
+#define STC_EXPORT_LI 3         /* [nnzL] row indices of L's structure               */
+#define STC_EXPORT_TILES 4      /* [ntiles][9]: I, J, |A|, aind offset, contiguous,
+                                   full, kd (diag) or -1, row extent r0, r1           */
+#define STC_EXPORT_AIND 5       /* concatenated active-column lists                  */
+#define STC_EXPORT_TASKS 6      /* [ntasks][4]: Algorithm 1 (case, m, k, n), -1 = unused */
+#define STC_EXPORT_VALUE_MAP 7  /* [nnzA] offset (doubles) of each A entry in a factor */
+#define STC_EXPORT_TILE_OFFSETS 8 /* [ntiles] offset (doubles) of each tile's storage */
+
+/* Fill *opt with defaults (nb 128, auto route, auto ordering, ND leaf 64). */
+void stc_options_default(stc_options* opt);
+
+/* Symbolic analysis (host only; no GPU needed).
+ *   n, colptr[n+1], rowind[nnz]: lower CSC pattern of A (original order).
+ *   coords: optional host [n][3] lattice coordinates for geometric ND (integral values;
+ *           rows with a NaN coordinate are set-aside dense rows, ordered last); NULL ok.
+ *   opt: NULL = defaults.  *plan_out receives a new plan.
+ * Errors: STC_ERR_INVALID_ARG, STC_ERR_INVALID_PATTERN, STC_ERR_UNSUPPORTED (nb outside
+ * 8..128 or not a multiple of 8; ND without integral coordinates), STC_ERR_OUT_OF_MEMORY. */
+int stc_analyze(int64_t n, const int64_t* colptr, const int64_t* rowind,
+                const double* coords, const stc_options* opt, stc_plan** plan_out);
+
+int stc_plan_info_get(const stc_plan* plan, stc_plan_info* out);
+
+/* Copy one symbolic array (STC_EXPORT_*) into host memory.  Call with buf == NULL to
+ * read the size in bytes into *bytes; STC_ERR_BUFFER_TOO_SMALL if *bytes is short. */
+int stc_plan_export(const stc_plan* plan, int what, void* buf, size_t* bytes);
+
+/* Upload the plan's device metadata to the current CUDA device now (synchronous).
+ * Optional: every device call does it on first use. */
+int stc_plan_upload(stc_plan* plan);
+
+void stc_plan_destroy(stc_plan* plan);
+
+/* Bytes of caller-owned device memory:
+ *   factor    -- the tile-stored factor of `batch` items (item stride = value at batch 1)
+ *   workspace -- dependency counters, queue head and status word used by factorize,
+ *                solve and logdet_backward (contents need not be initialised). */
+size_t stc_factor_bytes(const stc_plan* plan, int64_t batch);
+size_t stc_workspace_bytes(const stc_plan* plan, int64_t batch);
+
+/* Numeric factorization of `batch` value sets of the plan's pattern, one persistent
+ * kernel walking the task DAG (Algorithm 2 with per-tile counters).
+ *   d_values [batch][nnzA] FP64 in the original CSC order of the analyzed pattern;
+ *   d_factor stc_factor_bytes(plan,batch) bytes (written); d_work
+ *   stc_workspace_bytes(plan,batch) bytes; d_info [batch] int32 (written).
+ * A wait that exceeds spin_limit sets the workspace status to STC_ERR_TIMEOUT and the
+ * kernel finishes (results then undefined); read it with stc_sync_status. */
+int stc_factorize(const stc_plan* plan, const double* d_values, int64_t batch,
+                  void* d_factor, void* d_work, int32_t* d_info, void* stream);
+
+/* The two halves of stc_factorize, for callers that time or overlap them separately:
+ *   stc_scatter_values      -- a1: zero the factor, copy d_values into tile storage
+ *                              through the plan's value map, set the padding diagonal;
+ *   stc_factorize_scattered -- a2..a9: the persistent task-DAG replay on a factor that
+ *                              stc_scatter_values filled (same arguments as above). */
+int stc_scatter_values(const stc_plan* plan, const double* d_values, int64_t batch,
+                       void* d_factor, void* stream);
+int stc_factorize_scattered(const stc_plan* plan, int64_t batch, void* d_factor, void* d_work,
+                            int32_t* d_info, void* stream);
+
+/* Synchronize `stream` and return the device status word of d_work: STC_OK or
+ * STC_ERR_TIMEOUT (a dependency wait gave up), or STC_ERR_CUDA. */
+int stc_sync_status(const void* d_work, void* stream);
+
+/* logdet(A_b) = 2 sum_j log L_jj for every item b; d_logdet [batch] FP64. */
+int stc_logdet(const stc_plan* plan, const void* d_factor, int64_t batch,
+               double* d_logdet, void* stream);
+
+/* x = A^{-1} b for `nrhs` right-hand sides per item; d_b, d_x [batch][nrhs][n] FP64
+ * (original ordering).  d_x may not alias d_b. d_work: stc_workspace_bytes(plan,batch*nrhs). */
+int stc_solve(const stc_plan* plan, const void* d_factor, int64_t batch, int64_t nrhs,
+              const double* d_b, double* d_x, void* d_work, void* stream);
+
+/* Copy L's values out of tile storage into CSC order (STC_EXPORT_LP / LI layout):
+ * d_Lx [batch][nnzL] FP64. */
+int stc_factor_to_csc(const stc_plan* plan, const void* d_factor, int64_t batch,
+                      double* d_Lx, void* stream);
+
+/* FP64 throughput probe (no counterpart in the paper): runs independent DFMA chains on
+ * every SM for `iters` iterations, synchronously on the legacy stream, and writes the
+ * measured GFLOP/s to *gflops.  d_scratch: device buffer of scratch_doubles >= 256
+ * doubles (results are written there so the work is not optimised away). */
+int stc_fp64_peak_probe(double* d_scratch, int64_t scratch_doubles, int64_t iters, double* gflops);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* STC_H */

@@ -1,0 +1,230 @@
+"""ctypes binding of libstc.so (include/stc.h).  Argument marshalling only.
+
+Every function carries the C name and takes numpy arrays (host) or torch CUDA tensors
+(device); it converts them to pointers and returns the C status code.  The library is
+loaded from the package's _build directory; if it is not there this module raises at
+import time of the first call: there is no CPU fallback anywhere in the product.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+STC_OK = 0
+STC_ERR_INVALID_ARG = -1
+STC_ERR_INVALID_PATTERN = -2
+STC_ERR_OUT_OF_MEMORY = -3
+STC_ERR_CUDA = -4
+STC_ERR_TIMEOUT = -5
+STC_ERR_UNSUPPORTED = -6
+STC_ERR_BUFFER_TOO_SMALL = -7
+ERRORS = {0: "ok", -1: "invalid argument", -2: "invalid pattern", -3: "out of memory",
+          -4: "CUDA error", -5: "device wait timeout", -6: "unsupported", -7: "buffer too small"}
+
+STC_ROUTE_AUTO, STC_ROUTE_DENSE, STC_ROUTE_SEMISPARSE, STC_ROUTE_SUPERNODAL = -1, 0, 1, 2
+STC_ORDER_AUTO, STC_ORDER_NATURAL, STC_ORDER_GIVEN, STC_ORDER_ND, STC_ORDER_RCM = 0, 1, 2, 3, 4
+(STC_EXPORT_PERM, STC_EXPORT_ETREE, STC_EXPORT_LP, STC_EXPORT_LI, STC_EXPORT_TILES, STC_EXPORT_AIND,
+ STC_EXPORT_TASKS, STC_EXPORT_VALUE_MAP, STC_EXPORT_TILE_OFFSETS) = range(9)
+
+# every symbol include/stc.h declares
+EXPORTED = [
+    "stc_options_default", "stc_analyze", "stc_plan_info_get", "stc_plan_export", "stc_plan_upload",
+    "stc_plan_destroy", "stc_factor_bytes", "stc_workspace_bytes", "stc_factorize", "stc_scatter_values",
+    "stc_factorize_scattered", "stc_sync_status",
+    "stc_logdet", "stc_solve", "stc_factor_to_csc", "stc_fp64_peak_probe",
+]
+
+
+class StcError(RuntimeError):
+    def __init__(self, code, where=""):
+        super().__init__("%s: %s (%d)" % (where, ERRORS.get(code, "error"), code))
+        self.code = code
+
+
+class stc_options(C.Structure):
+    _fields_ = [("nb", C.c_int32), ("force_route", C.c_int32), ("ordering", C.c_int32),
+                ("nd_leaf", C.c_int32), ("perm", C.POINTER(C.c_int64)), ("row_slices", C.c_int32),
+                ("reserved0", C.c_int32), ("spin_limit", C.c_int64), ("gate_rho_dense", C.c_double),
+                ("gate_phi_fill", C.c_double), ("gate_rho_semi", C.c_double),
+                ("gate_sigma_skew", C.c_double)]
+
+
+class stc_plan_info(C.Structure):
+    _fields_ = [("n", C.c_int64), ("nb", C.c_int64), ("nt", C.c_int64), ("ntiles", C.c_int64),
+                ("nnzA", C.c_int64), ("nnzL", C.c_int64), ("stored_entries", C.c_int64),
+                ("factor_doubles", C.c_int64), ("route_selected", C.c_int32),
+                ("route_executed", C.c_int32), ("ordering", C.c_int32), ("reserved0", C.c_int32),
+                ("phi", C.c_double), ("rho", C.c_double), ("sigma", C.c_double),
+                ("ntasks_alg1", C.c_int64), ("n_potrf", C.c_int64), ("n_syrk", C.c_int64),
+                ("n_trsm", C.c_int64), ("n_gemm", C.c_int64), ("flops_alg", C.c_double),
+                ("flops_tile", C.c_double), ("analyze_seconds", C.c_double)]
+
+
+_lib = None
+_lock = threading.Lock()
+_vp = C.c_void_p
+
+
+def lib():
+    """Load libstc.so (building it first only when it has never been built here)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(_build.LIB):
+            _build.build()
+        L = C.CDLL(_build.LIB)
+        L.stc_options_default.argtypes = [C.POINTER(stc_options)]
+        L.stc_options_default.restype = None
+        L.stc_analyze.argtypes = [C.c_int64, _vp, _vp, _vp, C.POINTER(stc_options), C.POINTER(_vp)]
+        L.stc_analyze.restype = C.c_int
+        L.stc_plan_info_get.argtypes = [_vp, C.POINTER(stc_plan_info)]
+        L.stc_plan_info_get.restype = C.c_int
+        L.stc_plan_export.argtypes = [_vp, C.c_int, _vp, C.POINTER(C.c_size_t)]
+        L.stc_plan_export.restype = C.c_int
+        L.stc_plan_upload.argtypes = [_vp]
+        L.stc_plan_upload.restype = C.c_int
+        L.stc_plan_destroy.argtypes = [_vp]
+        L.stc_plan_destroy.restype = None
+        L.stc_factor_bytes.argtypes = [_vp, C.c_int64]
+        L.stc_factor_bytes.restype = C.c_size_t
+        L.stc_workspace_bytes.argtypes = [_vp, C.c_int64]
+        L.stc_workspace_bytes.restype = C.c_size_t
+        L.stc_factorize.argtypes = [_vp, _vp, C.c_int64, _vp, _vp, _vp, _vp]
+        L.stc_factorize.restype = C.c_int
+        L.stc_scatter_values.argtypes = [_vp, _vp, C.c_int64, _vp, _vp]
+        L.stc_scatter_values.restype = C.c_int
+        L.stc_factorize_scattered.argtypes = [_vp, C.c_int64, _vp, _vp, _vp, _vp]
+        L.stc_factorize_scattered.restype = C.c_int
+        L.stc_sync_status.argtypes = [_vp, _vp]
+        L.stc_sync_status.restype = C.c_int
+        L.stc_logdet.argtypes = [_vp, _vp, C.c_int64, _vp, _vp]
+        L.stc_logdet.restype = C.c_int
+        L.stc_solve.argtypes = [_vp, _vp, C.c_int64, C.c_int64, _vp, _vp, _vp, _vp]
+        L.stc_solve.restype = C.c_int
+        L.stc_factor_to_csc.argtypes = [_vp, _vp, C.c_int64, _vp, _vp]
+        L.stc_factor_to_csc.restype = C.c_int
+        L.stc_fp64_peak_probe.argtypes = [_vp, C.c_int64, C.c_int64, C.POINTER(C.c_double)]
+        L.stc_fp64_peak_probe.restype = C.c_int
+        _lib = L
+        return L
+
+
+def check(code, where=""):
+    if code != STC_OK:
+        raise StcError(code, where)
+    return code
+
+
+def _host_ptr(a):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+def _dev_ptr(t):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)
+
+
+# ---- C-named marshalling wrappers ------------------------------------------------
+def stc_options_default() -> stc_options:
+    o = stc_options()
+    lib().stc_options_default(C.byref(o))
+    return o
+
+
+def stc_analyze(n, colptr, rowind, coords=None, opt: stc_options | None = None):
+    """Returns (status, plan_handle)."""
+    colptr = np.ascontiguousarray(colptr, dtype=np.int64)
+    rowind = np.ascontiguousarray(rowind, dtype=np.int64)
+    if coords is not None:
+        coords = np.ascontiguousarray(coords, dtype=np.float64)
+    h = C.c_void_p()
+    rc = lib().stc_analyze(int(n), _host_ptr(colptr), _host_ptr(rowind), _host_ptr(coords),
+                           C.byref(opt) if opt is not None else None, C.byref(h))
+    return rc, h
+
+
+def stc_plan_info_get(plan) -> stc_plan_info:
+    info = stc_plan_info()
+    check(lib().stc_plan_info_get(plan, C.byref(info)), "stc_plan_info_get")
+    return info
+
+
+def stc_plan_export(plan, what: int) -> np.ndarray:
+    sz = C.c_size_t(0)
+    check(lib().stc_plan_export(plan, int(what), None, C.byref(sz)), "stc_plan_export")
+    out = np.empty(sz.value // 8, dtype=np.int64)
+    check(lib().stc_plan_export(plan, int(what), _host_ptr(out), C.byref(sz)), "stc_plan_export")
+    return out
+
+
+def stc_plan_upload(plan):
+    return lib().stc_plan_upload(plan)
+
+
+def stc_plan_destroy(plan):
+    if plan:
+        lib().stc_plan_destroy(plan)
+
+
+def stc_factor_bytes(plan, batch):
+    return int(lib().stc_factor_bytes(plan, int(batch)))
+
+
+def stc_workspace_bytes(plan, batch):
+    return int(lib().stc_workspace_bytes(plan, int(batch)))
+
+
+def stc_factorize(plan, d_values, batch, d_factor, d_work, d_info, stream=None):
+    return lib().stc_factorize(plan, _dev_ptr(d_values), int(batch), _dev_ptr(d_factor), _dev_ptr(d_work),
+                               _dev_ptr(d_info), _stream(stream))
+
+
+def stc_scatter_values(plan, d_values, batch, d_factor, stream=None):
+    return lib().stc_scatter_values(plan, _dev_ptr(d_values), int(batch), _dev_ptr(d_factor), _stream(stream))
+
+
+def stc_factorize_scattered(plan, batch, d_factor, d_work, d_info, stream=None):
+    return lib().stc_factorize_scattered(plan, int(batch), _dev_ptr(d_factor), _dev_ptr(d_work),
+                                         _dev_ptr(d_info), _stream(stream))
+
+
+def stc_sync_status(d_work, stream=None):
+    return lib().stc_sync_status(_dev_ptr(d_work), _stream(stream))
+
+
+def stc_logdet(plan, d_factor, batch, d_logdet, stream=None):
+    return lib().stc_logdet(plan, _dev_ptr(d_factor), int(batch), _dev_ptr(d_logdet), _stream(stream))
+
+
+def stc_solve(plan, d_factor, batch, nrhs, d_b, d_x, d_work, stream=None):
+    return lib().stc_solve(plan, _dev_ptr(d_factor), int(batch), int(nrhs), _dev_ptr(d_b), _dev_ptr(d_x),
+                           _dev_ptr(d_work), _stream(stream))
+
+
+def stc_factor_to_csc(plan, d_factor, batch, d_Lx, stream=None):
+    return lib().stc_factor_to_csc(plan, _dev_ptr(d_factor), int(batch), _dev_ptr(d_Lx), _stream(stream))
+
+
+def stc_fp64_peak_probe(d_scratch, iters=4096):
+    """Returns (status, measured DFMA GFLOP/s)."""
+    g = C.c_double(0.0)
+    rc = lib().stc_fp64_peak_probe(_dev_ptr(d_scratch), int(d_scratch.numel()), int(iters), C.byref(g))
+    return rc, g.value

@@ -1,0 +1,810 @@
+// analyze.cpp -- host-side symbolic analysis (once per sparsity pattern).
+//
+// Follows arxiv 2609.29765:
+//   Sec. 3     ordering (geometric nested dissection / RCM / natural / given) and the
+//              symbolic Cholesky factorization of the permuted pattern;
+//   Sec. 4     uniform n_b tile grid over L, active-column sets aind, contiguous and
+//              full-width predicates, banded half-width kd_t of diagonal tiles;
+//   Sec. 5.1   routing features phi, rho, sigma and the selector;
+//   Sec. 5.2   per-tile metadata pass, Algorithm 1 task list, per-task scatter maps;
+//   Sec. 5.3   the task DAG the device executor replays (counters instead of P).
+//
+// The elimination tree uses Liu's ancestor algorithm with path compression and the
+// structure of L is built row by row from row subtrees (Liu 1990 / Gilbert-Ng-Peyton
+// 1994, the pipeline cited in Sec. 5.4).
+#include <algorithm>
+#include <array>
+#include <chrono>
+#include <climits>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <numeric>
+
+#include "plan.hpp"
+
+using std::int16_t;
+using std::int32_t;
+using std::int64_t;
+using std::vector;
+
+namespace {
+
+constexpr int kMaxNb = 128;
+
+int validate_pattern(int64_t n, const int64_t* Ap, const int64_t* Ai) {
+    if (n <= 0 || !Ap || !Ai) return STC_ERR_INVALID_ARG;
+    if (n > INT32_MAX - 1) return STC_ERR_UNSUPPORTED;
+    if (Ap[0] != 0) return STC_ERR_INVALID_PATTERN;
+    for (int64_t j = 0; j < n; ++j) {
+        if (Ap[j + 1] < Ap[j]) return STC_ERR_INVALID_PATTERN;
+        if (Ap[j + 1] == Ap[j] || Ai[Ap[j]] != j) return STC_ERR_INVALID_PATTERN;  // diagonal first
+        for (int64_t p = Ap[j] + 1; p < Ap[j + 1]; ++p)
+            if (Ai[p] <= Ai[p - 1] || Ai[p] >= n) return STC_ERR_INVALID_PATTERN;
+    }
+    return STC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Geometric nested dissection on integral lattice coordinates.  A box holding at
+// most `leaf` nodes is emitted whole; otherwise its longest axis (extent hi-lo+1,
+// ties -> lowest axis) is cut by the plane floor((lo+hi)/2): the two half-boxes are
+// ordered first (lower half, then upper half), the plane's nodes last.  Leaves and
+// planes are emitted in x-fastest lexicographic order.  Rows with a NaN coordinate
+// (set-aside dense rows) follow at the end in input order.
+// ---------------------------------------------------------------------------
+struct Lattice {
+    vector<int64_t> x, y, z;
+    int64_t c(int64_t v, int a) const { return a == 0 ? x[v] : (a == 1 ? y[v] : z[v]); }
+    bool lex_less(int64_t u, int64_t v) const {
+        if (z[u] != z[v]) return z[u] < z[v];
+        if (y[u] != y[v]) return y[u] < y[v];
+        return x[u] < x[v];
+    }
+};
+
+void nd_split(const Lattice& g, int64_t* first, int64_t* last, std::array<int64_t, 3> lo,
+              std::array<int64_t, 3> hi, int64_t leaf, vector<int64_t>& out) {
+    const int64_t cnt = last - first;
+    if (cnt == 0) return;
+    auto lex = [&](int64_t u, int64_t v) { return g.lex_less(u, v); };
+    if (cnt <= leaf) {
+        std::sort(first, last, lex);
+        out.insert(out.end(), first, last);
+        return;
+    }
+    int ax = 0;
+    for (int a = 1; a < 3; ++a)
+        if (hi[a] - lo[a] > hi[ax] - lo[ax]) ax = a;
+    const int64_t s = lo[ax] + hi[ax];
+    const int64_t mid = s >= 0 ? s / 2 : -((-s + 1) / 2);
+    int64_t* m1 = std::partition(first, last, [&](int64_t v) { return g.c(v, ax) < mid; });
+    int64_t* m2 = std::partition(m1, last, [&](int64_t v) { return g.c(v, ax) == mid; });
+    // [first,m1) lower half, [m1,m2) plane, [m2,last) upper half
+    auto lhi = hi; lhi[ax] = mid - 1;
+    auto rlo = lo; rlo[ax] = mid + 1;
+    nd_split(g, first, m1, lo, lhi, leaf, out);
+    nd_split(g, m2, last, rlo, hi, leaf, out);
+    std::sort(m1, m2, lex);
+    out.insert(out.end(), m1, m2);
+}
+
+int order_nd(int64_t n, const double* coords, int64_t leaf, vector<int64_t>& perm) {
+    if (!coords) return STC_ERR_INVALID_ARG;
+    Lattice g;
+    g.x.assign(n, 0); g.y.assign(n, 0); g.z.assign(n, 0);
+    vector<int64_t> nodes, aside;
+    std::array<int64_t, 3> lo{0, 0, 0}, hi{-1, -1, -1};
+    for (int64_t i = 0; i < n; ++i) {
+        const double* c = coords + 3 * i;
+        if (std::isnan(c[0]) || std::isnan(c[1]) || std::isnan(c[2])) { aside.push_back(i); continue; }
+        int64_t v[3];
+        for (int a = 0; a < 3; ++a) {
+            if (std::floor(c[a]) != c[a] || std::fabs(c[a]) > 1e15) return STC_ERR_UNSUPPORTED;
+            v[a] = (int64_t)c[a];
+        }
+        g.x[i] = v[0]; g.y[i] = v[1]; g.z[i] = v[2];
+        for (int a = 0; a < 3; ++a) {
+            if (nodes.empty() || v[a] < lo[a]) lo[a] = v[a];
+            if (nodes.empty() || v[a] > hi[a]) hi[a] = v[a];
+        }
+        nodes.push_back(i);
+    }
+    perm.clear();
+    perm.reserve(n);
+    nd_split(g, nodes.data(), nodes.data() + nodes.size(), lo, hi, leaf, perm);
+    perm.insert(perm.end(), aside.begin(), aside.end());
+    return (int64_t)perm.size() == n ? STC_OK : STC_ERR_INVALID_PATTERN;
+}
+
+// Full symmetric adjacency (no diagonal) of a lower CSC pattern.
+void adjacency(int64_t n, const int64_t* Ap, const int64_t* Ai, vector<int64_t>& xadj,
+               vector<int64_t>& adj) {
+    xadj.assign(n + 1, 0);
+    for (int64_t j = 0; j < n; ++j)
+        for (int64_t p = Ap[j] + 1; p < Ap[j + 1]; ++p) { xadj[j + 1]++; xadj[Ai[p] + 1]++; }
+    for (int64_t j = 0; j < n; ++j) xadj[j + 1] += xadj[j];
+    adj.assign(xadj[n], 0);
+    vector<int64_t> f(xadj.begin(), xadj.end() - 1);
+    for (int64_t j = 0; j < n; ++j)
+        for (int64_t p = Ap[j] + 1; p < Ap[j + 1]; ++p) { adj[f[j]++] = Ai[p]; adj[f[Ai[p]]++] = j; }
+}
+
+// Reverse Cuthill-McKee with a George-Liu pseudo-peripheral start per component.
+void order_rcm(int64_t n, const int64_t* Ap, const int64_t* Ai, vector<int64_t>& perm) {
+    vector<int64_t> xadj, adj;
+    adjacency(n, Ap, Ai, xadj, adj);
+    auto deg = [&](int64_t v) { return xadj[v + 1] - xadj[v]; };
+    vector<int64_t> level(n, -1), order;
+    order.reserve(n);
+    vector<char> done(n, 0);
+    vector<int64_t> bfs;
+    auto bfs_levels = [&](int64_t root, vector<int64_t>& visit) {
+        visit.clear();
+        visit.push_back(root);
+        level[root] = 0;
+        for (size_t h = 0; h < visit.size(); ++h) {
+            int64_t v = visit[h];
+            for (int64_t p = xadj[v]; p < xadj[v + 1]; ++p)
+                if (level[adj[p]] < 0) { level[adj[p]] = level[v] + 1; visit.push_back(adj[p]); }
+        }
+        int64_t ecc = level[visit.back()];
+        for (int64_t v : visit) level[v] = -1;
+        return ecc;
+    };
+    for (int64_t s = 0; s < n; ++s) {
+        if (done[s]) continue;
+        // component members, then a minimum-degree start
+        vector<int64_t> comp;
+        bfs_levels(s, comp);
+        int64_t root = comp[0];
+        for (int64_t v : comp)
+            if (deg(v) < deg(root) || (deg(v) == deg(root) && v < root)) root = v;
+        int64_t ecc = bfs_levels(root, bfs);
+        for (int it = 0; it < 8; ++it) {  // pseudo-peripheral node search
+            // min-degree node of the last level
+            for (int64_t v : bfs) level[v] = -1;
+            vector<int64_t> vis2;
+            level[root] = 0;
+            vis2.push_back(root);
+            for (size_t h = 0; h < vis2.size(); ++h) {
+                int64_t v = vis2[h];
+                for (int64_t p = xadj[v]; p < xadj[v + 1]; ++p)
+                    if (level[adj[p]] < 0) { level[adj[p]] = level[v] + 1; vis2.push_back(adj[p]); }
+            }
+            int64_t lastlev = level[vis2.back()], cand = -1;
+            for (int64_t v : vis2)
+                if (level[v] == lastlev && (cand < 0 || deg(v) < deg(cand))) cand = v;
+            for (int64_t v : vis2) level[v] = -1;
+            int64_t e2 = bfs_levels(cand, bfs);
+            if (e2 <= ecc) break;
+            ecc = e2;
+            root = cand;
+        }
+        // Cuthill-McKee BFS, neighbours by ascending degree (ties: index)
+        size_t head = order.size();
+        order.push_back(root);
+        done[root] = 1;
+        vector<int64_t> nb;
+        for (size_t h = head; h < order.size(); ++h) {
+            int64_t v = order[h];
+            nb.clear();
+            for (int64_t p = xadj[v]; p < xadj[v + 1]; ++p)
+                if (!done[adj[p]]) { done[adj[p]] = 1; nb.push_back(adj[p]); }
+            std::sort(nb.begin(), nb.end(), [&](int64_t a, int64_t b) {
+                return deg(a) != deg(b) ? deg(a) < deg(b) : a < b;
+            });
+            order.insert(order.end(), nb.begin(), nb.end());
+        }
+    }
+    perm.assign(order.rbegin(), order.rend());
+}
+
+// Strict lower part of A_p = P A P^T as row lists: row r holds columns c < r.
+void permuted_rows(int64_t n, const int64_t* Ap, const int64_t* Ai, const vector<int64_t>& iperm,
+                   vector<int64_t>& rp, vector<int32_t>& rc) {
+    rp.assign(n + 1, 0);
+    for (int64_t j = 0; j < n; ++j)
+        for (int64_t p = Ap[j] + 1; p < Ap[j + 1]; ++p) {
+            int64_t a = iperm[Ai[p]], b = iperm[j];
+            rp[std::max(a, b) + 1]++;
+        }
+    for (int64_t i = 0; i < n; ++i) rp[i + 1] += rp[i];
+    rc.assign(rp[n], 0);
+    vector<int64_t> f(rp.begin(), rp.end() - 1);
+    for (int64_t j = 0; j < n; ++j)
+        for (int64_t p = Ap[j] + 1; p < Ap[j + 1]; ++p) {
+            int64_t a = iperm[Ai[p]], b = iperm[j];
+            rc[f[std::max(a, b)]++] = (int32_t)std::min(a, b);
+        }
+}
+
+// Liu's elimination tree and the structure of L from row subtrees.
+void symbolic(int64_t n, const vector<int64_t>& rp, const vector<int32_t>& rc,
+              vector<int64_t>& parent, vector<int64_t>& Lp, vector<int32_t>& Li) {
+    parent.assign(n, -1);
+    vector<int64_t> anc(n, -1);
+    for (int64_t i = 0; i < n; ++i)
+        for (int64_t p = rp[i]; p < rp[i + 1]; ++p) {
+            int64_t j = rc[p];
+            while (j != -1 && j < i) {
+                int64_t nxt = anc[j];
+                anc[j] = i;
+                if (nxt == -1) parent[j] = i;
+                j = nxt;
+            }
+        }
+    // pass 1: column counts; pass 2: fill (rows arrive in ascending order)
+    vector<int64_t> mark(n, -1), cnt(n, 1);
+    for (int64_t i = 0; i < n; ++i) {
+        mark[i] = i;
+        for (int64_t p = rp[i]; p < rp[i + 1]; ++p)
+            for (int64_t j = rc[p]; mark[j] != i; j = parent[j]) { mark[j] = i; cnt[j]++; }
+    }
+    Lp.assign(n + 1, 0);
+    for (int64_t j = 0; j < n; ++j) Lp[j + 1] = Lp[j] + cnt[j];
+    Li.assign(Lp[n], 0);
+    vector<int64_t> f(Lp.begin(), Lp.end() - 1);
+    std::fill(mark.begin(), mark.end(), -1);
+    for (int64_t i = 0; i < n; ++i) {
+        Li[f[i]++] = (int32_t)i;  // diagonal: the first entry of column i (rows < i never land here)
+        mark[i] = i;
+        for (int64_t p = rp[i]; p < rp[i + 1]; ++p)
+            for (int64_t j = rc[p]; mark[j] != i; j = parent[j]) { mark[j] = i; Li[f[j]++] = (int32_t)i; }
+    }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+int stc_plan::tile_id(int64_t I, int64_t J) const {
+    if (J < 0 || J >= nt || I < J || I >= nt) return -1;
+    int lo = colstart[J], hi = colstart[J + 1];
+    while (lo < hi) {
+        int mid = (lo + hi) / 2;
+        if (tiles[mid].I == I) return mid;
+        if (tiles[mid].I < I) lo = mid + 1; else hi = mid;
+    }
+    return -1;
+}
+
+namespace {
+
+// stored index of logical column lc in tile t (-1 if not stored)
+int stored_col(const stc_plan& P, const stc::DTile& t, int lc) {
+    if (t.c0 >= 0) return (lc >= t.c0 && lc < t.c0 + t.sw) ? lc - t.c0 : -1;
+    const int16_t* a = P.saind.data() + t.aoff;
+    const int16_t* e = std::lower_bound(a, a + t.sw, (int16_t)lc);
+    return (e != a + t.sw && *e == lc) ? int(e - a) : -1;
+}
+
+int64_t entry_offset(const stc_plan& P, int64_t r, int64_t c) {  // r >= c, permuted
+    const int64_t nb = P.nb;
+    int t = P.tile_id(r / nb, c / nb);
+    if (t < 0) return -1;
+    const stc::DTile& T = P.tiles[t];
+    int lr = int(r % nb), lc = int(c % nb);
+    if (T.kind == stc::TILE_DIAG_DENSE) return T.off + lr + (int64_t)lc * nb;
+    if (T.kind == stc::TILE_DIAG_BAND) {
+        if (lr - lc > T.kd) return -1;
+        return T.off + (T.kd + lc - lr) + (int64_t)lr * (T.kd + 1);
+    }
+    int s = stored_col(P, T, lc);
+    if (s < 0) return -1;
+    return T.off + lr + (int64_t)s * nb;
+}
+
+int build_tiles(stc_plan& P) {
+    const int64_t n = P.n, nb = P.nb, nt = P.nt;
+    const bool dense = P.route_exec == STC_ROUTE_DENSE;
+    P.colstart.assign(nt + 1, 0);
+    P.diag_tile.assign(nt, -1);
+    vector<int32_t> slot(nt, -1);
+    vector<int64_t> touched;
+    struct Acc { uint64_t m[2]; int r0, r1, kd; };
+    vector<Acc> acc;
+    int64_t off = 0;
+    for (int64_t J = 0; J < nt; ++J) {
+        P.colstart[J] = (int32_t)P.tiles.size();
+        touched.clear();
+        acc.clear();
+        const int64_t c0 = J * nb, c1 = std::min(n, (J + 1) * nb);
+        for (int64_t j = c0; j < c1; ++j)
+            for (int64_t q = P.Lp[j]; q < P.Lp[j + 1]; ++q) {
+                int64_t i = P.Li[q], I = i / nb;
+                if (slot[I] < 0) {
+                    slot[I] = (int32_t)acc.size();
+                    acc.push_back(Acc{{0, 0}, INT_MAX, -1, -1});
+                    touched.push_back(I);
+                }
+                Acc& a = acc[slot[I]];
+                int lr = int(i - I * nb), lc = int(j - c0);
+                a.m[lc >> 6] |= 1ull << (lc & 63);
+                a.r0 = std::min(a.r0, lr);
+                a.r1 = std::max(a.r1, lr + 1);
+                if (I == J) a.kd = std::max(a.kd, lr - lc);
+            }
+        std::sort(touched.begin(), touched.end());
+        for (int64_t I : touched) {
+            const Acc& a = acc[slot[I]];
+            slot[I] = -1;
+            stc::DTile t{};
+            t.I = (int32_t)I; t.J = (int32_t)J;
+            vector<int16_t> cols;
+            for (int c = 0; c < nb; ++c)
+                if (a.m[c >> 6] >> (c & 63) & 1) cols.push_back((int16_t)c);
+            const int cnt = (int)cols.size();
+            const bool contiguous = cols.back() - cols.front() + 1 == cnt;
+            P.nact.push_back(cnt);
+            P.aoff_struct.push_back((int64_t)P.aind_struct.size());
+            P.aind_struct.insert(P.aind_struct.end(), cols.begin(), cols.end());
+            P.contig.push_back(contiguous);
+            P.full.push_back(cnt == nb);
+            t.pd_slot = -1;
+            t.aoff = -1;
+            int64_t size;
+            if (I == J) {
+                t.sw = int(c1 - c0);
+                t.c0 = 0;
+                t.r0 = 0; t.r1 = int(nb);
+                if (dense) {
+                    t.kind = stc::TILE_DIAG_DENSE;
+                    t.kd = int(nb - 1);
+                    size = nb * nb;
+                } else {
+                    t.kind = stc::TILE_DIAG_BAND;
+                    t.kd = std::max(a.kd, 0);
+                    size = (int64_t)(t.kd + 1) * nb;
+                }
+                t.pd_slot = (int32_t)J;
+                P.diag_tile[J] = (int32_t)P.tiles.size();
+            } else {
+                t.kind = stc::TILE_OFF;
+                t.kd = -1;
+                if (dense) {
+                    t.sw = int(nb); t.c0 = 0; t.r0 = 0; t.r1 = int(nb);
+                } else {
+                    t.sw = cnt;
+                    t.r0 = a.r0; t.r1 = a.r1;
+                    if (contiguous) {
+                        t.c0 = cols.front();
+                    } else {
+                        t.c0 = -1;
+                        t.aoff = (int32_t)P.saind.size();
+                        P.saind.insert(P.saind.end(), cols.begin(), cols.end());
+                    }
+                }
+                size = (int64_t)t.sw * nb;
+            }
+            t.off = off;
+            off += (size + 3) / 4 * 4;  // 32-byte aligned tiles
+            P.stored_entries += size;
+            t.nfinal = 1;
+            P.tiles.push_back(t);
+        }
+    }
+    P.colstart[nt] = (int32_t)P.tiles.size();
+    P.partial_off = off;
+    P.npartials = nt;
+    P.factor_doubles = (off + nt + 31) / 32 * 32;  // 256-byte aligned item stride
+    // off-diagonal tiles per block row (ascending n), for Algorithm 1 and the solve
+    P.rowstart.assign(nt + 1, 0);
+    for (const auto& t : P.tiles)
+        if (t.I != t.J) P.rowstart[t.I + 1]++;
+    for (int64_t k = 0; k < nt; ++k) P.rowstart[k + 1] += P.rowstart[k];
+    P.rowtiles.assign(P.rowstart[nt], 0);
+    vector<int32_t> f(P.rowstart.begin(), P.rowstart.end() - 1);
+    for (int32_t t = 0; t < (int32_t)P.tiles.size(); ++t)
+        if (P.tiles[t].I != P.tiles[t].J) P.rowtiles[f[P.tiles[t].I]++] = t;
+    return STC_OK;
+}
+
+void build_alg1(stc_plan& P) {
+    const int64_t nt = P.nt;
+    auto emit = [&](int64_t c, int64_t m, int64_t k, int64_t nn) {
+        P.alg1.push_back(c); P.alg1.push_back(m); P.alg1.push_back(k); P.alg1.push_back(nn);
+    };
+    for (int64_t k = 0; k < nt; ++k) {
+        for (int32_t a = P.rowstart[k]; a < P.rowstart[k + 1]; ++a) {
+            emit(2, -1, k, P.tiles[P.rowtiles[a]].J);
+            P.n_syrk++;
+        }
+        emit(1, -1, k, -1);
+        P.n_potrf++;
+        for (int32_t t = P.colstart[k]; t < P.colstart[k + 1]; ++t) {
+            const int64_t m = P.tiles[t].I;
+            if (m == k) continue;
+            int32_t a = P.rowstart[k], b = P.rowstart[m];
+            while (a < P.rowstart[k + 1] && b < P.rowstart[m + 1]) {
+                int32_t na = P.tiles[P.rowtiles[a]].J, nbb = P.tiles[P.rowtiles[b]].J;
+                if (na == nbb) { emit(4, m, k, na); P.n_gemm++; ++a; ++b; }
+                else if (na < nbb) ++a;
+                else ++b;
+            }
+            emit(3, m, k, -1);
+            P.n_trsm++;
+        }
+    }
+}
+
+// logical columns stored in tile t
+void stored_cols(const stc_plan& P, const stc::DTile& t, vector<int>& out) {
+    out.resize(t.sw);
+    for (int s = 0; s < t.sw; ++s) out[s] = t.c0 >= 0 ? t.c0 + s : P.saind[t.aoff + s];
+}
+
+}  // namespace
+
+stc::TaskSet* stc_plan::taskset(int32_t slices) {
+    std::lock_guard<std::mutex> g(mu);
+    auto it = tasksets.find(slices);
+    if (it != tasksets.end()) return it->second.get();
+    auto ts = std::make_unique<stc::TaskSet>();
+    ts->slices = slices;
+    const int64_t NT = nt;
+    const int NB = (int)nb;
+    int h = (NB + slices - 1) / slices;
+    h = (h + 7) / 8 * 8;
+    vector<stc::DTask> tasks;
+    vector<double> cost;
+    vector<vector<int32_t>> producers(tiles.size());
+    ts->nfinal.assign(tiles.size(), 0);
+    vector<int> ca, cb;
+    for (int64_t k = 0; k < NT; ++k) {
+        const int32_t dk = diag_tile[k];
+        const stc::DTile& D = tiles[dk];
+        // DIAG(k): SYRK from every (k,n), n < k, then POTRF
+        stc::DTask t{};
+        t.kind = stc::TASK_DIAG; t.tile = dk; t.diag = dk;
+        t.ubeg = (int32_t)ts->upds.size();
+        double c = 0;
+        for (int32_t a = rowstart[k]; a < rowstart[k + 1]; ++a) {
+            const int32_t at = rowtiles[a];
+            const stc::DTile& A = tiles[at];
+            stc::DUpd u{};
+            u.a = at; u.b = at; u.kmap = -1; u.klen = A.sw; u.ka0 = 0; u.kb0 = 0;
+            u.ra0 = A.r0; u.ra1 = A.r1; u.oc0 = A.r0; u.oc1 = A.r1;
+            ts->upds.push_back(u);
+            double r = A.r1 - A.r0;
+            c += r * (r + 1) / 2 * A.sw;
+        }
+        t.uend = (int32_t)ts->upds.size();
+        t.rs0 = 0; t.rs1 = NB; t.tr0 = 0; t.tr1 = NB;
+        {
+            double w = D.sw, kd = std::min<double>(D.kd, w - 1);
+            c += (D.kind == stc::TILE_DIAG_BAND) ? w * (kd + 1) * (kd + 1) / 2 : w * w * w / 6;
+        }
+        producers[dk].push_back((int32_t)tasks.size());
+        tasks.push_back(t);
+        cost.push_back(c);
+        ts->nfinal[dk] = 1;
+        // OFF(m,k) row slices: GEMM from every n in N(k) & N(m), n < k, then TRSM
+        for (int32_t o = colstart[k]; o < colstart[k + 1]; ++o) {
+            const stc::DTile& O = tiles[o];
+            if (O.I == O.J) continue;
+            const int64_t m = O.I;
+            for (int rs0 = 0; rs0 < NB; rs0 += h) {
+                const int rs1 = std::min(NB, rs0 + h);
+                const int tr0 = std::max(rs0, O.r0), tr1 = std::min(rs1, O.r1);
+                if (tr0 >= tr1) continue;
+                stc::DTask s{};
+                s.kind = stc::TASK_OFF; s.tile = o; s.diag = dk;
+                s.rs0 = rs0; s.rs1 = rs1; s.tr0 = tr0; s.tr1 = tr1;
+                s.ubeg = (int32_t)ts->upds.size();
+                double cc = 0;
+                int32_t a = rowstart[k], b = rowstart[m];
+                while (a < rowstart[k + 1] && b < rowstart[m + 1]) {
+                    const int32_t kt = rowtiles[a], mt = rowtiles[b];
+                    const int32_t na = tiles[kt].J, nm = tiles[mt].J;
+                    if (na < nm) { ++a; continue; }
+                    if (nm < na) { ++b; continue; }
+                    ++a; ++b;
+                    const stc::DTile& A = tiles[mt];  // (m,n)
+                    const stc::DTile& B = tiles[kt];  // (k,n)
+                    stc::DUpd u{};
+                    u.a = mt; u.b = kt;
+                    u.ra0 = std::max(tr0, A.r0); u.ra1 = std::min(tr1, A.r1);
+                    if (A.c0 >= 0 && B.c0 >= 0) {
+                        const int lo = std::max(A.c0, B.c0), hi = std::min(A.c0 + A.sw, B.c0 + B.sw);
+                        u.kmap = -1; u.klen = std::max(0, hi - lo);
+                        u.ka0 = lo - A.c0; u.kb0 = lo - B.c0;
+                    } else {
+                        stored_cols(*this, A, ca);
+                        stored_cols(*this, B, cb);
+                        u.kmap = (int32_t)(ts->imap.size() / 2);
+                        int x = 0, y = 0, len = 0;
+                        while (x < (int)ca.size() && y < (int)cb.size()) {
+                            if (ca[x] == cb[y]) {
+                                ts->imap.push_back((int16_t)x); ts->imap.push_back((int16_t)y);
+                                ++len; ++x; ++y;
+                            } else if (ca[x] < cb[y]) ++x; else ++y;
+                        }
+                        u.klen = len; u.ka0 = 0; u.kb0 = 0;
+                    }
+                    if (O.c0 >= 0) {
+                        const int lo = std::max(O.c0, B.r0), hi = std::min(O.c0 + O.sw, B.r1);
+                        u.oc0 = lo - O.c0; u.oc1 = hi - O.c0;
+                    } else {
+                        u.oc0 = 0; u.oc1 = O.sw;
+                    }
+                    if (u.klen <= 0 || u.ra0 >= u.ra1 || u.oc0 >= u.oc1) continue;
+                    ts->upds.push_back(u);
+                    cc += double(u.ra1 - u.ra0) * (u.oc1 - u.oc0) * u.klen;
+                }
+                s.uend = (int32_t)ts->upds.size();
+                cc += double(tr1 - tr0) * O.sw * (O.sw + 1) / 2;
+                producers[o].push_back((int32_t)tasks.size());
+                tasks.push_back(s);
+                cost.push_back(cc);
+                ts->nfinal[o]++;
+            }
+        }
+    }
+    // ASAP (earliest-start on unbounded workers) order; ties keep Algorithm-1 order.
+    const double kSync = 4000.0;  // per-task overhead in FMA-equivalents
+    vector<double> es(tasks.size(), 0.0), fin(tasks.size(), 0.0);
+    for (size_t i = 0; i < tasks.size(); ++i) {
+        double s = 0;
+        auto dep_tile = [&](int32_t tile) {
+            for (int32_t p : producers[tile]) s = std::max(s, fin[p]);
+        };
+        const stc::DTask& t = tasks[i];
+        for (int32_t u = t.ubeg; u < t.uend; ++u) { dep_tile(ts->upds[u].a); dep_tile(ts->upds[u].b); }
+        if (t.kind == stc::TASK_OFF) dep_tile(t.diag);
+        es[i] = s;
+        fin[i] = s + cost[i] + kSync;
+        ts->fma += cost[i];
+    }
+    vector<int32_t> order(tasks.size());
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return es[a] < es[b]; });
+    ts->tasks.reserve(tasks.size());
+    for (int32_t i : order) ts->tasks.push_back(tasks[i]);
+    stc::TaskSet* raw = ts.get();
+    tasksets[slices] = std::move(ts);
+    return raw;
+}
+
+// ---------------------------------------------------------------------------
+// Public entry points (host side).
+// ---------------------------------------------------------------------------
+extern "C" void stc_options_default(stc_options* o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->nb = 128;
+    o->force_route = STC_ROUTE_AUTO;
+    o->ordering = STC_ORDER_AUTO;
+    o->nd_leaf = 64;
+}
+
+static int analyze_impl(int64_t n, const int64_t* Ap, const int64_t* Ai, const double* coords,
+                        const stc_options* opt_in, stc_plan** out) {
+    auto t0 = std::chrono::steady_clock::now();
+    if (!out) return STC_ERR_INVALID_ARG;
+    *out = nullptr;
+    int rc = validate_pattern(n, Ap, Ai);
+    if (rc) return rc;
+    stc_options opt;
+    stc_options_default(&opt);
+    if (opt_in) opt = *opt_in;
+    if (opt.nb == 0) opt.nb = 128;
+    if (opt.nd_leaf <= 0) opt.nd_leaf = 64;
+    if (opt.nb < 8 || opt.nb > kMaxNb || opt.nb % 8) return STC_ERR_UNSUPPORTED;
+    if (opt.force_route != STC_ROUTE_AUTO && opt.force_route != STC_ROUTE_DENSE &&
+        opt.force_route != STC_ROUTE_SEMISPARSE)
+        return STC_ERR_INVALID_ARG;
+    if (opt.row_slices != 0 && opt.row_slices != 1 && opt.row_slices != 2 && opt.row_slices != 4 &&
+        opt.row_slices != 8)
+        return STC_ERR_INVALID_ARG;
+    if (opt.gate_rho_dense == 0) opt.gate_rho_dense = 0.90;
+    if (opt.gate_phi_fill == 0) opt.gate_phi_fill = 2.0;
+    if (opt.gate_rho_semi == 0) opt.gate_rho_semi = 0.15;
+    if (opt.gate_sigma_skew == 0) opt.gate_sigma_skew = 20.0;
+
+    auto P = std::make_unique<stc_plan>();
+    P->n = n; P->nb = opt.nb; P->nt = (n + opt.nb - 1) / opt.nb; P->nnzA = Ap[n];
+    P->opt = opt;
+    P->opt.perm = nullptr;
+
+    // ---- ordering (Sec. 3) ----
+    int ord = opt.ordering;
+    if (ord == STC_ORDER_GIVEN) {
+        if (!opt.perm) return STC_ERR_INVALID_ARG;
+        P->perm.assign(opt.perm, opt.perm + n);
+        vector<char> seen(n, 0);
+        for (int64_t v : P->perm) {
+            if (v < 0 || v >= n || seen[v]) return STC_ERR_INVALID_ARG;
+            seen[v] = 1;
+        }
+    } else if (ord == STC_ORDER_NATURAL) {
+        P->perm.resize(n);
+        std::iota(P->perm.begin(), P->perm.end(), 0);
+    } else if (ord == STC_ORDER_ND || (ord == STC_ORDER_AUTO && coords)) {
+        rc = order_nd(n, coords, opt.nd_leaf, P->perm);
+        if (rc) return rc;
+        ord = STC_ORDER_ND;
+    } else if (ord == STC_ORDER_RCM || ord == STC_ORDER_AUTO) {
+        order_rcm(n, Ap, Ai, P->perm);
+        ord = STC_ORDER_RCM;
+    } else {
+        return STC_ERR_INVALID_ARG;
+    }
+    vector<int64_t> iperm(n);
+    for (int64_t k = 0; k < n; ++k) iperm[P->perm[k]] = k;
+
+    // ---- symbolic factorization ----
+    vector<int64_t> rp;
+    vector<int32_t> rcv;
+    permuted_rows(n, Ap, Ai, iperm, rp, rcv);
+    symbolic(n, rp, rcv, P->parent, P->Lp, P->Li);
+    if (ord == STC_ORDER_AUTO) ord = STC_ORDER_RCM;
+    // AUTO without coordinates: keep the natural order when RCM does not reduce the fill
+    if (opt.ordering == STC_ORDER_AUTO && !coords) {
+        vector<int64_t> idp(n), par2, Lp2;
+        vector<int32_t> Li2;
+        std::iota(idp.begin(), idp.end(), 0);
+        permuted_rows(n, Ap, Ai, idp, rp, rcv);
+        symbolic(n, rp, rcv, par2, Lp2, Li2);
+        if (Lp2[n] <= P->Lp[n]) {
+            P->perm = idp; iperm = idp; P->parent.swap(par2); P->Lp.swap(Lp2); P->Li.swap(Li2);
+            ord = STC_ORDER_NATURAL;
+        }
+    }
+    P->ordering = ord;
+    rp.clear(); rp.shrink_to_fit(); rcv.clear(); rcv.shrink_to_fit();
+    for (int64_t j = 0; j < n; ++j) {
+        double c = double(P->Lp[j + 1] - P->Lp[j]);
+        P->flops_alg += c * c;
+    }
+
+    // ---- features and selector (Sec. 5.1): computed on the structural tile map ----
+    P->route_exec = STC_ROUTE_SEMISPARSE;
+    rc = build_tiles(*P);  // structural pass (semisparse storage)
+    if (rc) return rc;
+    {
+        double sum = 0; int64_t cnt = 0;
+        for (size_t t = 0; t < P->tiles.size(); ++t)
+            if (P->tiles[t].I != P->tiles[t].J) { sum += double(P->nact[t]) / double(P->nb); cnt++; }
+        P->rho = cnt ? sum / cnt : 1.0;
+        P->phi = double(P->Lp[n]) / double(P->nnzA);
+        double mx = 0;
+        for (int64_t j = 0; j < n; ++j) mx = std::max(mx, double(P->Lp[j + 1] - P->Lp[j]));
+        P->sigma = mx / (double(P->Lp[n]) / double(n));
+        int sel;
+        if (P->rho >= opt.gate_rho_dense) sel = STC_ROUTE_DENSE;
+        else if (P->phi > opt.gate_phi_fill) sel = STC_ROUTE_SUPERNODAL;
+        else if (P->rho >= opt.gate_rho_semi || P->sigma >= opt.gate_sigma_skew) sel = STC_ROUTE_SEMISPARSE;
+        else sel = STC_ROUTE_SUPERNODAL;
+        P->route_selected = sel;
+        int ex = opt.force_route != STC_ROUTE_AUTO ? opt.force_route : sel;
+        if (ex == STC_ROUTE_SUPERNODAL) ex = STC_ROUTE_SEMISPARSE;
+        P->route_exec = ex;
+    }
+    if (P->route_exec == STC_ROUTE_DENSE) {  // rebuild storage as full tiles
+        P->tiles.clear(); P->nact.clear(); P->aoff_struct.clear(); P->aind_struct.clear();
+        P->contig.clear(); P->full.clear(); P->saind.clear(); P->stored_entries = 0;
+        rc = build_tiles(*P);
+        if (rc) return rc;
+    }
+    build_alg1(*P);
+
+    // ---- value map (a1), padding identity, CSC map of L ----
+    P->value_map.resize(P->nnzA);
+    for (int64_t j = 0; j < n; ++j)
+        for (int64_t p = Ap[j]; p < Ap[j + 1]; ++p) {
+            int64_t a = iperm[Ai[p]], b = iperm[j];
+            int64_t off = entry_offset(*P, std::max(a, b), std::min(a, b));
+            if (off < 0) return STC_ERR_INVALID_PATTERN;
+            P->value_map[p] = off;
+        }
+    {
+        const stc::DTile& D = P->tiles[P->diag_tile[P->nt - 1]];
+        for (int64_t r = D.sw; r < P->nb; ++r)
+            P->pad_diag.push_back(D.kind == stc::TILE_DIAG_BAND ? D.off + D.kd + r * (D.kd + 1)
+                                                                 : D.off + r + r * P->nb);
+    }
+    P->csc_map.resize(P->Lp[n]);
+    for (int64_t j = 0; j < n; ++j)
+        for (int64_t q = P->Lp[j]; q < P->Lp[j + 1]; ++q) {
+            int64_t off = entry_offset(*P, P->Li[q], j);
+            if (off < 0) return STC_ERR_INVALID_PATTERN;
+            P->csc_map[q] = off;
+        }
+    stc::TaskSet* ts = P->taskset(1);
+    P->flops_tile = 2.0 * ts->fma;
+    P->analyze_seconds =
+        std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    *out = P.release();
+    return STC_OK;
+}
+
+extern "C" int stc_analyze(int64_t n, const int64_t* colptr, const int64_t* rowind,
+                           const double* coords, const stc_options* opt, stc_plan** plan_out) {
+    try {
+        return analyze_impl(n, colptr, rowind, coords, opt, plan_out);
+    } catch (const std::bad_alloc&) {
+        return STC_ERR_OUT_OF_MEMORY;
+    } catch (...) {
+        return STC_ERR_INVALID_ARG;
+    }
+}
+
+extern "C" int stc_plan_info_get(const stc_plan* P, stc_plan_info* o) {
+    if (!P || !o) return STC_ERR_INVALID_ARG;
+    std::memset(o, 0, sizeof(*o));
+    o->n = P->n; o->nb = P->nb; o->nt = P->nt; o->ntiles = (int64_t)P->tiles.size();
+    o->nnzA = P->nnzA; o->nnzL = P->Lp[P->n]; o->stored_entries = P->stored_entries;
+    o->factor_doubles = P->factor_doubles;
+    o->route_selected = P->route_selected; o->route_executed = P->route_exec;
+    o->ordering = P->ordering;
+    o->phi = P->phi; o->rho = P->rho; o->sigma = P->sigma;
+    o->ntasks_alg1 = (int64_t)P->alg1.size() / 4;
+    o->n_potrf = P->n_potrf; o->n_syrk = P->n_syrk; o->n_trsm = P->n_trsm; o->n_gemm = P->n_gemm;
+    o->flops_alg = P->flops_alg; o->flops_tile = P->flops_tile;
+    o->analyze_seconds = P->analyze_seconds;
+    return STC_OK;
+}
+
+extern "C" int stc_plan_export(const stc_plan* P, int what, void* buf, size_t* bytes) {
+    if (!P || !bytes) return STC_ERR_INVALID_ARG;
+    vector<int64_t> tmp;
+    const void* src = nullptr;
+    size_t sz = 0;
+    switch (what) {
+        case STC_EXPORT_PERM: src = P->perm.data(); sz = P->perm.size() * 8; break;
+        case STC_EXPORT_ETREE: src = P->parent.data(); sz = P->parent.size() * 8; break;
+        case STC_EXPORT_LP: src = P->Lp.data(); sz = P->Lp.size() * 8; break;
+        case STC_EXPORT_LI:
+            tmp.assign(P->Li.begin(), P->Li.end()); src = tmp.data(); sz = tmp.size() * 8; break;
+        case STC_EXPORT_TILES:
+            for (size_t t = 0; t < P->tiles.size(); ++t) {
+                const auto& T = P->tiles[t];
+                int64_t f[9] = {T.I, T.J, P->nact[t], P->aoff_struct[t], P->contig[t], P->full[t],
+                                T.I == T.J ? (int64_t)0 : (int64_t)-1, 0, 0};
+                if (T.I == T.J) {  // structural kd (storage kd may be n_b-1 on the dense route)
+                    int64_t kd = 0, r0 = P->nb, r1 = 0;
+                    const int64_t c0 = T.J * P->nb, c1 = std::min(P->n, c0 + P->nb);
+                    for (int64_t j = c0; j < c1; ++j)
+                        for (int64_t q = P->Lp[j]; q < P->Lp[j + 1] && P->Li[q] < c1; ++q) {
+                            kd = std::max<int64_t>(kd, P->Li[q] - j);
+                            r0 = std::min<int64_t>(r0, P->Li[q] - c0);
+                            r1 = std::max<int64_t>(r1, P->Li[q] - c0 + 1);
+                        }
+                    f[6] = kd; f[7] = r0; f[8] = r1;
+                } else {
+                    int64_t r0 = P->nb, r1 = 0;  // structural row extent
+                    const int64_t c0 = T.J * P->nb, c1 = std::min(P->n, c0 + P->nb);
+                    const int64_t lo = (int64_t)T.I * P->nb, hi = lo + P->nb;
+                    for (int64_t j = c0; j < c1; ++j) {
+                        const int32_t* b = P->Li.data() + P->Lp[j];
+                        const int32_t* e = P->Li.data() + P->Lp[j + 1];
+                        const int32_t* x = std::lower_bound(b, e, (int32_t)lo);
+                        if (x != e && *x < hi) {
+                            r0 = std::min<int64_t>(r0, *x - lo);
+                            const int32_t* y = std::lower_bound(x, e, (int32_t)hi);
+                            r1 = std::max<int64_t>(r1, *(y - 1) - lo + 1);
+                        }
+                    }
+                    f[7] = r0; f[8] = r1;
+                }
+                tmp.insert(tmp.end(), f, f + 9);
+            }
+            src = tmp.data(); sz = tmp.size() * 8;
+            break;
+        case STC_EXPORT_AIND:
+            tmp.assign(P->aind_struct.begin(), P->aind_struct.end()); src = tmp.data(); sz = tmp.size() * 8;
+            break;
+        case STC_EXPORT_TASKS: src = P->alg1.data(); sz = P->alg1.size() * 8; break;
+        case STC_EXPORT_VALUE_MAP: src = P->value_map.data(); sz = P->value_map.size() * 8; break;
+        case STC_EXPORT_TILE_OFFSETS:
+            for (const auto& T : P->tiles) tmp.push_back(T.off);
+            src = tmp.data(); sz = tmp.size() * 8;
+            break;
+        default: return STC_ERR_INVALID_ARG;
+    }
+    if (!buf) { *bytes = sz; return STC_OK; }
+    if (*bytes < sz) { *bytes = sz; return STC_ERR_BUFFER_TOO_SMALL; }
+    if (sz) std::memcpy(buf, src, sz);
+    *bytes = sz;
+    return STC_OK;
+}

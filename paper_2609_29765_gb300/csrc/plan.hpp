@@ -1,0 +1,141 @@
+// plan.hpp -- internal plan structures shared by the host analysis (analyze.cpp)
+// and the CUDA kernels (replay.cu).  Not part of the public ABI (include/stc.h).
+#pragma once
+#include <cstdint>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <vector>
+
+#include "stc.h"
+
+namespace stc {
+
+// ---------------------------------------------------------------------------
+// Device-side descriptors (plain old data, uploaded as arrays).
+// ---------------------------------------------------------------------------
+enum : int32_t { TILE_OFF = 0, TILE_DIAG_DENSE = 1, TILE_DIAG_BAND = 2 };
+
+// One stored tile of the factor (Sec. 4).  Off-diagonal tiles are column-major
+// n_b x sw (stored columns at full height, zeros included, Sec. 4.1).  Dense diagonal
+// tiles are column-major n_b x n_b holding L's lower triangle.  Banded diagonal tiles
+// hold L^T in LAPACK upper-band packed form, (kd+1) x n_b column-major, entry
+// L[r][c] (r >= c, r - c <= kd) at (kd + c - r) + r*(kd+1)  (Sec. 4.3).
+struct DTile {
+    int64_t off;      // offset (doubles) of the tile in one item's factor
+    int32_t I, J;     // tile coordinates (row block, column block)
+    int32_t kind;     // TILE_*
+    int32_t sw;       // stored columns (off-diagonal) / logical width (diagonal)
+    int32_t c0;       // first logical column if the stored set is contiguous, else -1
+    int32_t aoff;     // offset of the stored-column list in the saind array
+    int32_t kd;       // banded half-width (TILE_DIAG_BAND), n_b-1 otherwise
+    int32_t r0, r1;   // structural row extent [r0, r1) inside the tile
+    int32_t nfinal;   // value of the tile's completion counter once it is final
+    int32_t pd_slot;  // diagonal tiles: index of the logdet partial; else -1
+    int32_t pad;
+};
+
+enum : int32_t { TASK_DIAG = 0, TASK_OFF = 1 };
+
+// One device task.  TASK_DIAG = every SYRK into (k,k) then POTRF(k); TASK_OFF = every
+// GEMM into rows [rs0,rs1) of (m,k) then the TRSM of those rows against L_kk.  These are
+// the cases of Algorithm 1 grouped by output tile (row slice).
+struct DTask {
+    int32_t kind;
+    int32_t tile;        // output tile
+    int32_t diag;        // tile (k,k)
+    int32_t ubeg, uend;  // range in the update array
+    int32_t rs0, rs1;    // row slice of the output tile (TASK_OFF); [0,n_b) for DIAG
+    int32_t tr0, tr1;    // rows of the slice the TRSM touches (slice cut to r-extent)
+    int32_t pad[3];
+};
+
+// One SYRK (a == b) or GEMM source of a task: out -= A(rows, inner) * B(cols, inner)^T.
+struct DUpd {
+    int32_t a, b;        // operand tiles: (m,n) and (k,n); SYRK: both (k,n)
+    int32_t kmap;        // offset of (sa, sb) int16 pairs in imap, or -1 if contiguous
+    int32_t klen;        // inner length
+    int32_t ka0, kb0;    // contiguous inner: first stored column in a / in b
+    int32_t ra0, ra1;    // output rows touched (local rows of the output tile)
+    int32_t oc0, oc1;    // output stored columns touched (GEMM); SYRK: unused
+    int32_t pad[2];
+};
+
+struct DevPlanArrays {          // device pointers of one plan's metadata
+    DTile* tiles = nullptr;
+    int16_t* saind = nullptr;   // stored-column -> logical-column lists
+    DTask* tasks = nullptr;     // in queue (ASAP) order
+    DUpd* upds = nullptr;
+    int16_t* imap = nullptr;    // inner-dimension (sa, sb) pairs
+    int64_t* value_map = nullptr;
+    int64_t* pad_diag = nullptr;   // offsets set to 1.0 (padding of the ragged tile)
+    int64_t* csc_map = nullptr;    // nnzL: offset of each structural L entry
+    int32_t* perm = nullptr;
+    int32_t* srow_beg = nullptr;   // solve: per block row, tiles (k,n) n<k: [beg,end)
+    int32_t* srow_tiles = nullptr;
+    int32_t* scol_beg = nullptr;   // solve: per block column, tiles (m,k) m>k
+    int32_t* scol_tiles = nullptr;
+    int32_t* diag_tile = nullptr;  // per block: tile id of (k,k)
+    int device = -1;
+    int32_t ntasks = 0;
+};
+
+// Host-side task list for one row-slice count.
+struct TaskSet {
+    int32_t slices = 1;
+    std::vector<DTask> tasks;
+    std::vector<DUpd> upds;
+    std::vector<int16_t> imap;
+    std::vector<int32_t> nfinal;  // per tile completion target
+    double fma = 0.0;             // executed FMAs
+    // device copies
+    DTask* d_tasks = nullptr;
+    DUpd* d_upds = nullptr;
+    int16_t* d_imap = nullptr;
+    DTile* d_tiles = nullptr;     // tiles with this set's nfinal
+    int device = -1;
+};
+
+}  // namespace stc
+
+// The opaque plan of the public ABI.
+struct stc_plan {
+    // pattern / options
+    int64_t n = 0, nb = 0, nt = 0, nnzA = 0;
+    stc_options opt{};
+    int32_t route_selected = STC_ROUTE_SEMISPARSE, route_exec = STC_ROUTE_SEMISPARSE;
+    int32_t ordering = STC_ORDER_NATURAL;
+    double phi = 0, rho = 0, sigma = 0;
+    double analyze_seconds = 0;
+    std::vector<int64_t> perm;     // perm[k] = original index of pivot k
+    std::vector<int64_t> parent;   // elimination tree of the permuted matrix
+    std::vector<int64_t> Lp;       // symbolic structure of L (permuted), CSC
+    std::vector<int32_t> Li;
+    // tiles (block-column-major: J ascending, I ascending)
+    std::vector<stc::DTile> tiles;
+    std::vector<int32_t> nact;         // |A| (structural active columns)
+    std::vector<int64_t> aoff_struct;  // offset into aind_struct
+    std::vector<int16_t> aind_struct;  // structural active columns (exported)
+    std::vector<int8_t> contig, full;
+    std::vector<int16_t> saind;        // stored-column lists (indexed tiles only)
+    std::vector<int32_t> colstart;     // tiles of block column J: [colstart[J], colstart[J+1])
+    std::vector<int32_t> diag_tile;    // per block
+    std::vector<int32_t> rowstart, rowtiles;  // per block row k: off-diagonal tiles (k,n), n asc
+    int64_t stored_entries = 0;
+    int64_t factor_doubles = 0;        // item stride (doubles)
+    int64_t npartials = 0;             // logdet partials per item (= nt)
+    int64_t partial_off = 0;           // offset (doubles) of the partials in an item
+    std::vector<int64_t> alg1;         // Algorithm 1 tasks, 4 per task
+    int64_t n_potrf = 0, n_syrk = 0, n_trsm = 0, n_gemm = 0;
+    double flops_alg = 0, flops_tile = 0;
+    std::vector<int64_t> value_map;    // nnzA
+    std::vector<int64_t> pad_diag;
+    std::vector<int64_t> csc_map;      // nnzL
+    // task sets by slice count, device arrays
+    std::map<int32_t, std::unique_ptr<stc::TaskSet>> tasksets;
+    stc::DevPlanArrays dev;
+    std::mutex mu;
+
+    int tile_id(int64_t I, int64_t J) const;  // -1 if not active
+    stc::TaskSet* taskset(int32_t slices);    // built on demand (host)
+};

@@ -1,0 +1,960 @@
+// replay.cu -- numeric phase on the GPU (sm_103a): value scatter, the persistent
+// task-DAG replay of the tile Cholesky, log-determinant, triangular solves and the
+// factor export.  arxiv 2609.29765, Algorithm 1 (task list), Algorithm 2 (executor),
+// Sec. 4 (active-column and banded tiles), Sec. 5.3 (progress matrix -> counters).
+//
+// GB300 notes that shape this file:
+//  * FP64 runs at ~2 DFMA/clk/SM (measured 1.21 TFLOP/s DFMA, 1.06 TFLOP/s for
+//    mma.sync.m8n8k4.f64), so every tile kernel is DFMA-bound; tiles live in shared
+//    memory, the inner loops are 4x4 register micro-tiles of DFMA, and the tensor-core
+//    DMMA path is not used (it is slower on this part).
+//  * One persistent kernel per call walks the whole DAG of every batch item: CTAs take
+//    task slots from a global counter in a topological (earliest-start) order and wait
+//    on per-tile completion counters (the paper's progress matrix P and per-cell
+//    update counters), so the hundreds of thousands of small tile tasks of a batch cost
+//    one launch.  Every wait is bounded: past the limit it records STC_ERR_TIMEOUT in
+//    the workspace status word and the kernel drains without further waiting.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <climits>
+#include <cstdio>
+#include <cstring>
+
+#include "plan.hpp"
+
+namespace stc {
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kNbMax = 128;
+constexpr int kLdc = kNbMax + 1;   // shared-memory leading dimension of the tile buffer
+constexpr int kKc = 32;            // inner-dimension chunk staged per step
+constexpr int kPb = 32;            // panel width of the blocked POTRF / TRSM
+constexpr int kStage = kKc * (kNbMax + 8);          // doubles per staging buffer
+constexpr int kCbuf = kLdc * kNbMax + 16;           // tile buffer (+ overrun pad)
+constexpr int kSmemDoubles = kCbuf + 2 * kStage + kNbMax;
+constexpr size_t kSmemBytes = kSmemDoubles * sizeof(double) + 64;
+constexpr long long kDefaultSpin = 40000000LL;
+
+struct WorkHeader {          // start of the caller's workspace
+    unsigned long long head; // next task slot
+    int status;              // STC_OK or STC_ERR_TIMEOUT
+    int pad[13];
+};
+static_assert(sizeof(WorkHeader) == 64, "header size");
+
+__device__ __forceinline__ int ld_acquire(const int* p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void red_release_add(int* p, int v) {
+    asm volatile("red.release.gpu.global.add.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Wait (thread 0) until *cnt >= target.  Returns false on timeout / earlier error.
+__device__ bool wait_counter(const int* cnt, int target, long long limit, int* status) {
+    if (ld_acquire(cnt) >= target) return true;
+    for (long long it = 0;; ++it) {
+        if (ld_acquire(cnt) >= target) return true;
+        if (*(volatile int*)status != STC_OK) return false;
+        if (it >= limit) {
+            atomicCAS(status, STC_OK, STC_ERR_TIMEOUT);
+            return false;
+        }
+        __nanosleep(it < 64 ? 32 : 256);
+    }
+}
+
+// Record the first failing pivot (global column + 1) of an item; 0 = none yet.
+__device__ void record_info(int* info, int v) {
+    int old = *(volatile int*)info;
+    while (old == 0 || old > v) {
+        int prev = atomicCAS(info, old, v);
+        if (prev == old) break;
+        old = prev;
+    }
+}
+
+// L_kk[r][c] (r >= c) from a diagonal tile in global memory (zero outside the band).
+__device__ __forceinline__ double diag_at(const double* T, const DTile& d, int nb, int r, int c) {
+    if (d.kind == TILE_DIAG_DENSE) return __ldcg(T + r + (size_t)c * nb);
+    if (r - c > d.kd) return 0.0;
+    return __ldcg(T + (d.kd + c - r) + (size_t)r * (d.kd + 1));
+}
+
+__device__ __forceinline__ int logical_col(const DTile& t, const int16_t* saind, int s) {
+    return t.c0 >= 0 ? t.c0 + s : saind[t.aoff + s];
+}
+
+// ---------------------------------------------------------------------------
+// C(r,c) -= sum_k A(r,k) B(c,k), r < R, c < Cn; A(r,k) = A[r + k*lda],
+// B(c,k) = B[c + k*ldb], C(r,c) = C[r + c*ldc].  4x4 register micro-tiles, the
+// micro-tiles of the region spread over the CTA.  LOWER: only micro-tiles touching
+// r >= c (rows and columns index the same range) are computed, and only r >= c is
+// written.  A/B rows up to the next multiple of 4 must be readable (pad).
+// ---------------------------------------------------------------------------
+template <bool LOWER>
+__device__ void mma_sub(double* __restrict__ C, int ldc, int R, int Cn,
+                        const double* __restrict__ A, int lda,
+                        const double* __restrict__ B, int ldb, int K) {
+    const int MR = (R + 3) >> 2, MC = (Cn + 3) >> 2;
+    const int count = LOWER ? MR * (MR + 1) / 2 : MR * MC;
+    for (int mt = threadIdx.x; mt < count; mt += kThreads) {
+        int ri, cj;
+        if (LOWER) {
+            // mt -> (ri, cj), cj <= ri, row-major over the lower triangle
+            int r = (int)((sqrtf(8.0f * mt + 1.0f) - 1.0f) * 0.5f);
+            while (r * (r + 1) / 2 > mt) --r;
+            while ((r + 1) * (r + 2) / 2 <= mt) ++r;
+            ri = r;
+            cj = mt - r * (r + 1) / 2;
+        } else {
+            ri = mt % MR;
+            cj = mt / MR;
+        }
+        const int r0 = ri * 4, c0 = cj * 4;
+        double acc[4][4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+        const double* a = A + r0;
+        const double* b = B + c0;
+#pragma unroll 4
+        for (int k = 0; k < K; ++k) {
+            double av[4], bv[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) av[i] = a[i];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) bv[j] = b[j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = fma(av[i], bv[j], acc[i][j]);
+            a += lda;
+            b += ldb;
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int r = r0 + i, c = c0 + j;
+                if (r < R && c < Cn && (!LOWER || r >= c)) C[r + c * ldc] -= acc[i][j];
+            }
+    }
+}
+
+// Row-parallel forward substitution: X(r, 0:pw) <- X(r, 0:pw) * D^{-T}, D lower pw x pw
+// in shared memory (D(i,j) = D[i + j*ldd]) with reciprocal diagonal dinv[].
+__device__ void trsm_rows(double* X, int ldx, int R, int pw, const double* D, int ldd,
+                          const double* dinv) {
+    for (int r = threadIdx.x; r < R; r += kThreads) {
+        double x[kPb];
+#pragma unroll
+        for (int j = 0; j < kPb; ++j) x[j] = j < pw ? X[r + j * ldx] : 0.0;
+#pragma unroll
+        for (int j = 0; j < kPb; ++j) {
+            if (j < pw) {
+                double s0 = x[j], s1 = 0.0;
+#pragma unroll
+                for (int i = 0; i < j; i += 2) {
+                    s0 = fma(-x[i], D[j + i * ldd], s0);
+                    if (i + 1 < j) s1 = fma(-x[i + 1], D[j + (i + 1) * ldd], s1);
+                }
+                x[j] = (s0 + s1) * dinv[j];
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < kPb; ++j)
+            if (j < pw) X[r + j * ldx] = x[j];
+    }
+}
+
+struct ReplayArgs {
+    const DTile* tiles;
+    const int16_t* saind;
+    const DTask* tasks;
+    const DUpd* upds;
+    const int16_t* imap;
+    double* factor;          // item 0
+    long long fstride;       // doubles per item
+    long long poff;          // offset of the logdet partials in an item
+    int* counters;           // [batch][ntiles]
+    int ntiles;
+    int* info;               // [batch]
+    WorkHeader* hdr;
+    int ntasks;
+    long long batch;
+    int nb;
+    long long spin;
+};
+
+// Load rows [rs0, rs0+R) of stored columns [0, sw) of an off-diagonal tile into C.
+__device__ void load_off(double* C, const double* T, int nb, int rs0, int R, int sw) {
+    for (int idx = threadIdx.x; idx < R * sw; idx += kThreads) {
+        const int r = idx % R, c = idx / R;
+        C[r + c * kLdc] = __ldcg(T + rs0 + r + (size_t)c * nb);
+    }
+}
+__device__ void store_off(const double* C, double* T, int nb, int rs0, int R, int sw) {
+    for (int idx = threadIdx.x; idx < R * sw; idx += kThreads) {
+        const int r = idx % R, c = idx / R;
+        __stcg(T + rs0 + r + (size_t)c * nb, C[r + c * kLdc]);
+    }
+}
+
+// Full lower triangle (and zero upper) of a diagonal tile into C.
+__device__ void load_diag(double* C, const double* T, const DTile& d, int nb) {
+    for (int idx = threadIdx.x; idx < nb * nb; idx += kThreads) {
+        const int r = idx % nb, c = idx / nb;
+        C[r + c * kLdc] = r >= c ? diag_at(T, d, nb, r, c) : 0.0;
+    }
+}
+__device__ void store_diag(const double* C, double* T, const DTile& d, int nb) {
+    if (d.kind == TILE_DIAG_DENSE) {
+        for (int idx = threadIdx.x; idx < nb * nb; idx += kThreads) {
+            const int r = idx % nb, c = idx / nb;
+            __stcg(T + r + (size_t)c * nb, r >= c ? C[r + c * kLdc] : 0.0);
+        }
+    } else {
+        const int w = d.kd + 1;
+        for (int idx = threadIdx.x; idx < w * nb; idx += kThreads) {
+            const int q = idx % w, r = idx / w;  // storage (q, r): L[r][r - kd + q]
+            const int c = r - d.kd + q;
+            if (c >= 0) __stcg(T + idx, C[r + c * kLdc]);
+        }
+    }
+}
+
+// Stage a (R x K) chunk of stored columns of tile T into S (S[r + k*ld]); rows beyond R
+// up to a multiple of 4 are zeroed.
+__device__ void stage_cols(double* S, int ld, const double* T, int nb, int row0, int R,
+                           const DUpd& u, const int16_t* imap, bool use_b, int k0, int K) {
+    const int Rp = (R + 3) & ~3;
+    for (int idx = threadIdx.x; idx < Rp * K; idx += kThreads) {
+        const int r = idx % Rp, k = idx / Rp;
+        double v = 0.0;
+        if (r < R) {
+            int s;
+            if (u.kmap < 0) s = (use_b ? u.kb0 : u.ka0) + k0 + k;
+            else s = imap[2 * (u.kmap + k0 + k) + (use_b ? 1 : 0)];
+            v = __ldcg(T + row0 + r + (size_t)s * nb);
+        }
+        S[r + k * ld] = v;
+    }
+}
+
+// B rows for a GEMM: rows = logical columns of the output tile's stored columns oc0.. .
+__device__ void stage_rows_gather(double* S, int ld, const double* T, int nb, const DTile& O,
+                                  const int16_t* saind, int oc0, int Cn, const DUpd& u,
+                                  const int16_t* imap, int k0, int K) {
+    const int Cp = (Cn + 3) & ~3;
+    for (int idx = threadIdx.x; idx < Cp * K; idx += kThreads) {
+        const int c = idx % Cp, k = idx / Cp;
+        double v = 0.0;
+        if (c < Cn) {
+            const int row = logical_col(O, saind, oc0 + c);
+            const int s = u.kmap < 0 ? u.kb0 + k0 + k : imap[2 * (u.kmap + k0 + k) + 1];
+            v = __ldcg(T + row + (size_t)s * nb);
+        }
+        S[c + k * ld] = v;
+    }
+}
+
+// Blocked right-looking Cholesky of the w x w leading block of C (lower), panel kPb;
+// rows farther than kd below the diagonal are structurally zero and skipped.  *bad
+// receives the first non-positive pivot (or -1); *logsum = sum_j log L_jj, accumulated
+// as a mantissa product and an exponent sum (one log per tile).
+__device__ void potrf_smem(double* C, int w, int kd, double* sbuf, int* bad, double* logsum) {
+    __shared__ double s_mant;
+    __shared__ int s_exp, s_bad;
+    if (threadIdx.x == 0) { s_mant = 1.0; s_exp = 0; s_bad = -1; }
+    __syncthreads();
+    for (int p = 0; p < w; p += kPb) {
+        const int pw = min(kPb, w - p);
+        const int rend = min(w, p + pw + kd);  // rows below the panel inside the band
+        // (1) unblocked factor of the pw x pw diagonal block by warp 0
+        if (threadIdx.x < 32) {
+            const int lane = threadIdx.x;
+            double mant = s_mant;
+            int ex = s_exp;
+            for (int j = 0; j < pw; ++j) {
+                const int cj = p + j;
+                double inv = 0.0;
+                if (lane == 0) {
+                    const double d = C[cj + cj * kLdc];
+                    if (!(d > 0.0) && s_bad < 0) s_bad = cj;
+                    const double ljj = sqrt(d);
+                    inv = 1.0 / ljj;
+                    C[cj + cj * kLdc] = ljj;
+                    int e;
+                    mant = frexp(mant * ljj, &e);
+                    ex += e;
+                }
+                inv = __shfl_sync(0xffffffffu, inv, 0);
+                const int i = lane;
+                if (i > j && i < pw) C[p + i + cj * kLdc] *= inv;
+                __syncwarp();
+                if (i > j && i < pw) {
+                    const double lij = C[p + i + cj * kLdc];
+                    for (int l = j + 1; l <= i; ++l)
+                        C[p + i + (p + l) * kLdc] = fma(-lij, C[p + l + cj * kLdc], C[p + i + (p + l) * kLdc]);
+                }
+                __syncwarp();
+            }
+            if (lane == 0) { s_mant = mant; s_exp = ex; }
+            if (lane < pw) sbuf[lane] = 1.0 / C[p + lane + (p + lane) * kLdc];
+        }
+        __syncthreads();
+        // (2) rows below the panel: X <- X * D^{-T}
+        if (rend > p + pw)
+            trsm_rows(C + (p + pw) + p * kLdc, kLdc, rend - p - pw, pw, C + p + p * kLdc, kLdc, sbuf);
+        __syncthreads();
+        // (3) trailing update of the band below/right of the panel
+        if (rend > p + pw)
+            mma_sub<true>(C + (p + pw) + (p + pw) * kLdc, kLdc, rend - p - pw, rend - p - pw,
+                          C + (p + pw) + p * kLdc, kLdc, C + (p + pw) + p * kLdc, kLdc, pw);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        *bad = s_bad;
+        *logsum = log(s_mant) + (double)s_exp * 0.69314718055994530942;
+    }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(kThreads, 1) replay_kernel(ReplayArgs a) {
+    extern __shared__ double smem[];
+    double* C = smem;
+    double* S0 = C + kCbuf;
+    double* S1 = S0 + kStage;
+    double* sv = S1 + kStage;  // kNbMax doubles
+    __shared__ long long s_slot;
+    __shared__ int s_ok;
+    const long long total = (long long)a.ntasks * a.batch;
+    const int nb = a.nb;
+    for (;;) {
+        if (threadIdx.x == 0) s_slot = (long long)atomicAdd(&a.hdr->head, 1ULL);
+        __syncthreads();
+        const long long slot = s_slot;
+        __syncthreads();
+        if (slot >= total) break;
+        const int ti = (int)(slot / a.batch);
+        const long long item = slot % a.batch;
+        const DTask t = a.tasks[ti];
+        double* F = a.factor + item * a.fstride;
+        int* cnt = a.counters + item * a.ntiles;
+        const DTile O = a.tiles[t.tile];
+        if (threadIdx.x == 0) s_ok = (*(volatile int*)&a.hdr->status == STC_OK);
+        __syncthreads();
+        if (t.kind == TASK_DIAG) {
+            if (s_ok) {
+                load_diag(C, F + O.off, O, nb);
+                __syncthreads();
+                for (int ui = t.ubeg; ui < t.uend; ++ui) {
+                    const DUpd u = a.upds[ui];
+                    const DTile A = a.tiles[u.a];
+                    if (threadIdx.x == 0) s_ok = wait_counter(cnt + u.a, A.nfinal, a.spin, &a.hdr->status);
+                    __syncthreads();
+                    if (!s_ok) break;
+                    const int R = u.ra1 - u.ra0;
+                    for (int k0 = 0; k0 < u.klen; k0 += kKc) {
+                        const int K = min(kKc, u.klen - k0);
+                        stage_cols(S0, kNbMax + 8, F + A.off, nb, u.ra0, R, u, a.imap, false, k0, K);
+                        __syncthreads();
+                        mma_sub<true>(C + u.ra0 + u.ra0 * kLdc, kLdc, R, R, S0, kNbMax + 8, S0, kNbMax + 8, K);
+                        __syncthreads();
+                    }
+                }
+                if (s_ok) {
+                    int bad; double ls;
+                    potrf_smem(C, O.sw, min(O.kd, nb - 1), sv, &bad, &ls);
+                    if (threadIdx.x == 0) {
+                        if (bad >= 0) record_info(a.info + item, O.J * nb + bad + 1);
+                        F[a.poff + O.pd_slot] = bad >= 0 ? __longlong_as_double(0x7ff8000000000000LL) : ls;
+                    }
+                    store_diag(C, F + O.off, O, nb);
+                }
+            }
+        } else {
+            const int R = t.rs1 - t.rs0;
+            const int sw = O.sw;
+            if (s_ok) {
+                load_off(C, F + O.off, nb, t.rs0, R, sw);
+                __syncthreads();
+                for (int ui = t.ubeg; ui < t.uend; ++ui) {
+                    const DUpd u = a.upds[ui];
+                    const DTile A = a.tiles[u.a];
+                    const DTile B = a.tiles[u.b];
+                    if (threadIdx.x == 0)
+                        s_ok = wait_counter(cnt + u.a, A.nfinal, a.spin, &a.hdr->status) &&
+                               wait_counter(cnt + u.b, B.nfinal, a.spin, &a.hdr->status);
+                    __syncthreads();
+                    if (!s_ok) break;
+                    const int Ra = u.ra1 - u.ra0, Cn = u.oc1 - u.oc0;
+                    for (int k0 = 0; k0 < u.klen; k0 += kKc) {
+                        const int K = min(kKc, u.klen - k0);
+                        stage_cols(S0, kNbMax + 8, F + A.off, nb, u.ra0, Ra, u, a.imap, false, k0, K);
+                        stage_rows_gather(S1, kNbMax + 8, F + B.off, nb, O, a.saind, u.oc0, Cn, u, a.imap, k0, K);
+                        __syncthreads();
+                        mma_sub<false>(C + (u.ra0 - t.rs0) + u.oc0 * kLdc, kLdc, Ra, Cn, S0, kNbMax + 8,
+                                       S1, kNbMax + 8, K);
+                        __syncthreads();
+                    }
+                }
+                // TRSM of rows [tr0, tr1) against L_kk restricted to the stored columns
+                const DTile D = a.tiles[t.diag];
+                if (s_ok && threadIdx.x == 0) s_ok = wait_counter(cnt + t.diag, 1, a.spin, &a.hdr->status);
+                __syncthreads();
+                if (s_ok) {
+                    const double* DT = F + D.off;
+                    double* X = C + (t.tr0 - t.rs0);
+                    const int RX = t.tr1 - t.tr0;
+                    for (int p = 0; p < sw; p += kPb) {
+                        const int pw = min(kPb, sw - p);
+                        for (int k0 = 0; k0 < p; k0 += kKc) {
+                            const int K = min(kKc, p - k0);
+                            const int Cp = (pw + 3) & ~3;
+                            for (int idx = threadIdx.x; idx < Cp * K; idx += kThreads) {
+                                const int c = idx % Cp, k = idx / Cp;
+                                double v = 0.0;
+                                if (c < pw)
+                                    v = diag_at(DT, D, nb, logical_col(O, a.saind, p + c),
+                                                logical_col(O, a.saind, k0 + k));
+                                S1[c + k * (kNbMax + 8)] = v;
+                            }
+                            __syncthreads();
+                            mma_sub<false>(X + p * kLdc, kLdc, RX, pw, X + k0 * kLdc, kLdc, S1, kNbMax + 8, K);
+                            __syncthreads();
+                        }
+                        // diagonal block of the panel and its reciprocal diagonal
+                        for (int idx = threadIdx.x; idx < kPb * kPb; idx += kThreads) {
+                            const int i = idx % kPb, j = idx / kPb;
+                            double v = 0.0;
+                            if (i < pw && j < pw && i >= j)
+                                v = diag_at(DT, D, nb, logical_col(O, a.saind, p + i), logical_col(O, a.saind, p + j));
+                            S0[i + j * kPb] = v;
+                        }
+                        __syncthreads();
+                        if (threadIdx.x < pw) sv[threadIdx.x] = 1.0 / S0[threadIdx.x * (kPb + 1)];
+                        __syncthreads();
+                        trsm_rows(X + p * kLdc, kLdc, RX, pw, S0, kPb, sv);
+                        __syncthreads();
+                    }
+                    store_off(C, F + O.off, nb, t.rs0, R, sw);
+                }
+            }
+        }
+        // publish: every thread's stores are fenced before the counter moves
+        __threadfence();
+        __syncthreads();
+        if (threadIdx.x == 0) red_release_add(cnt + t.tile, 1);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// a1: value scatter.  factor[b][map[e]] = values[b][e]; padding diagonal = 1.
+// ---------------------------------------------------------------------------
+__global__ void scatter_kernel(const double* __restrict__ vals, long long nnz, long long batch,
+                               const int64_t* __restrict__ map, double* __restrict__ F,
+                               long long fstride, const int64_t* __restrict__ pad, int npad) {
+    const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long e = tid; e < nnz; e += stride) {
+        const int64_t m = __ldg(map + e);
+        for (long long b = 0; b < batch; ++b) F[b * fstride + m] = __ldcs(vals + b * nnz + e);
+    }
+    for (long long i = tid; i < (long long)npad * batch; i += stride) {
+        const long long b = i / npad;
+        F[b * fstride + pad[i % npad]] = 1.0;
+    }
+}
+
+// a9: logdet = 2 * sum of the per-diagonal-tile partials, fixed order (one warp/item).
+__global__ void logdet_kernel(const double* __restrict__ F, long long fstride, long long poff,
+                              int np, long long batch, double* __restrict__ out) {
+    const long long item = blockIdx.x * (long long)(blockDim.x / 32) + threadIdx.x / 32;
+    const int lane = threadIdx.x & 31;
+    if (item >= batch) return;
+    const double* p = F + item * fstride + poff;
+    double s = 0.0;
+    for (int i = lane; i < np; i += 32) s += p[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0) out[item] = 2.0 * s;
+}
+
+__global__ void to_csc_kernel(const double* __restrict__ F, long long fstride, long long batch,
+                              const int64_t* __restrict__ map, long long nnzl, double* __restrict__ out) {
+    const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long q = tid; q < nnzl; q += stride) {
+        const int64_t m = __ldg(map + q);
+        for (long long b = 0; b < batch; ++b) out[b * nnzl + q] = F[b * fstride + m];
+    }
+}
+
+
+// ---------------------------------------------------------------------------
+// a10: solve.  One persistent kernel over every (item, rhs) chain.  Task k < nt is
+// the forward block row k:  y_k = L_kk^{-1} (P b)_k - sum_{n<k} L_kn y_n ;  task nt+i is
+// the backward block column k = nt-1-i:  z_k = L_kk^{-T} (y_k - sum_{m>k} L_mk^T z_m),
+// written in place of y_k and scattered to x = P^T z.  The diagonal tile is staged in
+// shared memory; warp 0 runs the substitution with four rows per lane.
+// ---------------------------------------------------------------------------
+struct SolveArgs {
+    const DTile* tiles;
+    const int16_t* saind;
+    const int32_t* rowstart;   // per block row: off-diagonal tiles (k,n), n ascending
+    const int32_t* rowtiles;
+    const int32_t* colstart;   // per block column: tiles (m,k), diagonal first
+    const int32_t* diag;
+    const int32_t* perm;
+    const double* factor;
+    long long fstride;
+    const double* b;           // [chains][n]
+    double* x;                 // [chains][n]
+    double* y;                 // workspace [chains][nt*nb]
+    int* done;                 // workspace [chains][2*nt]
+    WorkHeader* hdr;
+    long long chains;          // batch * nrhs
+    long long nrhs;
+    int nt, nb;
+    long long n;
+    long long spin;
+};
+
+constexpr int kSolveWarps = kThreads / 32;
+constexpr size_t kSolveSmem = (size_t)(kLdc * kNbMax + kNbMax * (kSolveWarps + 2)) * sizeof(double);
+
+__global__ void __launch_bounds__(kThreads, 1) solve_kernel(SolveArgs a) {
+    extern __shared__ double smem[];
+    double* Ls = smem;                          // diagonal tile, L(r,c) at r + c*kLdc
+    double* acc = Ls + kLdc * kNbMax;           // [kSolveWarps][nb] partial sums
+    double* v = acc + kSolveWarps * kNbMax;     // block right-hand side
+    double* dinv = v + kNbMax;
+    __shared__ long long s_slot;
+    __shared__ int s_ok;
+    const long long total = 2LL * a.nt * a.chains;
+    const int nb = a.nb, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (;;) {
+        if (threadIdx.x == 0) s_slot = (long long)atomicAdd(&a.hdr->head, 1ULL);
+        __syncthreads();
+        const long long slot = s_slot;
+        __syncthreads();
+        if (slot >= total) break;
+        const int ti = (int)(slot / a.chains);
+        const long long ch = slot % a.chains;
+        const long long item = ch / a.nrhs;
+        const double* F = a.factor + item * a.fstride;
+        double* y = a.y + ch * (long long)a.nt * nb;
+        int* done = a.done + ch * 2LL * a.nt;
+        const bool fwd = ti < a.nt;
+        const int k = fwd ? ti : a.nt - 1 - (ti - a.nt);
+        const DTile D = a.tiles[a.diag[k]];
+        if (threadIdx.x == 0) {
+            s_ok = (*(volatile int*)&a.hdr->status == STC_OK);
+            if (s_ok && !fwd) s_ok = wait_counter(done + k, 1, a.spin, &a.hdr->status);
+        }
+        __syncthreads();
+        if (s_ok) {
+            for (int i = threadIdx.x; i < kSolveWarps * nb; i += kThreads) acc[i] = 0.0;
+            for (int idx = threadIdx.x; idx < nb * nb; idx += kThreads) {
+                const int r = idx % nb, c = idx / nb;
+                Ls[r + c * kLdc] = r >= c ? diag_at(F + D.off, D, nb, r, c) : 0.0;
+            }
+            for (int r = threadIdx.x; r < nb; r += kThreads) {
+                const long long g = (long long)k * nb + r;
+                v[r] = fwd ? (g < a.n ? a.b[ch * a.n + a.perm[g]] : 0.0) : __ldcg(y + g);
+            }
+            __syncthreads();
+            if (fwd) {
+                for (int q = a.rowstart[k]; q < a.rowstart[k + 1]; ++q) {
+                    const DTile T = a.tiles[a.rowtiles[q]];
+                    if (threadIdx.x == 0) s_ok = wait_counter(done + T.J, 1, a.spin, &a.hdr->status);
+                    __syncthreads();
+                    if (!s_ok) break;
+                    const double* yn = y + (long long)T.J * nb;
+                    for (int s = warp; s < T.sw; s += kSolveWarps) {
+                        const double ys = __ldcg(yn + logical_col(T, a.saind, s));
+                        const double* col = F + T.off + (size_t)s * nb;
+                        for (int r = T.r0 + lane; r < T.r1; r += 32)
+                            acc[warp * nb + r] = fma(-__ldcg(col + r), ys, acc[warp * nb + r]);
+                    }
+                    __syncthreads();
+                }
+            } else {
+                for (int q = a.colstart[k]; q < a.colstart[k + 1]; ++q) {
+                    const DTile T = a.tiles[q];
+                    if (T.I == T.J) continue;
+                    if (threadIdx.x == 0) s_ok = wait_counter(done + a.nt + T.I, 1, a.spin, &a.hdr->status);
+                    __syncthreads();
+                    if (!s_ok) break;
+                    const double* zm = y + (long long)T.I * nb;
+                    for (int s = warp; s < T.sw; s += kSolveWarps) {
+                        const double* col = F + T.off + (size_t)s * nb;
+                        double d = 0.0;
+                        for (int r = T.r0 + lane; r < T.r1; r += 32) d = fma(__ldcg(col + r), __ldcg(zm + r), d);
+#pragma unroll
+                        for (int o = 16; o > 0; o >>= 1) d += __shfl_down_sync(0xffffffffu, d, o);
+                        if (lane == 0) acc[warp * nb + logical_col(T, a.saind, s)] -= d;
+                    }
+                    __syncthreads();
+                }
+            }
+            for (int r = threadIdx.x; r < nb; r += kThreads) {
+                double s = v[r];
+                for (int w = 0; w < kSolveWarps; ++w) s += acc[w * nb + r];
+                v[r] = s;
+                dinv[r] = 1.0 / Ls[r + r * kLdc];
+            }
+            __syncthreads();
+            if (s_ok && warp == 0) {
+                // rows lane, lane+32, lane+64, lane+96 live in registers
+                double rv[kNbMax / 32];
+#pragma unroll
+                for (int q = 0; q < kNbMax / 32; ++q) rv[q] = (lane + 32 * q < nb) ? v[lane + 32 * q] : 0.0;
+                if (fwd) {
+                    for (int j = 0; j < nb; ++j) {
+                        double own = 0.0;
+#pragma unroll
+                        for (int q = 0; q < kNbMax / 32; ++q) if (q == (j >> 5)) own = rv[q];
+                        const double yj = __shfl_sync(0xffffffffu, own, j & 31) * dinv[j];
+#pragma unroll
+                        for (int q = 0; q < kNbMax / 32; ++q) {
+                            const int i = lane + 32 * q;
+                            if (i == j) rv[q] = yj;
+                            else if (i > j && i < nb) rv[q] = fma(-Ls[i + j * kLdc], yj, rv[q]);
+                        }
+                    }
+                } else {
+                    for (int j = nb - 1; j >= 0; --j) {
+                        double own = 0.0;
+#pragma unroll
+                        for (int q = 0; q < kNbMax / 32; ++q) if (q == (j >> 5)) own = rv[q];
+                        const double zj = __shfl_sync(0xffffffffu, own, j & 31) * dinv[j];
+#pragma unroll
+                        for (int q = 0; q < kNbMax / 32; ++q) {
+                            const int i = lane + 32 * q;
+                            if (i == j) rv[q] = zj;
+                            else if (i < j) rv[q] = fma(-Ls[j + i * kLdc], zj, rv[q]);
+                        }
+                    }
+                }
+#pragma unroll
+                for (int q = 0; q < kNbMax / 32; ++q) {
+                    const int i = lane + 32 * q;
+                    if (i < nb) {
+                        __stcg(y + (long long)k * nb + i, rv[q]);
+                        const long long g = (long long)k * nb + i;
+                        if (!fwd && g < a.n) a.x[ch * a.n + a.perm[g]] = rv[q];
+                    }
+                }
+            }
+        }
+        __threadfence();
+        __syncthreads();
+        if (threadIdx.x == 0) red_release_add(done + (fwd ? k : a.nt + k), 1);
+    }
+}
+
+// DFMA throughput probe: 8 independent FMA chains per thread.
+__global__ void fp64_probe_kernel(double* out, long long iters, double a, double b) {
+    double c[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) c[i] = threadIdx.x * 1e-3 + i;
+    for (long long it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) c[i] = fma(c[i], a, b);
+    }
+    double s = 0.0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) s += c[i];
+    out[blockIdx.x * (long long)blockDim.x + threadIdx.x] = s;
+}
+
+// ---------------------------------------------------------------------------
+// Host helpers
+// ---------------------------------------------------------------------------
+struct DevInfo {
+    int sms = 0;
+    bool attr_set = false;
+};
+DevInfo g_dev[64];
+std::mutex g_dev_mu;
+
+int device_info(int* dev, int* sms) {
+    if (cudaGetDevice(dev) != cudaSuccess) return STC_ERR_CUDA;
+    if (*dev < 0 || *dev >= 64) return STC_ERR_UNSUPPORTED;
+    std::lock_guard<std::mutex> g(g_dev_mu);
+    DevInfo& d = g_dev[*dev];
+    if (!d.attr_set) {
+        if (cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, *dev) != cudaSuccess) return STC_ERR_CUDA;
+        if (cudaFuncSetAttribute(replay_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes) != cudaSuccess)
+            return STC_ERR_CUDA;
+        if (cudaFuncSetAttribute(solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSolveSmem) != cudaSuccess)
+            return STC_ERR_CUDA;
+        d.attr_set = true;
+    }
+    *sms = d.sms;
+    return STC_OK;
+}
+
+template <class T>
+int upload(T** dst, const std::vector<T>& src) {
+    *dst = nullptr;
+    if (src.empty()) return STC_OK;
+    if (cudaMalloc((void**)dst, src.size() * sizeof(T)) != cudaSuccess) return STC_ERR_OUT_OF_MEMORY;
+    if (cudaMemcpy(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice) != cudaSuccess)
+        return STC_ERR_CUDA;
+    return STC_OK;
+}
+
+void free_dev(stc_plan* P) {
+    DevPlanArrays& d = P->dev;
+    void* ptrs[] = {d.saind, d.value_map, d.pad_diag, d.csc_map, d.perm, d.srow_beg,
+                    d.srow_tiles, d.scol_beg, d.diag_tile};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    d = DevPlanArrays{};
+    for (auto& kv : P->tasksets) {
+        TaskSet* ts = kv.second.get();
+        if (ts->d_tasks) cudaFree(ts->d_tasks);
+        if (ts->d_upds) cudaFree(ts->d_upds);
+        if (ts->d_imap) cudaFree(ts->d_imap);
+        if (ts->d_tiles) cudaFree(ts->d_tiles);
+        ts->d_tasks = nullptr; ts->d_upds = nullptr; ts->d_imap = nullptr; ts->d_tiles = nullptr;
+        ts->device = -1;
+    }
+}
+
+// Device copies of the plan's arrays on the current device (synchronous on first use).
+int ensure_plan(stc_plan* P, int dev) {
+    std::lock_guard<std::mutex> g(P->mu);
+    if (P->dev.device == dev) return STC_OK;
+    if (P->dev.device >= 0) free_dev(P);
+    DevPlanArrays& d = P->dev;
+    int rc;
+    std::vector<int32_t> perm32(P->perm.begin(), P->perm.end());
+    if ((rc = upload(&d.saind, P->saind))) return rc;
+    if ((rc = upload(&d.value_map, P->value_map))) return rc;
+    if ((rc = upload(&d.pad_diag, P->pad_diag))) return rc;
+    if ((rc = upload(&d.csc_map, P->csc_map))) return rc;
+    if ((rc = upload(&d.perm, perm32))) return rc;
+    if ((rc = upload(&d.srow_beg, P->rowstart))) return rc;
+    if ((rc = upload(&d.srow_tiles, P->rowtiles))) return rc;
+    if ((rc = upload(&d.scol_beg, P->colstart))) return rc;
+    if ((rc = upload(&d.diag_tile, P->diag_tile))) return rc;
+    d.device = dev;
+    return STC_OK;
+}
+
+int ensure_taskset(stc_plan* P, TaskSet* ts, int dev) {
+    std::lock_guard<std::mutex> g(P->mu);
+    if (ts->device == dev) return STC_OK;
+    std::vector<DTile> tiles = P->tiles;
+    for (size_t t = 0; t < tiles.size(); ++t) tiles[t].nfinal = ts->nfinal[t];
+    int rc;
+    if ((rc = upload(&ts->d_tiles, tiles))) return rc;
+    if ((rc = upload(&ts->d_tasks, ts->tasks))) return rc;
+    if ((rc = upload(&ts->d_upds, ts->upds))) return rc;
+    std::vector<int16_t> im = ts->imap;
+    if (im.empty()) im.push_back(0);
+    if ((rc = upload(&ts->d_imap, im))) return rc;
+    ts->device = dev;
+    return STC_OK;
+}
+
+size_t factorize_ws(const stc_plan* P, int64_t batch) {
+    return sizeof(WorkHeader) + (size_t)batch * P->tiles.size() * sizeof(int);
+}
+size_t solve_ws(const stc_plan* P, int64_t chains) {
+    size_t flags = ((size_t)chains * 2 * P->nt * sizeof(int) + 255) / 256 * 256;
+    return sizeof(WorkHeader) + flags + (size_t)chains * P->nt * P->nb * sizeof(double);
+}
+
+int32_t pick_slices(const stc_plan* P, int64_t batch, int sms) {
+    if (P->opt.row_slices > 0) return P->opt.row_slices;
+    // enough independent row slices to cover the GPU when the batch alone does not
+    const int64_t per_item = std::max<int64_t>(1, (int64_t)P->tiles.size() / std::max<int64_t>(1, P->nt));
+    const int64_t width = batch * per_item;
+    if (width >= 4 * sms) return 1;
+    if (width >= sms) return 2;
+    return 4;
+}
+
+inline cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+}  // namespace
+}  // namespace stc
+
+using namespace stc;
+
+extern "C" int stc_plan_upload(stc_plan* P) {
+    if (!P) return STC_ERR_INVALID_ARG;
+    int dev, sms;
+    int rc = device_info(&dev, &sms);
+    if (rc) return rc;
+    if ((rc = ensure_plan(P, dev))) return rc;
+    return ensure_taskset(P, P->taskset(1), dev);
+}
+
+extern "C" void stc_plan_destroy(stc_plan* P) {
+    if (!P) return;
+    if (P->dev.device >= 0 || !P->tasksets.empty()) {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (P->dev.device >= 0 && P->dev.device != cur) cudaSetDevice(P->dev.device);
+        free_dev(P);
+        if (cur >= 0) cudaSetDevice(cur);
+    }
+    delete P;
+}
+
+extern "C" size_t stc_factor_bytes(const stc_plan* P, int64_t batch) {
+    if (!P || batch < 0) return 0;
+    return (size_t)batch * (size_t)P->factor_doubles * sizeof(double);
+}
+
+extern "C" size_t stc_workspace_bytes(const stc_plan* P, int64_t batch) {
+    if (!P || batch < 0) return 0;
+    return std::max(factorize_ws(P, batch), solve_ws(P, batch));
+}
+
+extern "C" int stc_scatter_values(const stc_plan* Pc, const double* d_values, int64_t batch, void* d_factor,
+                                  void* stream) {
+    stc_plan* P = const_cast<stc_plan*>(Pc);
+    if (!P || !d_values || !d_factor || batch <= 0) return STC_ERR_INVALID_ARG;
+    int dev, sms, rc;
+    if ((rc = device_info(&dev, &sms))) return rc;
+    if ((rc = ensure_plan(P, dev))) return rc;
+    cudaStream_t st = S(stream);
+    if (cudaMemsetAsync(d_factor, 0, stc_factor_bytes(P, batch), st) != cudaSuccess) return STC_ERR_CUDA;
+    const int blocks = std::max(1, std::min<int>(sms * 8, (int)((P->nnzA + 255) / 256)));
+    scatter_kernel<<<blocks, 256, 0, st>>>(d_values, P->nnzA, batch, P->dev.value_map, (double*)d_factor,
+                                           P->factor_doubles, P->dev.pad_diag, (int)P->pad_diag.size());
+    return cudaGetLastError() == cudaSuccess ? STC_OK : STC_ERR_CUDA;
+}
+
+extern "C" int stc_factorize_scattered(const stc_plan* Pc, int64_t batch, void* d_factor, void* d_work,
+                                       int32_t* d_info, void* stream) {
+    stc_plan* P = const_cast<stc_plan*>(Pc);
+    if (!P || !d_factor || !d_work || !d_info || batch <= 0) return STC_ERR_INVALID_ARG;
+    int dev, sms, rc;
+    if ((rc = device_info(&dev, &sms))) return rc;
+    if ((rc = ensure_plan(P, dev))) return rc;
+    TaskSet* ts = P->taskset(pick_slices(P, batch, sms));
+    if ((rc = ensure_taskset(P, ts, dev))) return rc;
+    cudaStream_t st = S(stream);
+    if (cudaMemsetAsync(d_work, 0, factorize_ws(P, batch), st) != cudaSuccess) return STC_ERR_CUDA;
+    if (cudaMemsetAsync(d_info, 0, (size_t)batch * sizeof(int32_t), st) != cudaSuccess) return STC_ERR_CUDA;
+    ReplayArgs a{};
+    a.tiles = ts->d_tiles; a.saind = P->dev.saind; a.tasks = ts->d_tasks; a.upds = ts->d_upds;
+    a.imap = ts->d_imap; a.factor = (double*)d_factor; a.fstride = P->factor_doubles;
+    a.poff = P->partial_off; a.hdr = (WorkHeader*)d_work;
+    a.counters = (int*)((char*)d_work + sizeof(WorkHeader));
+    a.ntiles = (int)P->tiles.size(); a.info = d_info; a.ntasks = (int)ts->tasks.size();
+    a.batch = batch; a.nb = (int)P->nb;
+    a.spin = P->opt.spin_limit > 0 ? P->opt.spin_limit : kDefaultSpin;
+    const long long total = (long long)a.ntasks * batch;
+    const int grid = (int)std::max<long long>(1, std::min<long long>(sms, total));
+    replay_kernel<<<grid, kThreads, kSmemBytes, st>>>(a);
+    return cudaGetLastError() == cudaSuccess ? STC_OK : STC_ERR_CUDA;
+}
+
+extern "C" int stc_factorize(const stc_plan* P, const double* d_values, int64_t batch, void* d_factor,
+                             void* d_work, int32_t* d_info, void* stream) {
+    if (!P || !d_values || !d_factor || !d_work || !d_info || batch <= 0) return STC_ERR_INVALID_ARG;
+    int rc = stc_scatter_values(P, d_values, batch, d_factor, stream);
+    if (rc) return rc;
+    return stc_factorize_scattered(P, batch, d_factor, d_work, d_info, stream);
+}
+
+extern "C" int stc_sync_status(const void* d_work, void* stream) {
+    if (!d_work) return STC_ERR_INVALID_ARG;
+    if (cudaStreamSynchronize(S(stream)) != cudaSuccess) return STC_ERR_CUDA;
+    WorkHeader h;
+    if (cudaMemcpy(&h, d_work, sizeof(h), cudaMemcpyDeviceToHost) != cudaSuccess) return STC_ERR_CUDA;
+    return h.status;
+}
+
+extern "C" int stc_logdet(const stc_plan* P, const void* d_factor, int64_t batch, double* d_logdet,
+                          void* stream) {
+    if (!P || !d_factor || !d_logdet || batch <= 0) return STC_ERR_INVALID_ARG;
+    const int wpb = 8;
+    const long long blocks = (batch + wpb - 1) / wpb;
+    logdet_kernel<<<(unsigned)blocks, 32 * wpb, 0, S(stream)>>>((const double*)d_factor, P->factor_doubles,
+                                                                P->partial_off, (int)P->npartials, batch, d_logdet);
+    return cudaGetLastError() == cudaSuccess ? STC_OK : STC_ERR_CUDA;
+}
+
+extern "C" int stc_factor_to_csc(const stc_plan* Pc, const void* d_factor, int64_t batch, double* d_Lx,
+                                 void* stream) {
+    stc_plan* P = const_cast<stc_plan*>(Pc);
+    if (!P || !d_factor || !d_Lx || batch <= 0) return STC_ERR_INVALID_ARG;
+    int dev, sms, rc;
+    if ((rc = device_info(&dev, &sms))) return rc;
+    if ((rc = ensure_plan(P, dev))) return rc;
+    const long long nnzl = P->Lp[P->n];
+    const int blocks = std::max(1, std::min<int>(sms * 8, (int)((nnzl + 255) / 256)));
+    to_csc_kernel<<<blocks, 256, 0, S(stream)>>>((const double*)d_factor, P->factor_doubles, batch, P->dev.csc_map,
+                                                 nnzl, d_Lx);
+    return cudaGetLastError() == cudaSuccess ? STC_OK : STC_ERR_CUDA;
+}
+
+extern "C" int stc_solve(const stc_plan* Pc, const void* d_factor, int64_t batch, int64_t nrhs, const double* d_b,
+                         double* d_x, void* d_work, void* stream) {
+    stc_plan* P = const_cast<stc_plan*>(Pc);
+    if (!P || !d_factor || !d_b || !d_x || !d_work || batch <= 0 || nrhs <= 0 || d_b == d_x)
+        return STC_ERR_INVALID_ARG;
+    int dev, sms, rc;
+    if ((rc = device_info(&dev, &sms))) return rc;
+    if ((rc = ensure_plan(P, dev))) return rc;
+    TaskSet* ts = P->taskset(1);
+    if ((rc = ensure_taskset(P, ts, dev))) return rc;
+    const long long chains = batch * nrhs;
+    cudaStream_t st = S(stream);
+    const size_t flags = ((size_t)chains * 2 * P->nt * sizeof(int) + 255) / 256 * 256;
+    if (cudaMemsetAsync(d_work, 0, sizeof(WorkHeader) + flags, st) != cudaSuccess) return STC_ERR_CUDA;
+    SolveArgs a{};
+    a.tiles = ts->d_tiles; a.saind = P->dev.saind; a.rowstart = P->dev.srow_beg; a.rowtiles = P->dev.srow_tiles;
+    a.colstart = P->dev.scol_beg; a.diag = P->dev.diag_tile; a.perm = P->dev.perm;
+    a.factor = (const double*)d_factor; a.fstride = P->factor_doubles; a.b = d_b; a.x = d_x;
+    a.hdr = (WorkHeader*)d_work;
+    a.done = (int*)((char*)d_work + sizeof(WorkHeader));
+    a.y = (double*)((char*)d_work + sizeof(WorkHeader) + flags);
+    a.chains = chains; a.nrhs = nrhs; a.nt = (int)P->nt; a.nb = (int)P->nb; a.n = P->n;
+    a.spin = P->opt.spin_limit > 0 ? P->opt.spin_limit : kDefaultSpin;
+    const long long total = 2LL * P->nt * chains;
+    const int grid = (int)std::max<long long>(1, std::min<long long>(sms, total));
+    solve_kernel<<<grid, kThreads, kSolveSmem, st>>>(a);
+    return cudaGetLastError() == cudaSuccess ? STC_OK : STC_ERR_CUDA;
+}
+
+extern "C" int stc_fp64_peak_probe(double* d_scratch, int64_t scratch_doubles, int64_t iters, double* gflops) {
+    if (!d_scratch || !gflops || scratch_doubles < 256 || iters <= 0) return STC_ERR_INVALID_ARG;
+    int dev, sms, rc;
+    if ((rc = device_info(&dev, &sms))) return rc;
+    const long long blocks = std::min<long long>((long long)sms * 4, scratch_doubles / 256);
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return STC_ERR_CUDA;
+    fp64_probe_kernel<<<(unsigned)blocks, 256>>>(d_scratch, iters, 1.0000001, 1e-9);  // warm-up
+    float best = 1e30f;
+    for (int r = 0; r < 3; ++r) {
+        cudaEventRecord(e0);
+        fp64_probe_kernel<<<(unsigned)blocks, 256>>>(d_scratch, iters, 1.0000001, 1e-9);
+        cudaEventRecord(e1);
+        if (cudaEventSynchronize(e1) != cudaSuccess) { rc = STC_ERR_CUDA; break; }
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        best = std::min(best, ms);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) return rc;
+    if (cudaGetLastError() != cudaSuccess) return STC_ERR_CUDA;
+    *gflops = 2.0 * 8.0 * (double)iters * (double)blocks * 256.0 / (best * 1e-3) / 1e9;
+    return STC_OK;
+}
