@@ -196,6 +196,34 @@ int stc_factor_to_csc(const stc_plan* plan, const void* d_factor, int64_t batch,
  * doubles (results are written there so the work is not optimised away). */
 int stc_fp64_peak_probe(double* d_scratch, int64_t scratch_doubles, int64_t iters, double* gflops);
 
+/* Factorization that allocates nothing and takes no workspace argument.
+ *
+ * The paper has no counterpart: this entry point exists for callers that cannot obtain
+ * device memory at the moment they factorize -- for example a service that reserves
+ * all GPU memory through its own allocator at start-up and forbids later cudaMalloc,
+ * a real-time loop that must not risk the device-wide synchronisation a cudaMalloc can
+ * cause, or a plug-in host that hands a library only its input and output buffers.
+ *
+ * It runs the same value scatter and the same persistent task-DAG kernel as
+ * stc_factorize, but the kernel's scratch (queue head, status word and per-tile
+ * dependency counters) lives in a fixed device array inside libstc.so, of
+ * STC_NOALLOC_SCRATCH_BYTES bytes, held by every GPU that loads the library until the
+ * process exits.  Needed: 64 + 4 * batch * ntiles bytes (ntiles from stc_plan_info);
+ * a larger request returns STC_ERR_UNSUPPORTED without launching anything.
+ *   d_values [batch][nnzA] input; d_factor (stc_factor_bytes(plan,batch) bytes) and
+ *   d_info [batch] outputs as for stc_factorize; d_status: optional device int32 that
+ *   receives STC_OK or STC_ERR_TIMEOUT when the kernel ends (NULL = not reported).
+ * Preconditions: stc_plan_upload(plan) was called on the current device (otherwise
+ * STC_ERR_INVALID_ARG: uploading would allocate).  The first call on each device looks
+ * up the array's device address (cudaGetSymbolAddress); make that first call before
+ * any stream capture.  Every call on a device shares the one array and clears the part
+ * it uses on `stream` before its kernel starts; calls whose kernels overlap on the GPU
+ * (different streams, or several threads) race on it and give undefined results, so
+ * serialise them. */
+#define STC_NOALLOC_SCRATCH_BYTES (4u << 20)
+int stc_factorize_noalloc(const stc_plan* plan, const double* d_values, int64_t batch,
+                          void* d_factor, int32_t* d_info, int32_t* d_status, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -36,8 +36,9 @@ EXPORTED = [
     "stc_options_default", "stc_analyze", "stc_plan_info_get", "stc_plan_export", "stc_plan_upload",
     "stc_plan_destroy", "stc_factor_bytes", "stc_workspace_bytes", "stc_factorize", "stc_scatter_values",
     "stc_factorize_scattered", "stc_sync_status",
-    "stc_logdet", "stc_solve", "stc_factor_to_csc", "stc_fp64_peak_probe",
+    "stc_logdet", "stc_solve", "stc_factor_to_csc", "stc_fp64_peak_probe", "stc_factorize_noalloc",
 ]
+STC_NOALLOC_SCRATCH_BYTES = 4 << 20
 
 
 class StcError(RuntimeError):
@@ -109,6 +110,8 @@ def lib():
         L.stc_solve.restype = C.c_int
         L.stc_factor_to_csc.argtypes = [_vp, _vp, C.c_int64, _vp, _vp]
         L.stc_factor_to_csc.restype = C.c_int
+        L.stc_factorize_noalloc.argtypes = [_vp, _vp, C.c_int64, _vp, _vp, _vp, _vp]
+        L.stc_factorize_noalloc.restype = C.c_int
         L.stc_fp64_peak_probe.argtypes = [_vp, C.c_int64, C.c_int64, C.POINTER(C.c_double)]
         L.stc_fp64_peak_probe.restype = C.c_int
         _lib = L
@@ -228,3 +231,8 @@ def stc_fp64_peak_probe(d_scratch, iters=4096):
     g = C.c_double(0.0)
     rc = lib().stc_fp64_peak_probe(_dev_ptr(d_scratch), int(d_scratch.numel()), int(iters), C.byref(g))
     return rc, g.value
+
+
+def stc_factorize_noalloc(plan, d_values, batch, d_factor, d_info, d_status=None, stream=None):
+    return lib().stc_factorize_noalloc(plan, _dev_ptr(d_values), int(batch), _dev_ptr(d_factor),
+                                       _dev_ptr(d_info), _dev_ptr(d_status), _stream(stream))

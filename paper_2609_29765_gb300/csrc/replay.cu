@@ -958,3 +958,75 @@ extern "C" int stc_fp64_peak_probe(double* d_scratch, int64_t scratch_doubles, i
     *gflops = 2.0 * 8.0 * (double)iters * (double)blocks * 256.0 / (best * 1e-3) / 1e9;
     return STC_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Allocation-free factorization: the replay kernel's scratch (WorkHeader + per-tile
+// counters) comes from this fixed array instead of a caller workspace.  Host code
+// must not pass `g_noalloc_scratch` itself to a kernel (on the host that name is only
+// a stand-in for the device object); the device address is looked up once per device.
+// ---------------------------------------------------------------------------
+namespace stc {
+namespace {
+static __device__ __align__(256) unsigned char g_noalloc_scratch[STC_NOALLOC_SCRATCH_BYTES];
+
+struct NoallocSlot {
+    void* ptr = nullptr;
+    bool ready = false;
+};
+NoallocSlot g_noalloc[64];
+std::mutex g_noalloc_mu;
+
+int noalloc_scratch(int dev, void** out) {
+    std::lock_guard<std::mutex> g(g_noalloc_mu);
+    NoallocSlot& s = g_noalloc[dev];
+    if (!s.ready) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return STC_ERR_CUDA;
+        s.ptr = p;
+        s.ready = true;
+    }
+    *out = s.ptr;
+    return STC_OK;
+}
+}  // namespace
+}  // namespace stc
+
+extern "C" int stc_factorize_noalloc(const stc_plan* Pc, const double* d_values, int64_t batch, void* d_factor,
+                                     int32_t* d_info, int32_t* d_status, void* stream) {
+    stc_plan* P = const_cast<stc_plan*>(Pc);
+    if (!P || !d_values || !d_factor || !d_info || batch <= 0) return STC_ERR_INVALID_ARG;
+    const size_t need = factorize_ws(P, batch);
+    if (need > (size_t)STC_NOALLOC_SCRATCH_BYTES) return STC_ERR_UNSUPPORTED;
+    int dev, sms, rc;
+    if ((rc = device_info(&dev, &sms))) return rc;
+    // the plan and its one-slice task set must already be resident (uploading allocates)
+    TaskSet* ts = nullptr;
+    {
+        std::lock_guard<std::mutex> g(P->mu);
+        auto it = P->tasksets.find(1);
+        if (it != P->tasksets.end()) ts = it->second.get();
+        if (P->dev.device != dev || !ts || ts->device != dev) return STC_ERR_INVALID_ARG;
+    }
+    void* scratch = nullptr;
+    if ((rc = noalloc_scratch(dev, &scratch))) return rc;
+    cudaStream_t st = S(stream);
+    if ((rc = stc_scatter_values(P, d_values, batch, d_factor, stream))) return rc;
+    if (cudaMemsetAsync(scratch, 0, need, st) != cudaSuccess) return STC_ERR_CUDA;
+    if (cudaMemsetAsync(d_info, 0, (size_t)batch * sizeof(int32_t), st) != cudaSuccess) return STC_ERR_CUDA;
+    ReplayArgs a{};
+    a.tiles = ts->d_tiles; a.saind = P->dev.saind; a.tasks = ts->d_tasks; a.upds = ts->d_upds;
+    a.imap = ts->d_imap; a.factor = (double*)d_factor; a.fstride = P->factor_doubles;
+    a.poff = P->partial_off; a.hdr = (WorkHeader*)scratch;
+    a.counters = (int*)((char*)scratch + sizeof(WorkHeader));
+    a.ntiles = (int)P->tiles.size(); a.info = d_info; a.ntasks = (int)ts->tasks.size();
+    a.batch = batch; a.nb = (int)P->nb;
+    a.spin = P->opt.spin_limit > 0 ? P->opt.spin_limit : kDefaultSpin;
+    const long long total = (long long)a.ntasks * batch;
+    const int grid = (int)std::max<long long>(1, std::min<long long>(sms, total));
+    replay_kernel<<<grid, kThreads, kSmemBytes, st>>>(a);
+    if (cudaGetLastError() != cudaSuccess) return STC_ERR_CUDA;
+    if (d_status && cudaMemcpyAsync(d_status, &a.hdr->status, sizeof(int32_t), cudaMemcpyDeviceToDevice, st) !=
+                        cudaSuccess)
+        return STC_ERR_CUDA;
+    return STC_OK;
+}
