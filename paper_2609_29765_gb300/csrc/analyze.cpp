@@ -445,39 +445,92 @@ stc::TaskSet* stc_plan::taskset(int32_t slices) {
     const int NB = (int)nb;
     int h = (NB + slices - 1) / slices;
     h = (h + 7) / 8 * 8;
+    // tasks in Algorithm-1 (topological) order first, with the model inputs of each:
+    // the source tiles its updates wait for (in order) and the final dependency
+    struct Meta {
+        std::vector<int32_t> srcs;   // per update: tiles it waits for (1 or 2)
+        std::vector<double> ucost;   // per update FMAs
+        std::vector<int8_t> nsrc;
+        int32_t final_tile = -1;     // tile awaited before the final op (-1: none)
+        double fcost = 0;
+    };
     vector<stc::DTask> tasks;
-    vector<double> cost;
+    vector<Meta> meta;
     vector<vector<int32_t>> producers(tiles.size());
     ts->nfinal.assign(tiles.size(), 0);
     vector<int> ca, cb;
+    auto potrf_cost = [&](const stc::DTile& D) {
+        double w = D.sw, kd = std::min<double>(D.kd, w - 1);
+        return (D.kind == stc::TILE_DIAG_BAND) ? w * (kd + 1) * (kd + 1) / 2 : w * w * w / 6;
+    };
     for (int64_t k = 0; k < NT; ++k) {
         const int32_t dk = diag_tile[k];
         const stc::DTile& D = tiles[dk];
-        // DIAG(k): SYRK from every (k,n), n < k, then POTRF
-        stc::DTask t{};
-        t.kind = stc::TASK_DIAG; t.tile = dk; t.diag = dk;
-        t.ubeg = (int32_t)ts->upds.size();
-        double c = 0;
-        for (int32_t a = rowstart[k]; a < rowstart[k + 1]; ++a) {
-            const int32_t at = rowtiles[a];
-            const stc::DTile& A = tiles[at];
-            stc::DUpd u{};
-            u.a = at; u.b = at; u.kmap = -1; u.klen = A.sw; u.ka0 = 0; u.kb0 = 0;
-            u.ra0 = A.r0; u.ra1 = A.r1; u.oc0 = A.r0; u.oc1 = A.r1;
-            ts->upds.push_back(u);
-            double r = A.r1 - A.r0;
-            c += r * (r + 1) / 2 * A.sw;
+        const bool has_syrk = rowstart[k + 1] > rowstart[k];
+        if (slices == 1 || !has_syrk) {
+            // TASK_DIAG: every SYRK from (k,n), n < k, then POTRF
+            stc::DTask t{};
+            Meta mt;
+            t.kind = stc::TASK_DIAG; t.tile = dk; t.diag = dk;
+            t.ubeg = (int32_t)ts->upds.size();
+            for (int32_t a = rowstart[k]; a < rowstart[k + 1]; ++a) {
+                const int32_t at = rowtiles[a];
+                const stc::DTile& A = tiles[at];
+                stc::DUpd u{};
+                u.a = at; u.b = at; u.kmap = -1; u.klen = A.sw; u.ka0 = 0; u.kb0 = 0;
+                u.ra0 = A.r0; u.ra1 = A.r1; u.oc0 = A.r0; u.oc1 = A.r1;
+                ts->upds.push_back(u);
+                double r = A.r1 - A.r0;
+                mt.srcs.push_back(at); mt.nsrc.push_back(1); mt.ucost.push_back(r * (r + 1) / 2 * A.sw);
+            }
+            t.uend = (int32_t)ts->upds.size();
+            t.rs0 = 0; t.rs1 = NB; t.tr0 = 0; t.tr1 = NB;
+            mt.fcost = potrf_cost(D);
+            producers[dk].push_back((int32_t)tasks.size());
+            tasks.push_back(t);
+            meta.push_back(mt);
+            ts->nfinal[dk] = 1;
+        } else {
+            // TASK_SYRK row slices of (k,k), then TASK_POTRF
+            int nsl = 0;
+            for (int rs0 = 0; rs0 < D.sw; rs0 += h) {
+                const int rs1 = std::min(D.sw, rs0 + h);
+                stc::DTask t{};
+                Meta mt;
+                t.kind = stc::TASK_SYRK; t.tile = dk; t.diag = dk;
+                t.rs0 = rs0; t.rs1 = rs1; t.tr0 = rs0; t.tr1 = rs1;
+                t.ubeg = (int32_t)ts->upds.size();
+                for (int32_t a = rowstart[k]; a < rowstart[k + 1]; ++a) {
+                    const int32_t at = rowtiles[a];
+                    const stc::DTile& A = tiles[at];
+                    const int ra = std::max(rs0, A.r0), rb = std::min(rs1, A.r1);
+                    if (ra >= rb) continue;
+                    stc::DUpd u{};
+                    u.a = at; u.b = at; u.kmap = -1; u.klen = A.sw; u.ka0 = 0; u.kb0 = 0;
+                    u.ra0 = ra; u.ra1 = rb; u.oc0 = A.r0; u.oc1 = rb;
+                    ts->upds.push_back(u);
+                    const double rows = rb - ra, cols_rect = ra - A.r0;
+                    mt.srcs.push_back(at); mt.nsrc.push_back(1);
+                    mt.ucost.push_back((rows * cols_rect + rows * (rows + 1) / 2) * A.sw);
+                }
+                t.uend = (int32_t)ts->upds.size();
+                if (t.uend == t.ubeg) continue;  // rows untouched by any SYRK
+                producers[dk].push_back((int32_t)tasks.size());
+                tasks.push_back(t);
+                meta.push_back(mt);
+                ++nsl;
+            }
+            stc::DTask p{};
+            Meta mp;
+            p.kind = stc::TASK_POTRF; p.tile = dk; p.diag = dk; p.ubeg = p.uend = (int32_t)ts->upds.size();
+            p.rs0 = 0; p.rs1 = NB; p.tr0 = 0; p.tr1 = NB; p.own_wait = nsl;
+            mp.final_tile = nsl > 0 ? dk : -1;
+            mp.fcost = potrf_cost(D);
+            producers[dk].push_back((int32_t)tasks.size());
+            tasks.push_back(p);
+            meta.push_back(mp);
+            ts->nfinal[dk] = nsl + 1;
         }
-        t.uend = (int32_t)ts->upds.size();
-        t.rs0 = 0; t.rs1 = NB; t.tr0 = 0; t.tr1 = NB;
-        {
-            double w = D.sw, kd = std::min<double>(D.kd, w - 1);
-            c += (D.kind == stc::TILE_DIAG_BAND) ? w * (kd + 1) * (kd + 1) / 2 : w * w * w / 6;
-        }
-        producers[dk].push_back((int32_t)tasks.size());
-        tasks.push_back(t);
-        cost.push_back(c);
-        ts->nfinal[dk] = 1;
         // OFF(m,k) row slices: GEMM from every n in N(k) & N(m), n < k, then TRSM
         for (int32_t o = colstart[k]; o < colstart[k + 1]; ++o) {
             const stc::DTile& O = tiles[o];
@@ -488,22 +541,23 @@ stc::TaskSet* stc_plan::taskset(int32_t slices) {
                 const int tr0 = std::max(rs0, O.r0), tr1 = std::min(rs1, O.r1);
                 if (tr0 >= tr1) continue;
                 stc::DTask s{};
+                Meta ms;
                 s.kind = stc::TASK_OFF; s.tile = o; s.diag = dk;
                 s.rs0 = rs0; s.rs1 = rs1; s.tr0 = tr0; s.tr1 = tr1;
                 s.ubeg = (int32_t)ts->upds.size();
-                double cc = 0;
                 int32_t a = rowstart[k], b = rowstart[m];
                 while (a < rowstart[k + 1] && b < rowstart[m + 1]) {
-                    const int32_t kt = rowtiles[a], mt = rowtiles[b];
-                    const int32_t na = tiles[kt].J, nm = tiles[mt].J;
+                    const int32_t kt = rowtiles[a], mtile = rowtiles[b];
+                    const int32_t na = tiles[kt].J, nm = tiles[mtile].J;
                     if (na < nm) { ++a; continue; }
                     if (nm < na) { ++b; continue; }
                     ++a; ++b;
-                    const stc::DTile& A = tiles[mt];  // (m,n)
-                    const stc::DTile& B = tiles[kt];  // (k,n)
+                    const stc::DTile& A = tiles[mtile];  // (m,n)
+                    const stc::DTile& B = tiles[kt];     // (k,n)
                     stc::DUpd u{};
-                    u.a = mt; u.b = kt;
+                    u.a = mtile; u.b = kt;
                     u.ra0 = std::max(tr0, A.r0); u.ra1 = std::min(tr1, A.r1);
+                    size_t imap_mark = ts->imap.size();
                     if (A.c0 >= 0 && B.c0 >= 0) {
                         const int lo = std::max(A.c0, B.c0), hi = std::min(A.c0 + A.sw, B.c0 + B.sw);
                         u.kmap = -1; u.klen = std::max(0, hi - lo);
@@ -527,38 +581,67 @@ stc::TaskSet* stc_plan::taskset(int32_t slices) {
                     } else {
                         u.oc0 = 0; u.oc1 = O.sw;
                     }
-                    if (u.klen <= 0 || u.ra0 >= u.ra1 || u.oc0 >= u.oc1) continue;
+                    if (u.klen <= 0 || u.ra0 >= u.ra1 || u.oc0 >= u.oc1) {
+                        ts->imap.resize(imap_mark);
+                        continue;
+                    }
                     ts->upds.push_back(u);
-                    cc += double(u.ra1 - u.ra0) * (u.oc1 - u.oc0) * u.klen;
+                    ms.srcs.push_back(mtile); ms.srcs.push_back(kt); ms.nsrc.push_back(2);
+                    ms.ucost.push_back(double(u.ra1 - u.ra0) * (u.oc1 - u.oc0) * u.klen);
                 }
                 s.uend = (int32_t)ts->upds.size();
-                cc += double(tr1 - tr0) * O.sw * (O.sw + 1) / 2;
+                ms.final_tile = dk;
+                ms.fcost = double(tr1 - tr0) * O.sw * (O.sw + 1) / 2;
                 producers[o].push_back((int32_t)tasks.size());
                 tasks.push_back(s);
-                cost.push_back(cc);
+                meta.push_back(ms);
                 ts->nfinal[o]++;
             }
         }
     }
-    // ASAP (earliest-start on unbounded workers) order; ties keep Algorithm-1 order.
-    const double kSync = 4000.0;  // per-task overhead in FMA-equivalents
-    vector<double> es(tasks.size(), 0.0), fin(tasks.size(), 0.0);
-    for (size_t i = 0; i < tasks.size(); ++i) {
-        double s = 0;
-        auto dep_tile = [&](int32_t tile) {
-            for (int32_t p : producers[tile]) s = std::max(s, fin[p]);
-        };
-        const stc::DTask& t = tasks[i];
-        for (int32_t u = t.ubeg; u < t.uend; ++u) { dep_tile(ts->upds[u].a); dep_tile(ts->upds[u].b); }
-        if (t.kind == stc::TASK_OFF) dep_tile(t.diag);
-        es[i] = s;
-        fin[i] = s + cost[i] + kSync;
-        ts->fma += cost[i];
+    // Queue order: earliest start on unbounded workers, where a task starts when its
+    // first input is final and runs its updates in order, each after its own inputs;
+    // the key is raised to exceed every dependency's key, so the order stays
+    // topological (a waited-for task is always taken from the queue earlier).
+    const double kSync = 3000.0;  // per-task overhead, FMA-equivalents
+    const size_t T = tasks.size();
+    vector<double> key(T, 0.0), fin(T, 0.0), tile_fin(tiles.size(), 0.0), tile_key(tiles.size(), 0.0);
+    vector<int32_t> remaining(tiles.size(), 0);
+    for (size_t t = 0; t < tiles.size(); ++t) remaining[t] = (int32_t)producers[t].size();
+    for (size_t i = 0; i < T; ++i) {
+        const Meta& mt = meta[i];
+        double kdep = 0.0;
+        for (int32_t s : mt.srcs) kdep = std::max(kdep, tile_key[s]);
+        if (mt.final_tile >= 0) kdep = std::max(kdep, tile_key[mt.final_tile]);
+        double first;
+        if (!mt.srcs.empty()) {
+            first = tile_fin[mt.srcs[0]];
+            if (mt.nsrc[0] == 2) first = std::max(first, tile_fin[mt.srcs[1]]);
+        } else {
+            first = mt.final_tile >= 0 ? tile_fin[mt.final_tile] : 0.0;
+        }
+        double t = first;
+        size_t q = 0;
+        for (size_t u = 0; u < mt.ucost.size(); ++u) {
+            double ready = tile_fin[mt.srcs[q]];
+            if (mt.nsrc[u] == 2) ready = std::max(ready, tile_fin[mt.srcs[q + 1]]);
+            q += mt.nsrc[u];
+            t = std::max(t, ready) + mt.ucost[u];
+        }
+        if (mt.final_tile >= 0) t = std::max(t, tile_fin[mt.final_tile]);
+        t += mt.fcost + kSync;
+        fin[i] = t;
+        key[i] = std::max(first, kdep + 1e-6);
+        ts->fma += std::accumulate(mt.ucost.begin(), mt.ucost.end(), 0.0) + mt.fcost;
+        // the task's own tile: final when its last producer is done
+        const int32_t o = tasks[i].tile;
+        tile_fin[o] = std::max(tile_fin[o], fin[i]);
+        tile_key[o] = std::max(tile_key[o], key[i]);
     }
-    vector<int32_t> order(tasks.size());
+    vector<int32_t> order(T);
     std::iota(order.begin(), order.end(), 0);
-    std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return es[a] < es[b]; });
-    ts->tasks.reserve(tasks.size());
+    std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return key[a] < key[b]; });
+    ts->tasks.reserve(T);
     for (int32_t i : order) ts->tasks.push_back(tasks[i]);
     stc::TaskSet* raw = ts.get();
     tasksets[slices] = std::move(ts);

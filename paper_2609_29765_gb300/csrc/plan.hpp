@@ -35,19 +35,22 @@ struct DTile {
     int32_t pad;
 };
 
-enum : int32_t { TASK_DIAG = 0, TASK_OFF = 1 };
+enum : int32_t { TASK_DIAG = 0, TASK_OFF = 1, TASK_SYRK = 2, TASK_POTRF = 3 };
 
-// One device task.  TASK_DIAG = every SYRK into (k,k) then POTRF(k); TASK_OFF = every
-// GEMM into rows [rs0,rs1) of (m,k) then the TRSM of those rows against L_kk.  These are
-// the cases of Algorithm 1 grouped by output tile (row slice).
+// One device task, the cases of Algorithm 1 grouped by output tile (row slice):
+//   TASK_DIAG  every SYRK into (k,k), then POTRF(k)                 (unsliced)
+//   TASK_SYRK  every SYRK into rows [rs0,rs1) of (k,k)              (row slice)
+//   TASK_POTRF POTRF(k) once `own_wait` SYRK slices have finished
+//   TASK_OFF   every GEMM into rows [rs0,rs1) of (m,k), then the TRSM of those rows
 struct DTask {
     int32_t kind;
     int32_t tile;        // output tile
     int32_t diag;        // tile (k,k)
     int32_t ubeg, uend;  // range in the update array
-    int32_t rs0, rs1;    // row slice of the output tile (TASK_OFF); [0,n_b) for DIAG
+    int32_t rs0, rs1;    // row slice of the output tile
     int32_t tr0, tr1;    // rows of the slice the TRSM touches (slice cut to r-extent)
-    int32_t pad[3];
+    int32_t own_wait;    // TASK_POTRF: completions of (k,k) to wait for
+    int32_t pad[2];
 };
 
 // One SYRK (a == b) or GEMM source of a task: out -= A(rows, inner) * B(cols, inner)^T.

@@ -90,16 +90,16 @@ __device__ __forceinline__ int logical_col(const DTile& t, const int16_t* saind,
 
 // ---------------------------------------------------------------------------
 // C(r,c) -= sum_k A(r,k) B(c,k), r < R, c < Cn; A(r,k) = A[r + k*lda],
-// B(c,k) = B[c + k*ldb], C(r,c) = C[r + c*ldc].  4x4 register micro-tiles, the
+// B(c,k) = B[c + k*ldb], C(r,c) = C[r + c*ldc].  TR x TC register micro-tiles, the
 // micro-tiles of the region spread over the CTA.  LOWER: only micro-tiles touching
 // r >= c (rows and columns index the same range) are computed, and only r >= c is
 // written.  A/B rows up to the next multiple of 4 must be readable (pad).
 // ---------------------------------------------------------------------------
-template <bool LOWER>
-__device__ void mma_sub(double* __restrict__ C, int ldc, int R, int Cn,
-                        const double* __restrict__ A, int lda,
-                        const double* __restrict__ B, int ldb, int K) {
-    const int MR = (R + 3) >> 2, MC = (Cn + 3) >> 2;
+template <bool LOWER, int TR, int TC>
+__device__ void mma_tiles(double* __restrict__ C, int ldc, int R, int Cn,
+                          const double* __restrict__ A, int lda,
+                          const double* __restrict__ B, int ldb, int K) {
+    const int MR = (R + TR - 1) / TR, MC = (Cn + TC - 1) / TC;
     const int count = LOWER ? MR * (MR + 1) / 2 : MR * MC;
     for (int mt = threadIdx.x; mt < count; mt += kThreads) {
         int ri, cj;
@@ -114,62 +114,99 @@ __device__ void mma_sub(double* __restrict__ C, int ldc, int R, int Cn,
             ri = mt % MR;
             cj = mt / MR;
         }
-        const int r0 = ri * 4, c0 = cj * 4;
-        double acc[4][4];
+        const int r0 = ri * TR, c0 = cj * TC;
+        double acc[TR][TC];
 #pragma unroll
-        for (int i = 0; i < 4; ++i)
+        for (int i = 0; i < TR; ++i)
 #pragma unroll
-            for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+            for (int j = 0; j < TC; ++j) acc[i][j] = 0.0;
         const double* a = A + r0;
         const double* b = B + c0;
 #pragma unroll 4
         for (int k = 0; k < K; ++k) {
-            double av[4], bv[4];
+            double av[TR], bv[TC];
 #pragma unroll
-            for (int i = 0; i < 4; ++i) av[i] = a[i];
+            for (int i = 0; i < TR; ++i) av[i] = a[i];
 #pragma unroll
-            for (int j = 0; j < 4; ++j) bv[j] = b[j];
+            for (int j = 0; j < TC; ++j) bv[j] = b[j];
 #pragma unroll
-            for (int i = 0; i < 4; ++i)
+            for (int i = 0; i < TR; ++i)
 #pragma unroll
-                for (int j = 0; j < 4; ++j) acc[i][j] = fma(av[i], bv[j], acc[i][j]);
+                for (int j = 0; j < TC; ++j) acc[i][j] = fma(av[i], bv[j], acc[i][j]);
             a += lda;
             b += ldb;
         }
 #pragma unroll
-        for (int i = 0; i < 4; ++i)
+        for (int i = 0; i < TR; ++i)
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
+            for (int j = 0; j < TC; ++j) {
                 const int r = r0 + i, c = c0 + j;
                 if (r < R && c < Cn && (!LOWER || r >= c)) C[r + c * ldc] -= acc[i][j];
             }
     }
 }
 
-// Row-parallel forward substitution: X(r, 0:pw) <- X(r, 0:pw) * D^{-T}, D lower pw x pw
-// in shared memory (D(i,j) = D[i + j*ldd]) with reciprocal diagonal dinv[].
-__device__ void trsm_rows(double* X, int ldx, int R, int pw, const double* D, int ldd,
-                          const double* dinv) {
-    for (int r = threadIdx.x; r < R; r += kThreads) {
-        double x[kPb];
+// 4x4 micro-tiles when they keep at least 3/4 of the CTA busy, else 2x2 (four times as
+// many micro-tiles, so narrow row slices still occupy every warp).
+template <bool LOWER>
+__device__ __forceinline__ void mma_sub(double* C, int ldc, int R, int Cn, const double* A, int lda,
+                                        const double* B, int ldb, int K) {
+    const int m4 = (R + 3) >> 2, n4 = (Cn + 3) >> 2;
+    const int c44 = LOWER ? m4 * (m4 + 1) / 2 : m4 * n4;
+    if (c44 >= (kThreads * 3) / 4)
+        mma_tiles<LOWER, 4, 4>(C, ldc, R, Cn, A, lda, B, ldb, K);
+    else
+        mma_tiles<LOWER, 2, 2>(C, ldc, R, Cn, A, lda, B, ldb, K);
+}
+
+// Forward substitution of a row block against a panel: X(r, 0:pw) <- X(r, 0:pw) D^{-T},
+// D lower pw x pw in shared memory (D(i,j) = D[i + j*ldd]), reciprocal diagonal dinv[].
+// TPR threads share a row: each keeps the columns j = q (mod TPR) in registers, the
+// owner of column j finishes x_j and broadcasts it by shuffle, and every thread then
+// removes x_j's contribution from its later columns (right-looking).
+template <int TPR>
+__device__ void trsm_rows_t(double* X, int ldx, int R, int pw, const double* D, int ldd,
+                            const double* dinv) {
+    constexpr int NJ = kPb / TPR;
+    const int q = threadIdx.x % TPR;
+    const int lane = threadIdx.x & 31;
+    const int base = lane - q;
+    for (int rr = threadIdx.x / TPR; rr < ((R + (kThreads / TPR) - 1) / (kThreads / TPR)) * (kThreads / TPR);
+         rr += kThreads / TPR) {
+        const bool live = rr < R;
+        double b[NJ];
 #pragma unroll
-        for (int j = 0; j < kPb; ++j) x[j] = j < pw ? X[r + j * ldx] : 0.0;
+        for (int s = 0; s < NJ; ++s) {
+            const int k = s * TPR + q;
+            b[s] = (live && k < pw) ? X[rr + k * ldx] : 0.0;
+        }
 #pragma unroll
         for (int j = 0; j < kPb; ++j) {
             if (j < pw) {
-                double s0 = x[j], s1 = 0.0;
+                const double xj = __shfl_sync(0xffffffffu, b[j / TPR] * dinv[j], base + (j % TPR));
+                if (q == j % TPR) b[j / TPR] = xj;
 #pragma unroll
-                for (int i = 0; i < j; i += 2) {
-                    s0 = fma(-x[i], D[j + i * ldd], s0);
-                    if (i + 1 < j) s1 = fma(-x[i + 1], D[j + (i + 1) * ldd], s1);
+                for (int s = 0; s < NJ; ++s) {
+                    const int k = s * TPR + q;
+                    if (k > j && k < pw) b[s] = fma(-xj, D[k + j * ldd], b[s]);
                 }
-                x[j] = (s0 + s1) * dinv[j];
             }
         }
+        if (live) {
 #pragma unroll
-        for (int j = 0; j < kPb; ++j)
-            if (j < pw) X[r + j * ldx] = x[j];
+            for (int s = 0; s < NJ; ++s) {
+                const int k = s * TPR + q;
+                if (k < pw) X[rr + k * ldx] = b[s];
+            }
+        }
     }
+}
+
+__device__ __forceinline__ void trsm_rows(double* X, int ldx, int R, int pw, const double* D, int ldd,
+                                          const double* dinv) {
+    if (R <= kThreads / 8) trsm_rows_t<8>(X, ldx, R, pw, D, ldd, dinv);
+    else if (R <= kThreads / 4) trsm_rows_t<4>(X, ldx, R, pw, D, ldd, dinv);
+    else trsm_rows_t<2>(X, ldx, R, pw, D, ldd, dinv);
 }
 
 struct ReplayArgs {
@@ -232,7 +269,7 @@ __device__ void store_diag(const double* C, double* T, const DTile& d, int nb) {
 // up to a multiple of 4 are zeroed.
 __device__ void stage_cols(double* S, int ld, const double* T, int nb, int row0, int R,
                            const DUpd& u, const int16_t* imap, bool use_b, int k0, int K) {
-    const int Rp = (R + 3) & ~3;
+    const int Rp = ((R + 3) & ~3) + 4;
     for (int idx = threadIdx.x; idx < Rp * K; idx += kThreads) {
         const int r = idx % Rp, k = idx / Rp;
         double v = 0.0;
@@ -263,56 +300,100 @@ __device__ void stage_rows_gather(double* S, int ld, const double* T, int nb, co
     }
 }
 
-// Blocked right-looking Cholesky of the w x w leading block of C (lower), panel kPb;
-// rows farther than kd below the diagonal are structurally zero and skipped.  *bad
-// receives the first non-positive pivot (or -1); *logsum = sum_j log L_jj, accumulated
-// as a mantissa product and an exponent sum (one log per tile).
+// Blocked right-looking Cholesky of the w x w leading block of C (lower) in shared
+// memory, panel width kPp = 8.  Per panel: warp 0 factors the 8x8 diagonal block in
+// registers (one row per lane, pivots broadcast by shuffle); the rows below the block
+// are solved against it, one row per thread; the rank-8 update of the trailing lower
+// triangle runs on every warp.  Rows more than kd below the diagonal are structurally
+// zero and skipped.  *bad receives the first non-positive pivot column (or -1);
+// *logsum = sum_j log L_jj, kept as a mantissa product and an exponent sum.
+constexpr int kPp = 8;
+
 __device__ void potrf_smem(double* C, int w, int kd, double* sbuf, int* bad, double* logsum) {
+    __shared__ double s_blk[kPp][kPp];  // L of the panel's diagonal block, s_blk[row][col]
+    __shared__ double s_inv[kPp];       // 1 / L_jj of the panel
     __shared__ double s_mant;
     __shared__ int s_exp, s_bad;
+    (void)sbuf;
     if (threadIdx.x == 0) { s_mant = 1.0; s_exp = 0; s_bad = -1; }
     __syncthreads();
-    for (int p = 0; p < w; p += kPb) {
-        const int pw = min(kPb, w - p);
-        const int rend = min(w, p + pw + kd);  // rows below the panel inside the band
-        // (1) unblocked factor of the pw x pw diagonal block by warp 0
-        if (threadIdx.x < 32) {
-            const int lane = threadIdx.x;
+    const int tid = threadIdx.x;
+    for (int p = 0; p < w; p += kPp) {
+        const int pw = min(kPp, w - p);
+        const int rend = min(w, p + pw + kd);  // panel rows inside the band: [p, rend)
+        // (1) warp 0: unblocked Cholesky of the pw x pw diagonal block
+        if (tid < 32) {
+            const int lane = tid;
+            double x[kPp];
+#pragma unroll
+            for (int l = 0; l < kPp; ++l) x[l] = (lane < pw && l <= lane) ? C[p + lane + (p + l) * kLdc] : 0.0;
             double mant = s_mant;
-            int ex = s_exp;
-            for (int j = 0; j < pw; ++j) {
-                const int cj = p + j;
-                double inv = 0.0;
-                if (lane == 0) {
-                    const double d = C[cj + cj * kLdc];
-                    if (!(d > 0.0) && s_bad < 0) s_bad = cj;
-                    const double ljj = sqrt(d);
-                    inv = 1.0 / ljj;
-                    C[cj + cj * kLdc] = ljj;
+            int ex = s_exp, badl = -1;
+#pragma unroll
+            for (int j = 0; j < kPp; ++j) {
+                if (j < pw) {
+                    double inv = 0.0;
+                    if (lane == j) {
+                        const double d = x[j];
+                        if (!(d > 0.0)) badl = p + j;
+                        inv = rsqrt(d);
+                        x[j] = d * inv;
+                    }
+                    inv = __shfl_sync(0xffffffffu, inv, j);
+                    if (lane > j) x[j] *= inv;
+#pragma unroll
+                    for (int l = j + 1; l < kPp; ++l) {
+                        const double llj = __shfl_sync(0xffffffffu, x[j], l);  // L[p+l][p+j]
+                        if (l < pw && lane >= l) x[l] = fma(-x[j], llj, x[l]);
+                    }
+                    if (lane == j) s_inv[j] = inv;
+                }
+            }
+            if (lane < pw) {
+#pragma unroll
+                for (int l = 0; l < kPp; ++l) s_blk[lane][l] = l <= lane ? x[l] : 0.0;
+#pragma unroll
+                for (int l = 0; l < kPp; ++l)
+                    if (l <= lane) C[p + lane + (p + l) * kLdc] = x[l];
+            }
+            // bad pivot (first one) and the logdet state live in lanes 0..pw-1
+#pragma unroll
+            for (int j = 0; j < kPp; ++j) {
+                const int bj = __shfl_sync(0xffffffffu, badl, j);
+                if (lane == 0 && j < pw && bj >= 0 && s_bad < 0) s_bad = bj;
+            }
+#pragma unroll
+            for (int j = 0; j < kPp; ++j) {
+                const double ljj = __shfl_sync(0xffffffffu, x[j], j);
+                if (lane == 0 && j < pw) {
                     int e;
                     mant = frexp(mant * ljj, &e);
                     ex += e;
                 }
-                inv = __shfl_sync(0xffffffffu, inv, 0);
-                const int i = lane;
-                if (i > j && i < pw) C[p + i + cj * kLdc] *= inv;
-                __syncwarp();
-                if (i > j && i < pw) {
-                    const double lij = C[p + i + cj * kLdc];
-                    for (int l = j + 1; l <= i; ++l)
-                        C[p + i + (p + l) * kLdc] = fma(-lij, C[p + l + cj * kLdc], C[p + i + (p + l) * kLdc]);
-                }
-                __syncwarp();
             }
             if (lane == 0) { s_mant = mant; s_exp = ex; }
-            if (lane < pw) sbuf[lane] = 1.0 / C[p + lane + (p + lane) * kLdc];
         }
         __syncthreads();
-        // (2) rows below the panel: X <- X * D^{-T}
-        if (rend > p + pw)
-            trsm_rows(C + (p + pw) + p * kLdc, kLdc, rend - p - pw, pw, C + p + p * kLdc, kLdc, sbuf);
+        // (2) rows below the block: x <- x * L_pp^{-T}, one row per thread
+        for (int i = p + pw + tid; i < rend; i += kThreads) {
+            double x[kPp];
+#pragma unroll
+            for (int l = 0; l < kPp; ++l) x[l] = l < pw ? C[i + (p + l) * kLdc] : 0.0;
+#pragma unroll
+            for (int j = 0; j < kPp; ++j) {
+                if (j < pw) {
+                    double sacc = x[j];
+#pragma unroll
+                    for (int l = 0; l < j; ++l) sacc = fma(-x[l], s_blk[j][l], sacc);
+                    x[j] = sacc * s_inv[j];
+                }
+            }
+#pragma unroll
+            for (int l = 0; l < kPp; ++l)
+                if (l < pw) C[i + (p + l) * kLdc] = x[l];
+        }
         __syncthreads();
-        // (3) trailing update of the band below/right of the panel
+        // (3) rank-pw update of the trailing lower triangle inside the band
         if (rend > p + pw)
             mma_sub<true>(C + (p + pw) + (p + pw) * kLdc, kLdc, rend - p - pw, rend - p - pw,
                           C + (p + pw) + p * kLdc, kLdc, C + (p + pw) + p * kLdc, kLdc, pw);
@@ -378,6 +459,61 @@ __global__ void __launch_bounds__(kThreads, 1) replay_kernel(ReplayArgs a) {
                     store_diag(C, F + O.off, O, nb);
                 }
             }
+        } else if (t.kind == TASK_SYRK) {
+            // rows [rs0, rs1) of (k,k): every SYRK update, lower part only
+            const int R = t.rs1 - t.rs0;
+            if (s_ok) {
+                const double* T = F + O.off;
+                for (int idx = threadIdx.x; idx < R * t.rs1; idx += kThreads) {
+                    const int r = idx % R, c = idx / R, gr = t.rs0 + r;
+                    C[r + c * kLdc] = c <= gr ? diag_at(T, O, nb, gr, c) : 0.0;
+                }
+                __syncthreads();
+                for (int ui = t.ubeg; ui < t.uend; ++ui) {
+                    const DUpd u = a.upds[ui];
+                    const DTile A = a.tiles[u.a];
+                    if (threadIdx.x == 0) s_ok = wait_counter(cnt + u.a, A.nfinal, a.spin, &a.hdr->status);
+                    __syncthreads();
+                    if (!s_ok) break;
+                    const int r0 = u.oc0, d0 = u.ra0, rb = u.ra1, Rs = rb - r0;
+                    for (int k0 = 0; k0 < u.klen; k0 += kKc) {
+                        const int K = min(kKc, u.klen - k0);
+                        stage_cols(S0, kNbMax + 8, F + A.off, nb, r0, Rs, u, a.imap, false, k0, K);
+                        __syncthreads();
+                        if (d0 > r0)
+                            mma_sub<false>(C + (d0 - t.rs0) + r0 * kLdc, kLdc, rb - d0, d0 - r0,
+                                           S0 + (d0 - r0), kNbMax + 8, S0, kNbMax + 8, K);
+                        mma_sub<true>(C + (d0 - t.rs0) + d0 * kLdc, kLdc, rb - d0, rb - d0,
+                                      S0 + (d0 - r0), kNbMax + 8, S0 + (d0 - r0), kNbMax + 8, K);
+                        __syncthreads();
+                    }
+                }
+                if (s_ok) {
+                    double* Tw = F + O.off;
+                    for (int idx = threadIdx.x; idx < R * t.rs1; idx += kThreads) {
+                        const int r = idx % R, c = idx / R, gr = t.rs0 + r;
+                        if (c > gr) continue;
+                        if (O.kind == TILE_DIAG_DENSE) __stcg(Tw + gr + (size_t)c * nb, C[r + c * kLdc]);
+                        else if (gr - c <= O.kd) __stcg(Tw + (O.kd + c - gr) + (size_t)gr * (O.kd + 1), C[r + c * kLdc]);
+                    }
+                }
+            }
+        } else if (t.kind == TASK_POTRF) {
+            if (s_ok && t.own_wait > 0) {
+                if (threadIdx.x == 0) s_ok = wait_counter(cnt + t.tile, t.own_wait, a.spin, &a.hdr->status);
+                __syncthreads();
+            }
+            if (s_ok) {
+                load_diag(C, F + O.off, O, nb);
+                __syncthreads();
+                int bad; double ls;
+                potrf_smem(C, O.sw, min(O.kd, nb - 1), sv, &bad, &ls);
+                if (threadIdx.x == 0) {
+                    if (bad >= 0) record_info(a.info + item, O.J * nb + bad + 1);
+                    F[a.poff + O.pd_slot] = bad >= 0 ? __longlong_as_double(0x7ff8000000000000LL) : ls;
+                }
+                store_diag(C, F + O.off, O, nb);
+            }
         } else {
             const int R = t.rs1 - t.rs0;
             const int sw = O.sw;
@@ -406,7 +542,7 @@ __global__ void __launch_bounds__(kThreads, 1) replay_kernel(ReplayArgs a) {
                 }
                 // TRSM of rows [tr0, tr1) against L_kk restricted to the stored columns
                 const DTile D = a.tiles[t.diag];
-                if (s_ok && threadIdx.x == 0) s_ok = wait_counter(cnt + t.diag, 1, a.spin, &a.hdr->status);
+                if (s_ok && threadIdx.x == 0) s_ok = wait_counter(cnt + t.diag, D.nfinal, a.spin, &a.hdr->status);
                 __syncthreads();
                 if (s_ok) {
                     const double* DT = F + D.off;
@@ -777,12 +913,18 @@ size_t solve_ws(const stc_plan* P, int64_t chains) {
 
 int32_t pick_slices(const stc_plan* P, int64_t batch, int sms) {
     if (P->opt.row_slices > 0) return P->opt.row_slices;
-    // enough independent row slices to cover the GPU when the batch alone does not
+    // Split heavy tiles so the chain POTRF -> TRSM -> SYRK of consecutive block columns
+    // is spread over several SMs (the per-SM FP64 rate is low), but no further than the
+    // batch needs: thinner slices cost efficiency inside each task.
+    if (P->nb < 48) return 1;
     const int64_t per_item = std::max<int64_t>(1, (int64_t)P->tiles.size() / std::max<int64_t>(1, P->nt));
-    const int64_t width = batch * per_item;
-    if (width >= 4 * sms) return 1;
-    if (width >= sms) return 2;
-    return 4;
+    const int64_t width = batch * per_item;  // independent tiles per block-column step
+    int s;
+    if (width >= sms) s = 2;
+    else if (width >= sms / 4) s = 4;
+    else s = 8;
+    if (P->nb < 96) s = std::max(1, s / 2);
+    return s;
 }
 
 inline cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s); }
