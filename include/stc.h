@@ -85,6 +85,10 @@ typedef struct stc_options {
     double gate_phi_fill;    /* 0 = default 2.0  */
     double gate_rho_semi;    /* 0 = default 0.15 */
     double gate_sigma_skew;  /* 0 = default 20   */
+    double queue_skew;       /* batched factorize: 0 (default) queues the items in
+                                lockstep (slot = task * batch + item); > 0 queues item b's
+                                tasks as if it started b/batch x queue_skew block-column
+                                periods late (a merged order built once per batch size)  */
 } stc_options;
 
 typedef struct stc_plan stc_plan;
@@ -189,6 +193,38 @@ int stc_solve(const stc_plan* plan, const void* d_factor, int64_t batch, int64_t
  * d_Lx [batch][nnzL] FP64. */
 int stc_factor_to_csc(const stc_plan* plan, const void* d_factor, int64_t batch,
                       double* d_Lx, void* stream);
+
+/* Selected inverse Sigma = (P A P^T)^{-1} on every stored entry of the tile storage
+ * (no counterpart in the paper, which leaves selected inversion to separate work,
+ * Sec. 6.3: Takahashi's recurrence on the same tile map, walked in reverse block-column
+ * order by one persistent kernel).  Sigma is exact on the structural entries of L;
+ * stored entries the symbolic factor proves zero hold unspecified finite values.
+ *   d_factor: a factor from stc_factorize; d_sigma: stc_factor_bytes(plan,batch) bytes
+ *   (written, same layout as the factor, must not alias it); d_work:
+ *   stc_workspace_bytes(plan,batch) bytes. */
+int stc_selinv(const stc_plan* plan, const void* d_factor, int64_t batch, void* d_sigma,
+               void* d_work, void* stream);
+
+/* Adjoint of logdet: d_gvalues[b][e] (+)= gout[b] * d logdet(A_b) / d a_e for every stored
+ * lower entry e of A (original CSC order), i.e. (2 - delta_ij) (A^{-1})_ij, A symmetric
+ * parametrised by its lower triangle.  d_gout [batch] or NULL (= 1); accumulate != 0 adds
+ * to d_gvalues.  Runs stc_selinv into d_sigma (scratch, stc_factor_bytes) first. */
+int stc_logdet_backward(const stc_plan* plan, const void* d_factor, int64_t batch,
+                        const double* d_gout, double* d_gvalues, int accumulate, void* d_sigma,
+                        void* d_work, void* stream);
+
+/* Symmetric outer-product adjoint, for quadratic forms and solves:
+ *   d_gvalues[b][e] (+)= scale[b] * (2 - delta_ij)/2 * (u_i v_j + u_j v_i),  e = (i, j)
+ * with u, v [batch][n] in the original ordering; scale [batch] or NULL (= 1).
+ * u = v = x gives d(x^T A x)/d a_e; u = A^{-1} b, v = A^{-1} g, scale = -1 gives the
+ * adjoint of the solve x = A^{-1} b for an upstream gradient g on x. */
+int stc_sym_outer_backward(const stc_plan* plan, int64_t batch, const double* d_u,
+                           const double* d_v, const double* d_scale, double* d_gvalues,
+                           int accumulate, void* stream);
+
+/* out[b] = x_b^T A_b x_b from the lower CSC values (d_values [batch][nnzA], d_x [batch][n]). */
+int stc_quad_form(const stc_plan* plan, int64_t batch, const double* d_values,
+                  const double* d_x, double* d_out, void* stream);
 
 /* FP64 throughput probe (no counterpart in the paper): runs independent DFMA chains on
  * every SM for `iters` iterations, synchronously on the legacy stream, and writes the

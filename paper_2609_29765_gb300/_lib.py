@@ -37,6 +37,7 @@ EXPORTED = [
     "stc_plan_destroy", "stc_factor_bytes", "stc_workspace_bytes", "stc_factorize", "stc_scatter_values",
     "stc_factorize_scattered", "stc_sync_status",
     "stc_logdet", "stc_solve", "stc_factor_to_csc", "stc_fp64_peak_probe", "stc_factorize_noalloc",
+    "stc_selinv", "stc_logdet_backward", "stc_sym_outer_backward", "stc_quad_form",
 ]
 STC_NOALLOC_SCRATCH_BYTES = 4 << 20
 
@@ -52,7 +53,7 @@ class stc_options(C.Structure):
                 ("nd_leaf", C.c_int32), ("perm", C.POINTER(C.c_int64)), ("row_slices", C.c_int32),
                 ("reserved0", C.c_int32), ("spin_limit", C.c_int64), ("gate_rho_dense", C.c_double),
                 ("gate_phi_fill", C.c_double), ("gate_rho_semi", C.c_double),
-                ("gate_sigma_skew", C.c_double)]
+                ("gate_sigma_skew", C.c_double), ("queue_skew", C.c_double)]
 
 
 class stc_plan_info(C.Structure):
@@ -110,6 +111,14 @@ def lib():
         L.stc_solve.restype = C.c_int
         L.stc_factor_to_csc.argtypes = [_vp, _vp, C.c_int64, _vp, _vp]
         L.stc_factor_to_csc.restype = C.c_int
+        L.stc_selinv.argtypes = [_vp, _vp, C.c_int64, _vp, _vp, _vp]
+        L.stc_selinv.restype = C.c_int
+        L.stc_logdet_backward.argtypes = [_vp, _vp, C.c_int64, _vp, _vp, C.c_int, _vp, _vp, _vp]
+        L.stc_logdet_backward.restype = C.c_int
+        L.stc_sym_outer_backward.argtypes = [_vp, C.c_int64, _vp, _vp, _vp, _vp, C.c_int, _vp]
+        L.stc_sym_outer_backward.restype = C.c_int
+        L.stc_quad_form.argtypes = [_vp, C.c_int64, _vp, _vp, _vp, _vp]
+        L.stc_quad_form.restype = C.c_int
         L.stc_factorize_noalloc.argtypes = [_vp, _vp, C.c_int64, _vp, _vp, _vp, _vp]
         L.stc_factorize_noalloc.restype = C.c_int
         L.stc_fp64_peak_probe.argtypes = [_vp, C.c_int64, C.c_int64, C.POINTER(C.c_double)]
@@ -236,3 +245,23 @@ def stc_fp64_peak_probe(d_scratch, iters=4096):
 def stc_factorize_noalloc(plan, d_values, batch, d_factor, d_info, d_status=None, stream=None):
     return lib().stc_factorize_noalloc(plan, _dev_ptr(d_values), int(batch), _dev_ptr(d_factor),
                                        _dev_ptr(d_info), _dev_ptr(d_status), _stream(stream))
+
+
+def stc_selinv(plan, d_factor, batch, d_sigma, d_work, stream=None):
+    return lib().stc_selinv(plan, _dev_ptr(d_factor), int(batch), _dev_ptr(d_sigma), _dev_ptr(d_work),
+                            _stream(stream))
+
+
+def stc_logdet_backward(plan, d_factor, batch, d_gout, d_gvalues, accumulate, d_sigma, d_work, stream=None):
+    return lib().stc_logdet_backward(plan, _dev_ptr(d_factor), int(batch), _dev_ptr(d_gout), _dev_ptr(d_gvalues),
+                                     int(accumulate), _dev_ptr(d_sigma), _dev_ptr(d_work), _stream(stream))
+
+
+def stc_sym_outer_backward(plan, batch, d_u, d_v, d_scale, d_gvalues, accumulate, stream=None):
+    return lib().stc_sym_outer_backward(plan, int(batch), _dev_ptr(d_u), _dev_ptr(d_v), _dev_ptr(d_scale),
+                                        _dev_ptr(d_gvalues), int(accumulate), _stream(stream))
+
+
+def stc_quad_form(plan, batch, d_values, d_x, d_out, stream=None):
+    return lib().stc_quad_form(plan, int(batch), _dev_ptr(d_values), _dev_ptr(d_x), _dev_ptr(d_out),
+                               _stream(stream))

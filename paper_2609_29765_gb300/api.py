@@ -30,7 +30,7 @@ class Plan:
     """Symbolic plan of one sparsity pattern (lower CSC, original order)."""
 
     def __init__(self, n, colptr, rowind, coords=None, nb=128, route="auto", ordering="auto",
-                 perm=None, nd_leaf=64, row_slices=0, spin_limit=0):
+                 perm=None, nd_leaf=64, row_slices=0, spin_limit=0, queue_skew=0.0):
         o = L.stc_options_default()
         o.nb = int(nb)
         o.force_route = ROUTES[route]
@@ -38,6 +38,7 @@ class Plan:
         o.nd_leaf = int(nd_leaf)
         o.row_slices = int(row_slices)
         o.spin_limit = int(spin_limit)
+        o.queue_skew = float(queue_skew)
         self._perm_keep = None
         if perm is not None:
             self._perm_keep = np.ascontiguousarray(perm, dtype=np.int64)
@@ -146,9 +147,122 @@ class Factor:
         L.check(L.stc_solve(self.plan.h, self.data, self.batch, nrhs, b, x, ws), "stc_solve")
         return x.squeeze(1) if squeeze else x
 
+    def selinv(self, out=None):
+        """Selected inverse in tile storage (same layout as the factor)."""
+        torch = _torch()
+        sig = torch.empty_like(self.data) if out is None else out
+        ws = self.plan.workspace(self.batch, self.data.device)
+        L.check(L.stc_selinv(self.plan.h, self.data, self.batch, sig, ws), "stc_selinv")
+        return Factor(self.plan, sig, self.info, self.batch)
+
+    def logdet_backward(self, gout=None, out=None, accumulate=False):
+        """(2 - delta_ij) (A^{-1})_ij * gout for every stored A entry: [batch, nnzA]."""
+        torch = _torch()
+        g = torch.empty(self.batch, self.plan.nnzA, dtype=torch.float64, device=self.data.device) \
+            if out is None else out
+        sig = torch.empty_like(self.data)
+        ws = self.plan.workspace(self.batch, self.data.device)
+        if gout is not None:
+            gout = gout.to(dtype=torch.float64).contiguous()
+        L.check(L.stc_logdet_backward(self.plan.h, self.data, self.batch, gout, g, int(accumulate), sig, ws),
+                "stc_logdet_backward")
+        return g
+
     def to_csc(self):
         """L's values in the CSC order of plan.export('Lp'/'Li'): [batch, nnzL]."""
         torch = _torch()
         out = torch.empty(self.batch, self.plan.nnzL, dtype=torch.float64, device=self.data.device)
         L.check(L.stc_factor_to_csc(self.plan.h, self.data, self.batch, out), "stc_factor_to_csc")
         return out
+
+
+# ---------------------------------------------------------------------------
+# Differentiation: torch.autograd.Function wrappers.  The forward and backward
+# arithmetic runs in libstc.so; torch only carries the tensors and the chain rule of
+# whatever produced the values (e.g. Q(theta)).
+# ---------------------------------------------------------------------------
+def _autograd():
+    torch = _torch()
+
+    class LogdetFn(torch.autograd.Function):
+        """logdet(A_b) for values [batch, nnzA]; backward = selected inverse."""
+
+        @staticmethod
+        def forward(ctx, values, plan):
+            fac = plan.factorize(values.detach())
+            ctx.plan, ctx.fac = plan, fac
+            return fac.logdet()
+
+        @staticmethod
+        def backward(ctx, gout):
+            g = ctx.fac.logdet_backward(gout.contiguous())
+            return g, None
+
+    class QuadFn(torch.autograd.Function):
+        """x_b^T A_b x_b; gradients for the values and for x."""
+
+        @staticmethod
+        def forward(ctx, values, x, plan):
+            values = values.detach().contiguous()
+            x = x.detach().contiguous()
+            out = torch.empty(values.shape[0], dtype=torch.float64, device=values.device)
+            L.check(L.stc_quad_form(plan.h, values.shape[0], values, x, out), "stc_quad_form")
+            ctx.save_for_backward(values, x)
+            ctx.plan = plan
+            return out
+
+        @staticmethod
+        def backward(ctx, gout):
+            values, x = ctx.saved_tensors
+            plan = ctx.plan
+            batch = values.shape[0]
+            gv = gx = None
+            if ctx.needs_input_grad[0]:
+                gv = torch.empty_like(values)
+                L.check(L.stc_sym_outer_backward(plan.h, batch, x, x, gout.contiguous(), gv, 0),
+                        "stc_sym_outer_backward")
+            if ctx.needs_input_grad[1]:
+                raise RuntimeError("quad_form: the gradient with respect to x is not provided "
+                                   "(treat x as a constant, or use solve for x-dependent terms)")
+            return gv, gx, None
+
+    class SolveFn(torch.autograd.Function):
+        """x = A_b^{-1} b_b; backward: g_b = A^{-1} g_x, g_A = -(2-delta)/2 (x_i g_j + x_j g_i)."""
+
+        @staticmethod
+        def forward(ctx, values, b, plan):
+            fac = plan.factorize(values.detach())
+            x = fac.solve(b.detach().contiguous())
+            ctx.plan, ctx.fac = plan, fac
+            ctx.save_for_backward(x)
+            return x
+
+        @staticmethod
+        def backward(ctx, gx):
+            (x,) = ctx.saved_tensors
+            g = ctx.fac.solve(gx.contiguous())
+            gv = None
+            if ctx.needs_input_grad[0]:
+                batch = x.shape[0]
+                gv = torch.empty(batch, ctx.plan.nnzA, dtype=torch.float64, device=x.device)
+                scale = torch.full((batch,), -1.0, dtype=torch.float64, device=x.device)
+                L.check(L.stc_sym_outer_backward(ctx.plan.h, batch, x.contiguous(), g.contiguous(), scale, gv, 0),
+                        "stc_sym_outer_backward")
+            return gv, g, None
+
+    return LogdetFn, QuadFn, SolveFn
+
+
+def logdet(values, plan):
+    """Differentiable logdet of each value set: values [batch, nnzA] -> [batch]."""
+    return _autograd()[0].apply(values, plan)
+
+
+def quad_form(values, x, plan):
+    """Differentiable x_b^T A_b x_b."""
+    return _autograd()[1].apply(values, x, plan)
+
+
+def solve(values, b, plan):
+    """Differentiable x = A^{-1} b, b [batch, n]."""
+    return _autograd()[2].apply(values, b, plan)

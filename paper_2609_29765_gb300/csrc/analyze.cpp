@@ -642,7 +642,12 @@ stc::TaskSet* stc_plan::taskset(int32_t slices) {
     std::iota(order.begin(), order.end(), 0);
     std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return key[a] < key[b]; });
     ts->tasks.reserve(T);
-    for (int32_t i : order) ts->tasks.push_back(tasks[i]);
+    ts->qkey.reserve(T);
+    for (int32_t i : order) {
+        ts->tasks.push_back(tasks[i]);
+        ts->qkey.push_back(key[i]);
+    }
+    ts->period = T ? key[order[T - 1]] / double(std::max<int64_t>(1, NT)) : 0.0;
     stc::TaskSet* raw = ts.get();
     tasksets[slices] = std::move(ts);
     return raw;
@@ -792,6 +797,61 @@ static int analyze_impl(int64_t n, const int64_t* Ap, const int64_t* Ai, const d
             int64_t off = entry_offset(*P, P->Li[q], j);
             if (off < 0) return STC_ERR_INVALID_PATTERN;
             P->csc_map[q] = off;
+        }
+    // ---- selected inverse: stored-index lookup, tasks in reverse block-column order ----
+    P->sinv.assign(P->tiles.size() * (size_t)P->nb, (int16_t)-1);
+    for (size_t t = 0; t < P->tiles.size(); ++t) {
+        const stc::DTile& T = P->tiles[t];
+        int16_t* row = P->sinv.data() + t * P->nb;
+        if (T.I == T.J) {
+            for (int c = 0; c < T.sw; ++c) row[c] = (int16_t)c;
+        } else {
+            for (int s2 = 0; s2 < T.sw; ++s2) row[T.c0 >= 0 ? T.c0 + s2 : P->saind[T.aoff + s2]] = (int16_t)s2;
+        }
+    }
+    for (int64_t k = P->nt - 1; k >= 0; --k) {
+        const int32_t dk = P->diag_tile[k];
+        for (int32_t o = P->colstart[k]; o < P->colstart[k + 1]; ++o) {
+            const stc::DTile& O = P->tiles[o];
+            if (O.I == O.J) continue;
+            stc::DSTask t{};
+            t.kind = stc::TASK_SOFF; t.tile = o; t.diag = dk; t.r0 = O.r0; t.r1 = O.r1;
+            t.cbeg = (int32_t)P->scons.size();
+            for (int32_t q = P->colstart[k]; q < P->colstart[k + 1]; ++q) {
+                const stc::DTile& Jt = P->tiles[q];
+                if (Jt.I == Jt.J) continue;
+                const int64_t j = Jt.I, m = O.I;
+                stc::DSCon c{};
+                c.ltile = q;
+                if (j == m) { c.stile = P->diag_tile[m]; c.mode = stc::SCON_DIAG; }
+                else if (m > j) { c.stile = P->tile_id(m, j); c.mode = stc::SCON_MJ; }
+                else { c.stile = P->tile_id(j, m); c.mode = stc::SCON_JM; }
+                if (c.stile < 0) continue;  // structurally zero block: no contribution
+                P->scons.push_back(c);
+            }
+            t.cend = (int32_t)P->scons.size();
+            P->stasks.push_back(t);
+        }
+        stc::DSTask d{};
+        d.kind = stc::TASK_SDIAG; d.tile = dk; d.diag = dk; d.r0 = 0; d.r1 = (int32_t)P->nb;
+        d.cbeg = (int32_t)P->scons.size();
+        for (int32_t q = P->colstart[k]; q < P->colstart[k + 1]; ++q) {
+            if (P->tiles[q].I == P->tiles[q].J) continue;
+            stc::DSCon c{};
+            c.ltile = q; c.stile = q; c.mode = stc::SCON_OWN;
+            P->scons.push_back(c);
+        }
+        d.cend = (int32_t)P->scons.size();
+        P->stasks.push_back(d);
+    }
+    P->vdiag.resize(P->nnzA);
+    P->arow.resize(P->nnzA);
+    P->acol.resize(P->nnzA);
+    for (int64_t j = 0; j < n; ++j)
+        for (int64_t p = Ap[j]; p < Ap[j + 1]; ++p) {
+            P->vdiag[p] = Ai[p] == j;
+            P->arow[p] = (int32_t)Ai[p];
+            P->acol[p] = (int32_t)j;
         }
     stc::TaskSet* ts = P->taskset(1);
     P->flops_tile = 2.0 * ts->fma;

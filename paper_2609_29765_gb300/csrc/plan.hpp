@@ -64,6 +64,32 @@ struct DUpd {
     int32_t pad[2];
 };
 
+// Selected inverse (Takahashi recurrence on the tile map), walked in reverse order.
+//   TASK_SOFF  Sigma_mk = -(sum_j Sigma_(m,j) L_jk) L_kk^{-1} on the stored columns of (m,k)
+//   TASK_SDIAG Sigma_kk from Z = sum_j Sigma_jk^T L_jk and the element recurrence inside
+//              the diagonal tile
+enum : int32_t { TASK_SOFF = 0, TASK_SDIAG = 1 };
+enum : int32_t { SCON_MJ = 0, SCON_JM = 1, SCON_DIAG = 2, SCON_OWN = 3 };
+
+struct DSTask {
+    int32_t kind;
+    int32_t tile;        // output tile (m,k) or (k,k)
+    int32_t diag;        // tile (k,k)
+    int32_t cbeg, cend;  // contributions
+    int32_t r0, r1;      // output rows computed (row extent)
+    int32_t pad;
+};
+
+// One contribution to a selected-inverse task.
+//   SCON_MJ:   Sigma tile (m,j), m > j, times L_jk      SCON_JM: Sigma tile (j,m)^T times L_jk
+//   SCON_DIAG: symmetric Sigma tile (m,m) times L_mk   SCON_OWN: Sigma_jk^T L_jk (diagonal task)
+struct DSCon {
+    int32_t ltile;       // L tile (j,k)
+    int32_t stile;       // Sigma tile read
+    int32_t mode;
+    int32_t pad;
+};
+
 struct DevPlanArrays {          // device pointers of one plan's metadata
     DTile* tiles = nullptr;
     int16_t* saind = nullptr;   // stored-column -> logical-column lists
@@ -79,6 +105,12 @@ struct DevPlanArrays {          // device pointers of one plan's metadata
     int32_t* scol_beg = nullptr;   // solve: per block column, tiles (m,k) m>k
     int32_t* scol_tiles = nullptr;
     int32_t* diag_tile = nullptr;  // per block: tile id of (k,k)
+    int16_t* sinv = nullptr;       // per tile, per logical column: stored index or -1
+    DSTask* stasks = nullptr;      // selected-inverse tasks
+    DSCon* scons = nullptr;
+    int8_t* vdiag = nullptr;       // per A entry: 1 on the diagonal
+    int32_t* arow = nullptr;       // per A entry: original row, column
+    int32_t* acol = nullptr;
     int device = -1;
     int32_t ntasks = 0;
 };
@@ -90,7 +122,10 @@ struct TaskSet {
     std::vector<DUpd> upds;
     std::vector<int16_t> imap;
     std::vector<int32_t> nfinal;  // per tile completion target
+    std::vector<double> qkey;     // modelled start of each task (queue order)
+    double period = 0.0;          // modelled time per block column
     double fma = 0.0;             // executed FMAs
+    std::map<int64_t, uint64_t*> d_queue;  // per batch: merged (task << 32 | item) order
     // device copies
     DTask* d_tasks = nullptr;
     DUpd* d_upds = nullptr;
@@ -134,6 +169,11 @@ struct stc_plan {
     std::vector<int64_t> value_map;    // nnzA
     std::vector<int64_t> pad_diag;
     std::vector<int64_t> csc_map;      // nnzL
+    std::vector<int16_t> sinv;         // ntiles x nb
+    std::vector<stc::DSTask> stasks;   // selected inverse, reverse block-column order
+    std::vector<stc::DSCon> scons;
+    std::vector<int8_t> vdiag;         // nnzA
+    std::vector<int32_t> arow, acol;   // nnzA (original indices)
     // task sets by slice count, device arrays
     std::map<int32_t, std::unique_ptr<stc::TaskSet>> tasksets;
     stc::DevPlanArrays dev;

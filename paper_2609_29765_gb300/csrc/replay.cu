@@ -17,6 +17,8 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <functional>
+#include <queue>
 #include <climits>
 #include <cstdio>
 #include <cstring>
@@ -86,6 +88,18 @@ __device__ __forceinline__ double diag_at(const double* T, const DTile& d, int n
 
 __device__ __forceinline__ int logical_col(const DTile& t, const int16_t* saind, int s) {
     return t.c0 >= 0 ? t.c0 + s : saind[t.aoff + s];
+}
+
+// Visit every (r, c), r < R, c < NC, with consecutive threads on consecutive rows: the
+// rows of a column go to a power-of-two group of threads (bit operations only, no
+// integer division), the groups take columns in turn.  f must not synchronise.
+template <class Fn>
+__device__ __forceinline__ void for_rc(int R, int NC, Fn f) {
+    const int rp = R <= 1 ? 1 : min(kThreads / 2, 1 << (32 - __clz(R - 1)));
+    const int sh = 31 - __clz(rp);
+    const int r0 = threadIdx.x & (rp - 1);
+    for (int c = threadIdx.x >> sh; c < NC; c += kThreads >> sh)
+        for (int r = r0; r < R; r += rp) f(r, c);
 }
 
 // ---------------------------------------------------------------------------
@@ -164,7 +178,7 @@ __device__ __forceinline__ void mma_sub(double* C, int ldc, int R, int Cn, const
 // TPR threads share a row: each keeps the columns j = q (mod TPR) in registers, the
 // owner of column j finishes x_j and broadcasts it by shuffle, and every thread then
 // removes x_j's contribution from its later columns (right-looking).
-template <int TPR>
+template <int TPR, bool BACK>
 __device__ void trsm_rows_t(double* X, int ldx, int R, int pw, const double* D, int ldd,
                             const double* dinv) {
     constexpr int NJ = kPb / TPR;
@@ -181,14 +195,16 @@ __device__ void trsm_rows_t(double* X, int ldx, int R, int pw, const double* D, 
             b[s] = (live && k < pw) ? X[rr + k * ldx] : 0.0;
         }
 #pragma unroll
-        for (int j = 0; j < kPb; ++j) {
+        for (int jj = 0; jj < kPb; ++jj) {
+            const int j = BACK ? kPb - 1 - jj : jj;
             if (j < pw) {
                 const double xj = __shfl_sync(0xffffffffu, b[j / TPR] * dinv[j], base + (j % TPR));
                 if (q == j % TPR) b[j / TPR] = xj;
 #pragma unroll
                 for (int s = 0; s < NJ; ++s) {
                     const int k = s * TPR + q;
-                    if (k > j && k < pw) b[s] = fma(-xj, D[k + j * ldd], b[s]);
+                    if (!BACK && k > j && k < pw) b[s] = fma(-xj, D[k + j * ldd], b[s]);
+                    if (BACK && k < j) b[s] = fma(-xj, D[j + k * ldd], b[s]);
                 }
             }
         }
@@ -202,11 +218,19 @@ __device__ void trsm_rows_t(double* X, int ldx, int R, int pw, const double* D, 
     }
 }
 
+// Forward (X D^{-T}) or backward (X D^{-1}) substitution of a row block against a
+// lower pw x pw panel block D, choosing 2, 4 or 8 threads per row from the row count.
+template <bool BACK>
+__device__ __forceinline__ void trsm_rows_dir(double* X, int ldx, int R, int pw, const double* D, int ldd,
+                                              const double* dinv) {
+    if (R <= kThreads / 8) trsm_rows_t<8, BACK>(X, ldx, R, pw, D, ldd, dinv);
+    else if (R <= kThreads / 4) trsm_rows_t<4, BACK>(X, ldx, R, pw, D, ldd, dinv);
+    else trsm_rows_t<2, BACK>(X, ldx, R, pw, D, ldd, dinv);
+}
+
 __device__ __forceinline__ void trsm_rows(double* X, int ldx, int R, int pw, const double* D, int ldd,
                                           const double* dinv) {
-    if (R <= kThreads / 8) trsm_rows_t<8>(X, ldx, R, pw, D, ldd, dinv);
-    else if (R <= kThreads / 4) trsm_rows_t<4>(X, ldx, R, pw, D, ldd, dinv);
-    else trsm_rows_t<2>(X, ldx, R, pw, D, ldd, dinv);
+    trsm_rows_dir<false>(X, ldx, R, pw, D, ldd, dinv);
 }
 
 struct ReplayArgs {
@@ -226,42 +250,30 @@ struct ReplayArgs {
     long long batch;
     int nb;
     long long spin;
+    const uint64_t* queue;   // (task << 32 | item) per slot, or null: slot = task*batch+item
 };
 
 // Load rows [rs0, rs0+R) of stored columns [0, sw) of an off-diagonal tile into C.
 __device__ void load_off(double* C, const double* T, int nb, int rs0, int R, int sw) {
-    for (int idx = threadIdx.x; idx < R * sw; idx += kThreads) {
-        const int r = idx % R, c = idx / R;
-        C[r + c * kLdc] = __ldcg(T + rs0 + r + (size_t)c * nb);
-    }
+    for_rc(R, sw, [&](int r, int c) { C[r + c * kLdc] = __ldcg(T + rs0 + r + (size_t)c * nb); });
 }
 __device__ void store_off(const double* C, double* T, int nb, int rs0, int R, int sw) {
-    for (int idx = threadIdx.x; idx < R * sw; idx += kThreads) {
-        const int r = idx % R, c = idx / R;
-        __stcg(T + rs0 + r + (size_t)c * nb, C[r + c * kLdc]);
-    }
+    for_rc(R, sw, [&](int r, int c) { __stcg(T + rs0 + r + (size_t)c * nb, C[r + c * kLdc]); });
 }
 
 // Full lower triangle (and zero upper) of a diagonal tile into C.
 __device__ void load_diag(double* C, const double* T, const DTile& d, int nb) {
-    for (int idx = threadIdx.x; idx < nb * nb; idx += kThreads) {
-        const int r = idx % nb, c = idx / nb;
-        C[r + c * kLdc] = r >= c ? diag_at(T, d, nb, r, c) : 0.0;
-    }
+    for_rc(nb, nb, [&](int r, int c) { C[r + c * kLdc] = r >= c ? diag_at(T, d, nb, r, c) : 0.0; });
 }
 __device__ void store_diag(const double* C, double* T, const DTile& d, int nb) {
     if (d.kind == TILE_DIAG_DENSE) {
-        for (int idx = threadIdx.x; idx < nb * nb; idx += kThreads) {
-            const int r = idx % nb, c = idx / nb;
-            __stcg(T + r + (size_t)c * nb, r >= c ? C[r + c * kLdc] : 0.0);
-        }
+        for_rc(nb, nb, [&](int r, int c) { __stcg(T + r + (size_t)c * nb, r >= c ? C[r + c * kLdc] : 0.0); });
     } else {
         const int w = d.kd + 1;
-        for (int idx = threadIdx.x; idx < w * nb; idx += kThreads) {
-            const int q = idx % w, r = idx / w;  // storage (q, r): L[r][r - kd + q]
+        for_rc(w, nb, [&](int q, int r) {  // storage (q, r): L[r][r - kd + q]
             const int c = r - d.kd + q;
-            if (c >= 0) __stcg(T + idx, C[r + c * kLdc]);
-        }
+            if (c >= 0) __stcg(T + q + (size_t)r * w, C[r + c * kLdc]);
+        });
     }
 }
 
@@ -270,8 +282,7 @@ __device__ void store_diag(const double* C, double* T, const DTile& d, int nb) {
 __device__ void stage_cols(double* S, int ld, const double* T, int nb, int row0, int R,
                            const DUpd& u, const int16_t* imap, bool use_b, int k0, int K) {
     const int Rp = ((R + 3) & ~3) + 4;
-    for (int idx = threadIdx.x; idx < Rp * K; idx += kThreads) {
-        const int r = idx % Rp, k = idx / Rp;
+    for_rc(Rp, K, [&](int r, int k) {
         double v = 0.0;
         if (r < R) {
             int s;
@@ -280,16 +291,15 @@ __device__ void stage_cols(double* S, int ld, const double* T, int nb, int row0,
             v = __ldcg(T + row0 + r + (size_t)s * nb);
         }
         S[r + k * ld] = v;
-    }
+    });
 }
 
 // B rows for a GEMM: rows = logical columns of the output tile's stored columns oc0.. .
 __device__ void stage_rows_gather(double* S, int ld, const double* T, int nb, const DTile& O,
                                   const int16_t* saind, int oc0, int Cn, const DUpd& u,
                                   const int16_t* imap, int k0, int K) {
-    const int Cp = (Cn + 3) & ~3;
-    for (int idx = threadIdx.x; idx < Cp * K; idx += kThreads) {
-        const int c = idx % Cp, k = idx / Cp;
+    const int Cp = ((Cn + 3) & ~3) + 4;
+    for_rc(Cp, K, [&](int c, int k) {
         double v = 0.0;
         if (c < Cn) {
             const int row = logical_col(O, saind, oc0 + c);
@@ -297,7 +307,7 @@ __device__ void stage_rows_gather(double* S, int ld, const double* T, int nb, co
             v = __ldcg(T + row + (size_t)s * nb);
         }
         S[c + k * ld] = v;
-    }
+    });
 }
 
 // Blocked right-looking Cholesky of the w x w leading block of C (lower) in shared
@@ -422,8 +432,16 @@ __global__ void __launch_bounds__(kThreads, 1) replay_kernel(ReplayArgs a) {
         const long long slot = s_slot;
         __syncthreads();
         if (slot >= total) break;
-        const int ti = (int)(slot / a.batch);
-        const long long item = slot % a.batch;
+        int ti;
+        long long item;
+        if (a.queue) {
+            const uint64_t e = a.queue[slot];
+            ti = (int)(e >> 32);
+            item = (long long)(e & 0xffffffffULL);
+        } else {
+            ti = (int)(slot / a.batch);
+            item = slot % a.batch;
+        }
         const DTask t = a.tasks[ti];
         double* F = a.factor + item * a.fstride;
         int* cnt = a.counters + item * a.ntiles;
@@ -464,10 +482,10 @@ __global__ void __launch_bounds__(kThreads, 1) replay_kernel(ReplayArgs a) {
             const int R = t.rs1 - t.rs0;
             if (s_ok) {
                 const double* T = F + O.off;
-                for (int idx = threadIdx.x; idx < R * t.rs1; idx += kThreads) {
-                    const int r = idx % R, c = idx / R, gr = t.rs0 + r;
+                for_rc(R, t.rs1, [&](int r, int c) {
+                    const int gr = t.rs0 + r;
                     C[r + c * kLdc] = c <= gr ? diag_at(T, O, nb, gr, c) : 0.0;
-                }
+                });
                 __syncthreads();
                 for (int ui = t.ubeg; ui < t.uend; ++ui) {
                     const DUpd u = a.upds[ui];
@@ -490,12 +508,12 @@ __global__ void __launch_bounds__(kThreads, 1) replay_kernel(ReplayArgs a) {
                 }
                 if (s_ok) {
                     double* Tw = F + O.off;
-                    for (int idx = threadIdx.x; idx < R * t.rs1; idx += kThreads) {
-                        const int r = idx % R, c = idx / R, gr = t.rs0 + r;
-                        if (c > gr) continue;
+                    for_rc(R, t.rs1, [&](int r, int c) {
+                        const int gr = t.rs0 + r;
+                        if (c > gr) return;
                         if (O.kind == TILE_DIAG_DENSE) __stcg(Tw + gr + (size_t)c * nb, C[r + c * kLdc]);
                         else if (gr - c <= O.kd) __stcg(Tw + (O.kd + c - gr) + (size_t)gr * (O.kd + 1), C[r + c * kLdc]);
-                    }
+                    });
                 }
             }
         } else if (t.kind == TASK_POTRF) {
@@ -552,15 +570,14 @@ __global__ void __launch_bounds__(kThreads, 1) replay_kernel(ReplayArgs a) {
                         const int pw = min(kPb, sw - p);
                         for (int k0 = 0; k0 < p; k0 += kKc) {
                             const int K = min(kKc, p - k0);
-                            const int Cp = (pw + 3) & ~3;
-                            for (int idx = threadIdx.x; idx < Cp * K; idx += kThreads) {
-                                const int c = idx % Cp, k = idx / Cp;
+                            const int Cp = ((pw + 3) & ~3) + 4;
+                            for_rc(Cp, K, [&](int c, int k) {
                                 double v = 0.0;
                                 if (c < pw)
                                     v = diag_at(DT, D, nb, logical_col(O, a.saind, p + c),
                                                 logical_col(O, a.saind, k0 + k));
                                 S1[c + k * (kNbMax + 8)] = v;
-                            }
+                            });
                             __syncthreads();
                             mma_sub<false>(X + p * kLdc, kLdc, RX, pw, X + k0 * kLdc, kLdc, S1, kNbMax + 8, K);
                             __syncthreads();
@@ -697,10 +714,7 @@ __global__ void __launch_bounds__(kThreads, 1) solve_kernel(SolveArgs a) {
         __syncthreads();
         if (s_ok) {
             for (int i = threadIdx.x; i < kSolveWarps * nb; i += kThreads) acc[i] = 0.0;
-            for (int idx = threadIdx.x; idx < nb * nb; idx += kThreads) {
-                const int r = idx % nb, c = idx / nb;
-                Ls[r + c * kLdc] = r >= c ? diag_at(F + D.off, D, nb, r, c) : 0.0;
-            }
+            for_rc(nb, nb, [&](int r, int c) { Ls[r + c * kLdc] = r >= c ? diag_at(F + D.off, D, nb, r, c) : 0.0; });
             for (int r = threadIdx.x; r < nb; r += kThreads) {
                 const long long g = (long long)k * nb + r;
                 v[r] = fwd ? (g < a.n ? a.b[ch * a.n + a.perm[g]] : 0.0) : __ldcg(y + g);
@@ -812,6 +826,285 @@ __global__ void fp64_probe_kernel(double* out, long long iters, double a, double
 }
 
 // ---------------------------------------------------------------------------
+// a12: selected inverse Sigma = A_p^{-1} on the stored tiles (Takahashi recurrence,
+// Takahashi 1973; not in the paper, which leaves selected inversion to separate work),
+// one persistent kernel walking block columns in reverse order with per-tile counters.
+// Off-diagonal tile:  Sigma_mk = -(sum_j Sigma_(m,j) L_jk) L_kk^{-1}  (stored columns of
+// (m,k); entries the symbolic factor proves zero are never read by structural outputs).
+// Diagonal tile: Z = sum_j Sigma_jk^T L_jk, then column c = w-1..0 of the tile:
+//   Sigma_rc = (-Z_rc - sum_{i>c} L_ic Sigma_ri) / L_cc          (r > c)
+//   Sigma_cc = 1/L_cc^2 + (-Z_cc - sum_{i>c} L_ic Sigma_ic) / L_cc
+// ---------------------------------------------------------------------------
+struct SelinvArgs {
+    const DTile* tiles;
+    const int16_t* saind;
+    const int16_t* sinv;     // [ntiles][nb]
+    const DSTask* tasks;
+    const DSCon* cons;
+    const double* factor;
+    double* sigma;
+    long long fstride;
+    int* counters;           // [batch][ntiles]
+    int ntiles;
+    WorkHeader* hdr;
+    int ntasks;
+    long long batch;
+    int nb;
+    long long spin;
+};
+
+__device__ __forceinline__ double sym_at(const double* T, const DTile& d, int nb, int r, int c) {
+    return r >= c ? diag_at(T, d, nb, r, c) : diag_at(T, d, nb, c, r);
+}
+
+__global__ void __launch_bounds__(kThreads, 1) selinv_kernel(SelinvArgs a) {
+    extern __shared__ double smem[];
+    double* C = smem;
+    double* S0 = C + kCbuf;
+    double* S1 = S0 + kStage;
+    double* sv = S1 + kStage;
+    __shared__ long long s_slot;
+    __shared__ int s_ok;
+    __shared__ double s_red[32];
+    const long long total = (long long)a.ntasks * a.batch;
+    const int nb = a.nb;
+    constexpr int LDS = kNbMax + 8;
+    for (;;) {
+        if (threadIdx.x == 0) s_slot = (long long)atomicAdd(&a.hdr->head, 1ULL);
+        __syncthreads();
+        const long long slot = s_slot;
+        __syncthreads();
+        if (slot >= total) break;
+        const int ti = (int)(slot / a.batch);
+        const long long item = slot % a.batch;
+        const DSTask t = a.tasks[ti];
+        const double* Lf = a.factor + item * a.fstride;
+        double* Sg = a.sigma + item * a.fstride;
+        int* cnt = a.counters + item * a.ntiles;
+        const DTile O = a.tiles[t.tile];
+        const DTile D = a.tiles[t.diag];
+        if (threadIdx.x == 0) s_ok = (*(volatile int*)&a.hdr->status == STC_OK);
+        __syncthreads();
+        if (t.kind == TASK_SOFF && s_ok) {
+            const int R = t.r1 - t.r0, sw = O.sw;
+            for_rc(R, sw, [&](int r, int c) { C[r + c * kLdc] = 0.0; });
+            __syncthreads();
+            for (int ci = t.cbeg; ci < t.cend; ++ci) {
+                const DSCon cn = a.cons[ci];
+                const DTile Lt = a.tiles[cn.ltile];
+                const DTile St = a.tiles[cn.stile];
+                if (threadIdx.x == 0) s_ok = wait_counter(cnt + cn.stile, 1, a.spin, &a.hdr->status);
+                __syncthreads();
+                if (!s_ok) break;
+                const double* LT = Lf + Lt.off;
+                const double* ST = Sg + St.off;
+                const int16_t* si_S = a.sinv + (size_t)cn.stile * nb;
+                const int16_t* si_L = a.sinv + (size_t)cn.ltile * nb;
+                for (int i0 = Lt.r0; i0 < Lt.r1; i0 += kKc) {
+                    const int K = min(kKc, Lt.r1 - i0);
+                    const int Rp = ((R + 3) & ~3) + 4, Cp = ((sw + 3) & ~3) + 4;
+                    for_rc(Rp, K, [&](int r, int kk) {
+                        double v = 0.0;
+                        if (r < R) {
+                            const int gr = t.r0 + r, i = i0 + kk;
+                            if (cn.mode == SCON_MJ) {
+                                const int sidx = si_S[i];
+                                if (sidx >= 0) v = __ldcg(ST + gr + (size_t)sidx * nb);
+                            } else if (cn.mode == SCON_JM) {
+                                const int sidx = si_S[gr];
+                                if (sidx >= 0) v = __ldcg(ST + i + (size_t)sidx * nb);
+                            } else {
+                                v = sym_at(ST, St, nb, gr, i);
+                            }
+                        }
+                        S0[r + kk * LDS] = v;
+                    });
+                    for_rc(Cp, K, [&](int c, int kk) {
+                        double v = 0.0;
+                        if (c < sw) {
+                            const int sl = si_L[logical_col(O, a.saind, c)];
+                            if (sl >= 0) v = __ldcg(LT + (i0 + kk) + (size_t)sl * nb);
+                        }
+                        S1[c + kk * LDS] = v;
+                    });
+                    __syncthreads();
+                    mma_sub<false>(C, kLdc, R, sw, S0, LDS, S1, LDS, K);  // C = -sum Sigma L
+                    __syncthreads();
+                }
+            }
+            if (s_ok) {
+                // X L_g = C on the stored columns, panels from the right (backward)
+                const double* DT = Lf + D.off;
+                for (int p = ((sw - 1) / kPb) * kPb; p >= 0; p -= kPb) {
+                    const int pw = min(kPb, sw - p);
+                    for (int k0 = p + pw; k0 < sw; k0 += kKc) {
+                        const int K = min(kKc, sw - k0);
+                        const int Cp = ((pw + 3) & ~3) + 4;
+                        for_rc(Cp, K, [&](int c, int kk) {
+                            double v = 0.0;
+                            if (c < pw)
+                                v = diag_at(DT, D, nb, logical_col(O, a.saind, k0 + kk), logical_col(O, a.saind, p + c));
+                            S1[c + kk * LDS] = v;
+                        });
+                        __syncthreads();
+                        mma_sub<false>(C + p * kLdc, kLdc, R, pw, C + k0 * kLdc, kLdc, S1, LDS, K);
+                        __syncthreads();
+                    }
+                    for (int idx = threadIdx.x; idx < kPb * kPb; idx += kThreads) {
+                        const int i = idx & (kPb - 1), j = idx / kPb;
+                        double v = 0.0;
+                        if (i < pw && j < pw && i >= j)
+                            v = diag_at(DT, D, nb, logical_col(O, a.saind, p + i), logical_col(O, a.saind, p + j));
+                        S0[i + j * kPb] = v;
+                    }
+                    __syncthreads();
+                    if (threadIdx.x < pw) sv[threadIdx.x] = 1.0 / S0[threadIdx.x * (kPb + 1)];
+                    __syncthreads();
+                    trsm_rows_dir<true>(C + p * kLdc, kLdc, R, pw, S0, kPb, sv);
+                    __syncthreads();
+                }
+                double* T = Sg + O.off;
+                for_rc(R, sw, [&](int r, int c) { __stcg(T + t.r0 + r + (size_t)c * nb, C[r + c * kLdc]); });
+            }
+        } else if (t.kind == TASK_SDIAG && s_ok) {
+            const int w = O.sw;
+            const int kd = min(O.kd, nb - 1);
+            for_rc(nb, nb, [&](int r, int c) { C[r + c * kLdc] = 0.0; });
+            __syncthreads();
+            for (int ci = t.cbeg; ci < t.cend; ++ci) {
+                const DSCon cn = a.cons[ci];
+                const DTile Tt = a.tiles[cn.ltile];
+                if (threadIdx.x == 0) s_ok = wait_counter(cnt + cn.stile, 1, a.spin, &a.hdr->status);
+                __syncthreads();
+                if (!s_ok) break;
+                const double* LT = Lf + Tt.off;
+                const double* ST = Sg + Tt.off;
+                const bool contig = Tt.c0 >= 0;
+                const int M = contig ? Tt.sw : w;   // rows/cols of the Z block
+                const int16_t* si = a.sinv + (size_t)cn.ltile * nb;
+                for (int i0 = Tt.r0; i0 < Tt.r1; i0 += kKc) {
+                    const int K = min(kKc, Tt.r1 - i0);
+                    const int Mp = ((M + 3) & ~3) + 4;
+                    for_rc(Mp, K, [&](int r, int kk) {
+                        double vs = 0.0, vl = 0.0;
+                        if (r < M) {
+                            const int sidx = contig ? r : si[r];
+                            if (sidx >= 0) {
+                                vs = __ldcg(ST + (i0 + kk) + (size_t)sidx * nb);
+                                vl = __ldcg(LT + (i0 + kk) + (size_t)sidx * nb);
+                            }
+                        }
+                        S0[r + kk * LDS] = vs;
+                        S1[r + kk * LDS] = vl;
+                    });
+                    __syncthreads();
+                    double* Cz = contig ? C + Tt.c0 * (1 + kLdc) : C;
+                    mma_sub<true>(Cz, kLdc, M, M, S0, LDS, S1, LDS, K);  // C = -Z (lower)
+                    __syncthreads();
+                }
+            }
+            if (s_ok) {
+                // packed lower triangle of L_kk in the staging area: (r, c) at c*nb - c(c-1)/2 + r - c
+                double* Lp = S0;
+                const double* DT = Lf + D.off;
+                for_rc(nb, nb, [&](int r, int c) {
+                    if (r >= c) Lp[c * nb - c * (c - 1) / 2 + (r - c)] = diag_at(DT, D, nb, r, c);
+                });
+                __syncthreads();
+                for (int c = w - 1; c >= 0; --c) {
+                    const double* Lc = Lp + c * nb - c * (c - 1) / 2 - c;  // Lc[i] = L[i][c]
+                    const double inv = 1.0 / Lc[c];
+                    const int iend = min(w, c + kd + 1);
+                    for (int r = c + 1 + threadIdx.x; r < iend; r += kThreads) {
+                        double s0 = C[r + c * kLdc], s1 = 0.0;
+                        int i = c + 1;
+                        for (; i + 1 < iend; i += 2) {
+                            s0 = fma(-Lc[i], i >= r ? C[i + r * kLdc] : C[r + i * kLdc], s0);
+                            s1 = fma(-Lc[i + 1], i + 1 >= r ? C[i + 1 + r * kLdc] : C[r + (i + 1) * kLdc], s1);
+                        }
+                        if (i < iend) s0 = fma(-Lc[i], i >= r ? C[i + r * kLdc] : C[r + i * kLdc], s0);
+                        C[r + c * kLdc] = (s0 + s1) * inv;
+                    }
+                    __syncthreads();
+                    if (threadIdx.x < 32) {
+                        double sacc = 0.0;
+                        for (int i = c + 1 + threadIdx.x; i < iend; i += 32) sacc = fma(Lc[i], C[i + c * kLdc], sacc);
+#pragma unroll
+                        for (int o = 16; o > 0; o >>= 1) sacc += __shfl_down_sync(0xffffffffu, sacc, o);
+                        if (threadIdx.x == 0) C[c + c * kLdc] = inv * inv + (C[c + c * kLdc] - sacc) * inv;
+                    }
+                    __syncthreads();
+                }
+                store_diag(C, Sg + O.off, O, nb);
+            }
+        }
+        __threadfence();
+        __syncthreads();
+        if (threadIdx.x == 0) red_release_add(cnt + t.tile, 1);
+    }
+    (void)s_red;
+}
+
+// d logdet / d a_e = gout_b (2 - delta_e) Sigma_e, gathered through the value map.
+__global__ void grad_gather_kernel(const double* __restrict__ Sg, long long fstride, long long batch,
+                                   const int64_t* __restrict__ map, const int8_t* __restrict__ vdiag, long long nnz,
+                                   const double* __restrict__ gout, double* __restrict__ g, int accumulate) {
+    const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long e = tid; e < nnz; e += stride) {
+        const int64_t m = __ldg(map + e);
+        const double w = vdiag[e] ? 1.0 : 2.0;
+        for (long long b = 0; b < batch; ++b) {
+            double v = w * Sg[b * fstride + m] * (gout ? gout[b] : 1.0);
+            if (accumulate) v += g[b * nnz + e];
+            g[b * nnz + e] = v;
+        }
+    }
+}
+
+// g_e = scale_b (2 - delta_e)/2 (u_i v_j + u_j v_i) for A entry e = (i, j).
+__global__ void outer_grad_kernel(const int32_t* __restrict__ arow, const int32_t* __restrict__ acol,
+                                  const int8_t* __restrict__ vdiag, long long nnz, long long batch,
+                                  const double* __restrict__ u, const double* __restrict__ v, long long n,
+                                  const double* __restrict__ scale, double* __restrict__ g, int accumulate) {
+    const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long e = tid; e < nnz; e += stride) {
+        const long long i = arow[e], j = acol[e];
+        const double w = vdiag[e] ? 0.5 : 1.0;
+        for (long long b = 0; b < batch; ++b) {
+            const double* ub = u + b * n;
+            const double* vb = v + b * n;
+            double val = w * (ub[i] * vb[j] + ub[j] * vb[i]) * (scale ? scale[b] : 1.0);
+            if (accumulate) val += g[b * nnz + e];
+            g[b * nnz + e] = val;
+        }
+    }
+}
+
+// out_b = x_b^T A_b x_b = sum_e (2 - delta_e) a_e x_i x_j  (one block per item, fixed order)
+__global__ void quad_form_kernel(const int32_t* __restrict__ arow, const int32_t* __restrict__ acol,
+                                 const int8_t* __restrict__ vdiag, long long nnz, const double* __restrict__ vals,
+                                 const double* __restrict__ x, long long n, double* __restrict__ out) {
+    __shared__ double red[kThreads / 32];
+    const long long b = blockIdx.x;
+    const double* xb = x + b * n;
+    const double* ab = vals + b * nnz;
+    double s = 0.0;
+    for (long long e = threadIdx.x; e < nnz; e += blockDim.x)
+        s += (vdiag[e] ? 1.0 : 2.0) * ab[e] * xb[arow[e]] * xb[acol[e]];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x / 32); ++w) t += red[w];
+        out[b] = t;
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Host helpers
 // ---------------------------------------------------------------------------
 struct DevInfo {
@@ -832,6 +1125,8 @@ int device_info(int* dev, int* sms) {
             return STC_ERR_CUDA;
         if (cudaFuncSetAttribute(solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSolveSmem) != cudaSuccess)
             return STC_ERR_CUDA;
+        if (cudaFuncSetAttribute(selinv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes) != cudaSuccess)
+            return STC_ERR_CUDA;
         d.attr_set = true;
     }
     *sms = d.sms;
@@ -851,7 +1146,8 @@ int upload(T** dst, const std::vector<T>& src) {
 void free_dev(stc_plan* P) {
     DevPlanArrays& d = P->dev;
     void* ptrs[] = {d.saind, d.value_map, d.pad_diag, d.csc_map, d.perm, d.srow_beg,
-                    d.srow_tiles, d.scol_beg, d.diag_tile};
+                    d.srow_tiles, d.scol_beg, d.diag_tile, d.sinv, d.stasks, d.scons, d.vdiag,
+                    d.arow, d.acol};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     d = DevPlanArrays{};
@@ -861,6 +1157,8 @@ void free_dev(stc_plan* P) {
         if (ts->d_upds) cudaFree(ts->d_upds);
         if (ts->d_imap) cudaFree(ts->d_imap);
         if (ts->d_tiles) cudaFree(ts->d_tiles);
+        for (auto& q : ts->d_queue) cudaFree(q.second);
+        ts->d_queue.clear();
         ts->d_tasks = nullptr; ts->d_upds = nullptr; ts->d_imap = nullptr; ts->d_tiles = nullptr;
         ts->device = -1;
     }
@@ -883,6 +1181,12 @@ int ensure_plan(stc_plan* P, int dev) {
     if ((rc = upload(&d.srow_tiles, P->rowtiles))) return rc;
     if ((rc = upload(&d.scol_beg, P->colstart))) return rc;
     if ((rc = upload(&d.diag_tile, P->diag_tile))) return rc;
+    if ((rc = upload(&d.sinv, P->sinv))) return rc;
+    if ((rc = upload(&d.stasks, P->stasks))) return rc;
+    if ((rc = upload(&d.scons, P->scons))) return rc;
+    if ((rc = upload(&d.vdiag, P->vdiag))) return rc;
+    if ((rc = upload(&d.arow, P->arow))) return rc;
+    if ((rc = upload(&d.acol, P->acol))) return rc;
     d.device = dev;
     return STC_OK;
 }
@@ -900,6 +1204,41 @@ int ensure_taskset(stc_plan* P, TaskSet* ts, int dev) {
     if (im.empty()) im.push_back(0);
     if ((rc = upload(&ts->d_imap, im))) return rc;
     ts->device = dev;
+    return STC_OK;
+}
+
+// Merged queue for a batch: item b's tasks keep their earliest-start order and are
+// keyed as if the item started b/batch * skew block-column periods late.  Built on the
+// host and uploaded once per batch size (synchronous), then cached with the task set.
+int ensure_queue(stc_plan* P, TaskSet* ts, int64_t batch, uint64_t** out) {
+    *out = nullptr;
+    const double skew = P->opt.queue_skew;
+    if (batch <= 1 || !(skew > 0.0) || batch > 0xffffffffLL) return STC_OK;
+    std::lock_guard<std::mutex> g(P->mu);
+    auto it = ts->d_queue.find(batch);
+    if (it != ts->d_queue.end()) { *out = it->second; return STC_OK; }
+    const size_t T = ts->tasks.size();
+    std::vector<uint64_t> q;
+    q.reserve(T * (size_t)batch);
+    typedef std::pair<double, int64_t> E;
+    std::priority_queue<E, std::vector<E>, std::greater<E>> h;
+    std::vector<size_t> pos((size_t)batch, 0);
+    auto phi = [&](int64_t b) { return skew * ts->period * double(b) / double(batch); };
+    for (int64_t b = 0; b < batch; ++b) h.push(E(ts->qkey[0] + phi(b), b));
+    while (!h.empty()) {
+        const int64_t b = h.top().second;
+        h.pop();
+        q.push_back((uint64_t)pos[b] << 32 | (uint64_t)b);
+        if (++pos[b] < T) h.push(E(ts->qkey[pos[b]] + phi(b), b));
+    }
+    uint64_t* d = nullptr;
+    if (cudaMalloc((void**)&d, q.size() * sizeof(uint64_t)) != cudaSuccess) return STC_ERR_OUT_OF_MEMORY;
+    if (cudaMemcpy(d, q.data(), q.size() * sizeof(uint64_t), cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaFree(d);
+        return STC_ERR_CUDA;
+    }
+    ts->d_queue[batch] = d;
+    *out = d;
     return STC_OK;
 }
 
@@ -989,6 +1328,8 @@ extern "C" int stc_factorize_scattered(const stc_plan* Pc, int64_t batch, void* 
     if ((rc = ensure_plan(P, dev))) return rc;
     TaskSet* ts = P->taskset(pick_slices(P, batch, sms));
     if ((rc = ensure_taskset(P, ts, dev))) return rc;
+    uint64_t* queue = nullptr;
+    if ((rc = ensure_queue(P, ts, batch, &queue))) return rc;
     cudaStream_t st = S(stream);
     if (cudaMemsetAsync(d_work, 0, factorize_ws(P, batch), st) != cudaSuccess) return STC_ERR_CUDA;
     if (cudaMemsetAsync(d_info, 0, (size_t)batch * sizeof(int32_t), st) != cudaSuccess) return STC_ERR_CUDA;
@@ -1000,6 +1341,7 @@ extern "C" int stc_factorize_scattered(const stc_plan* Pc, int64_t batch, void* 
     a.ntiles = (int)P->tiles.size(); a.info = d_info; a.ntasks = (int)ts->tasks.size();
     a.batch = batch; a.nb = (int)P->nb;
     a.spin = P->opt.spin_limit > 0 ? P->opt.spin_limit : kDefaultSpin;
+    a.queue = queue;
     const long long total = (long long)a.ntasks * batch;
     const int grid = (int)std::max<long long>(1, std::min<long long>(sms, total));
     replay_kernel<<<grid, kThreads, kSmemBytes, st>>>(a);
@@ -1099,6 +1441,70 @@ extern "C" int stc_fp64_peak_probe(double* d_scratch, int64_t scratch_doubles, i
     if (cudaGetLastError() != cudaSuccess) return STC_ERR_CUDA;
     *gflops = 2.0 * 8.0 * (double)iters * (double)blocks * 256.0 / (best * 1e-3) / 1e9;
     return STC_OK;
+}
+
+extern "C" int stc_selinv(const stc_plan* Pc, const void* d_factor, int64_t batch, void* d_sigma, void* d_work,
+                          void* stream) {
+    stc_plan* P = const_cast<stc_plan*>(Pc);
+    if (!P || !d_factor || !d_sigma || !d_work || batch <= 0 || d_factor == d_sigma) return STC_ERR_INVALID_ARG;
+    int dev, sms, rc;
+    if ((rc = device_info(&dev, &sms))) return rc;
+    if ((rc = ensure_plan(P, dev))) return rc;
+    TaskSet* ts = P->taskset(1);
+    if ((rc = ensure_taskset(P, ts, dev))) return rc;
+    cudaStream_t st = S(stream);
+    if (cudaMemsetAsync(d_sigma, 0, stc_factor_bytes(P, batch), st) != cudaSuccess) return STC_ERR_CUDA;
+    if (cudaMemsetAsync(d_work, 0, factorize_ws(P, batch), st) != cudaSuccess) return STC_ERR_CUDA;
+    SelinvArgs a{};
+    a.tiles = ts->d_tiles; a.saind = P->dev.saind; a.sinv = P->dev.sinv; a.tasks = P->dev.stasks;
+    a.cons = P->dev.scons; a.factor = (const double*)d_factor; a.sigma = (double*)d_sigma;
+    a.fstride = P->factor_doubles; a.hdr = (WorkHeader*)d_work;
+    a.counters = (int*)((char*)d_work + sizeof(WorkHeader)); a.ntiles = (int)P->tiles.size();
+    a.ntasks = (int)P->stasks.size(); a.batch = batch; a.nb = (int)P->nb;
+    a.spin = P->opt.spin_limit > 0 ? P->opt.spin_limit : kDefaultSpin;
+    const long long total = (long long)a.ntasks * batch;
+    const int grid = (int)std::max<long long>(1, std::min<long long>(sms, total));
+    selinv_kernel<<<grid, kThreads, kSmemBytes, st>>>(a);
+    return cudaGetLastError() == cudaSuccess ? STC_OK : STC_ERR_CUDA;
+}
+
+extern "C" int stc_logdet_backward(const stc_plan* Pc, const void* d_factor, int64_t batch, const double* d_gout,
+                                   double* d_gvalues, int accumulate, void* d_sigma, void* d_work, void* stream) {
+    stc_plan* P = const_cast<stc_plan*>(Pc);
+    if (!P || !d_gvalues) return STC_ERR_INVALID_ARG;
+    int rc = stc_selinv(P, d_factor, batch, d_sigma, d_work, stream);
+    if (rc) return rc;
+    int sms = g_dev[P->dev.device].sms;
+    const int blocks = std::max(1, std::min<int>(sms * 8, (int)((P->nnzA + 255) / 256)));
+    grad_gather_kernel<<<blocks, 256, 0, S(stream)>>>((const double*)d_sigma, P->factor_doubles, batch,
+                                                       P->dev.value_map, P->dev.vdiag, P->nnzA, d_gout, d_gvalues,
+                                                       accumulate);
+    return cudaGetLastError() == cudaSuccess ? STC_OK : STC_ERR_CUDA;
+}
+
+extern "C" int stc_sym_outer_backward(const stc_plan* Pc, int64_t batch, const double* d_u, const double* d_v,
+                                      const double* d_scale, double* d_gvalues, int accumulate, void* stream) {
+    stc_plan* P = const_cast<stc_plan*>(Pc);
+    if (!P || !d_u || !d_v || !d_gvalues || batch <= 0) return STC_ERR_INVALID_ARG;
+    int dev, sms, rc;
+    if ((rc = device_info(&dev, &sms))) return rc;
+    if ((rc = ensure_plan(P, dev))) return rc;
+    const int blocks = std::max(1, std::min<int>(sms * 8, (int)((P->nnzA + 255) / 256)));
+    outer_grad_kernel<<<blocks, 256, 0, S(stream)>>>(P->dev.arow, P->dev.acol, P->dev.vdiag, P->nnzA, batch, d_u, d_v,
+                                                      P->n, d_scale, d_gvalues, accumulate);
+    return cudaGetLastError() == cudaSuccess ? STC_OK : STC_ERR_CUDA;
+}
+
+extern "C" int stc_quad_form(const stc_plan* Pc, int64_t batch, const double* d_values, const double* d_x,
+                             double* d_out, void* stream) {
+    stc_plan* P = const_cast<stc_plan*>(Pc);
+    if (!P || !d_values || !d_x || !d_out || batch <= 0) return STC_ERR_INVALID_ARG;
+    int dev, sms, rc;
+    if ((rc = device_info(&dev, &sms))) return rc;
+    if ((rc = ensure_plan(P, dev))) return rc;
+    quad_form_kernel<<<(unsigned)batch, kThreads, 0, S(stream)>>>(P->dev.arow, P->dev.acol, P->dev.vdiag, P->nnzA,
+                                                                  d_values, d_x, P->n, d_out);
+    return cudaGetLastError() == cudaSuccess ? STC_OK : STC_ERR_CUDA;
 }
 
 // ---------------------------------------------------------------------------
