@@ -176,6 +176,23 @@ int stc_scatter_values(const stc_plan* plan, const double* d_values, int64_t bat
 int stc_factorize_scattered(const stc_plan* plan, int64_t batch, void* d_factor, void* d_work,
                             int32_t* d_info, void* stream);
 
+/* Mixed batches: several plans (patterns of different sizes), each with its own batch of
+ * value sets, factorized by ONE persistent kernel launch whose queue merges the plans'
+ * task lists in earliest-start order (up to STC_GROUP_MAX_PLANS plans).
+ *   stc_group_create: host + device set-up (synchronous; uploads the plans and the merged
+ *     queue); plans must outlive the group; batch[p] in 1 .. 2^28-1.
+ *   stc_factorize_group: d_values[p], d_factor[p], d_info[p] are host arrays of device
+ *     pointers laid out as for stc_factorize with batch[p]; d_work:
+ *     stc_group_workspace_bytes(group) bytes.  logdet / solve then run per plan. */
+#define STC_GROUP_MAX_PLANS 8
+typedef struct stc_group stc_group;
+int stc_group_create(int32_t nplans, const stc_plan* const* plans, const int64_t* batch,
+                     stc_group** group_out);
+size_t stc_group_workspace_bytes(const stc_group* group);
+int stc_factorize_group(stc_group* group, const double* const* d_values, void* const* d_factor,
+                        int32_t* const* d_info, void* d_work, void* stream);
+void stc_group_destroy(stc_group* group);
+
 /* Synchronize `stream` and return the device status word of d_work: STC_OK or
  * STC_ERR_TIMEOUT (a dependency wait gave up), or STC_ERR_CUDA. */
 int stc_sync_status(const void* d_work, void* stream);

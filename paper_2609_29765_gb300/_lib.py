@@ -38,6 +38,7 @@ EXPORTED = [
     "stc_factorize_scattered", "stc_sync_status",
     "stc_logdet", "stc_solve", "stc_factor_to_csc", "stc_fp64_peak_probe", "stc_factorize_noalloc",
     "stc_selinv", "stc_logdet_backward", "stc_sym_outer_backward", "stc_quad_form",
+    "stc_group_create", "stc_group_workspace_bytes", "stc_factorize_group", "stc_group_destroy",
 ]
 STC_NOALLOC_SCRATCH_BYTES = 4 << 20
 
@@ -111,6 +112,14 @@ def lib():
         L.stc_solve.restype = C.c_int
         L.stc_factor_to_csc.argtypes = [_vp, _vp, C.c_int64, _vp, _vp]
         L.stc_factor_to_csc.restype = C.c_int
+        L.stc_group_create.argtypes = [C.c_int32, C.POINTER(_vp), C.POINTER(C.c_int64), C.POINTER(_vp)]
+        L.stc_group_create.restype = C.c_int
+        L.stc_group_workspace_bytes.argtypes = [_vp]
+        L.stc_group_workspace_bytes.restype = C.c_size_t
+        L.stc_factorize_group.argtypes = [_vp, C.POINTER(_vp), C.POINTER(_vp), C.POINTER(_vp), _vp, _vp]
+        L.stc_factorize_group.restype = C.c_int
+        L.stc_group_destroy.argtypes = [_vp]
+        L.stc_group_destroy.restype = None
         L.stc_selinv.argtypes = [_vp, _vp, C.c_int64, _vp, _vp, _vp]
         L.stc_selinv.restype = C.c_int
         L.stc_logdet_backward.argtypes = [_vp, _vp, C.c_int64, _vp, _vp, C.c_int, _vp, _vp, _vp]
@@ -265,3 +274,30 @@ def stc_sym_outer_backward(plan, batch, d_u, d_v, d_scale, d_gvalues, accumulate
 def stc_quad_form(plan, batch, d_values, d_x, d_out, stream=None):
     return lib().stc_quad_form(plan, int(batch), _dev_ptr(d_values), _dev_ptr(d_x), _dev_ptr(d_out),
                                _stream(stream))
+
+
+def stc_group_create(plans, batches):
+    """Returns (status, group_handle)."""
+    n = len(plans)
+    arr = (C.c_void_p * n)(*[p.value if isinstance(p, C.c_void_p) else p for p in plans])
+    bat = (C.c_int64 * n)(*[int(b) for b in batches])
+    h = C.c_void_p()
+    rc = lib().stc_group_create(n, arr, bat, C.byref(h))
+    return rc, h
+
+
+def stc_group_workspace_bytes(group):
+    return int(lib().stc_group_workspace_bytes(group))
+
+
+def stc_factorize_group(group, d_values, d_factor, d_info, d_work, stream=None):
+    n = len(d_values)
+    pv = (C.c_void_p * n)(*[_dev_ptr(t).value for t in d_values])
+    pf = (C.c_void_p * n)(*[_dev_ptr(t).value for t in d_factor])
+    pi = (C.c_void_p * n)(*[_dev_ptr(t).value for t in d_info])
+    return lib().stc_factorize_group(group, pv, pf, pi, _dev_ptr(d_work), _stream(stream))
+
+
+def stc_group_destroy(group):
+    if group:
+        lib().stc_group_destroy(group)

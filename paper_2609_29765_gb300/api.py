@@ -176,6 +176,86 @@ class Factor:
         return out
 
 
+class GraphedFactorize:
+    """scatter + factorize + logdet of a fixed batch size captured in one CUDA graph.
+
+    First use of a plan on a device uploads its metadata (synchronous); that happens in
+    a warm-up run before capture, after which every library call on the stream is a
+    kernel launch or a memset, so the whole step replays as one graph launch.
+    """
+
+    def __init__(self, plan: Plan, batch: int, device=None):
+        torch = _torch()
+        dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+        self.plan, self.batch = plan, int(batch)
+        plan.upload()
+        self.values = torch.zeros(self.batch, plan.nnzA, dtype=torch.float64, device=dev)
+        self.factor = torch.empty(plan.factor_bytes(self.batch) // 8, dtype=torch.float64, device=dev)
+        self.info = torch.empty(self.batch, dtype=torch.int32, device=dev)
+        self.logdet = torch.empty(self.batch, dtype=torch.float64, device=dev)
+        self.ws = plan.workspace(self.batch, dev)
+        side = torch.cuda.Stream(device=dev)
+        side.wait_stream(torch.cuda.current_stream(dev))
+        with torch.cuda.stream(side):
+            self._step()
+        torch.cuda.current_stream(dev).wait_stream(side)
+        torch.cuda.synchronize(dev)
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph):
+            self._step()
+
+    def _step(self):
+        L.check(L.stc_factorize(self.plan.h, self.values, self.batch, self.factor, self.ws, self.info),
+                "stc_factorize")
+        L.check(L.stc_logdet(self.plan.h, self.factor, self.batch, self.logdet), "stc_logdet")
+
+    def __call__(self, values):
+        """Copy values [batch, nnzA] into the graph's input and replay; returns logdet."""
+        self.values.copy_(values)
+        self.graph.replay()
+        return self.logdet
+
+    def factor_view(self) -> "Factor":
+        return Factor(self.plan, self.factor, self.info, self.batch)
+
+
+class Group:
+    """Several plans, each with its own batch, factorized by one persistent launch."""
+
+    def __init__(self, plans, batches):
+        self.plans, self.batches = list(plans), [int(b) for b in batches]
+        self.h = None
+        rc, h = L.stc_group_create([p.h for p in self.plans], self.batches)
+        L.check(rc, "stc_group_create")
+        self.h = h
+        self._ws = None
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            L.stc_group_destroy(self.h)
+            self.h = None
+
+    def factorize(self, values_list):
+        """values_list[p]: CUDA float64 [batch_p, nnzA_p]; returns one Factor per plan."""
+        torch = _torch()
+        dev = values_list[0].device
+        facs, infos = [], []
+        for P, b, v in zip(self.plans, self.batches, values_list):
+            if v.shape != (b, P.nnzA) or v.dtype != torch.float64:
+                raise ValueError("values must be float64 [batch_p, nnzA_p]")
+            facs.append(torch.empty(P.factor_bytes(b) // 8, dtype=torch.float64, device=dev))
+            infos.append(torch.empty(b, dtype=torch.int32, device=dev))
+        nbytes = L.stc_group_workspace_bytes(self.h)
+        if self._ws is None or self._ws.numel() < nbytes:
+            self._ws = torch.empty(max(nbytes, 64), dtype=torch.uint8, device=dev)
+        vals = [v.contiguous() for v in values_list]
+        L.check(L.stc_factorize_group(self.h, vals, facs, infos, self._ws), "stc_factorize_group")
+        return [Factor(P, f, i, b) for P, f, i, b in zip(self.plans, facs, infos, self.batches)]
+
+    def status(self) -> int:
+        return L.stc_sync_status(self._ws)
+
+
 # ---------------------------------------------------------------------------
 # Differentiation: torch.autograd.Function wrappers.  The forward and backward
 # arithmetic runs in libstc.so; torch only carries the tensors and the chain rule of

@@ -17,6 +17,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <memory>
 #include <functional>
 #include <queue>
 #include <climits>
@@ -233,7 +234,7 @@ __device__ __forceinline__ void trsm_rows(double* X, int ldx, int R, int pw, con
     trsm_rows_dir<false>(X, ldx, R, pw, D, ldd, dinv);
 }
 
-struct ReplayArgs {
+struct ReplayArgs {        // one job: a plan and a batch of value sets
     const DTile* tiles;
     const int16_t* saind;
     const DTask* tasks;
@@ -250,8 +251,22 @@ struct ReplayArgs {
     long long batch;
     int nb;
     long long spin;
-    const uint64_t* queue;   // (task << 32 | item) per slot, or null: slot = task*batch+item
 };
+
+// One launch of the replay kernel: up to kMaxJobs jobs (plans) in one persistent grid.
+// Queue entry of a slot: job << 60 | task << 28 | item; without a queue (one job) the
+// slot is task * batch + item (all items of a task in lockstep).
+constexpr int kMaxJobs = 8;
+struct ReplayLaunch {
+    ReplayArgs job[kMaxJobs];
+    int njobs;
+    const uint64_t* queue;
+    long long total;
+    WorkHeader* hdr;
+};
+__host__ __device__ __forceinline__ uint64_t qpack(int job, int task, long long item) {
+    return (uint64_t)job << 60 | (uint64_t)(uint32_t)task << 28 | (uint64_t)item;
+}
 
 // Load rows [rs0, rs0+R) of stored columns [0, sw) of an off-diagonal tile into C.
 __device__ void load_off(double* C, const double* T, int nb, int rs0, int R, int sw) {
@@ -416,7 +431,7 @@ __device__ void potrf_smem(double* C, int w, int kd, double* sbuf, int* bad, dou
     __syncthreads();
 }
 
-__global__ void __launch_bounds__(kThreads, 1) replay_kernel(ReplayArgs a) {
+__global__ void __launch_bounds__(kThreads, 1) replay_kernel(const __grid_constant__ ReplayLaunch Lc) {
     extern __shared__ double smem[];
     double* C = smem;
     double* S0 = C + kCbuf;
@@ -424,24 +439,27 @@ __global__ void __launch_bounds__(kThreads, 1) replay_kernel(ReplayArgs a) {
     double* sv = S1 + kStage;  // kNbMax doubles
     __shared__ long long s_slot;
     __shared__ int s_ok;
-    const long long total = (long long)a.ntasks * a.batch;
-    const int nb = a.nb;
+    const long long total = Lc.total;
     for (;;) {
-        if (threadIdx.x == 0) s_slot = (long long)atomicAdd(&a.hdr->head, 1ULL);
+        if (threadIdx.x == 0) s_slot = (long long)atomicAdd(&Lc.hdr->head, 1ULL);
         __syncthreads();
         const long long slot = s_slot;
         __syncthreads();
         if (slot >= total) break;
-        int ti;
+        int ti, jb;
         long long item;
-        if (a.queue) {
-            const uint64_t e = a.queue[slot];
-            ti = (int)(e >> 32);
-            item = (long long)(e & 0xffffffffULL);
+        if (Lc.queue) {
+            const uint64_t e = Lc.queue[slot];
+            jb = (int)(e >> 60);
+            ti = (int)((e >> 28) & 0xffffffffULL);
+            item = (long long)(e & ((1ULL << 28) - 1));
         } else {
-            ti = (int)(slot / a.batch);
-            item = slot % a.batch;
+            jb = 0;
+            ti = (int)(slot / Lc.job[0].batch);
+            item = slot % Lc.job[0].batch;
         }
+        const ReplayArgs& a = Lc.job[jb];
+        const int nb = a.nb;
         const DTask t = a.tasks[ti];
         double* F = a.factor + item * a.fstride;
         int* cnt = a.counters + item * a.ntiles;
@@ -865,7 +883,6 @@ __global__ void __launch_bounds__(kThreads, 1) selinv_kernel(SelinvArgs a) {
     double* sv = S1 + kStage;
     __shared__ long long s_slot;
     __shared__ int s_ok;
-    __shared__ double s_red[32];
     const long long total = (long long)a.ntasks * a.batch;
     const int nb = a.nb;
     constexpr int LDS = kNbMax + 8;
@@ -1042,7 +1059,6 @@ __global__ void __launch_bounds__(kThreads, 1) selinv_kernel(SelinvArgs a) {
         __syncthreads();
         if (threadIdx.x == 0) red_release_add(cnt + t.tile, 1);
     }
-    (void)s_red;
 }
 
 // d logdet / d a_e = gout_b (2 - delta_e) Sigma_e, gathered through the value map.
@@ -1213,7 +1229,7 @@ int ensure_taskset(stc_plan* P, TaskSet* ts, int dev) {
 int ensure_queue(stc_plan* P, TaskSet* ts, int64_t batch, uint64_t** out) {
     *out = nullptr;
     const double skew = P->opt.queue_skew;
-    if (batch <= 1 || !(skew > 0.0) || batch > 0xffffffffLL) return STC_OK;
+    if (batch <= 1 || !(skew > 0.0) || batch >= (1LL << 28)) return STC_OK;
     std::lock_guard<std::mutex> g(P->mu);
     auto it = ts->d_queue.find(batch);
     if (it != ts->d_queue.end()) { *out = it->second; return STC_OK; }
@@ -1228,7 +1244,7 @@ int ensure_queue(stc_plan* P, TaskSet* ts, int64_t batch, uint64_t** out) {
     while (!h.empty()) {
         const int64_t b = h.top().second;
         h.pop();
-        q.push_back((uint64_t)pos[b] << 32 | (uint64_t)b);
+        q.push_back(qpack(0, (int)pos[b], b));
         if (++pos[b] < T) h.push(E(ts->qkey[pos[b]] + phi(b), b));
     }
     uint64_t* d = nullptr;
@@ -1240,6 +1256,16 @@ int ensure_queue(stc_plan* P, TaskSet* ts, int64_t batch, uint64_t** out) {
     ts->d_queue[batch] = d;
     *out = d;
     return STC_OK;
+}
+
+void fill_job(ReplayArgs& a, const stc_plan* P, const TaskSet* ts, void* d_factor, int* counters, int32_t* d_info,
+              int64_t batch, WorkHeader* hdr) {
+    a.tiles = ts->d_tiles; a.saind = P->dev.saind; a.tasks = ts->d_tasks; a.upds = ts->d_upds;
+    a.imap = ts->d_imap; a.factor = (double*)d_factor; a.fstride = P->factor_doubles;
+    a.poff = P->partial_off; a.hdr = hdr; a.counters = counters;
+    a.ntiles = (int)P->tiles.size(); a.info = d_info; a.ntasks = (int)ts->tasks.size();
+    a.batch = batch; a.nb = (int)P->nb;
+    a.spin = P->opt.spin_limit > 0 ? P->opt.spin_limit : kDefaultSpin;
 }
 
 size_t factorize_ws(const stc_plan* P, int64_t batch) {
@@ -1333,18 +1359,15 @@ extern "C" int stc_factorize_scattered(const stc_plan* Pc, int64_t batch, void* 
     cudaStream_t st = S(stream);
     if (cudaMemsetAsync(d_work, 0, factorize_ws(P, batch), st) != cudaSuccess) return STC_ERR_CUDA;
     if (cudaMemsetAsync(d_info, 0, (size_t)batch * sizeof(int32_t), st) != cudaSuccess) return STC_ERR_CUDA;
-    ReplayArgs a{};
-    a.tiles = ts->d_tiles; a.saind = P->dev.saind; a.tasks = ts->d_tasks; a.upds = ts->d_upds;
-    a.imap = ts->d_imap; a.factor = (double*)d_factor; a.fstride = P->factor_doubles;
-    a.poff = P->partial_off; a.hdr = (WorkHeader*)d_work;
-    a.counters = (int*)((char*)d_work + sizeof(WorkHeader));
-    a.ntiles = (int)P->tiles.size(); a.info = d_info; a.ntasks = (int)ts->tasks.size();
-    a.batch = batch; a.nb = (int)P->nb;
-    a.spin = P->opt.spin_limit > 0 ? P->opt.spin_limit : kDefaultSpin;
-    a.queue = queue;
-    const long long total = (long long)a.ntasks * batch;
-    const int grid = (int)std::max<long long>(1, std::min<long long>(sms, total));
-    replay_kernel<<<grid, kThreads, kSmemBytes, st>>>(a);
+    ReplayLaunch Lc{};
+    fill_job(Lc.job[0], P, ts, d_factor, (int*)((char*)d_work + sizeof(WorkHeader)), d_info, batch,
+             (WorkHeader*)d_work);
+    Lc.njobs = 1;
+    Lc.queue = queue;
+    Lc.hdr = (WorkHeader*)d_work;
+    Lc.total = (long long)ts->tasks.size() * batch;
+    const int grid = (int)std::max<long long>(1, std::min<long long>(sms, Lc.total));
+    replay_kernel<<<grid, kThreads, kSmemBytes, st>>>(Lc);
     return cudaGetLastError() == cudaSuccess ? STC_OK : STC_ERR_CUDA;
 }
 
@@ -1508,6 +1531,120 @@ extern "C" int stc_quad_form(const stc_plan* Pc, int64_t batch, const double* d_
 }
 
 // ---------------------------------------------------------------------------
+// Mixed batches of several plans in one launch.
+// ---------------------------------------------------------------------------
+struct stc_group {
+    std::vector<stc_plan*> plans;
+    std::vector<int64_t> batch;
+    std::vector<TaskSet*> ts;
+    std::vector<size_t> cnt_off;  // byte offset of each job's counters in the workspace
+    size_t ws_bytes = 0;
+    uint64_t* d_queue = nullptr;
+    long long total = 0;
+    int device = -1;
+};
+
+extern "C" int stc_group_create(int32_t nplans, const stc_plan* const* plans, const int64_t* batch,
+                                stc_group** out) {
+    if (!out) return STC_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (nplans < 1 || nplans > kMaxJobs || !plans || !batch) return STC_ERR_INVALID_ARG;
+    int dev, sms, rc;
+    if ((rc = device_info(&dev, &sms))) return rc;
+    auto g = std::make_unique<stc_group>();
+    g->device = dev;
+    int64_t btot = 0;
+    for (int p = 0; p < nplans; ++p) {
+        if (!plans[p] || batch[p] <= 0 || batch[p] >= (1LL << 28)) return STC_ERR_INVALID_ARG;
+        btot += batch[p];
+    }
+    size_t off = sizeof(WorkHeader);
+    for (int p = 0; p < nplans; ++p) {
+        stc_plan* P = const_cast<stc_plan*>(plans[p]);
+        if ((rc = ensure_plan(P, dev))) return rc;
+        TaskSet* ts = P->taskset(pick_slices(P, btot, sms));
+        if ((rc = ensure_taskset(P, ts, dev))) return rc;
+        g->plans.push_back(P);
+        g->batch.push_back(batch[p]);
+        g->ts.push_back(ts);
+        g->cnt_off.push_back(off);
+        off += ((size_t)batch[p] * P->tiles.size() * sizeof(int) + 255) / 256 * 256;
+    }
+    g->ws_bytes = off;
+    // merged queue: plans' task lists in earliest-start order, each task expanded to its
+    // plan's batch items in lockstep
+    std::vector<uint64_t> q;
+    size_t nslots = 0;
+    for (int p = 0; p < nplans; ++p) nslots += g->ts[p]->tasks.size() * (size_t)batch[p];
+    q.reserve(nslots);
+    typedef std::pair<double, int> E;
+    std::priority_queue<E, std::vector<E>, std::greater<E>> h;
+    std::vector<size_t> pos(nplans, 0);
+    for (int p = 0; p < nplans; ++p)
+        if (!g->ts[p]->tasks.empty()) h.push(E(g->ts[p]->qkey[0], p));
+    while (!h.empty()) {
+        const int p = h.top().second;
+        h.pop();
+        const size_t t = pos[p];
+        for (int64_t b = 0; b < batch[p]; ++b) q.push_back(qpack(p, (int)t, b));
+        if (++pos[p] < g->ts[p]->tasks.size()) h.push(E(g->ts[p]->qkey[pos[p]], p));
+    }
+    g->total = (long long)q.size();
+    if (cudaMalloc((void**)&g->d_queue, std::max<size_t>(1, q.size()) * sizeof(uint64_t)) != cudaSuccess)
+        return STC_ERR_OUT_OF_MEMORY;
+    if (!q.empty() && cudaMemcpy(g->d_queue, q.data(), q.size() * sizeof(uint64_t), cudaMemcpyHostToDevice) !=
+                          cudaSuccess) {
+        cudaFree(g->d_queue);
+        return STC_ERR_CUDA;
+    }
+    *out = g.release();
+    return STC_OK;
+}
+
+extern "C" size_t stc_group_workspace_bytes(const stc_group* g) { return g ? g->ws_bytes : 0; }
+
+extern "C" int stc_factorize_group(stc_group* g, const double* const* d_values, void* const* d_factor,
+                                   int32_t* const* d_info, void* d_work, void* stream) {
+    if (!g || !d_values || !d_factor || !d_info || !d_work) return STC_ERR_INVALID_ARG;
+    const int np = (int)g->plans.size();
+    for (int p = 0; p < np; ++p)
+        if (!d_values[p] || !d_factor[p] || !d_info[p]) return STC_ERR_INVALID_ARG;
+    int dev, sms, rc;
+    if ((rc = device_info(&dev, &sms))) return rc;
+    if (dev != g->device) return STC_ERR_INVALID_ARG;
+    cudaStream_t st = S(stream);
+    for (int p = 0; p < np; ++p)
+        if ((rc = stc_scatter_values(g->plans[p], d_values[p], g->batch[p], d_factor[p], stream))) return rc;
+    if (cudaMemsetAsync(d_work, 0, g->ws_bytes, st) != cudaSuccess) return STC_ERR_CUDA;
+    ReplayLaunch Lc{};
+    for (int p = 0; p < np; ++p) {
+        if (cudaMemsetAsync(d_info[p], 0, (size_t)g->batch[p] * sizeof(int32_t), st) != cudaSuccess)
+            return STC_ERR_CUDA;
+        fill_job(Lc.job[p], g->plans[p], g->ts[p], d_factor[p], (int*)((char*)d_work + g->cnt_off[p]), d_info[p],
+                 g->batch[p], (WorkHeader*)d_work);
+    }
+    Lc.njobs = np;
+    Lc.queue = g->d_queue;
+    Lc.hdr = (WorkHeader*)d_work;
+    Lc.total = g->total;
+    const int grid = (int)std::max<long long>(1, std::min<long long>(sms, Lc.total));
+    replay_kernel<<<grid, kThreads, kSmemBytes, st>>>(Lc);
+    return cudaGetLastError() == cudaSuccess ? STC_OK : STC_ERR_CUDA;
+}
+
+extern "C" void stc_group_destroy(stc_group* g) {
+    if (!g) return;
+    if (g->d_queue) {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (g->device >= 0 && g->device != cur) cudaSetDevice(g->device);
+        cudaFree(g->d_queue);
+        if (cur >= 0) cudaSetDevice(cur);
+    }
+    delete g;
+}
+
+// ---------------------------------------------------------------------------
 // Allocation-free factorization: the replay kernel's scratch (WorkHeader + per-tile
 // counters) comes from this fixed array instead of a caller workspace.  Host code
 // must not pass `g_noalloc_scratch` itself to a kernel (on the host that name is only
@@ -1561,19 +1698,17 @@ extern "C" int stc_factorize_noalloc(const stc_plan* Pc, const double* d_values,
     if ((rc = stc_scatter_values(P, d_values, batch, d_factor, stream))) return rc;
     if (cudaMemsetAsync(scratch, 0, need, st) != cudaSuccess) return STC_ERR_CUDA;
     if (cudaMemsetAsync(d_info, 0, (size_t)batch * sizeof(int32_t), st) != cudaSuccess) return STC_ERR_CUDA;
-    ReplayArgs a{};
-    a.tiles = ts->d_tiles; a.saind = P->dev.saind; a.tasks = ts->d_tasks; a.upds = ts->d_upds;
-    a.imap = ts->d_imap; a.factor = (double*)d_factor; a.fstride = P->factor_doubles;
-    a.poff = P->partial_off; a.hdr = (WorkHeader*)scratch;
-    a.counters = (int*)((char*)scratch + sizeof(WorkHeader));
-    a.ntiles = (int)P->tiles.size(); a.info = d_info; a.ntasks = (int)ts->tasks.size();
-    a.batch = batch; a.nb = (int)P->nb;
-    a.spin = P->opt.spin_limit > 0 ? P->opt.spin_limit : kDefaultSpin;
-    const long long total = (long long)a.ntasks * batch;
-    const int grid = (int)std::max<long long>(1, std::min<long long>(sms, total));
-    replay_kernel<<<grid, kThreads, kSmemBytes, st>>>(a);
+    ReplayLaunch Lc{};
+    fill_job(Lc.job[0], P, ts, d_factor, (int*)((char*)scratch + sizeof(WorkHeader)), d_info, batch,
+             (WorkHeader*)scratch);
+    Lc.njobs = 1;
+    Lc.queue = nullptr;
+    Lc.hdr = (WorkHeader*)scratch;
+    Lc.total = (long long)ts->tasks.size() * batch;
+    const int grid = (int)std::max<long long>(1, std::min<long long>(sms, Lc.total));
+    replay_kernel<<<grid, kThreads, kSmemBytes, st>>>(Lc);
     if (cudaGetLastError() != cudaSuccess) return STC_ERR_CUDA;
-    if (d_status && cudaMemcpyAsync(d_status, &a.hdr->status, sizeof(int32_t), cudaMemcpyDeviceToDevice, st) !=
+    if (d_status && cudaMemcpyAsync(d_status, &Lc.hdr->status, sizeof(int32_t), cudaMemcpyDeviceToDevice, st) !=
                         cudaSuccess)
         return STC_ERR_CUDA;
     return STC_OK;
