@@ -38,6 +38,7 @@ N, BW, NB = 200_000, 200, 128
 SMS, DFMA_PER_CLK, MAX_MHZ = 152, 2, 2070.0
 # nominal FP64 ALU peak from unit counts and the maximum SM clock (TFLOP/s)
 PEAK_FP64_NOMINAL = SMS * DFMA_PER_CLK * 2 * MAX_MHZ * 1e6 / 1e12
+HBM_GBS = 6678.5  # measured copy bandwidth of the GB300s (MEASURED_PEAKS.json)
 
 
 def parse():
@@ -189,14 +190,20 @@ def run_ours(args):
     ev = lambda: torch.cuda.Event(enable_timing=True)
 
     def step(vals, bvec, xout, rp=None):
-        L.check(L.stc_scatter_values(P.h, vals, batch, fac), "scatter")
         if rp is not None:
             rp[0].record(st)
-        L.check(L.stc_factorize_scattered(P.h, batch, fac, ws, info), "factorize")
+        L.check(L.stc_scatter_values(P.h, vals, batch, fac), "scatter")
         if rp is not None:
             rp[1].record(st)
+        L.check(L.stc_factorize_scattered(P.h, batch, fac, ws, info), "factorize")
+        if rp is not None:
+            rp[2].record(st)
         L.check(L.stc_logdet(P.h, fac, batch, ld), "logdet")
+        if rp is not None:
+            rp[3].record(st)
         L.check(L.stc_solve(P.h, fac, batch, 1, bvec, xout, ws), "solve")
+        if rp is not None:
+            rp[4].record(st)
 
     def barrier():
         torch.cuda.synchronize()
@@ -216,7 +223,7 @@ def run_ours(args):
     assert int(info.abs().sum()) == 0 and bool(torch.isfinite(ld).all())
     # ---- timed, inputs resident in HBM
     clocks = Clocks(local) if rank == 0 else None
-    rps = [(ev(), ev()) for _ in range(args.steps)]
+    rps = [tuple(ev() for _ in range(5)) for _ in range(args.steps)]
     barrier()
     e0, e1 = ev(), ev()
     e0.record(st)
@@ -226,7 +233,10 @@ def run_ours(args):
     barrier()
     ck = clocks.stop() if clocks else None
     ms_step = e0.elapsed_time(e1) / args.steps
-    ms_replay = sum(a.elapsed_time(b) for a, b in rps) / args.steps
+    ms_scatter = sum(r[0].elapsed_time(r[1]) for r in rps) / args.steps
+    ms_replay = sum(r[1].elapsed_time(r[2]) for r in rps) / args.steps
+    ms_logdet = sum(r[2].elapsed_time(r[3]) for r in rps) / args.steps
+    ms_solve = sum(r[3].elapsed_time(r[4]) for r in rps) / args.steps
     L.check(L.stc_sync_status(ws), "device status")
     # ---- e2e: host buffers in, logdet + x back out, every step
     e2e_ms = 0.0
@@ -279,6 +289,9 @@ def run_ours(args):
         if dist is not None:
             dist.destroy_process_group()
         return
+    stored = P.info["stored_entries"]
+    scat_bytes = P.factor_bytes(batch) + batch * nnz * 16 + nnz * 8
+    solve_bytes = batch * (2 * stored * 8 + 2 * n * 8)
     total_items = batch * world
     value = total_items / (ms_step * 1e-3)
     flops_alg = P.info["flops_alg"]
@@ -302,6 +315,17 @@ def run_ours(args):
                      "frac_of_measured_dfma": achieved / (dfma_gflops / 1e3),
                      "tile_flops_per_factorization": P.info["flops_tile"],
                      "ms_replay": ms_replay},
+        "kernels": {
+            "scatter_kernel": {"ms": ms_scatter, "bound": "hbm", "unit": "GB/s",
+                               "achieved": scat_bytes / (ms_scatter * 1e-3) / 1e9,
+                               "peak": HBM_GBS, "frac": scat_bytes / (ms_scatter * 1e-3) / 1e9 / HBM_GBS,
+                               "work": "zero-fill of the factor + values read + map read + scattered writes"},
+            "solve_kernel": {"ms": ms_solve, "bound": "hbm", "unit": "GB/s",
+                             "achieved": solve_bytes / (ms_solve * 1e-3) / 1e9,
+                             "peak": HBM_GBS, "frac": solve_bytes / (ms_solve * 1e-3) / 1e9 / HBM_GBS,
+                             "work": "factor tiles read twice (forward + backward) + b, x"},
+            "logdet_kernel": {"ms": ms_logdet},
+        },
         "gpu_launches": 4 * args.steps,
         "clocks": ck,
         "analyze_seconds": P.info["analyze_seconds"],

@@ -155,10 +155,11 @@ def stcov_values(theta, nx: int = 60, ny: int = 60, nt: int = 50, nborder: int =
 def stcov_dtheta(theta, nx: int = 60, ny: int = 60, nt: int = 50, nborder: int = 20):
     """dQ/d(tau, rho, kappa) on stcov_pattern's lower CSC pattern, shape [3, nnz].
 
-    The border block does not depend on theta.
+    The border block does not depend on theta.  Each derivative matrix is placed on the
+    pattern by matching (column, row) keys, so pattern entries a derivative does not
+    touch get 0.
     """
     tau, rho, kappa = (float(v) for v in theta)
-    nf = nx * ny * nt
     R = ar1_precision(nt, rho)
     S = _spde(nx, ny, kappa)
     dR = sp.diags([np.full(nt - 1, -1.0), np.r_[0.0, np.full(nt - 2, 2.0 * rho), 0.0],
@@ -168,17 +169,16 @@ def stcov_dtheta(theta, nx: int = 60, ny: int = 60, nt: int = 50, nborder: int =
     dS = 2.0 * kappa * (sp.kron(sp.identity(ny), Kx) + sp.kron(Ky, sp.identity(nx)))
     mats = [sp.kron(R, S), tau * sp.kron(dR, S), tau * sp.kron(R, dS)]
     Ap, Ai, _ = stcov_pattern(nx, ny, nt, nborder)
-    n = nf + nborder
+    n = len(Ap) - 1
+    pkey = np.repeat(np.arange(n, dtype=np.int64), np.diff(Ap)) * n + Ai
     out = np.zeros((3, Ai.shape[0]))
-    col = np.repeat(np.arange(n), np.diff(Ap))
     for k, M in enumerate(mats):
-        M = sp.csr_matrix(M)
-        # entries of the field block on the (bigger) pattern; border entries stay 0
-        Mf = sp.bmat([[M, None], [None, sp.csr_matrix((nborder, nborder))]], format="csc") \
-            if nborder else sp.csc_matrix(M)
-        Mf = Mf.tocsc()
-        vals = np.asarray(Mf[Ai, col]).ravel()
-        out[k] = vals
+        Mp, Mi, Mx = lower_csc(M)
+        mkey = np.repeat(np.arange(Mp.shape[0] - 1, dtype=np.int64), np.diff(Mp)) * n + Mi
+        pos = np.searchsorted(pkey, mkey)
+        if np.any(pos >= len(pkey)) or np.any(pkey[np.minimum(pos, len(pkey) - 1)] != mkey):
+            raise AssertionError("derivative entry outside the pattern")
+        out[k, pos] = Mx
     return out
 
 
