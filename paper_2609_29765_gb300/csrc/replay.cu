@@ -698,14 +698,80 @@ struct SolveArgs {
 };
 
 constexpr int kSolveWarps = kThreads / 32;
-constexpr size_t kSolveSmem = (size_t)(kLdc * kNbMax + kNbMax * (kSolveWarps + 2)) * sizeof(double);
+constexpr size_t kSolveSmem = (size_t)kLdc * kNbMax * sizeof(double);
+
+// Diagonal-block substitution, panels of 32: warp 0 solves the panel's 32x32 triangle
+// with its rows (forward) or columns (backward) in registers, one lane per row/column,
+// pivots broadcast by shuffle; the rows below (forward) or above (backward) the panel
+// are then updated with one thread per row.  v holds the right-hand side and is
+// overwritten by the solution.
+template <bool BACK>
+__device__ void diag_solve(double* v, const double* Ls, const DTile& D, int nb, int w) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int kd = min(D.kd, nb - 1);
+    const int np = (w + 31) / 32;
+    for (int qi = 0; qi < np; ++qi) {
+        const int p = BACK ? (np - 1 - qi) * 32 : qi * 32;
+        const int pw = min(32, w - p);
+        if (warp == 0) {
+            double Lr[32];
+            double vi = 0.0, dinv = 1.0;
+            if (lane < pw) {
+#pragma unroll
+                for (int l = 0; l < 32; ++l) {
+                    // forward: row p+lane, columns p+l <= row; backward: column p+lane, rows p+l >= it
+                    const int r = BACK ? p + l : p + lane, c = BACK ? p + lane : p + l;
+                    Lr[l] = (l < pw && r >= c) ? Ls[r + c * kLdc] : 0.0;
+                }
+                vi = v[p + lane];
+                dinv = 1.0 / Ls[(p + lane) * (kLdc + 1)];
+            } else {
+#pragma unroll
+                for (int l = 0; l < 32; ++l) Lr[l] = 0.0;
+            }
+#pragma unroll
+            for (int jj = 0; jj < 32; ++jj) {
+                const int j = BACK ? 31 - jj : jj;
+                if (j < pw) {
+                    const double yj = __shfl_sync(0xffffffffu, vi * dinv, j);
+                    if (lane == j) vi = yj;
+                    if (!BACK && lane > j) vi = fma(-Lr[j], yj, vi);
+                    if (BACK && lane < j) vi = fma(-Lr[j], yj, vi);
+                }
+            }
+            if (lane < pw) v[p + lane] = vi;
+        }
+        __syncthreads();
+        if (!BACK) {
+            const int rend = min(w, p + pw + kd);
+            for (int r = p + pw + threadIdx.x; r < rend; r += kThreads) {
+                double s0 = v[r], s1 = 0.0;
+                for (int l = 0; l < pw; l += 2) {
+                    s0 = fma(-Ls[r + (p + l) * kLdc], v[p + l], s0);
+                    if (l + 1 < pw) s1 = fma(-Ls[r + (p + l + 1) * kLdc], v[p + l + 1], s1);
+                }
+                v[r] = s0 + s1;
+            }
+        } else {
+            const int cbeg = max(0, p - kd);
+            for (int c = cbeg + threadIdx.x; c < p; c += kThreads) {
+                double s0 = v[c], s1 = 0.0;
+                for (int l = 0; l < pw; l += 2) {
+                    s0 = fma(-Ls[p + l + c * kLdc], v[p + l], s0);
+                    if (l + 1 < pw) s1 = fma(-Ls[p + l + 1 + c * kLdc], v[p + l + 1], s1);
+                }
+                v[c] = s0 + s1;
+            }
+        }
+        __syncthreads();
+    }
+}
 
 __global__ void __launch_bounds__(kThreads, 1) solve_kernel(SolveArgs a) {
     extern __shared__ double smem[];
-    double* Ls = smem;                          // diagonal tile, L(r,c) at r + c*kLdc
-    double* acc = Ls + kLdc * kNbMax;           // [kSolveWarps][nb] partial sums
-    double* v = acc + kSolveWarps * kNbMax;     // block right-hand side
-    double* dinv = v + kNbMax;
+    double* Ls = smem;                             // diagonal tile, L(r,c) at r + c*kLdc
+    __shared__ double acc[kSolveWarps * kNbMax];   // per-warp partial sums
+    __shared__ double v[kNbMax];                   // block right-hand side / solution
     __shared__ long long s_slot;
     __shared__ int s_ok;
     const long long total = 2LL * a.nt * a.chains;
@@ -739,6 +805,7 @@ __global__ void __launch_bounds__(kThreads, 1) solve_kernel(SolveArgs a) {
             }
             __syncthreads();
             if (fwd) {
+                // acc -= L_kn y_n over the off-diagonal tiles of block row k
                 for (int q = a.rowstart[k]; q < a.rowstart[k + 1]; ++q) {
                     const DTile T = a.tiles[a.rowtiles[q]];
                     if (threadIdx.x == 0) s_ok = wait_counter(done + T.J, 1, a.spin, &a.hdr->status);
@@ -754,6 +821,7 @@ __global__ void __launch_bounds__(kThreads, 1) solve_kernel(SolveArgs a) {
                     __syncthreads();
                 }
             } else {
+                // acc -= L_mk^T z_m over the tiles below the diagonal in block column k
                 for (int q = a.colstart[k]; q < a.colstart[k + 1]; ++q) {
                     const DTile T = a.tiles[q];
                     if (T.I == T.J) continue;
@@ -773,52 +841,18 @@ __global__ void __launch_bounds__(kThreads, 1) solve_kernel(SolveArgs a) {
                 }
             }
             for (int r = threadIdx.x; r < nb; r += kThreads) {
-                double s = v[r];
-                for (int w = 0; w < kSolveWarps; ++w) s += acc[w * nb + r];
-                v[r] = s;
-                dinv[r] = 1.0 / Ls[r + r * kLdc];
+                double sacc = v[r];
+                for (int w2 = 0; w2 < kSolveWarps; ++w2) sacc += acc[w2 * nb + r];
+                v[r] = sacc;
             }
             __syncthreads();
-            if (s_ok && warp == 0) {
-                // rows lane, lane+32, lane+64, lane+96 live in registers
-                double rv[kNbMax / 32];
-#pragma unroll
-                for (int q = 0; q < kNbMax / 32; ++q) rv[q] = (lane + 32 * q < nb) ? v[lane + 32 * q] : 0.0;
-                if (fwd) {
-                    for (int j = 0; j < nb; ++j) {
-                        double own = 0.0;
-#pragma unroll
-                        for (int q = 0; q < kNbMax / 32; ++q) if (q == (j >> 5)) own = rv[q];
-                        const double yj = __shfl_sync(0xffffffffu, own, j & 31) * dinv[j];
-#pragma unroll
-                        for (int q = 0; q < kNbMax / 32; ++q) {
-                            const int i = lane + 32 * q;
-                            if (i == j) rv[q] = yj;
-                            else if (i > j && i < nb) rv[q] = fma(-Ls[i + j * kLdc], yj, rv[q]);
-                        }
-                    }
-                } else {
-                    for (int j = nb - 1; j >= 0; --j) {
-                        double own = 0.0;
-#pragma unroll
-                        for (int q = 0; q < kNbMax / 32; ++q) if (q == (j >> 5)) own = rv[q];
-                        const double zj = __shfl_sync(0xffffffffu, own, j & 31) * dinv[j];
-#pragma unroll
-                        for (int q = 0; q < kNbMax / 32; ++q) {
-                            const int i = lane + 32 * q;
-                            if (i == j) rv[q] = zj;
-                            else if (i < j) rv[q] = fma(-Ls[j + i * kLdc], zj, rv[q]);
-                        }
-                    }
-                }
-#pragma unroll
-                for (int q = 0; q < kNbMax / 32; ++q) {
-                    const int i = lane + 32 * q;
-                    if (i < nb) {
-                        __stcg(y + (long long)k * nb + i, rv[q]);
-                        const long long g = (long long)k * nb + i;
-                        if (!fwd && g < a.n) a.x[ch * a.n + a.perm[g]] = rv[q];
-                    }
+            if (s_ok) {
+                if (fwd) diag_solve<false>(v, Ls, D, nb, nb);
+                else diag_solve<true>(v, Ls, D, nb, nb);
+                for (int i = threadIdx.x; i < nb; i += kThreads) {
+                    __stcg(y + (long long)k * nb + i, v[i]);
+                    const long long g = (long long)k * nb + i;
+                    if (!fwd && g < a.n) a.x[ch * a.n + a.perm[g]] = v[i];
                 }
             }
         }
@@ -1139,9 +1173,9 @@ int device_info(int* dev, int* sms) {
         if (cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, *dev) != cudaSuccess) return STC_ERR_CUDA;
         if (cudaFuncSetAttribute(replay_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes) != cudaSuccess)
             return STC_ERR_CUDA;
-        if (cudaFuncSetAttribute(solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSolveSmem) != cudaSuccess)
-            return STC_ERR_CUDA;
         if (cudaFuncSetAttribute(selinv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes) != cudaSuccess)
+            return STC_ERR_CUDA;
+        if (cudaFuncSetAttribute(solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSolveSmem) != cudaSuccess)
             return STC_ERR_CUDA;
         d.attr_set = true;
     }
