@@ -440,11 +440,14 @@ stc::TaskSet* stc_plan::taskset(int32_t slices) {
     auto it = tasksets.find(slices);
     if (it != tasksets.end()) return it->second.get();
     auto ts = std::make_unique<stc::TaskSet>();
-    ts->slices = slices;
     const int64_t NT = nt;
     const int NB = (int)nb;
-    int h = (NB + slices - 1) / slices;
+    // a device task holds at most 64 rows of an off-diagonal or SYRK tile
+    const int32_t eff = std::max<int32_t>(slices, (NB + 63) / 64);
+    ts->slices = eff;
+    int h = (NB + eff - 1) / eff;
     h = (h + 7) / 8 * 8;
+    if (h > 64) h = 64;
     // tasks in Algorithm-1 (topological) order first, with the model inputs of each:
     // the source tiles its updates wait for (in order) and the final dependency
     struct Meta {
@@ -467,7 +470,7 @@ stc::TaskSet* stc_plan::taskset(int32_t slices) {
         const int32_t dk = diag_tile[k];
         const stc::DTile& D = tiles[dk];
         const bool has_syrk = rowstart[k + 1] > rowstart[k];
-        if (slices == 1 || !has_syrk) {
+        if (eff == 1 || !has_syrk) {
             // TASK_DIAG: every SYRK from (k,n), n < k, then POTRF
             stc::DTask t{};
             Meta mt;
@@ -491,10 +494,30 @@ stc::TaskSet* stc_plan::taskset(int32_t slices) {
             meta.push_back(mt);
             ts->nfinal[dk] = 1;
         } else {
-            // TASK_SYRK row slices of (k,k), then TASK_POTRF
+            // TASK_SYRK row slices of (k,k), then TASK_POTRF.  Row r of the lower
+            // triangle costs ~(r+1): slices are cut (on 8-row boundaries, at most 64 rows)
+            // so that each carries about 1/eff of the triangle's work.
+            vector<int> cuts{0};
+            {
+                const double target = double(D.sw) * (D.sw + 1) / 2.0 / eff;
+                double accum = 0.0;
+                int start = 0;
+                for (int r = 0; r < D.sw; ++r) {
+                    accum += r + 1;
+                    const int len = r + 1 - start;
+                    if (r + 1 < D.sw && (len % 8 == 0) && (accum >= target || len >= 64)) {
+                        cuts.push_back(r + 1);
+                        start = r + 1;
+                        accum = 0.0;
+                    }
+                }
+                cuts.push_back(D.sw);
+            }
             int nsl = 0;
-            for (int rs0 = 0; rs0 < D.sw; rs0 += h) {
-                const int rs1 = std::min(D.sw, rs0 + h);
+            for (size_t ci = 0; ci + 1 < cuts.size(); ++ci) {
+                const int rs0 = cuts[ci];
+                const int rs1 = cuts[ci + 1];
+                if (rs1 <= rs0) continue;
                 stc::DTask t{};
                 Meta mt;
                 t.kind = stc::TASK_SYRK; t.tile = dk; t.diag = dk;

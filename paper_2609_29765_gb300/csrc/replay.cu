@@ -40,6 +40,22 @@ constexpr int kSmemDoubles = kCbuf + 2 * kStage + kNbMax;
 constexpr size_t kSmemBytes = kSmemDoubles * sizeof(double) + 64;
 constexpr long long kDefaultSpin = 40000000LL;
 
+// Replay-kernel geometry, sized for two resident CTAs per SM (so one CTA's dependency
+// waits and latency-bound phases overlap the other's DFMA work): off-diagonal and SYRK
+// tasks hold at most kRRows rows, diagonal tiles are held as a packed lower triangle,
+// and the inner dimension is staged 16 columns at a time.
+constexpr int kRRows = 64;
+constexpr int kRLd = kRRows + 1;
+constexpr int kRKc = 16;
+constexpr int kRStLd = kNbMax + 8;
+constexpr int kRStage = kRKc * kRStLd;
+constexpr int kRPacked = kNbMax * (kNbMax + 1) / 2;
+constexpr int kRCbuf = (kRLd * kNbMax > kRPacked ? kRLd * kNbMax : kRPacked) + 16;
+constexpr size_t kRSmemBytes = (size_t)(kRCbuf + 2 * kRStage + kNbMax) * sizeof(double);
+
+// packed lower triangle of an nb x nb tile, column-major: (r, c), r >= c
+__host__ __device__ __forceinline__ int pk(int nb, int r, int c) { return c * nb - (c * (c + 1)) / 2 + r; }
+
 struct WorkHeader {          // start of the caller's workspace
     unsigned long long head; // next task slot
     int status;              // STC_OK or STC_ERR_TIMEOUT
@@ -110,13 +126,14 @@ __device__ __forceinline__ void for_rc(int R, int NC, Fn f) {
 // r >= c (rows and columns index the same range) are computed, and only r >= c is
 // written.  A/B rows up to the next multiple of 4 must be readable (pad).
 // ---------------------------------------------------------------------------
-template <bool LOWER, int TR, int TC>
+template <bool LOWER, int TR, int TC, bool PACKED>
 __device__ void mma_tiles(double* __restrict__ C, int ldc, int R, int Cn,
                           const double* __restrict__ A, int lda,
-                          const double* __restrict__ B, int ldb, int K) {
+                          const double* __restrict__ B, int ldb, int K, int pnb, int pr0, int pc0,
+                          int tid0 = 0, int nthr = kThreads) {
     const int MR = (R + TR - 1) / TR, MC = (Cn + TC - 1) / TC;
     const int count = LOWER ? MR * (MR + 1) / 2 : MR * MC;
-    for (int mt = threadIdx.x; mt < count; mt += kThreads) {
+    for (int mt = (int)threadIdx.x - tid0; mt < count; mt += nthr) {
         int ri, cj;
         if (LOWER) {
             // mt -> (ri, cj), cj <= ri, row-major over the lower triangle
@@ -156,7 +173,10 @@ __device__ void mma_tiles(double* __restrict__ C, int ldc, int R, int Cn,
 #pragma unroll
             for (int j = 0; j < TC; ++j) {
                 const int r = r0 + i, c = c0 + j;
-                if (r < R && c < Cn && (!LOWER || r >= c)) C[r + c * ldc] -= acc[i][j];
+                if (r < R && c < Cn && (!LOWER || r >= c)) {
+                    if (PACKED) C[pk(pnb, pr0 + r, pc0 + c)] -= acc[i][j];
+                    else C[r + c * ldc] -= acc[i][j];
+                }
             }
     }
 }
@@ -169,9 +189,24 @@ __device__ __forceinline__ void mma_sub(double* C, int ldc, int R, int Cn, const
     const int m4 = (R + 3) >> 2, n4 = (Cn + 3) >> 2;
     const int c44 = LOWER ? m4 * (m4 + 1) / 2 : m4 * n4;
     if (c44 >= (kThreads * 3) / 4)
-        mma_tiles<LOWER, 4, 4>(C, ldc, R, Cn, A, lda, B, ldb, K);
+        mma_tiles<LOWER, 4, 4, false>(C, ldc, R, Cn, A, lda, B, ldb, K, 0, 0, 0);
     else
-        mma_tiles<LOWER, 2, 2>(C, ldc, R, Cn, A, lda, B, ldb, K);
+        mma_tiles<LOWER, 2, 2, false>(C, ldc, R, Cn, A, lda, B, ldb, K, 0, 0, 0);
+}
+
+// Same into a packed lower triangle P (pk layout, tile width pnb); the region starts at
+// (pr0, pc0) of the tile.
+template <bool LOWER>
+__device__ __forceinline__ void mma_sub_packed(double* P, int pnb, int pr0, int pc0, int R, int Cn,
+                                               const double* A, int lda, const double* B, int ldb, int K,
+                                               int tid0 = 0, int nthr = kThreads) {
+    if ((int)threadIdx.x < tid0 || (int)threadIdx.x >= tid0 + nthr) return;
+    const int m4 = (R + 3) >> 2, n4 = (Cn + 3) >> 2;
+    const int c44 = LOWER ? m4 * (m4 + 1) / 2 : m4 * n4;
+    if (c44 >= (nthr * 3) / 4)
+        mma_tiles<LOWER, 4, 4, true>(P, 0, R, Cn, A, lda, B, ldb, K, pnb, pr0, pc0, tid0, nthr);
+    else
+        mma_tiles<LOWER, 2, 2, true>(P, 0, R, Cn, A, lda, B, ldb, K, pnb, pr0, pc0, tid0, nthr);
 }
 
 // Forward substitution of a row block against a panel: X(r, 0:pw) <- X(r, 0:pw) D^{-T},
@@ -269,11 +304,29 @@ __host__ __device__ __forceinline__ uint64_t qpack(int job, int task, long long 
 }
 
 // Load rows [rs0, rs0+R) of stored columns [0, sw) of an off-diagonal tile into C.
-__device__ void load_off(double* C, const double* T, int nb, int rs0, int R, int sw) {
-    for_rc(R, sw, [&](int r, int c) { C[r + c * kLdc] = __ldcg(T + rs0 + r + (size_t)c * nb); });
+__device__ void load_off(double* C, int ldc, const double* T, int nb, int rs0, int R, int sw) {
+    for_rc(R, sw, [&](int r, int c) { C[r + c * ldc] = __ldcg(T + rs0 + r + (size_t)c * nb); });
 }
-__device__ void store_off(const double* C, double* T, int nb, int rs0, int R, int sw) {
-    for_rc(R, sw, [&](int r, int c) { __stcg(T + rs0 + r + (size_t)c * nb, C[r + c * kLdc]); });
+__device__ void store_off(const double* C, int ldc, double* T, int nb, int rs0, int R, int sw) {
+    for_rc(R, sw, [&](int r, int c) { __stcg(T + rs0 + r + (size_t)c * nb, C[r + c * ldc]); });
+}
+
+// Diagonal tile <-> packed lower triangle in shared memory.
+__device__ void load_diag_packed(double* P, const double* T, const DTile& d, int nb) {
+    for_rc(nb, nb, [&](int r, int c) {
+        if (r >= c) P[pk(nb, r, c)] = diag_at(T, d, nb, r, c);
+    });
+}
+__device__ void store_diag_packed(const double* P, double* T, const DTile& d, int nb) {
+    if (d.kind == TILE_DIAG_DENSE) {
+        for_rc(nb, nb, [&](int r, int c) { __stcg(T + r + (size_t)c * nb, r >= c ? P[pk(nb, r, c)] : 0.0); });
+    } else {
+        const int w = d.kd + 1;
+        for_rc(w, nb, [&](int q, int r) {  // storage (q, r): L[r][r - kd + q]
+            const int c = r - d.kd + q;
+            if (c >= 0) __stcg(T + q + (size_t)r * w, P[pk(nb, r, c)]);
+        });
+    }
 }
 
 // Full lower triangle (and zero upper) of a diagonal tile into C.
@@ -325,118 +378,160 @@ __device__ void stage_rows_gather(double* S, int ld, const double* T, int nb, co
     });
 }
 
-// Blocked right-looking Cholesky of the w x w leading block of C (lower) in shared
-// memory, panel width kPp = 8.  Per panel: warp 0 factors the 8x8 diagonal block in
-// registers (one row per lane, pivots broadcast by shuffle); the rows below the block
-// are solved against it, one row per thread; the rank-8 update of the trailing lower
-// triangle runs on every warp.  Rows more than kd below the diagonal are structurally
-// zero and skipped.  *bad receives the first non-positive pivot column (or -1);
-// *logsum = sum_j log L_jj, kept as a mantissa product and an exponent sum.
+// Blocked right-looking Cholesky of the w x w leading block of the packed lower
+// triangle P (pk layout, tile width nb) in shared memory, panel width kPp = 8, with a
+// one-panel look-ahead.  Per panel: warp 0 factors the 8x8 diagonal block in registers
+// (one row per lane, pivots broadcast by shuffle); the rows below the block are solved
+// against it, one row per thread, and copied to the staging buffer S; then the next
+// panel's columns get the rank-8 update first, so that warp 0 can factor the next
+// diagonal block while warps 1-7 apply the rest of the trailing update.  Rows more than
+// kd below the diagonal are structurally zero and skipped.  *bad receives the first
+// non-positive pivot column (or -1); *logsum = sum_j log L_jj, kept as a mantissa product
+// and an exponent sum.
 constexpr int kPp = 8;
 
-__device__ void potrf_smem(double* C, int w, int kd, double* sbuf, int* bad, double* logsum) {
-    __shared__ double s_blk[kPp][kPp];  // L of the panel's diagonal block, s_blk[row][col]
-    __shared__ double s_inv[kPp];       // 1 / L_jj of the panel
-    __shared__ double s_mant;
-    __shared__ int s_exp, s_bad;
-    (void)sbuf;
-    if (threadIdx.x == 0) { s_mant = 1.0; s_exp = 0; s_bad = -1; }
-    __syncthreads();
-    const int tid = threadIdx.x;
-    for (int p = 0; p < w; p += kPp) {
-        const int pw = min(kPp, w - p);
-        const int rend = min(w, p + pw + kd);  // panel rows inside the band: [p, rend)
-        // (1) warp 0: unblocked Cholesky of the pw x pw diagonal block
-        if (tid < 32) {
-            const int lane = tid;
-            double x[kPp];
+struct PotrfShared {
+    double blk[kPp][kPp];  // L of the current panel's diagonal block, blk[row][col]
+    double inv[kPp];       // 1 / L_jj of the panel
+    double mant;
+    int exp, bad;
+};
+
+// Warp 0 only: unblocked Cholesky of the pw x pw diagonal block at (p, p).
+__device__ void potrf_diag_block(double* P, int nb, int p, int pw, PotrfShared& sh) {
+    const int lane = threadIdx.x;
+    double x[kPp];
 #pragma unroll
-            for (int l = 0; l < kPp; ++l) x[l] = (lane < pw && l <= lane) ? C[p + lane + (p + l) * kLdc] : 0.0;
-            double mant = s_mant;
-            int ex = s_exp, badl = -1;
+    for (int l = 0; l < kPp; ++l) x[l] = (lane < pw && l <= lane) ? P[pk(nb, p + lane, p + l)] : 0.0;
+    int badl = -1;
 #pragma unroll
-            for (int j = 0; j < kPp; ++j) {
-                if (j < pw) {
-                    double inv = 0.0;
-                    if (lane == j) {
-                        const double d = x[j];
-                        if (!(d > 0.0)) badl = p + j;
-                        inv = rsqrt(d);
-                        x[j] = d * inv;
-                    }
-                    inv = __shfl_sync(0xffffffffu, inv, j);
-                    if (lane > j) x[j] *= inv;
-#pragma unroll
-                    for (int l = j + 1; l < kPp; ++l) {
-                        const double llj = __shfl_sync(0xffffffffu, x[j], l);  // L[p+l][p+j]
-                        if (l < pw && lane >= l) x[l] = fma(-x[j], llj, x[l]);
-                    }
-                    if (lane == j) s_inv[j] = inv;
-                }
+    for (int j = 0; j < kPp; ++j) {
+        if (j < pw) {
+            double inv = 0.0;
+            if (lane == j) {
+                const double d = x[j];
+                if (!(d > 0.0)) badl = p + j;
+                inv = rsqrt(d);
+                x[j] = d * inv;
             }
-            if (lane < pw) {
+            inv = __shfl_sync(0xffffffffu, inv, j);
+            if (lane > j) x[j] *= inv;
 #pragma unroll
-                for (int l = 0; l < kPp; ++l) s_blk[lane][l] = l <= lane ? x[l] : 0.0;
-#pragma unroll
-                for (int l = 0; l < kPp; ++l)
-                    if (l <= lane) C[p + lane + (p + l) * kLdc] = x[l];
+            for (int l = j + 1; l < kPp; ++l) {
+                const double llj = __shfl_sync(0xffffffffu, x[j], l);  // L[p+l][p+j]
+                if (l < pw && lane >= l) x[l] = fma(-x[j], llj, x[l]);
             }
-            // bad pivot (first one) and the logdet state live in lanes 0..pw-1
-#pragma unroll
-            for (int j = 0; j < kPp; ++j) {
-                const int bj = __shfl_sync(0xffffffffu, badl, j);
-                if (lane == 0 && j < pw && bj >= 0 && s_bad < 0) s_bad = bj;
-            }
-#pragma unroll
-            for (int j = 0; j < kPp; ++j) {
-                const double ljj = __shfl_sync(0xffffffffu, x[j], j);
-                if (lane == 0 && j < pw) {
-                    int e;
-                    mant = frexp(mant * ljj, &e);
-                    ex += e;
-                }
-            }
-            if (lane == 0) { s_mant = mant; s_exp = ex; }
+            if (lane == j) sh.inv[j] = inv;
         }
-        __syncthreads();
-        // (2) rows below the block: x <- x * L_pp^{-T}, one row per thread
-        for (int i = p + pw + tid; i < rend; i += kThreads) {
-            double x[kPp];
+    }
+    if (lane < pw) {
 #pragma unroll
-            for (int l = 0; l < kPp; ++l) x[l] = l < pw ? C[i + (p + l) * kLdc] : 0.0;
+        for (int l = 0; l < kPp; ++l) sh.blk[lane][l] = l <= lane ? x[l] : 0.0;
+#pragma unroll
+        for (int l = 0; l < kPp; ++l)
+            if (l <= lane) P[pk(nb, p + lane, p + l)] = x[l];
+    }
+    double mant = sh.mant;
+    int ex = sh.exp;
+#pragma unroll
+    for (int j = 0; j < kPp; ++j) {
+        const int bj = __shfl_sync(0xffffffffu, badl, j);
+        const double ljj = __shfl_sync(0xffffffffu, x[j], j);
+        if (lane == 0 && j < pw) {
+            if (bj >= 0 && sh.bad < 0) sh.bad = bj;
+            int e;
+            mant = frexp(mant * ljj, &e);
+            ex += e;
+        }
+    }
+    if (lane == 0) { sh.mant = mant; sh.exp = ex; }
+}
+
+// All threads: rows [p+pw, rend) of panel p solved against the diagonal block; the solved
+// rows also go to S (row i at S[i - p - pw], column l at stride kRStLd), zero-padded.
+__device__ void potrf_rows_below(double* P, int nb, int p, int pw, int rend, double* S, const PotrfShared& sh) {
+    const int R2 = rend - p - pw;
+    const int R2p = ((max(R2, 0) + 3) & ~3) + 4;
+    for (int rr = threadIdx.x; rr < R2p; rr += kThreads) {
+        const int i = p + pw + rr;
+        double x[kPp];
+        if (rr < R2) {
+#pragma unroll
+            for (int l = 0; l < kPp; ++l) x[l] = l < pw ? P[pk(nb, i, p + l)] : 0.0;
 #pragma unroll
             for (int j = 0; j < kPp; ++j) {
                 if (j < pw) {
                     double sacc = x[j];
 #pragma unroll
-                    for (int l = 0; l < j; ++l) sacc = fma(-x[l], s_blk[j][l], sacc);
-                    x[j] = sacc * s_inv[j];
+                    for (int l = 0; l < j; ++l) sacc = fma(-x[l], sh.blk[j][l], sacc);
+                    x[j] = sacc * sh.inv[j];
                 }
             }
 #pragma unroll
             for (int l = 0; l < kPp; ++l)
-                if (l < pw) C[i + (p + l) * kLdc] = x[l];
+                if (l < pw) P[pk(nb, i, p + l)] = x[l];
+        } else {
+#pragma unroll
+            for (int l = 0; l < kPp; ++l) x[l] = 0.0;
+        }
+#pragma unroll
+        for (int l = 0; l < kPp; ++l) S[rr + l * kRStLd] = x[l];
+    }
+}
+
+__device__ void potrf_packed(double* P, int nb, int w, int kd, double* S, int* bad, double* logsum) {
+    __shared__ PotrfShared sh;
+    if (threadIdx.x == 0) { sh.mant = 1.0; sh.exp = 0; sh.bad = -1; }
+    __syncthreads();
+    // panel 0
+    {
+        const int pw = min(kPp, w);
+        if (threadIdx.x < 32) potrf_diag_block(P, nb, 0, pw, sh);
+        __syncthreads();
+        potrf_rows_below(P, nb, 0, pw, min(w, pw + kd), S, sh);
+        __syncthreads();
+    }
+    for (int p = 0; p < w; p += kPp) {
+        const int pw = min(kPp, w - p);
+        const int rend = min(w, p + pw + kd);
+        const int pn = p + pw;
+        if (pn >= w) break;
+        const int pwn = min(kPp, w - pn);
+        const int Rn = rend - pn;  // rows of panel p's trailing region
+        // (A) next panel's columns first: rows [pn, rend) x columns [pn, pn+pwn)
+        if (Rn > 0) {
+            const int sq = min(pwn, Rn);
+            mma_sub_packed<true>(P, nb, pn, pn, sq, sq, S, kRStLd, S, kRStLd, pw);
+            if (Rn > pwn) mma_sub_packed<false>(P, nb, pn + pwn, pn, Rn - pwn, pwn, S + pwn, kRStLd, S, kRStLd, pw);
         }
         __syncthreads();
-        // (3) rank-pw update of the trailing lower triangle inside the band
-        if (rend > p + pw)
-            mma_sub<true>(C + (p + pw) + (p + pw) * kLdc, kLdc, rend - p - pw, rend - p - pw,
-                          C + (p + pw) + p * kLdc, kLdc, C + (p + pw) + p * kLdc, kLdc, pw);
+        // (B) warp 0 factors the next diagonal block while warps 1-7 finish the update
+        if (threadIdx.x < 32) {
+            potrf_diag_block(P, nb, pn, pwn, sh);
+        } else {
+            const int R3 = rend - pn - pwn;
+            if (R3 > 0)
+                mma_sub_packed<true>(P, nb, pn + pwn, pn + pwn, R3, R3, S + pwn, kRStLd, S + pwn, kRStLd, pw,
+                                     32, kThreads - 32);
+        }
+        __syncthreads();
+        // (C) rows below the next diagonal block
+        potrf_rows_below(P, nb, pn, pwn, min(w, pn + pwn + kd), S, sh);
         __syncthreads();
     }
     if (threadIdx.x == 0) {
-        *bad = s_bad;
-        *logsum = log(s_mant) + (double)s_exp * 0.69314718055994530942;
+        *bad = sh.bad;
+        *logsum = log(sh.mant) + (double)sh.exp * 0.69314718055994530942;
     }
     __syncthreads();
 }
 
-__global__ void __launch_bounds__(kThreads, 1) replay_kernel(const __grid_constant__ ReplayLaunch Lc) {
+__global__ void __launch_bounds__(kThreads, 2) replay_kernel(const __grid_constant__ ReplayLaunch Lc) {
     extern __shared__ double smem[];
-    double* C = smem;
-    double* S0 = C + kCbuf;
-    double* S1 = S0 + kStage;
-    double* sv = S1 + kStage;  // kNbMax doubles
+    double* C = smem;              // row-slice buffer (ld kRLd) or packed diagonal tile
+    double* S0 = C + kRCbuf;       // staging, kRKc columns of ld kRStLd
+    double* S1 = S0 + kRStage;
+    double* sv = S1 + kRStage;     // kNbMax doubles
     __shared__ long long s_slot;
     __shared__ int s_ok;
     const long long total = Lc.total;
@@ -466,9 +561,14 @@ __global__ void __launch_bounds__(kThreads, 1) replay_kernel(const __grid_consta
         const DTile O = a.tiles[t.tile];
         if (threadIdx.x == 0) s_ok = (*(volatile int*)&a.hdr->status == STC_OK);
         __syncthreads();
-        if (t.kind == TASK_DIAG) {
+        if (t.kind == TASK_DIAG || t.kind == TASK_POTRF) {
+            // (fused SYRKs +) POTRF on the whole diagonal tile, held as a packed triangle
+            if (s_ok && t.kind == TASK_POTRF && t.own_wait > 0) {
+                if (threadIdx.x == 0) s_ok = wait_counter(cnt + t.tile, t.own_wait, a.spin, &a.hdr->status);
+                __syncthreads();
+            }
             if (s_ok) {
-                load_diag(C, F + O.off, O, nb);
+                load_diag_packed(C, F + O.off, O, nb);
                 __syncthreads();
                 for (int ui = t.ubeg; ui < t.uend; ++ui) {
                     const DUpd u = a.upds[ui];
@@ -477,22 +577,22 @@ __global__ void __launch_bounds__(kThreads, 1) replay_kernel(const __grid_consta
                     __syncthreads();
                     if (!s_ok) break;
                     const int R = u.ra1 - u.ra0;
-                    for (int k0 = 0; k0 < u.klen; k0 += kKc) {
-                        const int K = min(kKc, u.klen - k0);
-                        stage_cols(S0, kNbMax + 8, F + A.off, nb, u.ra0, R, u, a.imap, false, k0, K);
+                    for (int k0 = 0; k0 < u.klen; k0 += kRKc) {
+                        const int K = min(kRKc, u.klen - k0);
+                        stage_cols(S0, kRStLd, F + A.off, nb, u.ra0, R, u, a.imap, false, k0, K);
                         __syncthreads();
-                        mma_sub<true>(C + u.ra0 + u.ra0 * kLdc, kLdc, R, R, S0, kNbMax + 8, S0, kNbMax + 8, K);
+                        mma_sub_packed<true>(C, nb, u.ra0, u.ra0, R, R, S0, kRStLd, S0, kRStLd, K);
                         __syncthreads();
                     }
                 }
                 if (s_ok) {
                     int bad; double ls;
-                    potrf_smem(C, O.sw, min(O.kd, nb - 1), sv, &bad, &ls);
+                    potrf_packed(C, nb, O.sw, min(O.kd, nb - 1), S0, &bad, &ls);
                     if (threadIdx.x == 0) {
                         if (bad >= 0) record_info(a.info + item, O.J * nb + bad + 1);
                         F[a.poff + O.pd_slot] = bad >= 0 ? __longlong_as_double(0x7ff8000000000000LL) : ls;
                     }
-                    store_diag(C, F + O.off, O, nb);
+                    store_diag_packed(C, F + O.off, O, nb);
                 }
             }
         } else if (t.kind == TASK_SYRK) {
@@ -502,7 +602,7 @@ __global__ void __launch_bounds__(kThreads, 1) replay_kernel(const __grid_consta
                 const double* T = F + O.off;
                 for_rc(R, t.rs1, [&](int r, int c) {
                     const int gr = t.rs0 + r;
-                    C[r + c * kLdc] = c <= gr ? diag_at(T, O, nb, gr, c) : 0.0;
+                    C[r + c * kRLd] = c <= gr ? diag_at(T, O, nb, gr, c) : 0.0;
                 });
                 __syncthreads();
                 for (int ui = t.ubeg; ui < t.uend; ++ui) {
@@ -512,15 +612,15 @@ __global__ void __launch_bounds__(kThreads, 1) replay_kernel(const __grid_consta
                     __syncthreads();
                     if (!s_ok) break;
                     const int r0 = u.oc0, d0 = u.ra0, rb = u.ra1, Rs = rb - r0;
-                    for (int k0 = 0; k0 < u.klen; k0 += kKc) {
-                        const int K = min(kKc, u.klen - k0);
-                        stage_cols(S0, kNbMax + 8, F + A.off, nb, r0, Rs, u, a.imap, false, k0, K);
+                    for (int k0 = 0; k0 < u.klen; k0 += kRKc) {
+                        const int K = min(kRKc, u.klen - k0);
+                        stage_cols(S0, kRStLd, F + A.off, nb, r0, Rs, u, a.imap, false, k0, K);
                         __syncthreads();
                         if (d0 > r0)
-                            mma_sub<false>(C + (d0 - t.rs0) + r0 * kLdc, kLdc, rb - d0, d0 - r0,
-                                           S0 + (d0 - r0), kNbMax + 8, S0, kNbMax + 8, K);
-                        mma_sub<true>(C + (d0 - t.rs0) + d0 * kLdc, kLdc, rb - d0, rb - d0,
-                                      S0 + (d0 - r0), kNbMax + 8, S0 + (d0 - r0), kNbMax + 8, K);
+                            mma_sub<false>(C + (d0 - t.rs0) + r0 * kRLd, kRLd, rb - d0, d0 - r0,
+                                           S0 + (d0 - r0), kRStLd, S0, kRStLd, K);
+                        mma_sub<true>(C + (d0 - t.rs0) + d0 * kRLd, kRLd, rb - d0, rb - d0,
+                                      S0 + (d0 - r0), kRStLd, S0 + (d0 - r0), kRStLd, K);
                         __syncthreads();
                     }
                 }
@@ -529,32 +629,16 @@ __global__ void __launch_bounds__(kThreads, 1) replay_kernel(const __grid_consta
                     for_rc(R, t.rs1, [&](int r, int c) {
                         const int gr = t.rs0 + r;
                         if (c > gr) return;
-                        if (O.kind == TILE_DIAG_DENSE) __stcg(Tw + gr + (size_t)c * nb, C[r + c * kLdc]);
-                        else if (gr - c <= O.kd) __stcg(Tw + (O.kd + c - gr) + (size_t)gr * (O.kd + 1), C[r + c * kLdc]);
+                        if (O.kind == TILE_DIAG_DENSE) __stcg(Tw + gr + (size_t)c * nb, C[r + c * kRLd]);
+                        else if (gr - c <= O.kd) __stcg(Tw + (O.kd + c - gr) + (size_t)gr * (O.kd + 1), C[r + c * kRLd]);
                     });
                 }
-            }
-        } else if (t.kind == TASK_POTRF) {
-            if (s_ok && t.own_wait > 0) {
-                if (threadIdx.x == 0) s_ok = wait_counter(cnt + t.tile, t.own_wait, a.spin, &a.hdr->status);
-                __syncthreads();
-            }
-            if (s_ok) {
-                load_diag(C, F + O.off, O, nb);
-                __syncthreads();
-                int bad; double ls;
-                potrf_smem(C, O.sw, min(O.kd, nb - 1), sv, &bad, &ls);
-                if (threadIdx.x == 0) {
-                    if (bad >= 0) record_info(a.info + item, O.J * nb + bad + 1);
-                    F[a.poff + O.pd_slot] = bad >= 0 ? __longlong_as_double(0x7ff8000000000000LL) : ls;
-                }
-                store_diag(C, F + O.off, O, nb);
             }
         } else {
             const int R = t.rs1 - t.rs0;
             const int sw = O.sw;
             if (s_ok) {
-                load_off(C, F + O.off, nb, t.rs0, R, sw);
+                load_off(C, kRLd, F + O.off, nb, t.rs0, R, sw);
                 __syncthreads();
                 for (int ui = t.ubeg; ui < t.uend; ++ui) {
                     const DUpd u = a.upds[ui];
@@ -566,13 +650,13 @@ __global__ void __launch_bounds__(kThreads, 1) replay_kernel(const __grid_consta
                     __syncthreads();
                     if (!s_ok) break;
                     const int Ra = u.ra1 - u.ra0, Cn = u.oc1 - u.oc0;
-                    for (int k0 = 0; k0 < u.klen; k0 += kKc) {
-                        const int K = min(kKc, u.klen - k0);
-                        stage_cols(S0, kNbMax + 8, F + A.off, nb, u.ra0, Ra, u, a.imap, false, k0, K);
-                        stage_rows_gather(S1, kNbMax + 8, F + B.off, nb, O, a.saind, u.oc0, Cn, u, a.imap, k0, K);
+                    for (int k0 = 0; k0 < u.klen; k0 += kRKc) {
+                        const int K = min(kRKc, u.klen - k0);
+                        stage_cols(S0, kRStLd, F + A.off, nb, u.ra0, Ra, u, a.imap, false, k0, K);
+                        stage_rows_gather(S1, kRStLd, F + B.off, nb, O, a.saind, u.oc0, Cn, u, a.imap, k0, K);
                         __syncthreads();
-                        mma_sub<false>(C + (u.ra0 - t.rs0) + u.oc0 * kLdc, kLdc, Ra, Cn, S0, kNbMax + 8,
-                                       S1, kNbMax + 8, K);
+                        mma_sub<false>(C + (u.ra0 - t.rs0) + u.oc0 * kRLd, kRLd, Ra, Cn, S0, kRStLd,
+                                       S1, kRStLd, K);
                         __syncthreads();
                     }
                 }
@@ -586,23 +670,23 @@ __global__ void __launch_bounds__(kThreads, 1) replay_kernel(const __grid_consta
                     const int RX = t.tr1 - t.tr0;
                     for (int p = 0; p < sw; p += kPb) {
                         const int pw = min(kPb, sw - p);
-                        for (int k0 = 0; k0 < p; k0 += kKc) {
-                            const int K = min(kKc, p - k0);
+                        for (int k0 = 0; k0 < p; k0 += kRKc) {
+                            const int K = min(kRKc, p - k0);
                             const int Cp = ((pw + 3) & ~3) + 4;
                             for_rc(Cp, K, [&](int c, int k) {
                                 double v = 0.0;
                                 if (c < pw)
                                     v = diag_at(DT, D, nb, logical_col(O, a.saind, p + c),
                                                 logical_col(O, a.saind, k0 + k));
-                                S1[c + k * (kNbMax + 8)] = v;
+                                S1[c + k * kRStLd] = v;
                             });
                             __syncthreads();
-                            mma_sub<false>(X + p * kLdc, kLdc, RX, pw, X + k0 * kLdc, kLdc, S1, kNbMax + 8, K);
+                            mma_sub<false>(X + p * kRLd, kRLd, RX, pw, X + k0 * kRLd, kRLd, S1, kRStLd, K);
                             __syncthreads();
                         }
                         // diagonal block of the panel and its reciprocal diagonal
                         for (int idx = threadIdx.x; idx < kPb * kPb; idx += kThreads) {
-                            const int i = idx % kPb, j = idx / kPb;
+                            const int i = idx & (kPb - 1), j = idx / kPb;
                             double v = 0.0;
                             if (i < pw && j < pw && i >= j)
                                 v = diag_at(DT, D, nb, logical_col(O, a.saind, p + i), logical_col(O, a.saind, p + j));
@@ -611,10 +695,10 @@ __global__ void __launch_bounds__(kThreads, 1) replay_kernel(const __grid_consta
                         __syncthreads();
                         if (threadIdx.x < pw) sv[threadIdx.x] = 1.0 / S0[threadIdx.x * (kPb + 1)];
                         __syncthreads();
-                        trsm_rows(X + p * kLdc, kLdc, RX, pw, S0, kPb, sv);
+                        trsm_rows(X + p * kRLd, kRLd, RX, pw, S0, kPb, sv);
                         __syncthreads();
                     }
-                    store_off(C, F + O.off, nb, t.rs0, R, sw);
+                    store_off(C, kRLd, F + O.off, nb, t.rs0, R, sw);
                 }
             }
         }
@@ -1171,7 +1255,7 @@ int device_info(int* dev, int* sms) {
     DevInfo& d = g_dev[*dev];
     if (!d.attr_set) {
         if (cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, *dev) != cudaSuccess) return STC_ERR_CUDA;
-        if (cudaFuncSetAttribute(replay_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes) != cudaSuccess)
+        if (cudaFuncSetAttribute(replay_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRSmemBytes) != cudaSuccess)
             return STC_ERR_CUDA;
         if (cudaFuncSetAttribute(selinv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes) != cudaSuccess)
             return STC_ERR_CUDA;
@@ -1292,6 +1376,15 @@ int ensure_queue(stc_plan* P, TaskSet* ts, int64_t batch, uint64_t** out) {
     return STC_OK;
 }
 
+// Two CTAs per SM hide one CTA's waits behind the other's arithmetic when many items
+// are in flight; with few items every task is on the critical path and gets an SM alone.
+long long batch_total(const ReplayLaunch& L) {
+    long long b = 0;
+    for (int j = 0; j < L.njobs; ++j) b += L.job[j].batch;
+    return b;
+}
+long long replay_ctas(int sms, long long batch) { return batch >= 16 ? 2LL * sms : (long long)sms; }
+
 void fill_job(ReplayArgs& a, const stc_plan* P, const TaskSet* ts, void* d_factor, int* counters, int32_t* d_info,
               int64_t batch, WorkHeader* hdr) {
     a.tiles = ts->d_tiles; a.saind = P->dev.saind; a.tasks = ts->d_tasks; a.upds = ts->d_upds;
@@ -1316,7 +1409,8 @@ int32_t pick_slices(const stc_plan* P, int64_t batch, int sms) {
     // is spread over several SMs (the per-SM FP64 rate is low), but no further than the
     // batch needs: thinner slices cost efficiency inside each task.
     if (P->nb < 48) return 1;
-    const int64_t per_item = std::max<int64_t>(1, (int64_t)P->tiles.size() / std::max<int64_t>(1, P->nt));
+    const int64_t per_item =
+        std::max<int64_t>(1, ((int64_t)P->tiles.size() + P->nt / 2) / std::max<int64_t>(1, P->nt));
     const int64_t width = batch * per_item;  // independent tiles per block-column step
     int s;
     if (width >= sms) s = 2;
@@ -1400,8 +1494,8 @@ extern "C" int stc_factorize_scattered(const stc_plan* Pc, int64_t batch, void* 
     Lc.queue = queue;
     Lc.hdr = (WorkHeader*)d_work;
     Lc.total = (long long)ts->tasks.size() * batch;
-    const int grid = (int)std::max<long long>(1, std::min<long long>(sms, Lc.total));
-    replay_kernel<<<grid, kThreads, kSmemBytes, st>>>(Lc);
+    const int grid = (int)std::max<long long>(1, std::min<long long>(replay_ctas(sms, batch_total(Lc)), Lc.total));
+    replay_kernel<<<grid, kThreads, kRSmemBytes, st>>>(Lc);
     return cudaGetLastError() == cudaSuccess ? STC_OK : STC_ERR_CUDA;
 }
 
@@ -1661,8 +1755,8 @@ extern "C" int stc_factorize_group(stc_group* g, const double* const* d_values, 
     Lc.queue = g->d_queue;
     Lc.hdr = (WorkHeader*)d_work;
     Lc.total = g->total;
-    const int grid = (int)std::max<long long>(1, std::min<long long>(sms, Lc.total));
-    replay_kernel<<<grid, kThreads, kSmemBytes, st>>>(Lc);
+    const int grid = (int)std::max<long long>(1, std::min<long long>(replay_ctas(sms, batch_total(Lc)), Lc.total));
+    replay_kernel<<<grid, kThreads, kRSmemBytes, st>>>(Lc);
     return cudaGetLastError() == cudaSuccess ? STC_OK : STC_ERR_CUDA;
 }
 
@@ -1739,8 +1833,8 @@ extern "C" int stc_factorize_noalloc(const stc_plan* Pc, const double* d_values,
     Lc.queue = nullptr;
     Lc.hdr = (WorkHeader*)scratch;
     Lc.total = (long long)ts->tasks.size() * batch;
-    const int grid = (int)std::max<long long>(1, std::min<long long>(sms, Lc.total));
-    replay_kernel<<<grid, kThreads, kSmemBytes, st>>>(Lc);
+    const int grid = (int)std::max<long long>(1, std::min<long long>(replay_ctas(sms, batch_total(Lc)), Lc.total));
+    replay_kernel<<<grid, kThreads, kRSmemBytes, st>>>(Lc);
     if (cudaGetLastError() != cudaSuccess) return STC_ERR_CUDA;
     if (d_status && cudaMemcpyAsync(d_status, &Lc.hdr->status, sizeof(int32_t), cudaMemcpyDeviceToDevice, st) !=
                         cudaSuccess)
