@@ -63,6 +63,22 @@ def workload_config(args, batch):
             "l2": "inputs larger than L2 (values %.1f GB, factor %.1f GB per step)"}
 
 
+def replay_traffic(n, batch):
+    """DRAM bytes per replay launch from the committed ncu capture (profiles/), scaled to
+    this launch; None when the kernel source changed since the capture."""
+    import hashlib
+    try:
+        rec = json.load(open(os.path.join(ROOT, "profiles", "replay_kernel_traffic.json")))
+        src = open(os.path.join(ROOT, "paper_2609_29765_gb300", "csrc", "replay.cu"), "rb").read()
+    except OSError:
+        return None
+    if hashlib.sha256(src).hexdigest()[:16] != rec["source_sha256_prefix"]:
+        return None
+    cap = rec["captured"]
+    per = (cap["dram_bytes_read"] + cap["dram_bytes_write"]) / (cap["n"] * cap["batch"])
+    return per * n * batch
+
+
 # ------------------------------------------------------------------ clocks
 class Clocks:
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -143,6 +159,21 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------------ ranks
+def rank_seeds(rank, batch):
+    """Value-set seeds of one rank: ranks factorize disjoint, contiguous seed ranges."""
+    return list(range(rank * batch, (rank + 1) * batch))
+
+
+def max_over_ranks(values, dist, device):
+    """Element-wise maximum of per-rank timings (ms) on every rank."""
+    import torch
+    t = torch.tensor(values, dtype=torch.float64, device=device)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.cpu()]
+
+
 # ------------------------------------------------------------------ ours
 def run_ours(args):
     import torch
@@ -173,8 +204,7 @@ def run_ours(args):
     # host (pinned) values for the e2e leg; device copies for the resident leg
     hv = torch.empty(batch, nnz, dtype=torch.float64, pin_memory=True)
     hb = torch.empty(batch, 1, n, dtype=torch.float64, pin_memory=True)
-    for b in range(batch):
-        seed = rank * batch + b
+    for b, seed in enumerate(rank_seeds(rank, batch)):
         hv[b].numpy()[:] = I.band_values(n, BW, seed, Ap, Ai)
         hb[b, 0].numpy()[:] = I.rhs(n, 1000 + seed)[0]
     dv = hv.to("cuda")
@@ -280,11 +310,7 @@ def run_ours(args):
     L.check(L.stc_sync_status(ws), "device status")
 
     # ---- max over ranks
-    vals = torch.tensor([ms_step, ms_replay, e2e_ms, ms_plain],
-                        dtype=torch.float64, device="cuda")
-    if dist is not None:
-        dist.all_reduce(vals, op=dist.ReduceOp.MAX)
-    ms_step, ms_replay, e2e_ms, ms_plain = (float(v) for v in vals.cpu())
+    ms_step, ms_replay, e2e_ms, ms_plain = max_over_ranks([ms_step, ms_replay, e2e_ms, ms_plain], dist, "cuda")
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
@@ -307,7 +333,7 @@ def run_ours(args):
         "plain": {"value": 1e3 / ms_plain, "unit": UNIT, "ms_per_factorization": ms_plain,
                   "note": "batch 1, one launch per factorization (+logdet+solve)"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": None,
+                     "frac": achieved / peak, "traffic": replay_traffic(args.n, batch),
                      "kernel": "replay_kernel (persistent task-DAG factorization)",
                      "work": "algorithmic flops sum_j c_j^2 = %.4g per factorization x %d" % (flops_alg, batch),
                      "peak_source": "nominal FP64 ALU: 152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz",

@@ -386,15 +386,14 @@ __device__ void stage_rows_gather(double* S, int ld, const double* T, int nb, co
 // panel's columns get the rank-8 update first, so that warp 0 can factor the next
 // diagonal block while warps 1-7 apply the rest of the trailing update.  Rows more than
 // kd below the diagonal are structurally zero and skipped.  *bad receives the first
-// non-positive pivot column (or -1); *logsum = sum_j log L_jj, kept as a mantissa product
-// and an exponent sum.
+// non-positive pivot column (or -1); *logsum = sum_j log L_jj, one log per diagonal entry
+// reduced in a fixed order at the end.
 constexpr int kPp = 8;
 
 struct PotrfShared {
     double blk[kPp][kPp];  // L of the current panel's diagonal block, blk[row][col]
     double inv[kPp];       // 1 / L_jj of the panel
-    double mant;
-    int exp, bad;
+    int bad;
 };
 
 // Warp 0 only: unblocked Cholesky of the pw x pw diagonal block at (p, p).
@@ -431,20 +430,8 @@ __device__ void potrf_diag_block(double* P, int nb, int p, int pw, PotrfShared& 
         for (int l = 0; l < kPp; ++l)
             if (l <= lane) P[pk(nb, p + lane, p + l)] = x[l];
     }
-    double mant = sh.mant;
-    int ex = sh.exp;
-#pragma unroll
-    for (int j = 0; j < kPp; ++j) {
-        const int bj = __shfl_sync(0xffffffffu, badl, j);
-        const double ljj = __shfl_sync(0xffffffffu, x[j], j);
-        if (lane == 0 && j < pw) {
-            if (bj >= 0 && sh.bad < 0) sh.bad = bj;
-            int e;
-            mant = frexp(mant * ljj, &e);
-            ex += e;
-        }
-    }
-    if (lane == 0) { sh.mant = mant; sh.exp = ex; }
+    const unsigned badmask = __ballot_sync(0xffffffffu, badl >= 0);
+    if (lane == 0 && badmask && sh.bad < 0) sh.bad = p + __ffs(badmask) - 1;
 }
 
 // All threads: rows [p+pw, rend) of panel p solved against the diagonal block; the solved
@@ -481,7 +468,7 @@ __device__ void potrf_rows_below(double* P, int nb, int p, int pw, int rend, dou
 
 __device__ void potrf_packed(double* P, int nb, int w, int kd, double* S, int* bad, double* logsum) {
     __shared__ PotrfShared sh;
-    if (threadIdx.x == 0) { sh.mant = 1.0; sh.exp = 0; sh.bad = -1; }
+    if (threadIdx.x == 0) sh.bad = -1;
     __syncthreads();
     // panel 0
     {
@@ -501,8 +488,9 @@ __device__ void potrf_packed(double* P, int nb, int w, int kd, double* S, int* b
         // (A) next panel's columns first: rows [pn, rend) x columns [pn, pn+pwn)
         if (Rn > 0) {
             const int sq = min(pwn, Rn);
-            mma_sub_packed<true>(P, nb, pn, pn, sq, sq, S, kRStLd, S, kRStLd, pw);
-            if (Rn > pwn) mma_sub_packed<false>(P, nb, pn + pwn, pn, Rn - pwn, pwn, S + pwn, kRStLd, S, kRStLd, pw);
+            mma_tiles<true, 2, 2, true>(P, 0, sq, sq, S, kRStLd, S, kRStLd, pw, nb, pn, pn);
+            if (Rn > pwn)
+                mma_tiles<false, 2, 2, true>(P, 0, Rn - pwn, pwn, S + pwn, kRStLd, S, kRStLd, pw, nb, pn + pwn, pn);
         }
         __syncthreads();
         // (B) warp 0 factors the next diagonal block while warps 1-7 finish the update
@@ -519,9 +507,19 @@ __device__ void potrf_packed(double* P, int nb, int w, int kd, double* S, int* b
         potrf_rows_below(P, nb, pn, pwn, min(w, pn + pwn + kd), S, sh);
         __syncthreads();
     }
+    // sum_j log L_jj: one log per thread, fixed-order tree reduction
+    __shared__ double s_red[kThreads / 32];
+    double lg = 0.0;
+    for (int j = threadIdx.x; j < w; j += kThreads) lg += log(P[pk(nb, j, j)]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) lg += __shfl_down_sync(0xffffffffu, lg, o);
+    if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = lg;
+    __syncthreads();
     if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int q = 0; q < kThreads / 32; ++q) t += s_red[q];
         *bad = sh.bad;
-        *logsum = log(sh.mant) + (double)sh.exp * 0.69314718055994530942;
+        *logsum = t;
     }
     __syncthreads();
 }
@@ -1412,12 +1410,9 @@ int32_t pick_slices(const stc_plan* P, int64_t batch, int sms) {
     const int64_t per_item =
         std::max<int64_t>(1, ((int64_t)P->tiles.size() + P->nt / 2) / std::max<int64_t>(1, P->nt));
     const int64_t width = batch * per_item;  // independent tiles per block-column step
-    int s;
-    if (width >= sms) s = 2;
-    else if (width >= sms / 4) s = 4;
-    else s = 8;
-    if (P->nb < 96) s = std::max(1, s / 2);
-    return s;
+    // measured on the n = 200,000 band (n_b = 128): 4 slices at 64 items, 8 at 1 item
+    const int s = width >= sms / 4 ? 4 : 8;
+    return P->nb < 96 ? std::max(1, s / 2) : s;
 }
 
 inline cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s); }
