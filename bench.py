@@ -51,6 +51,10 @@ def parse():
     p.add_argument("--n", type=int, default=N)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--workloads", default="c1,c3,c4,c5",
+                   help="other workloads measured after the headline, comma list or 'none'")
+    p.add_argument("--full-workloads", action="store_true",
+                   help="the other workloads at their full batch sizes (minutes)")
     return p.parse_args()
 
 
@@ -139,22 +143,71 @@ def oracle_sample(n, items, seed0=0):
     return times
 
 
+def _oracle_worker(n, seed, rounds, barrier, results):
+    from oracle import oracle as O
+    Ap, Ai = I.band_pattern(n, BW)
+    F = O.OracleFactor(n, Ap, Ai)
+    Ax = I.band_values(n, BW, seed, Ap, Ai)
+    b = I.rhs(n, 1000 + seed)[0]
+    for r in range(rounds):
+        barrier.wait()
+        t0 = time.time()
+        Lx, info = F.factor(Ax)
+        F.logdet(Lx)
+        F.solve(Lx, b)
+        results.put((r, t0, time.time()))
+
+
+def oracle_parallel(n, procs, rounds=1):
+    """The oracle on `procs` value sets at once, one single-threaded process per host core
+    (spawned, so safe before or after CUDA use), `rounds` times; returns the wall time of
+    each round (all processes start a round together)."""
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    barrier, results = ctx.Barrier(procs), ctx.Queue()
+    ps = [ctx.Process(target=_oracle_worker, args=(n, s, rounds, barrier, results)) for s in range(procs)]
+    for p in ps:
+        p.start()
+    try:
+        spans = [results.get(timeout=900) for _ in range(procs * rounds)]
+    finally:
+        for p in ps:
+            p.join(timeout=60)
+            if p.is_alive():
+                p.kill()
+    walls = []
+    for r in range(rounds):
+        sp = [(a, b) for q, a, b in spans if q == r]
+        walls.append(max(b for _, b in sp) - min(a for a, _ in sp))
+    return walls
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     steps, warm = args.steps, args.warmup
-    # each step is one factorization (+logdet+solve) of one value set: a bounded sample
-    times = oracle_sample(args.n, warm + steps)[warm:]
-    ms = 1e3 * sum(times) / len(times)
-    value = 1e3 / ms
+    cores = host_cores()
+    # each step: `cores` value sets factorized (+logdet+solve) at once, one oracle process per
+    # host core -- a bounded sample of the 64-set batch
+    walls = oracle_parallel(args.n, cores, warm + steps)[warm:]
+    ms = 1e3 * sum(walls) / len(walls)
+    value = cores * 1e3 / ms
     cfg = workload_config(args, args.batch)
     cfg["l2"] = "host run"
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": steps, "warmup": warm, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": cfg,
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": "one value set per step (factor+logdet+solve), single thread"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": "%d value sets per step (factor+logdet+solve), one single-threaded "
+                                       "oracle process per host core" % cores},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -174,6 +227,190 @@ def max_over_ranks(values, dist, device):
     return [float(v) for v in t.cpu()]
 
 
+# ------------------------------------------------------------------ other workloads
+def _events_ms(fn, reps, warm):
+    """Mean CUDA-event time (ms) of fn() on the current stream after `warm` untimed calls."""
+    import torch
+    for _ in range(warm):
+        fn()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(reps):
+        fn()
+    b.record()
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / reps
+
+
+def _fp64(flops, ms):
+    t = flops / (ms * 1e-3) / 1e12
+    return {"achieved_tflops": t, "frac": t / PEAK_FP64_NOMINAL}
+
+
+def _distinct_values(gen, count, distinct):
+    """[count, nnzA] host values cycling through `distinct` generated value sets."""
+    sets = [gen(s) for s in range(distinct)]
+    return np.stack([sets[i % distinct] for i in range(count)])
+
+
+def measure_workloads(args):
+    """Factorizations/s (plain per call vs batched) and adjoint gradients/s on the other
+    workloads, each timed with CUDA events after a warm-up; not part of the headline step."""
+    import torch
+    from paper_2609_29765_gb300 import _lib as L
+    from paper_2609_29765_gb300.api import Group, Plan
+
+    want = [] if args.workloads == "none" else args.workloads.split(",")
+    full = args.full_workloads
+    dev = lambda a: torch.as_tensor(np.ascontiguousarray(a), device="cuda")
+    out = {}
+
+    def plain_and_batched(P, vals, reps_b, reps_p, with_solve):
+        batch = vals.shape[0]
+        fac = torch.empty(P.factor_bytes(batch) // 8, dtype=torch.float64, device="cuda")
+        info = torch.empty(batch, dtype=torch.int32, device="cuda")
+        ld = torch.empty(batch, dtype=torch.float64, device="cuda")
+        ws = P.workspace(batch)
+        b = torch.ones(batch, 1, P.n, dtype=torch.float64, device="cuda")
+        x = torch.empty_like(b)
+
+        def run(bt):
+            L.check(L.stc_factorize(P.h, vals[:bt], bt, fac, ws, info), "factorize")
+            L.check(L.stc_logdet(P.h, fac, bt, ld), "logdet")
+            if with_solve:
+                L.check(L.stc_solve(P.h, fac, bt, 1, b[:bt], x[:bt], ws), "solve")
+        ms_b = _events_ms(lambda: run(batch), reps_b, 1)
+        ms_f = _events_ms(lambda: L.check(L.stc_factorize(P.h, vals, batch, fac, ws, info)), reps_b, 0)
+        ms_p = _events_ms(lambda: run(1), reps_p, 1)
+        L.check(L.stc_sync_status(ws), "device status")
+        assert int(info.abs().sum()) == 0
+        return ms_b, ms_f, ms_p
+
+    if "c1" in want:
+        Ap, Ai, _, coords = I.laplace2d_bordered(seed=0)
+        n = len(Ap) - 1
+        P = Plan(n, Ap, Ai, coords=coords, nb=64)
+        batch = 1024
+        vals = dev(_distinct_values(lambda s: I.laplace2d_bordered(seed=s)[2], batch, 16))
+        ms_b, ms_f, ms_p = plain_and_batched(P, vals, 5, 50, True)
+        out["c1"] = {"workload": "n=1,026 32x32 Laplacian + 0.1 I + 2 border rows, ND, n_b=64; factor+logdet+solve",
+                     "route": P.route, "route_selected": P.route_selected,
+                     "plain": {"value": 1e3 / ms_p, "unit": UNIT, "us_per_call": 1e3 * ms_p},
+                     "batched": {"value": batch * 1e3 / ms_b, "unit": UNIT, "batch": batch,
+                                 "values": "16 distinct value sets (seeds 0..15) cycled"},
+                     "note": "latency-bound: roofline fraction not meaningful"}
+        del vals
+    c3_plan = None
+    if "c3" in want or "c5" in want:
+        Ap, Ai, coords = I.stcov_pattern()
+        c3_plan = Plan(len(Ap) - 1, Ap, Ai, coords=coords, nb=64, route="semisparse")
+    if "c3" in want:
+        P = c3_plan
+        batch = 128 if full else 16
+        th = I.stcov_thetas(batch, 0)
+        vals = dev(_distinct_values(lambda s: I.stcov_values(th[s]), batch, 16 if full else 4))
+        ms_b, ms_f, ms_p = plain_and_batched(P, vals, 1 if full else 2, 2, False)
+        fa = P.info["flops_alg"]
+        out["c3"] = {"workload": "tau AR1(rho) x SPDE 9-point 60x60, 50 steps, + 20 border rows, n=180,020, "
+                                 "ND, n_b=64; factor+logdet",
+                     "route": P.route, "route_selected": P.route_selected,
+                     "plain": {"value": 1e3 / ms_p, "unit": UNIT, "ms_per_call": ms_p},
+                     "batched": {"value": batch * 1e3 / ms_b, "unit": UNIT, "batch": batch,
+                                 "values": "%d distinct theta draws cycled" % (16 if full else 4),
+                                 "note": "one launch of %d of the 256 theta sets (factors: %.0f GB)"
+                                         % (batch, P.factor_bytes(batch) / 1e9)},
+                     "roofline_replay": dict(_fp64(fa * batch, ms_f), bound="alu", peak=PEAK_FP64_NOMINAL,
+                                             work="sum_j c_j^2 = %.4g flops per factorization" % fa,
+                                             ms=ms_f)}
+        del vals
+    if "c5" in want:
+        P = c3_plan
+        batch = 64 if full else 8
+        th = I.stcov_thetas(batch, 0)
+        distinct = 16 if full else 4
+        vals = dev(_distinct_values(lambda s: I.stcov_values(th[s]), batch, distinct))
+        xs = dev(np.stack([I.rhs(P.n, s)[0] for s in range(batch)]))
+        fac = torch.empty(P.factor_bytes(batch) // 8, dtype=torch.float64, device="cuda")
+        sig = torch.empty_like(fac)
+        info = torch.empty(batch, dtype=torch.int32, device="cuda")
+        ld = torch.empty(batch, dtype=torch.float64, device="cuda")
+        q = torch.empty_like(ld)
+        g = torch.empty(batch, P.nnzA, dtype=torch.float64, device="cuda")
+        neg = torch.full((batch,), -1.0, dtype=torch.float64, device="cuda")
+        ws = P.workspace(batch)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+
+        def grad_step(rec=False):
+            if rec:
+                ev[0].record()
+            L.check(L.stc_factorize(P.h, vals, batch, fac, ws, info), "factorize")
+            L.check(L.stc_logdet(P.h, fac, batch, ld), "logdet")
+            if rec:
+                ev[1].record()
+            L.check(L.stc_logdet_backward(P.h, fac, batch, None, g, 0, sig, ws), "logdet_backward")
+            if rec:
+                ev[2].record()
+            L.check(L.stc_quad_form(P.h, batch, vals, xs, q), "quad_form")
+            L.check(L.stc_sym_outer_backward(P.h, batch, xs, xs, neg, g, 1), "outer_backward")
+            if rec:
+                ev[3].record()
+        grad_step()
+        torch.cuda.synchronize()
+        grad_step(True)
+        torch.cuda.synchronize()
+        L.check(L.stc_sync_status(ws), "device status")
+        assert int(info.abs().sum()) == 0
+        ms_tot = ev[0].elapsed_time(ev[3])
+        ms_bwd = ev[1].elapsed_time(ev[2])
+        fa = P.info["flops_alg"]
+        out["c5"] = {"workload": "d/dQ [logdet Q(theta) - x^T Q(theta) x] on the n=180,020 pattern above",
+                     "gradients": {"value": batch * 1e3 / ms_tot, "unit": "gradients/s", "batch": batch,
+                                   "values": "%d distinct theta draws cycled" % distinct,
+                                   "step": "factorize+logdet+selected inverse+gather+quad form+outer product",
+                                   "ms": ms_tot},
+                     "roofline_selinv": dict(_fp64(2 * fa * batch, ms_bwd), bound="alu", peak=PEAK_FP64_NOMINAL,
+                                             work="2 sum_j c_j^2 = %.4g flops per item (Takahashi)" % (2 * fa),
+                                             ms=ms_bwd),
+                     "gradient_w_r_t": "the nnzA values of Q; the 3-parameter theta chain is a host-side "
+                                       "contraction outside the step"}
+        del vals, fac, sig, g
+    c3_plan = None
+    if "c4" in want:
+        plans, vals, nfl = [], [], []
+        per = 8 if full else 2
+        for m in (32, 48, 64):
+            vs = [I.fem3d(m, m, m, seed=s)[2] for s in range(per)]
+            Ap, Ai, _, coords = I.fem3d(m, m, m, seed=0)
+            P = Plan(len(Ap) - 1, Ap, Ai, coords=coords, nb=64, route="dense")
+            plans.append(P)
+            vals.append(dev(np.stack(vs)))
+        P64 = plans[2]
+        fac = torch.empty(P64.factor_bytes(1) // 8, dtype=torch.float64, device="cuda")
+        info = torch.empty(1, dtype=torch.int32, device="cuda")
+        ws = P64.workspace(1)
+        ms_p = _events_ms(lambda: L.check(L.stc_factorize(P64.h, vals[2][:1], 1, fac, ws, info)), 1, 1)
+        L.check(L.stc_sync_status(ws), "device status")
+        del fac
+        G = Group(plans, [per] * 3)
+        ms_g = _events_ms(lambda: G.factorize(vals), 1, 1)
+        L.check(G.status(), "group status")
+        fl = sum(P.info["flops_alg"] for P in plans) * per
+        ft = sum(P.info["flops_tile"] for P in plans) * per
+        out["c4"] = {"workload": "7-point lognormal-conductance FEM + 1e-3 I, ND, n_b=64, forced dense route",
+                     "route_selected": P64.route_selected,
+                     "plain_64cubed": {"value": 1e3 / ms_p, "unit": UNIT, "ms_per_call": ms_p, "n": P64.n,
+                                       **_fp64(P64.info["flops_alg"], ms_p),
+                                       "tile_tflops": P64.info["flops_tile"] / (ms_p * 1e-3) / 1e12},
+                     "mixed_batch": {"value": 3 * per * 1e3 / ms_g, "unit": UNIT,
+                                     "items": "32^3, 48^3, 64^3 x %d each, one persistent launch" % per,
+                                     "ms": ms_g, **_fp64(fl, ms_g),
+                                     "tile_tflops": ft / (ms_g * 1e-3) / 1e12}}
+        del G, vals
+    torch.cuda.empty_cache()
+    return out
+
+
 # ------------------------------------------------------------------ ours
 def run_ours(args):
     import torch
@@ -191,10 +428,15 @@ def run_ours(args):
     # the CPU baseline runs first, before any GPU work of this process (rank 0, N=1 only)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cores = host_cores()
+        wall = oracle_parallel(args.n, cores)[0]
+        rate = cores / wall
         t = oracle_sample(args.n, 2, seed0=0)
-        cpu = {"value": len(t) / sum(t), "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": "2 value sets of the workload, factor+logdet+solve each, single thread, %.1f s"
-                         % sum(t)}
+        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": "%d value sets of the workload at once (factor+logdet+solve), one single-threaded "
+                         "oracle process per host core, %.1f s wall" % (cores, wall),
+               "single_thread": {"value": len(t) / sum(t), "unit": UNIT, "cores": 1,
+                                 "sample": "2 value sets, one after the other, %.1f s" % sum(t)}}
 
     n, batch = args.n, args.batch
     Ap, Ai = I.band_pattern(n, BW)
@@ -311,6 +553,12 @@ def run_ours(args):
 
     # ---- max over ranks
     ms_step, ms_replay, e2e_ms, ms_plain = max_over_ranks([ms_step, ms_replay, e2e_ms, ms_plain], dist, "cuda")
+    # ---- the other workloads (rank 0, after the headline; free the headline's buffers first)
+    workloads = None
+    if rank == 0 and args.workloads != "none":
+        del dv, db, fac, dx, fac1
+        torch.cuda.empty_cache()
+        workloads = measure_workloads(args)
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
@@ -362,6 +610,8 @@ def run_ours(args):
         line["e2e"] = {"value": total_items / (e2e_ms * 1e-3), "unit": UNIT,
                        "h2d_bytes_per_step": batch * (nnz + n) * 8,
                        "d2h_bytes_per_step": batch * (1 + n) * 8}
+    if workloads:
+        line["workloads"] = workloads
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

@@ -123,6 +123,13 @@ typedef struct stc_plan_info {
 #define STC_EXPORT_TASKS 6      /* [ntasks][4]: Algorithm 1 (case, m, k, n), -1 = unused */
 #define STC_EXPORT_VALUE_MAP 7  /* [nnzA] offset (doubles) of each A entry in a factor */
 #define STC_EXPORT_TILE_OFFSETS 8 /* [ntiles] offset (doubles) of each tile's storage */
+#define STC_EXPORT_CHUNK_EXTENTS 9 /* [ntiles][8][2]: for each group of 16 stored columns
+                                     of an off-diagonal tile, the first and one past the
+                                     last local row holding a structural entry of L in
+                                     those columns (n_b, 0 if none); (-1, -1) for groups
+                                     past the stored width and for diagonal tiles.  The
+                                     tile products skip rows outside these extents (the
+                                     paper computes on full-height columns, Sec. 4.1). */
 
 /* Fill *opt with defaults (nb 128, auto route, auto ordering, ND leaf 64). */
 void stc_options_default(stc_options* opt);

@@ -29,7 +29,7 @@ ERRORS = {0: "ok", -1: "invalid argument", -2: "invalid pattern", -3: "out of me
 STC_ROUTE_AUTO, STC_ROUTE_DENSE, STC_ROUTE_SEMISPARSE, STC_ROUTE_SUPERNODAL = -1, 0, 1, 2
 STC_ORDER_AUTO, STC_ORDER_NATURAL, STC_ORDER_GIVEN, STC_ORDER_ND, STC_ORDER_RCM = 0, 1, 2, 3, 4
 (STC_EXPORT_PERM, STC_EXPORT_ETREE, STC_EXPORT_LP, STC_EXPORT_LI, STC_EXPORT_TILES, STC_EXPORT_AIND,
- STC_EXPORT_TASKS, STC_EXPORT_VALUE_MAP, STC_EXPORT_TILE_OFFSETS) = range(9)
+ STC_EXPORT_TASKS, STC_EXPORT_VALUE_MAP, STC_EXPORT_TILE_OFFSETS, STC_EXPORT_CHUNK_EXTENTS) = range(10)
 
 # every symbol include/stc.h declares
 EXPORTED = [

@@ -301,20 +301,25 @@ int build_tiles(stc_plan& P) {
     P.diag_tile.assign(nt, -1);
     vector<int32_t> slot(nt, -1);
     vector<int64_t> touched;
-    struct Acc { uint64_t m[2]; int r0, r1, kd; };
+    struct Acc { uint64_t m[2]; int r0, r1, kd; int32_t ext; };
+    vector<int16_t> clo, chi;  // per tile slot of this block column: column row extents
     vector<Acc> acc;
     int64_t off = 0;
     for (int64_t J = 0; J < nt; ++J) {
         P.colstart[J] = (int32_t)P.tiles.size();
         touched.clear();
         acc.clear();
+        clo.clear();
+        chi.clear();
         const int64_t c0 = J * nb, c1 = std::min(n, (J + 1) * nb);
         for (int64_t j = c0; j < c1; ++j)
             for (int64_t q = P.Lp[j]; q < P.Lp[j + 1]; ++q) {
                 int64_t i = P.Li[q], I = i / nb;
                 if (slot[I] < 0) {
                     slot[I] = (int32_t)acc.size();
-                    acc.push_back(Acc{{0, 0}, INT_MAX, -1, -1});
+                    acc.push_back(Acc{{0, 0}, INT_MAX, -1, -1, (int32_t)clo.size()});
+                    clo.resize(clo.size() + nb, (int16_t)nb);
+                    chi.resize(chi.size() + nb, 0);
                     touched.push_back(I);
                 }
                 Acc& a = acc[slot[I]];
@@ -322,6 +327,8 @@ int build_tiles(stc_plan& P) {
                 a.m[lc >> 6] |= 1ull << (lc & 63);
                 a.r0 = std::min(a.r0, lr);
                 a.r1 = std::max(a.r1, lr + 1);
+                clo[a.ext + lc] = (int16_t)std::min<int>(clo[a.ext + lc], lr);
+                chi[a.ext + lc] = (int16_t)std::max<int>(chi[a.ext + lc], lr + 1);
                 if (I == J) a.kd = std::max(a.kd, lr - lc);
             }
         std::sort(touched.begin(), touched.end());
@@ -342,6 +349,7 @@ int build_tiles(stc_plan& P) {
             P.full.push_back(cnt == nb);
             t.pd_slot = -1;
             t.aoff = -1;
+            t.xoff = -1;
             int64_t size;
             if (I == J) {
                 t.sw = int(c1 - c0);
@@ -375,6 +383,18 @@ int build_tiles(stc_plan& P) {
                     }
                 }
                 size = (int64_t)t.sw * nb;
+                // row extents of each kExtW stored columns (dense route: all n_b columns)
+                t.xoff = (int32_t)(P.cext.size() / 2);
+                for (int s0 = 0; s0 < t.sw; s0 += stc::kExtW) {
+                    int lo = int(nb), hi = 0;
+                    for (int s = s0; s < std::min(t.sw, s0 + stc::kExtW); ++s) {
+                        const int lc = dense ? s : cols[s];
+                        lo = std::min<int>(lo, clo[a.ext + lc]);
+                        hi = std::max<int>(hi, chi[a.ext + lc]);
+                    }
+                    P.cext.push_back((int16_t)lo);
+                    P.cext.push_back((int16_t)hi);
+                }
             }
             t.off = off;
             off += (size + 3) / 4 * 4;  // 32-byte aligned tiles
@@ -435,6 +455,11 @@ void stored_cols(const stc_plan& P, const stc::DTile& t, vector<int>& out) {
 
 }  // namespace
 
+// Kernel geometry the cost model mirrors: inner-dimension chunk of the tile products
+// and panel width of the TRSM.
+constexpr int kChunk = stc::kExtW;
+constexpr int kPanel = 32;
+
 stc::TaskSet* stc_plan::taskset(int32_t slices) {
     std::lock_guard<std::mutex> g(mu);
     auto it = tasksets.find(slices);
@@ -462,6 +487,74 @@ stc::TaskSet* stc_plan::taskset(int32_t slices) {
     vector<vector<int32_t>> producers(tiles.size());
     ts->nfinal.assign(tiles.size(), 0);
     vector<int> ca, cb;
+    // executed FMAs of the chunked products, with the same extent skipping as the kernel
+    auto ext = [&](const stc::DTile& T, int s0, int s1, int& lo, int& hi) {
+        if (T.xoff < 0) { lo = 0; hi = NB; return; }
+        lo = NB; hi = 0;
+        for (int q = s0 / stc::kExtW; q <= s1 / stc::kExtW; ++q) {
+            lo = std::min<int>(lo, cext[2 * (T.xoff + q)]);
+            hi = std::max<int>(hi, cext[2 * (T.xoff + q) + 1]);
+        }
+    };
+    auto inner_range = [&](const stc::DUpd& u, int k0, int K, bool b, int& s0, int& s1) {
+        if (u.kmap < 0) {
+            s0 = (b ? u.kb0 : u.ka0) + k0;
+            s1 = s0 + K - 1;
+        } else {
+            s0 = ts->imap[2 * (u.kmap + k0) + (b ? 1 : 0)];
+            s1 = ts->imap[2 * (u.kmap + k0 + K - 1) + (b ? 1 : 0)];
+        }
+    };
+    auto syrk_cost = [&](const stc::DUpd& u, int r0, int d0, int rb) {  // rows [d0,rb), cols [r0,rb)
+        const stc::DTile& A = tiles[u.a];
+        double c = 0.0;
+        for (int k0 = 0; k0 < u.klen; k0 += kChunk) {
+            const int K = std::min(kChunk, u.klen - k0);
+            int s0, s1, lo, hi;
+            inner_range(u, k0, K, false, s0, s1);
+            ext(A, s0, s1, lo, hi);
+            const int e0 = std::max(d0, lo), e1 = std::min(rb, hi);
+            if (e0 >= e1) continue;
+            const double rows = e1 - e0, rect = std::max(0, std::min(d0, e1) - std::max(r0, lo));
+            c += (rows * rect + rows * (rows + 1) / 2) * K;
+        }
+        return c;
+    };
+    auto gemm_cost = [&](const stc::DUpd& u, const stc::DTile& O) {
+        const stc::DTile& A = tiles[u.a];
+        const stc::DTile& B = tiles[u.b];
+        double c = 0.0;
+        for (int k0 = 0; k0 < u.klen; k0 += kChunk) {
+            const int K = std::min(kChunk, u.klen - k0);
+            int s0, s1, alo, ahi, blo, bhi;
+            inner_range(u, k0, K, false, s0, s1);
+            ext(A, s0, s1, alo, ahi);
+            inner_range(u, k0, K, true, s0, s1);
+            ext(B, s0, s1, blo, bhi);
+            const int e0 = std::max(u.ra0, alo), e1 = std::min(u.ra1, ahi);
+            int c0 = u.oc0, c1 = u.oc1;
+            if (O.c0 >= 0) { c0 = std::max(c0, blo - O.c0); c1 = std::min(c1, bhi - O.c0); }
+            if (e0 < e1 && c0 < c1) c += double(e1 - e0) * (c1 - c0) * K;
+        }
+        return c;
+    };
+    auto trsm_cost = [&](const stc::DTile& O, int tr0, int tr1) {
+        double c = 0.0;
+        for (int p = 0; p < O.sw; p += kPanel) {
+            const int pw = std::min(kPanel, O.sw - p);
+            for (int k0 = 0; k0 < p; k0 += kChunk) {
+                int lo, hi;
+                ext(O, k0, std::min(p, k0 + kChunk) - 1, lo, hi);
+                const int x0 = std::max(tr0, lo), x1 = std::min(tr1, hi);
+                if (x0 < x1) c += double(x1 - x0) * pw * std::min(kChunk, p - k0);
+            }
+            int lo, hi;
+            ext(O, p, p + pw - 1, lo, hi);
+            const int y0 = std::max(tr0, lo), y1 = std::min(tr1, hi);
+            if (y0 < y1) c += double(y1 - y0) * pw * (pw + 1) / 2;
+        }
+        return c;
+    };
     auto potrf_cost = [&](const stc::DTile& D) {
         double w = D.sw, kd = std::min<double>(D.kd, w - 1);
         return (D.kind == stc::TILE_DIAG_BAND) ? w * (kd + 1) * (kd + 1) / 2 : w * w * w / 6;
@@ -483,8 +576,7 @@ stc::TaskSet* stc_plan::taskset(int32_t slices) {
                 u.a = at; u.b = at; u.kmap = -1; u.klen = A.sw; u.ka0 = 0; u.kb0 = 0;
                 u.ra0 = A.r0; u.ra1 = A.r1; u.oc0 = A.r0; u.oc1 = A.r1;
                 ts->upds.push_back(u);
-                double r = A.r1 - A.r0;
-                mt.srcs.push_back(at); mt.nsrc.push_back(1); mt.ucost.push_back(r * (r + 1) / 2 * A.sw);
+                mt.srcs.push_back(at); mt.nsrc.push_back(1); mt.ucost.push_back(syrk_cost(u, A.r0, A.r0, A.r1));
             }
             t.uend = (int32_t)ts->upds.size();
             t.rs0 = 0; t.rs1 = NB; t.tr0 = 0; t.tr1 = NB;
@@ -532,9 +624,8 @@ stc::TaskSet* stc_plan::taskset(int32_t slices) {
                     u.a = at; u.b = at; u.kmap = -1; u.klen = A.sw; u.ka0 = 0; u.kb0 = 0;
                     u.ra0 = ra; u.ra1 = rb; u.oc0 = A.r0; u.oc1 = rb;
                     ts->upds.push_back(u);
-                    const double rows = rb - ra, cols_rect = ra - A.r0;
                     mt.srcs.push_back(at); mt.nsrc.push_back(1);
-                    mt.ucost.push_back((rows * cols_rect + rows * (rows + 1) / 2) * A.sw);
+                    mt.ucost.push_back(syrk_cost(u, A.r0, ra, rb));
                 }
                 t.uend = (int32_t)ts->upds.size();
                 if (t.uend == t.ubeg) continue;  // rows untouched by any SYRK
@@ -610,11 +701,11 @@ stc::TaskSet* stc_plan::taskset(int32_t slices) {
                     }
                     ts->upds.push_back(u);
                     ms.srcs.push_back(mtile); ms.srcs.push_back(kt); ms.nsrc.push_back(2);
-                    ms.ucost.push_back(double(u.ra1 - u.ra0) * (u.oc1 - u.oc0) * u.klen);
+                    ms.ucost.push_back(gemm_cost(u, O));
                 }
                 s.uend = (int32_t)ts->upds.size();
                 ms.final_tile = dk;
-                ms.fcost = double(tr1 - tr0) * O.sw * (O.sw + 1) / 2;
+                ms.fcost = trsm_cost(O, tr0, tr1);
                 producers[o].push_back((int32_t)tasks.size());
                 tasks.push_back(s);
                 meta.push_back(ms);
@@ -966,6 +1057,20 @@ extern "C" int stc_plan_export(const stc_plan* P, int what, void* buf, size_t* b
             for (const auto& T : P->tiles) tmp.push_back(T.off);
             src = tmp.data(); sz = tmp.size() * 8;
             break;
+        case STC_EXPORT_CHUNK_EXTENTS: {
+            const int groups = stc::kMaxNb / stc::kExtW;
+            tmp.assign(P->tiles.size() * groups * 2, -1);
+            for (size_t t = 0; t < P->tiles.size(); ++t) {
+                const auto& T = P->tiles[t];
+                if (T.xoff < 0) continue;
+                for (int q = 0; q * stc::kExtW < T.sw; ++q) {
+                    tmp[(t * groups + q) * 2] = P->cext[2 * (T.xoff + q)];
+                    tmp[(t * groups + q) * 2 + 1] = P->cext[2 * (T.xoff + q) + 1];
+                }
+            }
+            src = tmp.data(); sz = tmp.size() * 8;
+            break;
+        }
         default: return STC_ERR_INVALID_ARG;
     }
     if (!buf) { *bytes = sz; return STC_OK; }

@@ -32,8 +32,14 @@ struct DTile {
     int32_t r0, r1;   // structural row extent [r0, r1) inside the tile
     int32_t nfinal;   // value of the tile's completion counter once it is final
     int32_t pd_slot;  // diagonal tiles: index of the logdet partial; else -1
-    int32_t pad;
+    int32_t xoff;     // off-diagonal tiles: first (lo, hi) pair in the chunk-extent array; else -1
 };
+
+// Structural row extent of each group of kExtW consecutive stored columns of an
+// off-diagonal tile: rows outside [lo, hi) are zero in all of those columns, so a
+// product over those columns can skip them (empty group: lo = n_b, hi = 0).
+constexpr int kExtW = 16;
+constexpr int kMaxNb = 128;  // largest tile size n_b
 
 enum : int32_t { TASK_DIAG = 0, TASK_OFF = 1, TASK_SYRK = 2, TASK_POTRF = 3 };
 
@@ -93,6 +99,7 @@ struct DSCon {
 struct DevPlanArrays {          // device pointers of one plan's metadata
     DTile* tiles = nullptr;
     int16_t* saind = nullptr;   // stored-column -> logical-column lists
+    int16_t* cext = nullptr;    // per-tile chunk row extents, (lo, hi) pairs
     DTask* tasks = nullptr;     // in queue (ASAP) order
     DUpd* upds = nullptr;
     int16_t* imap = nullptr;    // inner-dimension (sa, sb) pairs
@@ -156,6 +163,7 @@ struct stc_plan {
     std::vector<int16_t> aind_struct;  // structural active columns (exported)
     std::vector<int8_t> contig, full;
     std::vector<int16_t> saind;        // stored-column lists (indexed tiles only)
+    std::vector<int16_t> cext;         // (lo, hi) row extent per kExtW stored columns
     std::vector<int32_t> colstart;     // tiles of block column J: [colstart[J], colstart[J+1])
     std::vector<int32_t> diag_tile;    // per block
     std::vector<int32_t> rowstart, rowtiles;  // per block row k: off-diagonal tiles (k,n), n asc

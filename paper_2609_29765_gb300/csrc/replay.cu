@@ -47,6 +47,7 @@ constexpr long long kDefaultSpin = 40000000LL;
 constexpr int kRRows = 64;
 constexpr int kRLd = kRRows + 1;
 constexpr int kRKc = 16;
+static_assert(kRKc == kExtW, "chunk extents are kept per staged inner chunk");
 constexpr int kRStLd = kNbMax + 8;
 constexpr int kRStage = kRKc * kRStLd;
 constexpr int kRPacked = kNbMax * (kNbMax + 1) / 2;
@@ -147,11 +148,17 @@ __device__ void mma_tiles(double* __restrict__ C, int ldc, int R, int Cn,
             cj = mt / MR;
         }
         const int r0 = ri * TR, c0 = cj * TC;
+        // the accumulators start from C, so the update needs no separate subtraction
         double acc[TR][TC];
 #pragma unroll
         for (int i = 0; i < TR; ++i)
 #pragma unroll
-            for (int j = 0; j < TC; ++j) acc[i][j] = 0.0;
+            for (int j = 0; j < TC; ++j) {
+                const int r = r0 + i, c = c0 + j;
+                acc[i][j] = 0.0;
+                if (r < R && c < Cn && (!LOWER || r >= c))
+                    acc[i][j] = PACKED ? C[pk(pnb, pr0 + r, pc0 + c)] : C[r + c * ldc];
+            }
         const double* a = A + r0;
         const double* b = B + c0;
 #pragma unroll 4
@@ -164,7 +171,7 @@ __device__ void mma_tiles(double* __restrict__ C, int ldc, int R, int Cn,
 #pragma unroll
             for (int i = 0; i < TR; ++i)
 #pragma unroll
-                for (int j = 0; j < TC; ++j) acc[i][j] = fma(av[i], bv[j], acc[i][j]);
+                for (int j = 0; j < TC; ++j) acc[i][j] = fma(-av[i], bv[j], acc[i][j]);
             a += lda;
             b += ldb;
         }
@@ -174,8 +181,8 @@ __device__ void mma_tiles(double* __restrict__ C, int ldc, int R, int Cn,
             for (int j = 0; j < TC; ++j) {
                 const int r = r0 + i, c = c0 + j;
                 if (r < R && c < Cn && (!LOWER || r >= c)) {
-                    if (PACKED) C[pk(pnb, pr0 + r, pc0 + c)] -= acc[i][j];
-                    else C[r + c * ldc] -= acc[i][j];
+                    if (PACKED) C[pk(pnb, pr0 + r, pc0 + c)] = acc[i][j];
+                    else C[r + c * ldc] = acc[i][j];
                 }
             }
     }
@@ -272,6 +279,7 @@ __device__ __forceinline__ void trsm_rows(double* X, int ldx, int R, int pw, con
 struct ReplayArgs {        // one job: a plan and a batch of value sets
     const DTile* tiles;
     const int16_t* saind;
+    const int16_t* cext;     // chunk row extents of the off-diagonal tiles
     const DTask* tasks;
     const DUpd* upds;
     const int16_t* imap;
@@ -362,6 +370,30 @@ __device__ void stage_cols(double* S, int ld, const double* T, int nb, int row0,
     });
 }
 
+// Union [lo, hi) of the structural row extents of stored columns [s0, s1] of tile T
+// (rows outside are zero in every one of those columns); [0, nb) without extents.
+__device__ __forceinline__ void col_ext(const int16_t* __restrict__ cext, const DTile& T, int nb, int s0, int s1,
+                                        int& lo, int& hi) {
+    if (T.xoff < 0) { lo = 0; hi = nb; return; }
+    lo = nb; hi = 0;
+    for (int q = s0 / kExtW; q <= s1 / kExtW; ++q) {
+        lo = min(lo, (int)cext[2 * (T.xoff + q)]);
+        hi = max(hi, (int)cext[2 * (T.xoff + q) + 1]);
+    }
+}
+
+// Stored columns of the A (or B) operand covered by inner positions [k0, k0+K) of u.
+__device__ __forceinline__ void inner_cols(const DUpd& u, const int16_t* imap, bool b, int k0, int K,
+                                           int& s0, int& s1) {
+    if (u.kmap < 0) {
+        s0 = (b ? u.kb0 : u.ka0) + k0;
+        s1 = s0 + K - 1;
+    } else {
+        s0 = imap[2 * (u.kmap + k0) + (b ? 1 : 0)];
+        s1 = imap[2 * (u.kmap + k0 + K - 1) + (b ? 1 : 0)];
+    }
+}
+
 // B rows for a GEMM: rows = logical columns of the output tile's stored columns oc0.. .
 __device__ void stage_rows_gather(double* S, int ld, const double* T, int nb, const DTile& O,
                                   const int16_t* saind, int oc0, int Cn, const DUpd& u,
@@ -390,21 +422,23 @@ __device__ void stage_rows_gather(double* S, int ld, const double* T, int nb, co
 // reduced in a fixed order at the end.
 constexpr int kPp = 8;
 
+template <int PP>
 struct PotrfShared {
-    double blk[kPp][kPp];  // L of the current panel's diagonal block, blk[row][col]
-    double inv[kPp];       // 1 / L_jj of the panel
+    double blk[PP][PP];    // L of the current panel's diagonal block, blk[row][col]
+    double inv[PP];        // 1 / L_jj of the panel
     int bad;
 };
 
 // Warp 0 only: unblocked Cholesky of the pw x pw diagonal block at (p, p).
-__device__ void potrf_diag_block(double* P, int nb, int p, int pw, PotrfShared& sh) {
+template <int PP>
+__device__ void potrf_diag_block(double* P, int nb, int p, int pw, PotrfShared<PP>& sh) {
     const int lane = threadIdx.x;
-    double x[kPp];
+    double x[PP];
 #pragma unroll
-    for (int l = 0; l < kPp; ++l) x[l] = (lane < pw && l <= lane) ? P[pk(nb, p + lane, p + l)] : 0.0;
+    for (int l = 0; l < PP; ++l) x[l] = (lane < pw && l <= lane) ? P[pk(nb, p + lane, p + l)] : 0.0;
     int badl = -1;
 #pragma unroll
-    for (int j = 0; j < kPp; ++j) {
+    for (int j = 0; j < PP; ++j) {
         if (j < pw) {
             double inv = 0.0;
             if (lane == j) {
@@ -416,7 +450,7 @@ __device__ void potrf_diag_block(double* P, int nb, int p, int pw, PotrfShared& 
             inv = __shfl_sync(0xffffffffu, inv, j);
             if (lane > j) x[j] *= inv;
 #pragma unroll
-            for (int l = j + 1; l < kPp; ++l) {
+            for (int l = j + 1; l < PP; ++l) {
                 const double llj = __shfl_sync(0xffffffffu, x[j], l);  // L[p+l][p+j]
                 if (l < pw && lane >= l) x[l] = fma(-x[j], llj, x[l]);
             }
@@ -425,9 +459,9 @@ __device__ void potrf_diag_block(double* P, int nb, int p, int pw, PotrfShared& 
     }
     if (lane < pw) {
 #pragma unroll
-        for (int l = 0; l < kPp; ++l) sh.blk[lane][l] = l <= lane ? x[l] : 0.0;
+        for (int l = 0; l < PP; ++l) sh.blk[lane][l] = l <= lane ? x[l] : 0.0;
 #pragma unroll
-        for (int l = 0; l < kPp; ++l)
+        for (int l = 0; l < PP; ++l)
             if (l <= lane) P[pk(nb, p + lane, p + l)] = x[l];
     }
     const unsigned badmask = __ballot_sync(0xffffffffu, badl >= 0);
@@ -436,17 +470,19 @@ __device__ void potrf_diag_block(double* P, int nb, int p, int pw, PotrfShared& 
 
 // All threads: rows [p+pw, rend) of panel p solved against the diagonal block; the solved
 // rows also go to S (row i at S[i - p - pw], column l at stride kRStLd), zero-padded.
-__device__ void potrf_rows_below(double* P, int nb, int p, int pw, int rend, double* S, const PotrfShared& sh) {
+template <int PP>
+__device__ void potrf_rows_below(double* P, int nb, int p, int pw, int rend, double* S,
+                                 const PotrfShared<PP>& sh) {
     const int R2 = rend - p - pw;
     const int R2p = ((max(R2, 0) + 3) & ~3) + 4;
     for (int rr = threadIdx.x; rr < R2p; rr += kThreads) {
         const int i = p + pw + rr;
-        double x[kPp];
+        double x[PP];
         if (rr < R2) {
 #pragma unroll
-            for (int l = 0; l < kPp; ++l) x[l] = l < pw ? P[pk(nb, i, p + l)] : 0.0;
+            for (int l = 0; l < PP; ++l) x[l] = l < pw ? P[pk(nb, i, p + l)] : 0.0;
 #pragma unroll
-            for (int j = 0; j < kPp; ++j) {
+            for (int j = 0; j < PP; ++j) {
                 if (j < pw) {
                     double sacc = x[j];
 #pragma unroll
@@ -455,35 +491,36 @@ __device__ void potrf_rows_below(double* P, int nb, int p, int pw, int rend, dou
                 }
             }
 #pragma unroll
-            for (int l = 0; l < kPp; ++l)
+            for (int l = 0; l < PP; ++l)
                 if (l < pw) P[pk(nb, i, p + l)] = x[l];
         } else {
 #pragma unroll
-            for (int l = 0; l < kPp; ++l) x[l] = 0.0;
+            for (int l = 0; l < PP; ++l) x[l] = 0.0;
         }
 #pragma unroll
-        for (int l = 0; l < kPp; ++l) S[rr + l * kRStLd] = x[l];
+        for (int l = 0; l < PP; ++l) S[rr + l * kRStLd] = x[l];
     }
 }
 
+template <int PP>
 __device__ void potrf_packed(double* P, int nb, int w, int kd, double* S, int* bad, double* logsum) {
-    __shared__ PotrfShared sh;
+    __shared__ PotrfShared<PP> sh;
     if (threadIdx.x == 0) sh.bad = -1;
     __syncthreads();
     // panel 0
     {
-        const int pw = min(kPp, w);
+        const int pw = min(PP, w);
         if (threadIdx.x < 32) potrf_diag_block(P, nb, 0, pw, sh);
         __syncthreads();
         potrf_rows_below(P, nb, 0, pw, min(w, pw + kd), S, sh);
         __syncthreads();
     }
-    for (int p = 0; p < w; p += kPp) {
-        const int pw = min(kPp, w - p);
+    for (int p = 0; p < w; p += PP) {
+        const int pw = min(PP, w - p);
         const int rend = min(w, p + pw + kd);
         const int pn = p + pw;
         if (pn >= w) break;
-        const int pwn = min(kPp, w - pn);
+        const int pwn = min(PP, w - pn);
         const int Rn = rend - pn;  // rows of panel p's trailing region
         // (A) next panel's columns first: rows [pn, rend) x columns [pn, pn+pwn)
         if (Rn > 0) {
@@ -574,18 +611,22 @@ __global__ void __launch_bounds__(kThreads, 2) replay_kernel(const __grid_consta
                     if (threadIdx.x == 0) s_ok = wait_counter(cnt + u.a, A.nfinal, a.spin, &a.hdr->status);
                     __syncthreads();
                     if (!s_ok) break;
-                    const int R = u.ra1 - u.ra0;
                     for (int k0 = 0; k0 < u.klen; k0 += kRKc) {
                         const int K = min(kRKc, u.klen - k0);
-                        stage_cols(S0, kRStLd, F + A.off, nb, u.ra0, R, u, a.imap, false, k0, K);
+                        int s0, s1, lo, hi;
+                        inner_cols(u, a.imap, false, k0, K, s0, s1);
+                        col_ext(a.cext, A, nb, s0, s1, lo, hi);
+                        const int e0 = max(u.ra0, lo), e1 = min(u.ra1, hi);
+                        if (e0 >= e1) continue;  // the chunk is zero on these rows
+                        stage_cols(S0, kRStLd, F + A.off, nb, e0, e1 - e0, u, a.imap, false, k0, K);
                         __syncthreads();
-                        mma_sub_packed<true>(C, nb, u.ra0, u.ra0, R, R, S0, kRStLd, S0, kRStLd, K);
+                        mma_sub_packed<true>(C, nb, e0, e0, e1 - e0, e1 - e0, S0, kRStLd, S0, kRStLd, K);
                         __syncthreads();
                     }
                 }
                 if (s_ok) {
                     int bad; double ls;
-                    potrf_packed(C, nb, O.sw, min(O.kd, nb - 1), S0, &bad, &ls);
+                    potrf_packed<kPp>(C, nb, O.sw, min(O.kd, nb - 1), S0, &bad, &ls);
                     if (threadIdx.x == 0) {
                         if (bad >= 0) record_info(a.info + item, O.J * nb + bad + 1);
                         F[a.poff + O.pd_slot] = bad >= 0 ? __longlong_as_double(0x7ff8000000000000LL) : ls;
@@ -609,16 +650,23 @@ __global__ void __launch_bounds__(kThreads, 2) replay_kernel(const __grid_consta
                     if (threadIdx.x == 0) s_ok = wait_counter(cnt + u.a, A.nfinal, a.spin, &a.hdr->status);
                     __syncthreads();
                     if (!s_ok) break;
-                    const int r0 = u.oc0, d0 = u.ra0, rb = u.ra1, Rs = rb - r0;
+                    // output rows [d0, rb), columns [r0, rb) (rectangle left of d0, then triangle)
+                    const int r0 = u.oc0, d0 = u.ra0, rb = u.ra1;
                     for (int k0 = 0; k0 < u.klen; k0 += kRKc) {
                         const int K = min(kRKc, u.klen - k0);
-                        stage_cols(S0, kRStLd, F + A.off, nb, r0, Rs, u, a.imap, false, k0, K);
+                        int s0, s1, lo, hi;
+                        inner_cols(u, a.imap, false, k0, K, s0, s1);
+                        col_ext(a.cext, A, nb, s0, s1, lo, hi);
+                        const int q0 = max(r0, lo), e0 = max(d0, lo), e1 = min(rb, hi);
+                        if (e0 >= e1) continue;  // the chunk is zero on these rows
+                        stage_cols(S0, kRStLd, F + A.off, nb, q0, e1 - q0, u, a.imap, false, k0, K);
                         __syncthreads();
-                        if (d0 > r0)
-                            mma_sub<false>(C + (d0 - t.rs0) + r0 * kRLd, kRLd, rb - d0, d0 - r0,
-                                           S0 + (d0 - r0), kRStLd, S0, kRStLd, K);
-                        mma_sub<true>(C + (d0 - t.rs0) + d0 * kRLd, kRLd, rb - d0, rb - d0,
-                                      S0 + (d0 - r0), kRStLd, S0 + (d0 - r0), kRStLd, K);
+                        const int ch = min(d0, e1);
+                        if (ch > q0)
+                            mma_sub<false>(C + (e0 - t.rs0) + q0 * kRLd, kRLd, e1 - e0, ch - q0,
+                                           S0 + (e0 - q0), kRStLd, S0, kRStLd, K);
+                        mma_sub<true>(C + (e0 - t.rs0) + e0 * kRLd, kRLd, e1 - e0, e1 - e0,
+                                      S0 + (e0 - q0), kRStLd, S0 + (e0 - q0), kRStLd, K);
                         __syncthreads();
                     }
                 }
@@ -647,13 +695,22 @@ __global__ void __launch_bounds__(kThreads, 2) replay_kernel(const __grid_consta
                                wait_counter(cnt + u.b, B.nfinal, a.spin, &a.hdr->status);
                     __syncthreads();
                     if (!s_ok) break;
-                    const int Ra = u.ra1 - u.ra0, Cn = u.oc1 - u.oc0;
                     for (int k0 = 0; k0 < u.klen; k0 += kRKc) {
                         const int K = min(kRKc, u.klen - k0);
-                        stage_cols(S0, kRStLd, F + A.off, nb, u.ra0, Ra, u, a.imap, false, k0, K);
-                        stage_rows_gather(S1, kRStLd, F + B.off, nb, O, a.saind, u.oc0, Cn, u, a.imap, k0, K);
+                        int s0, s1, alo, ahi, blo, bhi;
+                        inner_cols(u, a.imap, false, k0, K, s0, s1);
+                        col_ext(a.cext, A, nb, s0, s1, alo, ahi);
+                        inner_cols(u, a.imap, true, k0, K, s0, s1);
+                        col_ext(a.cext, B, nb, s0, s1, blo, bhi);
+                        // rows of A and (contiguous output) columns of B that are nonzero here
+                        const int e0 = max(u.ra0, alo), e1 = min(u.ra1, ahi);
+                        int c0 = u.oc0, c1 = u.oc1;
+                        if (O.c0 >= 0) { c0 = max(c0, blo - O.c0); c1 = min(c1, bhi - O.c0); }
+                        if (e0 >= e1 || c0 >= c1) continue;
+                        stage_cols(S0, kRStLd, F + A.off, nb, e0, e1 - e0, u, a.imap, false, k0, K);
+                        stage_rows_gather(S1, kRStLd, F + B.off, nb, O, a.saind, c0, c1 - c0, u, a.imap, k0, K);
                         __syncthreads();
-                        mma_sub<false>(C + (u.ra0 - t.rs0) + u.oc0 * kRLd, kRLd, Ra, Cn, S0, kRStLd,
+                        mma_sub<false>(C + (e0 - t.rs0) + c0 * kRLd, kRLd, e1 - e0, c1 - c0, S0, kRStLd,
                                        S1, kRStLd, K);
                         __syncthreads();
                     }
@@ -663,13 +720,16 @@ __global__ void __launch_bounds__(kThreads, 2) replay_kernel(const __grid_consta
                 if (s_ok && threadIdx.x == 0) s_ok = wait_counter(cnt + t.diag, D.nfinal, a.spin, &a.hdr->status);
                 __syncthreads();
                 if (s_ok) {
+                    // rows of X outside a column group's extent are zero there and stay zero
                     const double* DT = F + D.off;
-                    double* X = C + (t.tr0 - t.rs0);
-                    const int RX = t.tr1 - t.tr0;
                     for (int p = 0; p < sw; p += kPb) {
                         const int pw = min(kPb, sw - p);
                         for (int k0 = 0; k0 < p; k0 += kRKc) {
                             const int K = min(kRKc, p - k0);
+                            int lo, hi;
+                            col_ext(a.cext, O, nb, k0, k0 + K - 1, lo, hi);
+                            const int x0 = max(t.tr0, lo), x1 = min(t.tr1, hi);
+                            if (x0 >= x1) continue;
                             const int Cp = ((pw + 3) & ~3) + 4;
                             for_rc(Cp, K, [&](int c, int k) {
                                 double v = 0.0;
@@ -679,9 +739,14 @@ __global__ void __launch_bounds__(kThreads, 2) replay_kernel(const __grid_consta
                                 S1[c + k * kRStLd] = v;
                             });
                             __syncthreads();
-                            mma_sub<false>(X + p * kRLd, kRLd, RX, pw, X + k0 * kRLd, kRLd, S1, kRStLd, K);
+                            double* X = C + (x0 - t.rs0);
+                            mma_sub<false>(X + p * kRLd, kRLd, x1 - x0, pw, X + k0 * kRLd, kRLd, S1, kRStLd, K);
                             __syncthreads();
                         }
+                        int lo, hi;
+                        col_ext(a.cext, O, nb, p, p + pw - 1, lo, hi);
+                        const int y0 = max(t.tr0, lo), y1 = min(t.tr1, hi);
+                        if (y0 >= y1) continue;
                         // diagonal block of the panel and its reciprocal diagonal
                         for (int idx = threadIdx.x; idx < kPb * kPb; idx += kThreads) {
                             const int i = idx & (kPb - 1), j = idx / kPb;
@@ -693,7 +758,7 @@ __global__ void __launch_bounds__(kThreads, 2) replay_kernel(const __grid_consta
                         __syncthreads();
                         if (threadIdx.x < pw) sv[threadIdx.x] = 1.0 / S0[threadIdx.x * (kPb + 1)];
                         __syncthreads();
-                        trsm_rows(X + p * kRLd, kRLd, RX, pw, S0, kPb, sv);
+                        trsm_rows(C + (y0 - t.rs0) + p * kRLd, kRLd, y1 - y0, pw, S0, kPb, sv);
                         __syncthreads();
                     }
                     store_off(C, kRLd, F + O.off, nb, t.rs0, R, sw);
@@ -1277,7 +1342,7 @@ int upload(T** dst, const std::vector<T>& src) {
 
 void free_dev(stc_plan* P) {
     DevPlanArrays& d = P->dev;
-    void* ptrs[] = {d.saind, d.value_map, d.pad_diag, d.csc_map, d.perm, d.srow_beg,
+    void* ptrs[] = {d.saind, d.cext, d.value_map, d.pad_diag, d.csc_map, d.perm, d.srow_beg,
                     d.srow_tiles, d.scol_beg, d.diag_tile, d.sinv, d.stasks, d.scons, d.vdiag,
                     d.arow, d.acol};
     for (void* p : ptrs)
@@ -1305,6 +1370,7 @@ int ensure_plan(stc_plan* P, int dev) {
     int rc;
     std::vector<int32_t> perm32(P->perm.begin(), P->perm.end());
     if ((rc = upload(&d.saind, P->saind))) return rc;
+    if ((rc = upload(&d.cext, P->cext))) return rc;
     if ((rc = upload(&d.value_map, P->value_map))) return rc;
     if ((rc = upload(&d.pad_diag, P->pad_diag))) return rc;
     if ((rc = upload(&d.csc_map, P->csc_map))) return rc;
@@ -1385,7 +1451,7 @@ long long replay_ctas(int sms, long long batch) { return batch >= 16 ? 2LL * sms
 
 void fill_job(ReplayArgs& a, const stc_plan* P, const TaskSet* ts, void* d_factor, int* counters, int32_t* d_info,
               int64_t batch, WorkHeader* hdr) {
-    a.tiles = ts->d_tiles; a.saind = P->dev.saind; a.tasks = ts->d_tasks; a.upds = ts->d_upds;
+    a.tiles = ts->d_tiles; a.saind = P->dev.saind; a.cext = P->dev.cext; a.tasks = ts->d_tasks; a.upds = ts->d_upds;
     a.imap = ts->d_imap; a.factor = (double*)d_factor; a.fstride = P->factor_doubles;
     a.poff = P->partial_off; a.hdr = hdr; a.counters = counters;
     a.ntiles = (int)P->tiles.size(); a.info = d_info; a.ntasks = (int)ts->tasks.size();

@@ -219,3 +219,42 @@ def test_export_buffer_too_small():
     buf = np.empty(1, dtype=np.int64)
     rc = L.lib().stc_plan_export(P.h, L.STC_EXPORT_PERM, buf.ctypes.data_as(L.C.c_void_p), L.C.byref(sz))
     assert rc == L.STC_ERR_BUFFER_TOO_SMALL and sz.value == 80
+
+
+def _chunk_extents_brute(F, t, nb, n, dense):
+    """Per off-diagonal tile and group of 16 stored columns, the structural row extent,
+    from the oracle's symbolic structure of L."""
+    out = np.full((len(t["I"]), 8, 2), -1, dtype=np.int64)
+    for k, (I_, J_) in enumerate(zip(t["I"], t["J"])):
+        if I_ == J_:
+            continue
+        if dense:
+            cols = np.arange(nb)
+        else:
+            cols = t["aind"][t["aoff"][k]:t["aoff"][k] + t["nact"][k]]
+        for q in range(0, len(cols), 16):
+            lo, hi = nb, 0
+            for lc in cols[q:q + 16]:
+                j = J_ * nb + lc
+                if j >= n:
+                    continue
+                rows = F.Li[F.Lp[j]:F.Lp[j + 1]]
+                rows = rows[rows // nb == I_] - I_ * nb
+                if len(rows):
+                    lo, hi = min(lo, int(rows.min())), max(hi, int(rows.max()) + 1)
+            out[k, q // 16] = (lo, hi)
+    return out
+
+
+@pytest.mark.parametrize("case", [c for c in _cases() if c[0] in ("c1_nd_nb64", "band_nb128",
+                                                                  "stcov_small_nd_nb32", "random0_given",
+                                                                  "random1_given")],
+                         ids=lambda c: c[0])
+@pytest.mark.parametrize("route", ["semisparse", "dense"])
+def test_chunk_row_extents_vs_oracle_structure(case, route):
+    name, n, Ap, Ai, coords, kw, perm = case
+    P = Plan(n, Ap, Ai, coords=coords, perm=perm, route=route, **kw)
+    F = O.OracleFactor(n, Ap, Ai, P.export("perm"))
+    t = F.tile_map(kw["nb"])
+    ext = P.export("chunk_extents")
+    assert np.array_equal(ext, _chunk_extents_brute(F, t, kw["nb"], n, route == "dense"))
