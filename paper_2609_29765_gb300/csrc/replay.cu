@@ -410,63 +410,13 @@ __device__ void stage_rows_gather(double* S, int ld, const double* T, int nb, co
     });
 }
 
-// Blocked right-looking Cholesky of the w x w leading block of the packed lower
-// triangle P (pk layout, tile width nb) in shared memory, panel width kPp = 8, with a
-// one-panel look-ahead.  Per panel: warp 0 factors the 8x8 diagonal block in registers
-// (one row per lane, pivots broadcast by shuffle); the rows below the block are solved
-// against it, one row per thread, and copied to the staging buffer S; then the next
-// panel's columns get the rank-8 update first, so that warp 0 can factor the next
-// diagonal block while warps 1-7 apply the rest of the trailing update.  Rows more than
-// kd below the diagonal are structurally zero and skipped.  *bad receives the first
-// non-positive pivot column (or -1); *logsum = sum_j log L_jj, one log per diagonal entry
-// reduced in a fixed order at the end.
-constexpr int kPp = 8;
-
+// POTRF of a diagonal tile held as a packed lower triangle (see potrf_packed below).
 template <int PP>
 struct PotrfShared {
     double blk[PP][PP];    // L of the current panel's diagonal block, blk[row][col]
     double inv[PP];        // 1 / L_jj of the panel
     int bad;
 };
-
-// Warp 0 only: unblocked Cholesky of the pw x pw diagonal block at (p, p).
-template <int PP>
-__device__ void potrf_diag_block(double* P, int nb, int p, int pw, PotrfShared<PP>& sh) {
-    const int lane = threadIdx.x;
-    double x[PP];
-#pragma unroll
-    for (int l = 0; l < PP; ++l) x[l] = (lane < pw && l <= lane) ? P[pk(nb, p + lane, p + l)] : 0.0;
-    int badl = -1;
-#pragma unroll
-    for (int j = 0; j < PP; ++j) {
-        if (j < pw) {
-            double inv = 0.0;
-            if (lane == j) {
-                const double d = x[j];
-                if (!(d > 0.0)) badl = p + j;
-                inv = rsqrt(d);
-                x[j] = d * inv;
-            }
-            inv = __shfl_sync(0xffffffffu, inv, j);
-            if (lane > j) x[j] *= inv;
-#pragma unroll
-            for (int l = j + 1; l < PP; ++l) {
-                const double llj = __shfl_sync(0xffffffffu, x[j], l);  // L[p+l][p+j]
-                if (l < pw && lane >= l) x[l] = fma(-x[j], llj, x[l]);
-            }
-            if (lane == j) sh.inv[j] = inv;
-        }
-    }
-    if (lane < pw) {
-#pragma unroll
-        for (int l = 0; l < PP; ++l) sh.blk[lane][l] = l <= lane ? x[l] : 0.0;
-#pragma unroll
-        for (int l = 0; l < PP; ++l)
-            if (l <= lane) P[pk(nb, p + lane, p + l)] = x[l];
-    }
-    const unsigned badmask = __ballot_sync(0xffffffffu, badl >= 0);
-    if (lane == 0 && badmask && sh.bad < 0) sh.bad = p + __ffs(badmask) - 1;
-}
 
 // All threads: rows [p+pw, rend) of panel p solved against the diagonal block; the solved
 // rows also go to S (row i at S[i - p - pw], column l at stride kRStLd), zero-padded.
@@ -502,49 +452,93 @@ __device__ void potrf_rows_below(double* P, int nb, int p, int pw, int rend, dou
     }
 }
 
-template <int PP>
+// Warp 0 only: the 8x8 diagonal block at (p, p), first reduced by the rank-kw update
+// from the solved rows of the previous panel (S rows 0..rv-1, columns at stride ld; rows
+// from rv on are outside the previous panel's band and zero there), then factored.  Each lane holds two entries of one row, (r, c0) and (r, c0 + 1) with
+// r = lane / 4 and c0 = 2 (lane % 4), so a pivot costs one reciprocal square root and
+// two fused multiply-adds per lane instead of one per later column.
+__device__ void potrf_diag8(double* P, int nb, int p, int pw, const double* S, int ld, int kw, int rv,
+                            PotrfShared<8>& sh) {
+    const int lane = threadIdx.x & 31;
+    const int r = lane >> 2, c0 = 2 * (lane & 3);
+    double x[2];
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+        const int c = c0 + e;
+        double v = 0.0;
+        if (r < pw && c <= r) {
+            v = P[pk(nb, p + r, p + c)];
+            if (r < rv)
+                for (int m = 0; m < kw; ++m) v = fma(-S[r + m * ld], S[c + m * ld], v);
+        }
+        x[e] = v;
+    }
+    int badl = -1;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        if (j < pw) {
+            const int src = 4 * j + (j >> 1);
+            const double d = __shfl_sync(0xffffffffu, x[j & 1], src);
+            if (!(d > 0.0) && badl < 0) badl = p + j;  // the first non-positive pivot
+            const double inv = rsqrt(d);
+            if ((lane & 3) == (j >> 1) && r >= j) x[j & 1] = (r == j) ? d * inv : x[j & 1] * inv;
+            // L(r, j) and L(c, j) of this lane's entries, then the rank-1 update
+            const double lr = __shfl_sync(0xffffffffu, x[j & 1], 4 * r + (j >> 1));
+            const double l0 = __shfl_sync(0xffffffffu, x[j & 1], 4 * c0 + (j >> 1));
+            const double l1 = __shfl_sync(0xffffffffu, x[j & 1], 4 * (c0 + 1) + (j >> 1));
+            if (c0 > j && r >= c0) x[0] = fma(-lr, l0, x[0]);
+            if (c0 + 1 > j && r >= c0 + 1) x[1] = fma(-lr, l1, x[1]);
+            if (lane == 0) sh.inv[j] = inv;
+        }
+    }
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+        const int c = c0 + e;
+        const bool in = r < pw && c <= r;
+        sh.blk[r][c] = in ? x[e] : 0.0;
+        if (in) P[pk(nb, p + r, p + c)] = x[e];
+    }
+    if (lane == 0 && badl >= 0 && sh.bad < 0) sh.bad = badl;
+}
+
+// Blocked right-looking Cholesky of the w x w leading block of the packed lower
+// triangle P (pk layout, tile width nb) in shared memory, panels of 8 with a one-panel
+// look-ahead: warp 0 applies the previous panel's rank-8 update to the next 8x8
+// diagonal block and factors it, while warps 1-7 update everything below that block
+// (the rest of the next panel's columns and the trailing triangle) in one pass; then
+// the rows below the new block are solved against it, one row per thread, and copied to
+// the staging buffer S for the next step.  Rows more than kd below the diagonal are
+// structurally zero and skipped.  *bad receives the first non-positive pivot column (or
+// -1); *logsum = sum_j log L_jj, one log per diagonal entry reduced in a fixed order.
 __device__ void potrf_packed(double* P, int nb, int w, int kd, double* S, int* bad, double* logsum) {
-    __shared__ PotrfShared<PP> sh;
+    __shared__ PotrfShared<8> sh;
     if (threadIdx.x == 0) sh.bad = -1;
     __syncthreads();
-    // panel 0
     {
-        const int pw = min(PP, w);
-        if (threadIdx.x < 32) potrf_diag_block(P, nb, 0, pw, sh);
+        const int pw = min(8, w);
+        if (threadIdx.x < 32) potrf_diag8(P, nb, 0, pw, S, kRStLd, 0, 0, sh);
         __syncthreads();
-        potrf_rows_below(P, nb, 0, pw, min(w, pw + kd), S, sh);
+        potrf_rows_below<8>(P, nb, 0, pw, min(w, pw + kd), S, sh);
         __syncthreads();
     }
-    for (int p = 0; p < w; p += PP) {
-        const int pw = min(PP, w - p);
+    for (int p = 0; p < w; p += 8) {
+        const int pw = min(8, w - p);
         const int rend = min(w, p + pw + kd);
         const int pn = p + pw;
         if (pn >= w) break;
-        const int pwn = min(PP, w - pn);
-        const int Rn = rend - pn;  // rows of panel p's trailing region
-        // (A) next panel's columns first: rows [pn, rend) x columns [pn, pn+pwn)
-        if (Rn > 0) {
-            const int sq = min(pwn, Rn);
-            mma_tiles<true, 2, 2, true>(P, 0, sq, sq, S, kRStLd, S, kRStLd, pw, nb, pn, pn);
-            if (Rn > pwn)
-                mma_tiles<false, 2, 2, true>(P, 0, Rn - pwn, pwn, S + pwn, kRStLd, S, kRStLd, pw, nb, pn + pwn, pn);
-        }
-        __syncthreads();
-        // (B) warp 0 factors the next diagonal block while warps 1-7 finish the update
+        const int pwn = min(8, w - pn);
+        const int R3 = rend - pn - pwn;  // rows below the next diagonal block
         if (threadIdx.x < 32) {
-            potrf_diag_block(P, nb, pn, pwn, sh);
-        } else {
-            const int R3 = rend - pn - pwn;
-            if (R3 > 0)
-                mma_sub_packed<true>(P, nb, pn + pwn, pn + pwn, R3, R3, S + pwn, kRStLd, S + pwn, kRStLd, pw,
-                                     32, kThreads - 32);
+            potrf_diag8(P, nb, pn, pwn, S, kRStLd, pw, rend - pn, sh);
+        } else if (R3 > 0) {
+            mma_sub_packed<false>(P, nb, pn + pwn, pn, R3, pwn, S + pwn, kRStLd, S, kRStLd, pw, 32, kThreads - 32);
+            mma_sub_packed<true>(P, nb, pn + pwn, pn + pwn, R3, R3, S + pwn, kRStLd, S + pwn, kRStLd, pw,
+                                 32, kThreads - 32);
         }
         __syncthreads();
-        // (C) rows below the next diagonal block
-        potrf_rows_below(P, nb, pn, pwn, min(w, pn + pwn + kd), S, sh);
+        potrf_rows_below<8>(P, nb, pn, pwn, min(w, pn + pwn + kd), S, sh);
         __syncthreads();
     }
-    // sum_j log L_jj: one log per thread, fixed-order tree reduction
     __shared__ double s_red[kThreads / 32];
     double lg = 0.0;
     for (int j = threadIdx.x; j < w; j += kThreads) lg += log(P[pk(nb, j, j)]);
@@ -626,7 +620,7 @@ __global__ void __launch_bounds__(kThreads, 2) replay_kernel(const __grid_consta
                 }
                 if (s_ok) {
                     int bad; double ls;
-                    potrf_packed<kPp>(C, nb, O.sw, min(O.kd, nb - 1), S0, &bad, &ls);
+                    potrf_packed(C, nb, O.sw, min(O.kd, nb - 1), S0, &bad, &ls);
                     if (threadIdx.x == 0) {
                         if (bad >= 0) record_info(a.info + item, O.J * nb + bad + 1);
                         F[a.poff + O.pd_slot] = bad >= 0 ? __longlong_as_double(0x7ff8000000000000LL) : ls;
