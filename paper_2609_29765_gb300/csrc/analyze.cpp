@@ -458,7 +458,7 @@ void stored_cols(const stc_plan& P, const stc::DTile& t, vector<int>& out) {
 // Kernel geometry the cost model mirrors: inner-dimension chunk of the tile products
 // and panel width of the TRSM.
 constexpr int kChunk = stc::kExtW;
-constexpr int kPanel = 32;
+constexpr int kPanel = stc::kPanelW;
 
 stc::TaskSet* stc_plan::taskset(int32_t slices) {
     std::lock_guard<std::mutex> g(mu);
@@ -555,6 +555,8 @@ stc::TaskSet* stc_plan::taskset(int32_t slices) {
         }
         return c;
     };
+    // the factored diagonal tile is published kPanel columns at a time (one count each)
+    auto diag_groups = [&](const stc::DTile& D) { return (D.sw + kPanel - 1) / kPanel; };
     auto potrf_cost = [&](const stc::DTile& D) {
         double w = D.sw, kd = std::min<double>(D.kd, w - 1);
         return (D.kind == stc::TILE_DIAG_BAND) ? w * (kd + 1) * (kd + 1) / 2 : w * w * w / 6;
@@ -584,7 +586,7 @@ stc::TaskSet* stc_plan::taskset(int32_t slices) {
             producers[dk].push_back((int32_t)tasks.size());
             tasks.push_back(t);
             meta.push_back(mt);
-            ts->nfinal[dk] = 1;
+            ts->nfinal[dk] = diag_groups(D);
         } else {
             // TASK_SYRK row slices of (k,k), then TASK_POTRF.  Row r of the lower
             // triangle costs ~(r+1): slices are cut (on 8-row boundaries, at most 64 rows)
@@ -643,7 +645,7 @@ stc::TaskSet* stc_plan::taskset(int32_t slices) {
             producers[dk].push_back((int32_t)tasks.size());
             tasks.push_back(p);
             meta.push_back(mp);
-            ts->nfinal[dk] = nsl + 1;
+            ts->nfinal[dk] = nsl + diag_groups(D);
         }
         // OFF(m,k) row slices: GEMM from every n in N(k) & N(m), n < k, then TRSM
         for (int32_t o = colstart[k]; o < colstart[k + 1]; ++o) {

@@ -40,6 +40,9 @@ struct DTile {
 // product over those columns can skip them (empty group: lo = n_b, hi = 0).
 constexpr int kExtW = 16;
 constexpr int kMaxNb = 128;  // largest tile size n_b
+// Panel width of the blocked TRSM; a factored diagonal tile is published to its TRSMs
+// this many columns at a time.
+constexpr int kPanelW = 32;
 
 enum : int32_t { TASK_DIAG = 0, TASK_OFF = 1, TASK_SYRK = 2, TASK_POTRF = 3 };
 

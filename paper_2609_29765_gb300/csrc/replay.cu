@@ -33,7 +33,7 @@ constexpr int kThreads = 256;
 constexpr int kNbMax = 128;
 constexpr int kLdc = kNbMax + 1;   // shared-memory leading dimension of the tile buffer
 constexpr int kKc = 32;            // inner-dimension chunk staged per step
-constexpr int kPb = 32;            // panel width of the blocked POTRF / TRSM
+constexpr int kPb = kPanelW;       // panel width of the blocked TRSM
 constexpr int kStage = kKc * (kNbMax + 8);          // doubles per staging buffer
 constexpr int kCbuf = kLdc * kNbMax + 16;           // tile buffer (+ overrun pad)
 constexpr int kSmemDoubles = kCbuf + 2 * kStage + kNbMax;
@@ -325,14 +325,18 @@ __device__ void load_diag_packed(double* P, const double* T, const DTile& d, int
         if (r >= c) P[pk(nb, r, c)] = diag_at(T, d, nb, r, c);
     });
 }
-__device__ void store_diag_packed(const double* P, double* T, const DTile& d, int nb) {
+// Columns [c0, c1) of the packed triangle back into the diagonal tile's storage (dense:
+// with the zero upper part; banded: the entries inside the band).
+__device__ void store_diag_cols(const double* P, double* T, const DTile& d, int nb, int c0, int c1) {
     if (d.kind == TILE_DIAG_DENSE) {
-        for_rc(nb, nb, [&](int r, int c) { __stcg(T + r + (size_t)c * nb, r >= c ? P[pk(nb, r, c)] : 0.0); });
+        for_rc(nb, c1 - c0, [&](int r, int cc) {
+            const int c = c0 + cc;
+            __stcg(T + r + (size_t)c * nb, r >= c ? P[pk(nb, r, c)] : 0.0);
+        });
     } else {
-        const int w = d.kd + 1;
-        for_rc(w, nb, [&](int q, int r) {  // storage (q, r): L[r][r - kd + q]
-            const int c = r - d.kd + q;
-            if (c >= 0) __stcg(T + q + (size_t)r * w, P[pk(nb, r, c)]);
+        for_rc(nb, c1 - c0, [&](int r, int cc) {
+            const int c = c0 + cc;
+            if (r >= c && r - c <= d.kd) __stcg(T + (d.kd + c - r) + (size_t)r * (d.kd + 1), P[pk(nb, r, c)]);
         });
     }
 }
@@ -510,7 +514,10 @@ __device__ void potrf_diag8(double* P, int nb, int p, int pw, const double* S, i
 // the staging buffer S for the next step.  Rows more than kd below the diagonal are
 // structurally zero and skipped.  *bad receives the first non-positive pivot column (or
 // -1); *logsum = sum_j log L_jj, one log per diagonal entry reduced in a fixed order.
-__device__ void potrf_packed(double* P, int nb, int w, int kd, double* S, int* bad, double* logsum) {
+// pub(c) is called by every thread (after a barrier) each time columns [c - kPb, c) have
+// become final, for c < w a multiple of kPb.
+template <class Pub>
+__device__ void potrf_packed(double* P, int nb, int w, int kd, double* S, int* bad, double* logsum, Pub pub) {
     __shared__ PotrfShared<8> sh;
     if (threadIdx.x == 0) sh.bad = -1;
     __syncthreads();
@@ -538,6 +545,7 @@ __device__ void potrf_packed(double* P, int nb, int w, int kd, double* S, int* b
         __syncthreads();
         potrf_rows_below<8>(P, nb, pn, pwn, min(w, pn + pwn + kd), S, sh);
         __syncthreads();
+        if (pn + pwn < w && (pn + pwn) % kPb == 0) pub(pn + pwn);
     }
     __shared__ double s_red[kThreads / 32];
     double lg = 0.0;
@@ -619,13 +627,22 @@ __global__ void __launch_bounds__(kThreads, 2) replay_kernel(const __grid_consta
                     }
                 }
                 if (s_ok) {
-                    int bad; double ls;
-                    potrf_packed(C, nb, O.sw, min(O.kd, nb - 1), S0, &bad, &ls);
+                    // columns are published kPb at a time as they become final, so the TRSMs
+                    // of this block column can start before the whole tile is factored
+                    int bad, done = 0;
+                    double ls;
+                    potrf_packed(C, nb, O.sw, min(O.kd, nb - 1), S0, &bad, &ls, [&](int c1) {
+                        store_diag_cols(C, F + O.off, O, nb, done, c1);
+                        done = c1;
+                        __threadfence();
+                        __syncthreads();
+                        if (threadIdx.x == 0) red_release_add(cnt + t.tile, 1);
+                    });
                     if (threadIdx.x == 0) {
                         if (bad >= 0) record_info(a.info + item, O.J * nb + bad + 1);
                         F[a.poff + O.pd_slot] = bad >= 0 ? __longlong_as_double(0x7ff8000000000000LL) : ls;
                     }
-                    store_diag_packed(C, F + O.off, O, nb);
+                    store_diag_cols(C, F + O.off, O, nb, done, nb);
                 }
             }
         } else if (t.kind == TASK_SYRK) {
@@ -710,14 +727,20 @@ __global__ void __launch_bounds__(kThreads, 2) replay_kernel(const __grid_consta
                     }
                 }
                 // TRSM of rows [tr0, tr1) against L_kk restricted to the stored columns
+                // L_kk arrives kPb columns at a time: its counter ends at nfinal and reaches
+                // nfinal - ng + q + 1 once columns [0, (q+1) kPb) are final
                 const DTile D = a.tiles[t.diag];
-                if (s_ok && threadIdx.x == 0) s_ok = wait_counter(cnt + t.diag, D.nfinal, a.spin, &a.hdr->status);
-                __syncthreads();
+                const int dbase = D.nfinal - (D.sw + kPb - 1) / kPb;
                 if (s_ok) {
                     // rows of X outside a column group's extent are zero there and stay zero
                     const double* DT = F + D.off;
                     for (int p = 0; p < sw; p += kPb) {
                         const int pw = min(kPb, sw - p);
+                        if (threadIdx.x == 0)
+                            s_ok = wait_counter(cnt + t.diag, dbase + logical_col(O, a.saind, p + pw - 1) / kPb + 1,
+                                                a.spin, &a.hdr->status);
+                        __syncthreads();
+                        if (!s_ok) break;
                         for (int k0 = 0; k0 < p; k0 += kRKc) {
                             const int K = min(kRKc, p - k0);
                             int lo, hi;
@@ -755,7 +778,7 @@ __global__ void __launch_bounds__(kThreads, 2) replay_kernel(const __grid_consta
                         trsm_rows(C + (y0 - t.rs0) + p * kRLd, kRLd, y1 - y0, pw, S0, kPb, sv);
                         __syncthreads();
                     }
-                    store_off(C, kRLd, F + O.off, nb, t.rs0, R, sw);
+                    if (s_ok) store_off(C, kRLd, F + O.off, nb, t.rs0, R, sw);
                 }
             }
         }
