@@ -473,6 +473,9 @@ stc::TaskSet* stc_plan::taskset(int32_t slices) {
     int h = (NB + eff - 1) / eff;
     h = (h + 7) / 8 * 8;
     if (h > 64) h = 64;
+    // at most kMaxSlices slices per tile (one completion bit per slice and panel)
+    if ((NB + h - 1) / h > stc::kMaxSlices) h = ((NB + stc::kMaxSlices - 1) / stc::kMaxSlices + 7) / 8 * 8;
+    ts->slice_h = h;
     // tasks in Algorithm-1 (topological) order first, with the model inputs of each:
     // the source tiles its updates wait for (in order) and the final dependency
     struct Meta {
@@ -658,7 +661,7 @@ stc::TaskSet* stc_plan::taskset(int32_t slices) {
                 if (tr0 >= tr1) continue;
                 stc::DTask s{};
                 Meta ms;
-                s.kind = stc::TASK_OFF; s.tile = o; s.diag = dk;
+                s.kind = stc::TASK_OFF; s.tile = o; s.diag = dk; s.slice = rs0 / h;
                 s.rs0 = rs0; s.rs1 = rs1; s.tr0 = tr0; s.tr1 = tr1;
                 s.ubeg = (int32_t)ts->upds.size();
                 int32_t a = rowstart[k], b = rowstart[m];
@@ -711,7 +714,8 @@ stc::TaskSet* stc_plan::taskset(int32_t slices) {
                 producers[o].push_back((int32_t)tasks.size());
                 tasks.push_back(s);
                 meta.push_back(ms);
-                ts->nfinal[o]++;
+                for (int q = 0; q * kPanel < O.sw; ++q)
+                    ts->nfinal[o] |= (int32_t)(1u << (q * stc::kMaxSlices + s.slice));
             }
         }
     }
@@ -764,6 +768,8 @@ stc::TaskSet* stc_plan::taskset(int32_t slices) {
         ts->qkey.push_back(key[i]);
     }
     ts->period = T ? key[order[T - 1]] / double(std::max<int64_t>(1, NT)) : 0.0;
+    const double makespan = T ? *std::max_element(fin.begin(), fin.end()) : 0.0;
+    ts->par = makespan > 0.0 ? ts->fma / makespan : 1.0;
     stc::TaskSet* raw = ts.get();
     tasksets[slices] = std::move(ts);
     return raw;

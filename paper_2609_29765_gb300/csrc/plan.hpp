@@ -43,6 +43,12 @@ constexpr int kMaxNb = 128;  // largest tile size n_b
 // Panel width of the blocked TRSM; a factored diagonal tile is published to its TRSMs
 // this many columns at a time.
 constexpr int kPanelW = 32;
+// Completion word of an off-diagonal tile: bit q * kMaxSlices + s is set once row slice
+// s has finished TRSM panel q (columns [q kPanelW, (q+1) kPanelW) of its rows are final),
+// so a consumer can wait for exactly the rows and columns it reads.  Diagonal tiles keep
+// a count (SYRK slices, then one per published kPanelW columns).
+constexpr int kMaxSlices = 8;
+static_assert((kMaxNb / kPanelW) * kMaxSlices <= 32, "completion word holds every (panel, slice) bit");
 
 enum : int32_t { TASK_DIAG = 0, TASK_OFF = 1, TASK_SYRK = 2, TASK_POTRF = 3 };
 
@@ -59,7 +65,8 @@ struct DTask {
     int32_t rs0, rs1;    // row slice of the output tile
     int32_t tr0, tr1;    // rows of the slice the TRSM touches (slice cut to r-extent)
     int32_t own_wait;    // TASK_POTRF: completions of (k,k) to wait for
-    int32_t pad[2];
+    int32_t slice;       // TASK_OFF: index of the row slice (rs0 / slice height)
+    int32_t pad;
 };
 
 // One SYRK (a == b) or GEMM source of a task: out -= A(rows, inner) * B(cols, inner)^T.
@@ -131,9 +138,11 @@ struct TaskSet {
     std::vector<DTask> tasks;
     std::vector<DUpd> upds;
     std::vector<int16_t> imap;
-    std::vector<int32_t> nfinal;  // per tile completion target
+    int32_t slice_h = 0;          // rows per slice of an off-diagonal tile
+    std::vector<int32_t> nfinal;  // per tile completion target (count, or bit mask)
     std::vector<double> qkey;     // modelled start of each task (queue order)
     double period = 0.0;          // modelled time per block column
+    double par = 0.0;             // modelled average parallelism (work / makespan)
     double fma = 0.0;             // executed FMAs
     std::map<int64_t, uint64_t*> d_queue;  // per batch: merged (task << 32 | item) order
     // device copies

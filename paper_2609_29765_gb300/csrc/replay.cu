@@ -87,6 +87,35 @@ __device__ bool wait_counter(const int* cnt, int target, long long limit, int* s
     }
 }
 
+// Wait (thread 0) until every bit of need is set in *cnt (an off-diagonal tile's
+// completion word).  Returns false on timeout / earlier error.
+__device__ bool wait_bits(const int* cnt, unsigned need, long long limit, int* status) {
+    if (((unsigned)ld_acquire(cnt) & need) == need) return true;
+    for (long long it = 0;; ++it) {
+        if (((unsigned)ld_acquire(cnt) & need) == need) return true;
+        if (*(volatile int*)status != STC_OK) return false;
+        if (it >= limit) {
+            atomicCAS(status, STC_OK, STC_ERR_TIMEOUT);
+            return false;
+        }
+        __nanosleep(it < 64 ? 32 : 256);
+    }
+}
+__device__ __forceinline__ void red_release_or(int* p, unsigned v) {
+    asm volatile("red.release.gpu.global.or.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Completion bits of an off-diagonal tile covering rows [lo, hi) (slices of h rows) and
+// stored columns [s0, s1].
+__device__ __forceinline__ unsigned off_need(int lo, int hi, int s0, int s1, int h) {
+    if (lo >= hi) return 0u;
+    const int a = lo / h, b = (hi - 1) / h;
+    const unsigned sl = ((2u << b) - 1u) & ~((1u << a) - 1u);
+    unsigned m = 0u;
+    for (int q = s0 / kPanelW; q <= s1 / kPanelW; ++q) m |= sl << (q * kMaxSlices);
+    return m;
+}
+
 // Record the first failing pivot (global column + 1) of an item; 0 = none yet.
 __device__ void record_info(int* info, int v) {
     int old = *(volatile int*)info;
@@ -293,6 +322,7 @@ struct ReplayArgs {        // one job: a plan and a batch of value sets
     int ntasks;
     long long batch;
     int nb;
+    int slice_h;             // rows per row slice of an off-diagonal tile
     long long spin;
 };
 
@@ -607,12 +637,10 @@ __global__ void __launch_bounds__(kThreads, 2) replay_kernel(const __grid_consta
             if (s_ok) {
                 load_diag_packed(C, F + O.off, O, nb);
                 __syncthreads();
-                for (int ui = t.ubeg; ui < t.uend; ++ui) {
+                for (int ui = t.ubeg; ui < t.uend && s_ok; ++ui) {
                     const DUpd u = a.upds[ui];
                     const DTile A = a.tiles[u.a];
-                    if (threadIdx.x == 0) s_ok = wait_counter(cnt + u.a, A.nfinal, a.spin, &a.hdr->status);
-                    __syncthreads();
-                    if (!s_ok) break;
+                    unsigned got = 0u;
                     for (int k0 = 0; k0 < u.klen; k0 += kRKc) {
                         const int K = min(kRKc, u.klen - k0);
                         int s0, s1, lo, hi;
@@ -620,6 +648,13 @@ __global__ void __launch_bounds__(kThreads, 2) replay_kernel(const __grid_consta
                         col_ext(a.cext, A, nb, s0, s1, lo, hi);
                         const int e0 = max(u.ra0, lo), e1 = min(u.ra1, hi);
                         if (e0 >= e1) continue;  // the chunk is zero on these rows
+                        const unsigned need = off_need(e0, e1, s0, s1, a.slice_h);
+                        if (need & ~got) {  // wait for exactly the rows and columns read
+                            if (threadIdx.x == 0) s_ok = wait_bits(cnt + u.a, need, a.spin, &a.hdr->status);
+                            __syncthreads();
+                            if (!s_ok) break;
+                            got |= need;
+                        }
                         stage_cols(S0, kRStLd, F + A.off, nb, e0, e1 - e0, u, a.imap, false, k0, K);
                         __syncthreads();
                         mma_sub_packed<true>(C, nb, e0, e0, e1 - e0, e1 - e0, S0, kRStLd, S0, kRStLd, K);
@@ -655,12 +690,10 @@ __global__ void __launch_bounds__(kThreads, 2) replay_kernel(const __grid_consta
                     C[r + c * kRLd] = c <= gr ? diag_at(T, O, nb, gr, c) : 0.0;
                 });
                 __syncthreads();
-                for (int ui = t.ubeg; ui < t.uend; ++ui) {
+                for (int ui = t.ubeg; ui < t.uend && s_ok; ++ui) {
                     const DUpd u = a.upds[ui];
                     const DTile A = a.tiles[u.a];
-                    if (threadIdx.x == 0) s_ok = wait_counter(cnt + u.a, A.nfinal, a.spin, &a.hdr->status);
-                    __syncthreads();
-                    if (!s_ok) break;
+                    unsigned got = 0u;
                     // output rows [d0, rb), columns [r0, rb) (rectangle left of d0, then triangle)
                     const int r0 = u.oc0, d0 = u.ra0, rb = u.ra1;
                     for (int k0 = 0; k0 < u.klen; k0 += kRKc) {
@@ -670,6 +703,13 @@ __global__ void __launch_bounds__(kThreads, 2) replay_kernel(const __grid_consta
                         col_ext(a.cext, A, nb, s0, s1, lo, hi);
                         const int q0 = max(r0, lo), e0 = max(d0, lo), e1 = min(rb, hi);
                         if (e0 >= e1) continue;  // the chunk is zero on these rows
+                        const unsigned need = off_need(q0, e1, s0, s1, a.slice_h);
+                        if (need & ~got) {
+                            if (threadIdx.x == 0) s_ok = wait_bits(cnt + u.a, need, a.spin, &a.hdr->status);
+                            __syncthreads();
+                            if (!s_ok) break;
+                            got |= need;
+                        }
                         stage_cols(S0, kRStLd, F + A.off, nb, q0, e1 - q0, u, a.imap, false, k0, K);
                         __syncthreads();
                         const int ch = min(d0, e1);
@@ -697,27 +737,37 @@ __global__ void __launch_bounds__(kThreads, 2) replay_kernel(const __grid_consta
             if (s_ok) {
                 load_off(C, kRLd, F + O.off, nb, t.rs0, R, sw);
                 __syncthreads();
-                for (int ui = t.ubeg; ui < t.uend; ++ui) {
+                for (int ui = t.ubeg; ui < t.uend && s_ok; ++ui) {
                     const DUpd u = a.upds[ui];
                     const DTile A = a.tiles[u.a];
                     const DTile B = a.tiles[u.b];
-                    if (threadIdx.x == 0)
-                        s_ok = wait_counter(cnt + u.a, A.nfinal, a.spin, &a.hdr->status) &&
-                               wait_counter(cnt + u.b, B.nfinal, a.spin, &a.hdr->status);
-                    __syncthreads();
-                    if (!s_ok) break;
+                    unsigned got_a = 0u, got_b = 0u;
                     for (int k0 = 0; k0 < u.klen; k0 += kRKc) {
                         const int K = min(kRKc, u.klen - k0);
-                        int s0, s1, alo, ahi, blo, bhi;
-                        inner_cols(u, a.imap, false, k0, K, s0, s1);
-                        col_ext(a.cext, A, nb, s0, s1, alo, ahi);
-                        inner_cols(u, a.imap, true, k0, K, s0, s1);
-                        col_ext(a.cext, B, nb, s0, s1, blo, bhi);
+                        int sa0, sa1, sb0, sb1, alo, ahi, blo, bhi;
+                        inner_cols(u, a.imap, false, k0, K, sa0, sa1);
+                        col_ext(a.cext, A, nb, sa0, sa1, alo, ahi);
+                        inner_cols(u, a.imap, true, k0, K, sb0, sb1);
+                        col_ext(a.cext, B, nb, sb0, sb1, blo, bhi);
                         // rows of A and (contiguous output) columns of B that are nonzero here
                         const int e0 = max(u.ra0, alo), e1 = min(u.ra1, ahi);
                         int c0 = u.oc0, c1 = u.oc1;
                         if (O.c0 >= 0) { c0 = max(c0, blo - O.c0); c1 = min(c1, bhi - O.c0); }
                         if (e0 >= e1 || c0 >= c1) continue;
+                        // rows of B read: the logical columns of output columns [c0, c1)
+                        const unsigned need_a = off_need(e0, e1, sa0, sa1, a.slice_h);
+                        const unsigned need_b =
+                            off_need(max(blo, logical_col(O, a.saind, c0)), min(bhi, logical_col(O, a.saind, c1 - 1) + 1),
+                                     sb0, sb1, a.slice_h);
+                        if ((need_a & ~got_a) | (need_b & ~got_b)) {
+                            if (threadIdx.x == 0)
+                                s_ok = wait_bits(cnt + u.a, need_a, a.spin, &a.hdr->status) &&
+                                       wait_bits(cnt + u.b, need_b, a.spin, &a.hdr->status);
+                            __syncthreads();
+                            if (!s_ok) break;
+                            got_a |= need_a;
+                            got_b |= need_b;
+                        }
                         stage_cols(S0, kRStLd, F + A.off, nb, e0, e1 - e0, u, a.imap, false, k0, K);
                         stage_rows_gather(S1, kRStLd, F + B.off, nb, O, a.saind, c0, c1 - c0, u, a.imap, k0, K);
                         __syncthreads();
@@ -763,29 +813,37 @@ __global__ void __launch_bounds__(kThreads, 2) replay_kernel(const __grid_consta
                         int lo, hi;
                         col_ext(a.cext, O, nb, p, p + pw - 1, lo, hi);
                         const int y0 = max(t.tr0, lo), y1 = min(t.tr1, hi);
-                        if (y0 >= y1) continue;
-                        // diagonal block of the panel and its reciprocal diagonal
-                        for (int idx = threadIdx.x; idx < kPb * kPb; idx += kThreads) {
-                            const int i = idx & (kPb - 1), j = idx / kPb;
-                            double v = 0.0;
-                            if (i < pw && j < pw && i >= j)
-                                v = diag_at(DT, D, nb, logical_col(O, a.saind, p + i), logical_col(O, a.saind, p + j));
-                            S0[i + j * kPb] = v;
+                        if (y0 < y1) {
+                            // diagonal block of the panel and its reciprocal diagonal
+                            for (int idx = threadIdx.x; idx < kPb * kPb; idx += kThreads) {
+                                const int i = idx & (kPb - 1), j = idx / kPb;
+                                double v = 0.0;
+                                if (i < pw && j < pw && i >= j)
+                                    v = diag_at(DT, D, nb, logical_col(O, a.saind, p + i),
+                                                logical_col(O, a.saind, p + j));
+                                S0[i + j * kPb] = v;
+                            }
+                            __syncthreads();
+                            if (threadIdx.x < pw) sv[threadIdx.x] = 1.0 / S0[threadIdx.x * (kPb + 1)];
+                            __syncthreads();
+                            trsm_rows(C + (y0 - t.rs0) + p * kRLd, kRLd, y1 - y0, pw, S0, kPb, sv);
+                            __syncthreads();
                         }
+                        // columns [p, p + pw) of this slice are final: publish them
+                        store_off(C + p * kRLd, kRLd, F + O.off + (size_t)p * nb, nb, t.rs0, R, pw);
+                        __threadfence();
                         __syncthreads();
-                        if (threadIdx.x < pw) sv[threadIdx.x] = 1.0 / S0[threadIdx.x * (kPb + 1)];
-                        __syncthreads();
-                        trsm_rows(C + (y0 - t.rs0) + p * kRLd, kRLd, y1 - y0, pw, S0, kPb, sv);
-                        __syncthreads();
+                        if (threadIdx.x == 0)
+                            red_release_or(cnt + t.tile, 1u << ((p / kPanelW) * kMaxSlices + t.slice));
                     }
-                    if (s_ok) store_off(C, kRLd, F + O.off, nb, t.rs0, R, sw);
                 }
             }
         }
-        // publish: every thread's stores are fenced before the counter moves
+        // publish: every thread's stores are fenced before the counter moves (off-diagonal
+        // tiles have published each panel already)
         __threadfence();
         __syncthreads();
-        if (threadIdx.x == 0) red_release_add(cnt + t.tile, 1);
+        if (threadIdx.x == 0 && t.kind != TASK_OFF) red_release_add(cnt + t.tile, 1);
     }
 }
 
@@ -1472,7 +1530,7 @@ void fill_job(ReplayArgs& a, const stc_plan* P, const TaskSet* ts, void* d_facto
     a.imap = ts->d_imap; a.factor = (double*)d_factor; a.fstride = P->factor_doubles;
     a.poff = P->partial_off; a.hdr = hdr; a.counters = counters;
     a.ntiles = (int)P->tiles.size(); a.info = d_info; a.ntasks = (int)ts->tasks.size();
-    a.batch = batch; a.nb = (int)P->nb;
+    a.batch = batch; a.nb = (int)P->nb; a.slice_h = ts->slice_h;
     a.spin = P->opt.spin_limit > 0 ? P->opt.spin_limit : kDefaultSpin;
 }
 
@@ -1484,17 +1542,18 @@ size_t solve_ws(const stc_plan* P, int64_t chains) {
     return sizeof(WorkHeader) + flags + (size_t)chains * P->nt * P->nb * sizeof(double);
 }
 
-int32_t pick_slices(const stc_plan* P, int64_t batch, int sms) {
+int32_t pick_slices(stc_plan* P, int64_t batch, int sms) {
     if (P->opt.row_slices > 0) return P->opt.row_slices;
     // Split heavy tiles so the chain POTRF -> TRSM -> SYRK of consecutive block columns
     // is spread over several SMs (the per-SM FP64 rate is low), but no further than the
     // batch needs: thinner slices cost efficiency inside each task.
     if (P->nb < 48) return 1;
-    const int64_t per_item =
-        std::max<int64_t>(1, ((int64_t)P->tiles.size() + P->nt / 2) / std::max<int64_t>(1, P->nt));
-    const int64_t width = batch * per_item;  // independent tiles per block-column step
-    // measured on the n = 200,000 band (n_b = 128): 4 slices at 64 items, 8 at 1 item
-    const int s = width >= sms / 4 ? 4 : 8;
+    // independent work in flight: the batch times the modelled parallelism of one item's
+    // task DAG (work over critical path); thresholds measured on the n = 200,000 band
+    // (2 slices at 64 items, 4 at 32, 8 at 16 and fewer), the spatio-temporal and FEM
+    // patterns (parallelism in the hundreds: unsliced)
+    const double width = (double)batch * P->taskset(2)->par;
+    const int s = width >= 0.6 * sms ? 2 : width >= 0.3 * sms ? 4 : 8;
     return P->nb < 96 ? std::max(1, s / 2) : s;
 }
 
