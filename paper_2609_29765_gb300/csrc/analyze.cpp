@@ -20,6 +20,7 @@
 #include <cstring>
 #include <new>
 #include <numeric>
+#include <limits>
 
 #include "plan.hpp"
 
@@ -484,6 +485,8 @@ stc::TaskSet* stc_plan::taskset(int32_t slices) {
         std::vector<int8_t> nsrc;
         int32_t final_tile = -1;     // tile awaited before the final op (-1: none)
         double fcost = 0;
+        bool trsm = false;           // TASK_OFF: the final op (TRSM) follows L_kk group by group
+        int npub = 0;                // >0: the task publishes its tile in npub steps
     };
     vector<stc::DTask> tasks;
     vector<Meta> meta;
@@ -586,6 +589,7 @@ stc::TaskSet* stc_plan::taskset(int32_t slices) {
             t.uend = (int32_t)ts->upds.size();
             t.rs0 = 0; t.rs1 = NB; t.tr0 = 0; t.tr1 = NB;
             mt.fcost = potrf_cost(D);
+            mt.npub = diag_groups(D);
             producers[dk].push_back((int32_t)tasks.size());
             tasks.push_back(t);
             meta.push_back(mt);
@@ -645,6 +649,7 @@ stc::TaskSet* stc_plan::taskset(int32_t slices) {
             p.rs0 = 0; p.rs1 = NB; p.tr0 = 0; p.tr1 = NB; p.own_wait = nsl;
             mp.final_tile = nsl > 0 ? dk : -1;
             mp.fcost = potrf_cost(D);
+            mp.npub = diag_groups(D);
             producers[dk].push_back((int32_t)tasks.size());
             tasks.push_back(p);
             meta.push_back(mp);
@@ -711,6 +716,8 @@ stc::TaskSet* stc_plan::taskset(int32_t slices) {
                 s.uend = (int32_t)ts->upds.size();
                 ms.final_tile = dk;
                 ms.fcost = trsm_cost(O, tr0, tr1);
+                ms.trsm = true;
+                ms.npub = (O.sw + kPanel - 1) / kPanel;
                 producers[o].push_back((int32_t)tasks.size());
                 tasks.push_back(s);
                 meta.push_back(ms);
@@ -719,15 +726,19 @@ stc::TaskSet* stc_plan::taskset(int32_t slices) {
             }
         }
     }
-    // Queue order: earliest start on unbounded workers, where a task starts when its
-    // first input is final and runs its updates in order, each after its own inputs;
+    // Queue order: earliest start on unbounded workers.  Tiles are published in steps
+    // (an off-diagonal slice per TRSM panel, a diagonal tile per kPanel factored
+    // columns), so a consumer can start on a tile's first published part ("avail") and
+    // finishes its use of it a fraction of its own work after the tile is final ("fin").
+    // A task starts when its first input is available and runs its updates in order;
     // the key is raised to exceed every dependency's key, so the order stays
     // topological (a waited-for task is always taken from the queue earlier).
     const double kSync = 3000.0;  // per-task overhead, FMA-equivalents
+    const double kInf = std::numeric_limits<double>::infinity();
     const size_t T = tasks.size();
     vector<double> key(T, 0.0), fin(T, 0.0), tile_fin(tiles.size(), 0.0), tile_key(tiles.size(), 0.0);
-    vector<int32_t> remaining(tiles.size(), 0);
-    for (size_t t = 0; t < tiles.size(); ++t) remaining[t] = (int32_t)producers[t].size();
+    vector<double> tile_avail(tiles.size(), kInf);
+    auto avail = [&](int32_t tl) { return tile_avail[tl] < kInf ? tile_avail[tl] : tile_fin[tl]; };
     for (size_t i = 0; i < T; ++i) {
         const Meta& mt = meta[i];
         double kdep = 0.0;
@@ -735,26 +746,40 @@ stc::TaskSet* stc_plan::taskset(int32_t slices) {
         if (mt.final_tile >= 0) kdep = std::max(kdep, tile_key[mt.final_tile]);
         double first;
         if (!mt.srcs.empty()) {
-            first = tile_fin[mt.srcs[0]];
-            if (mt.nsrc[0] == 2) first = std::max(first, tile_fin[mt.srcs[1]]);
+            first = avail(mt.srcs[0]);
+            if (mt.nsrc[0] == 2) first = std::max(first, avail(mt.srcs[1]));
+        } else if (mt.final_tile >= 0) {
+            first = mt.trsm ? avail(mt.final_tile) : tile_fin[mt.final_tile];  // POTRF: after its SYRKs
         } else {
-            first = mt.final_tile >= 0 ? tile_fin[mt.final_tile] : 0.0;
+            first = 0.0;
         }
         double t = first;
         size_t q = 0;
         for (size_t u = 0; u < mt.ucost.size(); ++u) {
-            double ready = tile_fin[mt.srcs[q]];
-            if (mt.nsrc[u] == 2) ready = std::max(ready, tile_fin[mt.srcs[q + 1]]);
+            double rs = avail(mt.srcs[q]), re = tile_fin[mt.srcs[q]];
+            if (mt.nsrc[u] == 2) {
+                rs = std::max(rs, avail(mt.srcs[q + 1]));
+                re = std::max(re, tile_fin[mt.srcs[q + 1]]);
+            }
             q += mt.nsrc[u];
-            t = std::max(t, ready) + mt.ucost[u];
+            t = std::max(std::max(t, rs) + mt.ucost[u], re + mt.ucost[u] / 4);
         }
-        if (mt.final_tile >= 0) t = std::max(t, tile_fin[mt.final_tile]);
-        t += mt.fcost + kSync;
+        double tf = t;  // start of the final operation
+        if (mt.final_tile >= 0 && mt.trsm) {
+            tf = std::max(t, avail(mt.final_tile));
+            t = std::max(tf + mt.fcost, tile_fin[mt.final_tile] + mt.fcost / 4);
+        } else if (mt.final_tile >= 0) {
+            tf = std::max(t, tile_fin[mt.final_tile]);
+            t = tf + mt.fcost;
+        } else {
+            t += mt.fcost;
+        }
+        t += kSync;
         fin[i] = t;
         key[i] = std::max(first, kdep + 1e-6);
         ts->fma += std::accumulate(mt.ucost.begin(), mt.ucost.end(), 0.0) + mt.fcost;
-        // the task's own tile: final when its last producer is done
         const int32_t o = tasks[i].tile;
+        if (mt.npub > 0) tile_avail[o] = std::min(tile_avail[o], tf + (t - tf) / mt.npub);
         tile_fin[o] = std::max(tile_fin[o], fin[i]);
         tile_key[o] = std::max(tile_key[o], key[i]);
     }
