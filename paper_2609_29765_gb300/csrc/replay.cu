@@ -994,6 +994,7 @@ __global__ void __launch_bounds__(kThreads, 1) solve_kernel(SolveArgs a) {
     double* Ls = smem;                             // diagonal tile, L(r,c) at r + c*kLdc
     __shared__ double acc[kSolveWarps * kNbMax];   // per-warp partial sums
     __shared__ double v[kNbMax];                   // block right-hand side / solution
+    __shared__ double ysm[kNbMax];                 // the y (or z) block an off-diagonal tile multiplies
     __shared__ long long s_slot;
     __shared__ int s_ok;
     const long long total = 2LL * a.nt * a.chains;
@@ -1027,37 +1028,60 @@ __global__ void __launch_bounds__(kThreads, 1) solve_kernel(SolveArgs a) {
             }
             __syncthreads();
             if (fwd) {
-                // acc -= L_kn y_n over the off-diagonal tiles of block row k
+                // acc -= L_kn y_n over the off-diagonal tiles of block row k (oldest n first):
+                // y_n's stored-column entries go to shared memory, then each thread owns one
+                // row and a residue class of columns, with four independent loads in flight
+                const int G = min(kThreads / nb, kSolveWarps), gr = threadIdx.x % nb, gq = threadIdx.x / nb;
                 for (int q = a.rowstart[k]; q < a.rowstart[k + 1]; ++q) {
                     const DTile T = a.tiles[a.rowtiles[q]];
                     if (threadIdx.x == 0) s_ok = wait_counter(done + T.J, 1, a.spin, &a.hdr->status);
                     __syncthreads();
                     if (!s_ok) break;
                     const double* yn = y + (long long)T.J * nb;
-                    for (int s = warp; s < T.sw; s += kSolveWarps) {
-                        const double ys = __ldcg(yn + logical_col(T, a.saind, s));
-                        const double* col = F + T.off + (size_t)s * nb;
-                        for (int r = T.r0 + lane; r < T.r1; r += 32)
-                            acc[warp * nb + r] = fma(-__ldcg(col + r), ys, acc[warp * nb + r]);
+                    for (int c = threadIdx.x; c < T.sw; c += kThreads) ysm[c] = __ldcg(yn + logical_col(T, a.saind, c));
+                    __syncthreads();
+                    if (gq < G && gr >= T.r0 && gr < T.r1) {
+                        const double* base = F + T.off + gr;
+                        double p0 = 0.0, p1 = 0.0, p2 = 0.0, p3 = 0.0;
+                        int c = gq;
+                        for (; c + 3 * G < T.sw; c += 4 * G) {
+                            p0 = fma(-__ldcg(base + (size_t)c * nb), ysm[c], p0);
+                            p1 = fma(-__ldcg(base + (size_t)(c + G) * nb), ysm[c + G], p1);
+                            p2 = fma(-__ldcg(base + (size_t)(c + 2 * G) * nb), ysm[c + 2 * G], p2);
+                            p3 = fma(-__ldcg(base + (size_t)(c + 3 * G) * nb), ysm[c + 3 * G], p3);
+                        }
+                        for (; c < T.sw; c += G) p0 = fma(-__ldcg(base + (size_t)c * nb), ysm[c], p0);
+                        acc[gq * nb + gr] += (p0 + p1) + (p2 + p3);
                     }
                     __syncthreads();
                 }
             } else {
-                // acc -= L_mk^T z_m over the tiles below the diagonal in block column k
-                for (int q = a.colstart[k]; q < a.colstart[k + 1]; ++q) {
+                // acc -= L_mk^T z_m over the tiles below the diagonal in block column k (oldest
+                // m first): z_m goes to shared memory, then each warp reduces four stored
+                // columns at a time over the rows, lanes striding the rows
+                for (int q = a.colstart[k + 1] - 1; q >= a.colstart[k]; --q) {
                     const DTile T = a.tiles[q];
                     if (T.I == T.J) continue;
                     if (threadIdx.x == 0) s_ok = wait_counter(done + a.nt + T.I, 1, a.spin, &a.hdr->status);
                     __syncthreads();
                     if (!s_ok) break;
                     const double* zm = y + (long long)T.I * nb;
-                    for (int s = warp; s < T.sw; s += kSolveWarps) {
-                        const double* col = F + T.off + (size_t)s * nb;
-                        double d = 0.0;
-                        for (int r = T.r0 + lane; r < T.r1; r += 32) d = fma(__ldcg(col + r), __ldcg(zm + r), d);
+                    for (int r = threadIdx.x; r < nb; r += kThreads) ysm[r] = __ldcg(zm + r);
+                    __syncthreads();
+                    for (int c0 = warp * 4; c0 < T.sw; c0 += kSolveWarps * 4) {
+                        double d[4] = {0.0, 0.0, 0.0, 0.0};
+                        for (int r = T.r0 + lane; r < T.r1; r += 32) {
+                            const double zr = ysm[r];
 #pragma unroll
-                        for (int o = 16; o > 0; o >>= 1) d += __shfl_down_sync(0xffffffffu, d, o);
-                        if (lane == 0) acc[warp * nb + logical_col(T, a.saind, s)] -= d;
+                            for (int j = 0; j < 4; ++j)
+                                if (c0 + j < T.sw) d[j] = fma(__ldcg(F + T.off + (size_t)(c0 + j) * nb + r), zr, d[j]);
+                        }
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) {
+#pragma unroll
+                            for (int o = 16; o > 0; o >>= 1) d[j] += __shfl_down_sync(0xffffffffu, d[j], o);
+                            if (lane == 0 && c0 + j < T.sw) acc[warp * nb + logical_col(T, a.saind, c0 + j)] -= d[j];
+                        }
                     }
                     __syncthreads();
                 }
