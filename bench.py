@@ -51,6 +51,8 @@ def parse():
     p.add_argument("--n", type=int, default=N)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--row-slices", type=int, default=0,
+                   help="row slices per off-diagonal tile (0: the library's choice)")
     p.add_argument("--workloads", default="c1,c3,c4,c5",
                    help="other workloads measured after the headline, comma list or 'none'")
     p.add_argument("--full-workloads", action="store_true",
@@ -440,7 +442,7 @@ def run_ours(args):
 
     n, batch = args.n, args.batch
     Ap, Ai = I.band_pattern(n, BW)
-    P = Plan(n, Ap, Ai, nb=NB, ordering="natural", route="semisparse")
+    P = Plan(n, Ap, Ai, nb=NB, ordering="natural", route="semisparse", row_slices=args.row_slices)
     P.upload()
     nnz = P.nnzA
     # host (pinned) values for the e2e leg; device copies for the resident leg
