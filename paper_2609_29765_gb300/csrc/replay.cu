@@ -784,6 +784,9 @@ __global__ void __launch_bounds__(kThreads, 2) replay_kernel(const __grid_consta
                 if (s_ok) {
                     // rows of X outside a column group's extent are zero there and stay zero
                     const double* DT = F + D.off;
+                    // right-looking by panels of kPb columns: solve panel p as soon as L_kk's
+                    // columns up to it are final, publish it, then update the later panels with
+                    // it, so the work left after the last columns of L_kk arrive is small
                     for (int p = 0; p < sw; p += kPb) {
                         const int pw = min(kPb, sw - p);
                         if (threadIdx.x == 0)
@@ -791,25 +794,6 @@ __global__ void __launch_bounds__(kThreads, 2) replay_kernel(const __grid_consta
                                                 a.spin, &a.hdr->status);
                         __syncthreads();
                         if (!s_ok) break;
-                        for (int k0 = 0; k0 < p; k0 += kRKc) {
-                            const int K = min(kRKc, p - k0);
-                            int lo, hi;
-                            col_ext(a.cext, O, nb, k0, k0 + K - 1, lo, hi);
-                            const int x0 = max(t.tr0, lo), x1 = min(t.tr1, hi);
-                            if (x0 >= x1) continue;
-                            const int Cp = ((pw + 3) & ~3) + 4;
-                            for_rc(Cp, K, [&](int c, int k) {
-                                double v = 0.0;
-                                if (c < pw)
-                                    v = diag_at(DT, D, nb, logical_col(O, a.saind, p + c),
-                                                logical_col(O, a.saind, k0 + k));
-                                S1[c + k * kRStLd] = v;
-                            });
-                            __syncthreads();
-                            double* X = C + (x0 - t.rs0);
-                            mma_sub<false>(X + p * kRLd, kRLd, x1 - x0, pw, X + k0 * kRLd, kRLd, S1, kRStLd, K);
-                            __syncthreads();
-                        }
                         int lo, hi;
                         col_ext(a.cext, O, nb, p, p + pw - 1, lo, hi);
                         const int y0 = max(t.tr0, lo), y1 = min(t.tr1, hi);
@@ -835,6 +819,27 @@ __global__ void __launch_bounds__(kThreads, 2) replay_kernel(const __grid_consta
                         __syncthreads();
                         if (threadIdx.x == 0)
                             red_release_or(cnt + t.tile, 1u << ((p / kPanelW) * kMaxSlices + t.slice));
+                        // X(:, pn:sw) -= X(:, p:p+pw) L_kk(later columns, panel p)^T
+                        const int pn = p + pw, Cn = sw - pn;
+                        if (Cn <= 0 || y0 >= y1) continue;
+                        for (int k0 = p; k0 < pn; k0 += kRKc) {
+                            const int K = min(kRKc, pn - k0);
+                            col_ext(a.cext, O, nb, k0, k0 + K - 1, lo, hi);
+                            const int x0 = max(t.tr0, lo), x1 = min(t.tr1, hi);
+                            if (x0 >= x1) continue;
+                            const int Cp = ((Cn + 3) & ~3) + 4;
+                            for_rc(Cp, K, [&](int c, int k) {
+                                double v = 0.0;
+                                if (c < Cn)
+                                    v = diag_at(DT, D, nb, logical_col(O, a.saind, pn + c),
+                                                logical_col(O, a.saind, k0 + k));
+                                S1[c + k * kRStLd] = v;
+                            });
+                            __syncthreads();
+                            double* X = C + (x0 - t.rs0);
+                            mma_sub<false>(X + pn * kRLd, kRLd, x1 - x0, Cn, X + k0 * kRLd, kRLd, S1, kRStLd, K);
+                            __syncthreads();
+                        }
                     }
                 }
             }
