@@ -461,9 +461,9 @@ void stored_cols(const stc_plan& P, const stc::DTile& t, vector<int>& out) {
 constexpr int kChunk = stc::kExtW;
 constexpr int kPanel = stc::kPanelW;
 
-stc::TaskSet* stc_plan::taskset(int32_t slices) {
+stc::TaskSet* stc_plan::taskset(int32_t slices, bool bl_order) {
     std::lock_guard<std::mutex> g(mu);
-    auto it = tasksets.find(slices);
+    auto it = tasksets.find(taskset_key(slices, bl_order));
     if (it != tasksets.end()) return it->second.get();
     auto ts = std::make_unique<stc::TaskSet>();
     const int64_t NT = nt;
@@ -783,6 +783,24 @@ stc::TaskSet* stc_plan::taskset(int32_t slices) {
         tile_fin[o] = std::max(tile_fin[o], fin[i]);
         tile_key[o] = std::max(tile_key[o], key[i]);
     }
+    if (bl_order) {
+        // Priority by bottom level: the longest modelled path from a task to the end of its
+        // item's DAG.  Predecessors rank strictly above their successors (every task costs
+        // at least kSync), so the descending order is topological.  Measured: better for a
+        // single factorization of a wide DAG (the 64^3 FEM pattern), worse for batches.
+        vector<double> cost(T), bl(T);
+        for (size_t i = 0; i < T; ++i)
+            cost[i] = bl[i] = std::accumulate(meta[i].ucost.begin(), meta[i].ucost.end(), 0.0) + meta[i].fcost + kSync;
+        for (size_t ii = T; ii-- > 0;) {
+            auto pull = [&](int32_t tile) {
+                for (int32_t d : producers[tile])
+                    if ((size_t)d != ii) bl[d] = std::max(bl[d], cost[d] + bl[ii]);
+            };
+            for (int32_t s2 : meta[ii].srcs) pull(s2);
+            if (meta[ii].final_tile >= 0) pull(meta[ii].final_tile);
+        }
+        for (size_t i = 0; i < T; ++i) key[i] = -bl[i];
+    }
     vector<int32_t> order(T);
     std::iota(order.begin(), order.end(), 0);
     std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return key[a] < key[b]; });
@@ -796,7 +814,7 @@ stc::TaskSet* stc_plan::taskset(int32_t slices) {
     const double makespan = T ? *std::max_element(fin.begin(), fin.end()) : 0.0;
     ts->par = makespan > 0.0 ? ts->fma / makespan : 1.0;
     stc::TaskSet* raw = ts.get();
-    tasksets[slices] = std::move(ts);
+    tasksets[taskset_key(slices, bl_order)] = std::move(ts);
     return raw;
 }
 

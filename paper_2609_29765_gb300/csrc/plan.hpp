@@ -200,5 +200,8 @@ struct stc_plan {
     std::mutex mu;
 
     int tile_id(int64_t I, int64_t J) const;  // -1 if not active
-    stc::TaskSet* taskset(int32_t slices);    // built on demand (host)
+    // built on demand (host); bl_order: queue by bottom level (longest path to the end of
+    // the item's DAG) instead of modelled earliest start
+    stc::TaskSet* taskset(int32_t slices, bool bl_order = false);
+    static int32_t taskset_key(int32_t slices, bool bl_order) { return slices * 2 + (bl_order ? 1 : 0); }
 };

@@ -1646,7 +1646,8 @@ extern "C" int stc_factorize_scattered(const stc_plan* Pc, int64_t batch, void* 
     int dev, sms, rc;
     if ((rc = device_info(&dev, &sms))) return rc;
     if ((rc = ensure_plan(P, dev))) return rc;
-    TaskSet* ts = P->taskset(pick_slices(P, batch, sms));
+    // one or two value sets: the item's own DAG width decides, so the critical path goes first
+    TaskSet* ts = P->taskset(pick_slices(P, batch, sms), batch <= 2);
     if ((rc = ensure_taskset(P, ts, dev))) return rc;
     uint64_t* queue = nullptr;
     if ((rc = ensure_queue(P, ts, batch, &queue))) return rc;
@@ -1982,7 +1983,7 @@ extern "C" int stc_factorize_noalloc(const stc_plan* Pc, const double* d_values,
     TaskSet* ts = nullptr;
     {
         std::lock_guard<std::mutex> g(P->mu);
-        auto it = P->tasksets.find(1);
+        auto it = P->tasksets.find(stc_plan::taskset_key(1, false));
         if (it != P->tasksets.end()) ts = it->second.get();
         if (P->dev.device != dev || !ts || ts->device != dev) return STC_ERR_INVALID_ARG;
     }
