@@ -349,11 +349,52 @@ __device__ void store_off(const double* C, int ldc, double* T, int nb, int rs0, 
     for_rc(R, sw, [&](int r, int c) { __stcg(T + rs0 + r + (size_t)c * nb, C[r + c * ldc]); });
 }
 
-// Diagonal tile <-> packed lower triangle in shared memory.
+// Rows [r0, r1) of a diagonal tile, read in storage order (coalesced) with four loads in
+// flight per thread: fn(r, c, L[r][c]) for every stored entry with r >= c (entries of a
+// banded tile outside the band are not visited).
+template <class Fn>
+__device__ void read_diag_rows(const double* T, const DTile& d, int nb, int r0, int r1, Fn fn) {
+    if (d.kind == TILE_DIAG_DENSE) {
+        const int R = r1 - r0, n = R * nb;  // column-major: runs of R rows per column
+        for (int b = threadIdx.x; b < n; b += 4 * kThreads) {
+            double v[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int j = b + u * kThreads;
+                v[u] = j < n ? __ldcg(T + (r0 + j % R) + (size_t)(j / R) * nb) : 0.0;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int j = b + u * kThreads, r = r0 + j % R, c = j / R;
+                if (j < n && r >= c) fn(r, c, v[u]);
+            }
+        }
+    } else {
+        const int w = d.kd + 1, n = (r1 - r0) * w;  // storage (q, r): L[r][r - kd + q] at q + r w
+        const double* base = T + (size_t)r0 * w;
+        for (int b = threadIdx.x; b < n; b += 4 * kThreads) {
+            double v[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int j = b + u * kThreads;
+                v[u] = j < n ? __ldcg(base + j) : 0.0;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int j = b + u * kThreads, r = r0 + j / w, c = r - d.kd + j % w;
+                if (j < n && c >= 0) fn(r, c, v[u]);
+            }
+        }
+    }
+}
+
+// Diagonal tile -> packed lower triangle in shared memory (zero outside a band).
 __device__ void load_diag_packed(double* P, const double* T, const DTile& d, int nb) {
-    for_rc(nb, nb, [&](int r, int c) {
-        if (r >= c) P[pk(nb, r, c)] = diag_at(T, d, nb, r, c);
-    });
+    if (d.kind == TILE_DIAG_BAND && d.kd < nb - 1) {
+        for (int i = threadIdx.x; i < nb * (nb + 1) / 2; i += kThreads) P[i] = 0.0;
+        __syncthreads();
+    }
+    read_diag_rows(T, d, nb, 0, nb, [&](int r, int c, double v) { P[pk(nb, r, c)] = v; });
 }
 // Columns [c0, c1) of the packed triangle back into the diagonal tile's storage (dense:
 // with the zero upper part; banded: the entries inside the band).
@@ -685,10 +726,9 @@ __global__ void __launch_bounds__(kThreads, 2) replay_kernel(const __grid_consta
             const int R = t.rs1 - t.rs0;
             if (s_ok) {
                 const double* T = F + O.off;
-                for_rc(R, t.rs1, [&](int r, int c) {
-                    const int gr = t.rs0 + r;
-                    C[r + c * kRLd] = c <= gr ? diag_at(T, O, nb, gr, c) : 0.0;
-                });
+                for_rc(R, t.rs1, [&](int r, int c) { C[r + c * kRLd] = 0.0; });
+                __syncthreads();
+                read_diag_rows(T, O, nb, t.rs0, t.rs1, [&](int r, int c, double v) { C[(r - t.rs0) + c * kRLd] = v; });
                 __syncthreads();
                 for (int ui = t.ubeg; ui < t.uend && s_ok; ++ui) {
                     const DUpd u = a.upds[ui];
@@ -925,13 +965,17 @@ struct SolveArgs {
 };
 
 constexpr int kSolveWarps = kThreads / 32;
+constexpr int kSolvePre = kNbMax / 2;  // tile entries per thread held across a wait (forward)
+static_assert(kNbMax <= 128 && kThreads == 256, "the solve's register prefetch covers 128 x 128 tiles");
 constexpr size_t kSolveSmem = (size_t)kLdc * kNbMax * sizeof(double);
 
-// Diagonal-block substitution, panels of 32: warp 0 solves the panel's 32x32 triangle
-// with its rows (forward) or columns (backward) in registers, one lane per row/column,
-// pivots broadcast by shuffle; the rows below (forward) or above (backward) the panel
-// are then updated with one thread per row.  v holds the right-hand side and is
-// overwritten by the solution.
+// Diagonal-block substitution with the unit lower triangular M = L diag(L)^{-1} (Ls
+// holds M, its columns scaled beforehand, off the dependency chain), panels of 32: warp 0
+// solves the panel's 32x32 triangle with its rows (forward) or columns (backward) in
+// registers, one lane per row/column, values broadcast by shuffle, so a step of the chain
+// is one shuffle and one FMA; the rows below (forward) or above (backward) the panel are
+// then updated with one thread per row.  Forward: v <- M^{-1} v (the caller scales by
+// diag(L)^{-1} afterwards); backward: v <- M^{-T} v (the caller scales before).
 template <bool BACK>
 __device__ void diag_solve(double* v, const double* Ls, const DTile& D, int nb, int w) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -942,16 +986,15 @@ __device__ void diag_solve(double* v, const double* Ls, const DTile& D, int nb, 
         const int pw = min(32, w - p);
         if (warp == 0) {
             double Lr[32];
-            double vi = 0.0, dinv = 1.0;
+            double vi = 0.0;
             if (lane < pw) {
 #pragma unroll
                 for (int l = 0; l < 32; ++l) {
-                    // forward: row p+lane, columns p+l <= row; backward: column p+lane, rows p+l >= it
+                    // forward: row p+lane, columns p+l < row; backward: column p+lane, rows p+l > it
                     const int r = BACK ? p + l : p + lane, c = BACK ? p + lane : p + l;
-                    Lr[l] = (l < pw && r >= c) ? Ls[r + c * kLdc] : 0.0;
+                    Lr[l] = (l < pw && r > c) ? Ls[r + c * kLdc] : 0.0;
                 }
                 vi = v[p + lane];
-                dinv = 1.0 / Ls[(p + lane) * (kLdc + 1)];
             } else {
 #pragma unroll
                 for (int l = 0; l < 32; ++l) Lr[l] = 0.0;
@@ -960,8 +1003,7 @@ __device__ void diag_solve(double* v, const double* Ls, const DTile& D, int nb, 
             for (int jj = 0; jj < 32; ++jj) {
                 const int j = BACK ? 31 - jj : jj;
                 if (j < pw) {
-                    const double yj = __shfl_sync(0xffffffffu, vi * dinv, j);
-                    if (lane == j) vi = yj;
+                    const double yj = __shfl_sync(0xffffffffu, vi, j);
                     if (!BACK && lane > j) vi = fma(-Lr[j], yj, vi);
                     if (BACK && lane < j) vi = fma(-Lr[j], yj, vi);
                 }
@@ -1000,6 +1042,7 @@ __global__ void __launch_bounds__(kThreads, 1) solve_kernel(SolveArgs a) {
     __shared__ double acc[kSolveWarps * kNbMax];   // per-warp partial sums
     __shared__ double v[kNbMax];                   // block right-hand side / solution
     __shared__ double ysm[kNbMax];                 // the y (or z) block an off-diagonal tile multiplies
+    __shared__ double sdinv[kNbMax];               // 1 / L_jj of the diagonal tile
     __shared__ long long s_slot;
     __shared__ int s_ok;
     const long long total = 2LL * a.nt * a.chains;
@@ -1026,36 +1069,54 @@ __global__ void __launch_bounds__(kThreads, 1) solve_kernel(SolveArgs a) {
         __syncthreads();
         if (s_ok) {
             for (int i = threadIdx.x; i < kSolveWarps * nb; i += kThreads) acc[i] = 0.0;
-            for_rc(nb, nb, [&](int r, int c) { Ls[r + c * kLdc] = r >= c ? diag_at(F + D.off, D, nb, r, c) : 0.0; });
+            for_rc(nb, nb, [&](int r, int c) { Ls[r + c * kLdc] = 0.0; });
+            __syncthreads();
+            read_diag_rows(F + D.off, D, nb, 0, nb, [&](int r, int c, double v) { Ls[r + c * kLdc] = v; });
             for (int r = threadIdx.x; r < nb; r += kThreads) {
                 const long long g = (long long)k * nb + r;
                 v[r] = fwd ? (g < a.n ? a.b[ch * a.n + a.perm[g]] : 0.0) : __ldcg(y + g);
             }
+            __syncthreads();
+            // L_kk = M diag(L_kk): scale the columns to M (unit diagonal) before any wait
+            for (int c = threadIdx.x; c < nb; c += kThreads) sdinv[c] = 1.0 / Ls[c * (kLdc + 1)];
+            __syncthreads();
+            for_rc(nb, nb, [&](int r, int c) { if (r > c) Ls[r + c * kLdc] *= sdinv[c]; });
+            if (!fwd)
+                for (int r = threadIdx.x; r < nb; r += kThreads) v[r] *= sdinv[r];
             __syncthreads();
             if (fwd) {
                 // acc -= L_kn y_n over the off-diagonal tiles of block row k (oldest n first):
                 // y_n's stored-column entries go to shared memory, then each thread owns one
                 // row and a residue class of columns, with four independent loads in flight
                 const int G = min(kThreads / nb, kSolveWarps), gr = threadIdx.x % nb, gq = threadIdx.x / nb;
+                // (the tile's entries go to registers before the wait for y_n, so only the
+                // multiply-adds remain once y_n is there)
                 for (int q = a.rowstart[k]; q < a.rowstart[k + 1]; ++q) {
                     const DTile T = a.tiles[a.rowtiles[q]];
+                    const bool act = gq < G && gr >= T.r0 && gr < T.r1;
+                    const double* base = F + T.off + gr;
+                    double pre[kSolvePre];
+#pragma unroll
+                    for (int i = 0; i < kSolvePre; ++i) {
+                        const int c = gq + i * G;
+                        pre[i] = (act && c < T.sw) ? __ldcg(base + (size_t)c * nb) : 0.0;
+                    }
                     if (threadIdx.x == 0) s_ok = wait_counter(done + T.J, 1, a.spin, &a.hdr->status);
                     __syncthreads();
                     if (!s_ok) break;
                     const double* yn = y + (long long)T.J * nb;
                     for (int c = threadIdx.x; c < T.sw; c += kThreads) ysm[c] = __ldcg(yn + logical_col(T, a.saind, c));
                     __syncthreads();
-                    if (gq < G && gr >= T.r0 && gr < T.r1) {
-                        const double* base = F + T.off + gr;
+                    if (act) {
                         double p0 = 0.0, p1 = 0.0, p2 = 0.0, p3 = 0.0;
-                        int c = gq;
-                        for (; c + 3 * G < T.sw; c += 4 * G) {
-                            p0 = fma(-__ldcg(base + (size_t)c * nb), ysm[c], p0);
-                            p1 = fma(-__ldcg(base + (size_t)(c + G) * nb), ysm[c + G], p1);
-                            p2 = fma(-__ldcg(base + (size_t)(c + 2 * G) * nb), ysm[c + 2 * G], p2);
-                            p3 = fma(-__ldcg(base + (size_t)(c + 3 * G) * nb), ysm[c + 3 * G], p3);
+#pragma unroll
+                        for (int i = 0; i < kSolvePre; i += 4) {
+                            const int c = gq + i * G;
+                            if (c < T.sw) p0 = fma(-pre[i], ysm[c], p0);
+                            if (c + G < T.sw) p1 = fma(-pre[i + 1], ysm[c + G], p1);
+                            if (c + 2 * G < T.sw) p2 = fma(-pre[i + 2], ysm[c + 2 * G], p2);
+                            if (c + 3 * G < T.sw) p3 = fma(-pre[i + 3], ysm[c + 3 * G], p3);
                         }
-                        for (; c < T.sw; c += G) p0 = fma(-__ldcg(base + (size_t)c * nb), ysm[c], p0);
                         acc[gq * nb + gr] += (p0 + p1) + (p2 + p3);
                     }
                     __syncthreads();
@@ -1067,39 +1128,60 @@ __global__ void __launch_bounds__(kThreads, 1) solve_kernel(SolveArgs a) {
                 for (int q = a.colstart[k + 1] - 1; q >= a.colstart[k]; --q) {
                     const DTile T = a.tiles[q];
                     if (T.I == T.J) continue;
+                    // this warp's columns c = 32 g + 4 warp + j and rows r = r0 + lane + 32 i,
+                    // loaded before the wait for z_m
+                    double pre[4][4][4];
+#pragma unroll
+                    for (int g = 0; g < 4; ++g)
+#pragma unroll
+                        for (int j = 0; j < 4; ++j)
+#pragma unroll
+                            for (int i = 0; i < 4; ++i) {
+                                const int c = 32 * g + warp * 4 + j, r = T.r0 + lane + 32 * i;
+                                pre[g][j][i] = (c < T.sw && r < T.r1) ? __ldcg(F + T.off + (size_t)c * nb + r) : 0.0;
+                            }
                     if (threadIdx.x == 0) s_ok = wait_counter(done + a.nt + T.I, 1, a.spin, &a.hdr->status);
                     __syncthreads();
                     if (!s_ok) break;
                     const double* zm = y + (long long)T.I * nb;
                     for (int r = threadIdx.x; r < nb; r += kThreads) ysm[r] = __ldcg(zm + r);
                     __syncthreads();
-                    for (int c0 = warp * 4; c0 < T.sw; c0 += kSolveWarps * 4) {
-                        double d[4] = {0.0, 0.0, 0.0, 0.0};
-                        for (int r = T.r0 + lane; r < T.r1; r += 32) {
-                            const double zr = ysm[r];
+                    double zr[4];
 #pragma unroll
-                            for (int j = 0; j < 4; ++j)
-                                if (c0 + j < T.sw) d[j] = fma(__ldcg(F + T.off + (size_t)(c0 + j) * nb + r), zr, d[j]);
-                        }
+                    for (int i = 0; i < 4; ++i) {
+                        const int r = T.r0 + lane + 32 * i;
+                        zr[i] = r < T.r1 ? ysm[r] : 0.0;
+                    }
+#pragma unroll
+                    for (int g = 0; g < 4; ++g)
 #pragma unroll
                         for (int j = 0; j < 4; ++j) {
+                            const int c = 32 * g + warp * 4 + j;
+                            double d = 0.0;
 #pragma unroll
-                            for (int o = 16; o > 0; o >>= 1) d[j] += __shfl_down_sync(0xffffffffu, d[j], o);
-                            if (lane == 0 && c0 + j < T.sw) acc[warp * nb + logical_col(T, a.saind, c0 + j)] -= d[j];
+                            for (int i = 0; i < 4; ++i) d = fma(pre[g][j][i], zr[i], d);
+#pragma unroll
+                            for (int o = 16; o > 0; o >>= 1) d += __shfl_down_sync(0xffffffffu, d, o);
+                            if (lane == 0 && c < T.sw) acc[warp * nb + logical_col(T, a.saind, c)] -= d;
                         }
-                    }
                     __syncthreads();
                 }
             }
+            // backward: the products enter scaled by 1/L_kk like the block itself
             for (int r = threadIdx.x; r < nb; r += kThreads) {
-                double sacc = v[r];
+                double sacc = 0.0;
                 for (int w2 = 0; w2 < kSolveWarps; ++w2) sacc += acc[w2 * nb + r];
-                v[r] = sacc;
+                v[r] = fwd ? v[r] + sacc : fma(sacc, sdinv[r], v[r]);
             }
             __syncthreads();
             if (s_ok) {
-                if (fwd) diag_solve<false>(v, Ls, D, nb, nb);
-                else diag_solve<true>(v, Ls, D, nb, nb);
+                if (fwd) {
+                    diag_solve<false>(v, Ls, D, nb, nb);
+                    for (int i = threadIdx.x; i < nb; i += kThreads) v[i] *= sdinv[i];
+                    __syncthreads();
+                } else {
+                    diag_solve<true>(v, Ls, D, nb, nb);
+                }
                 for (int i = threadIdx.x; i < nb; i += kThreads) {
                     __stcg(y + (long long)k * nb + i, v[i]);
                     const long long g = (long long)k * nb + i;
