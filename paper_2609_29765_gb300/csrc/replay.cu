@@ -349,41 +349,70 @@ __device__ void store_off(const double* C, int ldc, double* T, int nb, int rs0, 
     for_rc(R, sw, [&](int r, int c) { __stcg(T + rs0 + r + (size_t)c * nb, C[r + c * ldc]); });
 }
 
-// Rows [r0, r1) of a diagonal tile, read in storage order (coalesced) with four loads in
-// flight per thread: fn(r, c, L[r][c]) for every stored entry with r >= c (entries of a
-// banded tile outside the band are not visited).
+// Rows [r0, r1) of a diagonal tile, read in storage order (coalesced: a warp per stored
+// column of a dense tile, a warp per row of a banded one, up to eight loads in flight per
+// lane): fn(r, c, L[r][c]) for every stored entry with r >= c (entries of a banded tile
+// outside the band are not visited).
 template <class Fn>
 __device__ void read_diag_rows(const double* T, const DTile& d, int nb, int r0, int r1, Fn fn) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    constexpr int kW = kThreads / 32;
     if (d.kind == TILE_DIAG_DENSE) {
-        const int R = r1 - r0, n = R * nb;  // column-major: runs of R rows per column
-        for (int b = threadIdx.x; b < n; b += 4 * kThreads) {
-            double v[4];
+        for (int c = warp; c < nb; c += 2 * kW) {
+            double v[2][4];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int j = b + u * kThreads;
-                v[u] = j < n ? __ldcg(T + (r0 + j % R) + (size_t)(j / R) * nb) : 0.0;
-            }
+            for (int h = 0; h < 2; ++h)
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int j = b + u * kThreads, r = r0 + j % R, c = j / R;
-                if (j < n && r >= c) fn(r, c, v[u]);
-            }
+                for (int u = 0; u < 4; ++u) {
+                    const int cc = c + h * kW, r = r0 + lane + 32 * u;
+                    v[h][u] = (cc < nb && r < r1) ? __ldcg(T + r + (size_t)cc * nb) : 0.0;
+                }
+#pragma unroll
+            for (int h = 0; h < 2; ++h)
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int cc = c + h * kW, r = r0 + lane + 32 * u;
+                    if (cc < nb && r < r1 && r >= cc) fn(r, cc, v[h][u]);
+                }
         }
     } else {
-        const int w = d.kd + 1, n = (r1 - r0) * w;  // storage (q, r): L[r][r - kd + q] at q + r w
-        const double* base = T + (size_t)r0 * w;
-        for (int b = threadIdx.x; b < n; b += 4 * kThreads) {
-            double v[4];
+        const int w = d.kd + 1;  // storage (q, r): L[r][r - kd + q] at q + r w
+        for (int r = r0 + warp; r < r1; r += 2 * kW) {
+            double v[2][4];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int j = b + u * kThreads;
-                v[u] = j < n ? __ldcg(base + j) : 0.0;
-            }
+            for (int h = 0; h < 2; ++h)
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int j = b + u * kThreads, r = r0 + j / w, c = r - d.kd + j % w;
-                if (j < n && c >= 0) fn(r, c, v[u]);
-            }
+                for (int u = 0; u < 4; ++u) {
+                    const int rr = r + h * kW, q = lane + 32 * u;
+                    v[h][u] = (rr < r1 && q < w) ? __ldcg(T + q + (size_t)rr * w) : 0.0;
+                }
+#pragma unroll
+            for (int h = 0; h < 2; ++h)
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int rr = r + h * kW, q = lane + 32 * u, c = rr - d.kd + q;
+                    if (rr < r1 && q < w && c >= 0) fn(rr, c, v[h][u]);
+                }
+        }
+    }
+}
+
+// Entries L[r][c], r in [r0, r1), c in [c0, min(c1, r + 1)), written to a diagonal tile's
+// storage in storage order (a warp per stored column / per row): T <- get(r, c); banded
+// tiles only inside the band.
+template <class Get>
+__device__ void write_diag_rows(double* T, const DTile& d, int nb, int r0, int r1, int c0, int c1, Get get) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    constexpr int kW = kThreads / 32;
+    if (d.kind == TILE_DIAG_DENSE) {
+        for (int c = c0 + warp; c < c1; c += kW)
+            for (int r = max(r0, c) + lane; r < r1; r += 32) __stcg(T + r + (size_t)c * nb, get(r, c));
+    } else {
+        const int w = d.kd + 1;
+        for (int r = r0 + warp; r < r1; r += kW) {
+            // row r holds columns [r - kd, r]: the part inside [c0, c1)
+            const int ca = max(max(c0, r - d.kd), 0), cb = min(c1, r + 1);
+            for (int c = ca + lane; c < cb; c += 32) __stcg(T + (d.kd + c - r) + (size_t)r * w, get(r, c));
         }
     }
 }
@@ -405,10 +434,7 @@ __device__ void store_diag_cols(const double* P, double* T, const DTile& d, int 
             __stcg(T + r + (size_t)c * nb, r >= c ? P[pk(nb, r, c)] : 0.0);
         });
     } else {
-        for_rc(nb, c1 - c0, [&](int r, int cc) {
-            const int c = c0 + cc;
-            if (r >= c && r - c <= d.kd) __stcg(T + (d.kd + c - r) + (size_t)r * (d.kd + 1), P[pk(nb, r, c)]);
-        });
+        write_diag_rows(T, d, nb, c0, min(nb, c1 + d.kd), c0, c1, [&](int r, int c) { return P[pk(nb, r, c)]; });
     }
 }
 
@@ -762,13 +788,8 @@ __global__ void __launch_bounds__(kThreads, 2) replay_kernel(const __grid_consta
                     }
                 }
                 if (s_ok) {
-                    double* Tw = F + O.off;
-                    for_rc(R, t.rs1, [&](int r, int c) {
-                        const int gr = t.rs0 + r;
-                        if (c > gr) return;
-                        if (O.kind == TILE_DIAG_DENSE) __stcg(Tw + gr + (size_t)c * nb, C[r + c * kRLd]);
-                        else if (gr - c <= O.kd) __stcg(Tw + (O.kd + c - gr) + (size_t)gr * (O.kd + 1), C[r + c * kRLd]);
-                    });
+                    write_diag_rows(F + O.off, O, nb, t.rs0, t.rs1, 0, t.rs1,
+                                    [&](int r, int c) { return C[(r - t.rs0) + c * kRLd]; });
                 }
             }
         } else {
