@@ -860,18 +860,22 @@ __global__ void __launch_bounds__(kThreads, 2) replay_kernel(const __grid_consta
                         const int y0 = max(t.tr0, lo), y1 = min(t.tr1, hi);
                         if (y0 < y1) {
                             // diagonal block of the panel and its reciprocal diagonal
+                            // (consecutive threads along a stored row of a banded L_kk, down a
+                            // column of a dense one; leading dimension kPb + 1)
+                            const bool band = D.kind == TILE_DIAG_BAND;
                             for (int idx = threadIdx.x; idx < kPb * kPb; idx += kThreads) {
-                                const int i = idx & (kPb - 1), j = idx / kPb;
+                                const int i = band ? idx / kPb : idx & (kPb - 1);
+                                const int j = band ? idx & (kPb - 1) : idx / kPb;
                                 double v = 0.0;
                                 if (i < pw && j < pw && i >= j)
                                     v = diag_at(DT, D, nb, logical_col(O, a.saind, p + i),
                                                 logical_col(O, a.saind, p + j));
-                                S0[i + j * kPb] = v;
+                                S0[i + j * (kPb + 1)] = v;
                             }
                             __syncthreads();
-                            if (threadIdx.x < pw) sv[threadIdx.x] = 1.0 / S0[threadIdx.x * (kPb + 1)];
+                            if (threadIdx.x < pw) sv[threadIdx.x] = 1.0 / S0[threadIdx.x * (kPb + 2)];
                             __syncthreads();
-                            trsm_rows(C + (y0 - t.rs0) + p * kRLd, kRLd, y1 - y0, pw, S0, kPb, sv);
+                            trsm_rows(C + (y0 - t.rs0) + p * kRLd, kRLd, y1 - y0, pw, S0, kPb + 1, sv);
                             __syncthreads();
                         }
                         // columns [p, p + pw) of this slice are final: publish them
@@ -889,13 +893,23 @@ __global__ void __launch_bounds__(kThreads, 2) replay_kernel(const __grid_consta
                             const int x0 = max(t.tr0, lo), x1 = min(t.tr1, hi);
                             if (x0 >= x1) continue;
                             const int Cp = ((Cn + 3) & ~3) + 4;
-                            for_rc(Cp, K, [&](int c, int k) {
-                                double v = 0.0;
-                                if (c < Cn)
-                                    v = diag_at(DT, D, nb, logical_col(O, a.saind, pn + c),
-                                                logical_col(O, a.saind, k0 + k));
-                                S1[c + k * kRStLd] = v;
-                            });
+                            if (D.kind == TILE_DIAG_BAND) {
+                                // along stored rows of L_kk: consecutive threads on consecutive k
+                                for (int idx = threadIdx.x; idx < Cp * K; idx += kThreads) {
+                                    const int c = idx / K, k = idx - c * K;
+                                    S1[c + k * kRStLd] = c < Cn ? diag_at(DT, D, nb, logical_col(O, a.saind, pn + c),
+                                                                          logical_col(O, a.saind, k0 + k))
+                                                                : 0.0;
+                                }
+                            } else {
+                                for_rc(Cp, K, [&](int c, int k) {
+                                    double v = 0.0;
+                                    if (c < Cn)
+                                        v = diag_at(DT, D, nb, logical_col(O, a.saind, pn + c),
+                                                    logical_col(O, a.saind, k0 + k));
+                                    S1[c + k * kRStLd] = v;
+                                });
+                            }
                             __syncthreads();
                             double* X = C + (x0 - t.rs0);
                             mma_sub<false>(X + pn * kRLd, kRLd, x1 - x0, Cn, X + k0 * kRLd, kRLd, S1, kRStLd, K);
