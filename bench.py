@@ -512,24 +512,61 @@ def run_ours(args):
     ms_logdet = sum(r[2].elapsed_time(r[3]) for r in rps) / args.steps
     ms_solve = sum(r[3].elapsed_time(r[4]) for r in rps) / args.steps
     L.check(L.stc_sync_status(ws), "device status")
-    # ---- e2e: host buffers in, logdet + x back out, every step
+    # ---- e2e: host buffers in, logdet + x back out, every step.  The copies run on a
+    # second stream, double-buffered: step k+1's values and right-hand sides go up while
+    # step k factorizes, step k's logdet and x come back while step k+1 runs.
     e2e_ms = 0.0
     if not args.no_e2e:
-        for _ in range(1):
-            dv.copy_(hv, non_blocking=True)
-            step(dv, db, dx)
+        cs = torch.cuda.Stream()
+        bufs = [(dv, db, dx, ld),
+                (torch.empty_like(dv), torch.empty_like(db), torch.empty_like(dx), torch.empty_like(ld))]
+        ev_in = [ev(), ev()]
+        ev_done = [ev(), ev()]
+        ev_out = [ev(), ev()]
+
+        def step_io(vals, bvec, xout, ldout):
+            L.check(L.stc_scatter_values(P.h, vals, batch, fac), "scatter")
+            L.check(L.stc_factorize_scattered(P.h, batch, fac, ws, info), "factorize")
+            L.check(L.stc_logdet(P.h, fac, batch, ldout), "logdet")
+            L.check(L.stc_solve(P.h, fac, batch, 1, bvec, xout, ws), "solve")
+
+        def run_e2e(steps):
+            with torch.cuda.stream(cs):
+                bufs[0][0].copy_(hv, non_blocking=True)
+                bufs[0][1].copy_(hb, non_blocking=True)
+                ev_in[0].record(cs)
+            for k in range(steps):
+                j = k % 2
+                vals, bvec, xout, ldout = bufs[j]
+                st.wait_event(ev_in[j])
+                if k >= 2:
+                    st.wait_event(ev_out[j])      # step k-2's results have left this buffer
+                step_io(vals, bvec, xout, ldout)
+                ev_done[j].record(st)
+                with torch.cuda.stream(cs):
+                    if k + 1 < steps:
+                        jn = (k + 1) % 2
+                        if k >= 1:
+                            cs.wait_event(ev_done[jn])  # step k-1 no longer reads that buffer
+                        bufs[jn][0].copy_(hv, non_blocking=True)
+                        bufs[jn][1].copy_(hb, non_blocking=True)
+                        ev_in[jn].record(cs)
+                    cs.wait_event(ev_done[j])
+                    hld.copy_(ldout, non_blocking=True)
+                    hx.copy_(xout, non_blocking=True)
+                    ev_out[j].record(cs)
+            st.wait_stream(cs)
+
+        run_e2e(2)
         barrier()
         t0, t1 = ev(), ev()
         t0.record(st)
-        for k in range(args.steps):
-            dv.copy_(hv, non_blocking=True)
-            db.copy_(hb, non_blocking=True)
-            step(dv, db, dx)
-            hld.copy_(ld, non_blocking=True)
-            hx.copy_(dx, non_blocking=True)
+        cs.wait_stream(st)
+        run_e2e(args.steps)
         t1.record(st)
         barrier()
         e2e_ms = t0.elapsed_time(t1) / args.steps
+        del bufs
     # ---- plain: one factorization per launch (batch 1)
     fac1 = torch.empty(P.factor_bytes(1) // 8, dtype=torch.float64, device="cuda")
     info1 = torch.empty(1, dtype=torch.int32, device="cuda")
@@ -611,7 +648,9 @@ def run_ours(args):
     if not args.no_e2e:
         line["e2e"] = {"value": total_items / (e2e_ms * 1e-3), "unit": UNIT,
                        "h2d_bytes_per_step": batch * (nnz + n) * 8,
-                       "d2h_bytes_per_step": batch * (1 + n) * 8}
+                       "d2h_bytes_per_step": batch * (1 + n) * 8,
+                       "note": "pinned host buffers; every step's values and RHS copied in and logdet + x "
+                               "copied out on a second stream, double-buffered against the factorization"}
     if workloads:
         line["workloads"] = workloads
     print(json.dumps(line), flush=True)

@@ -1369,17 +1369,19 @@ __global__ void __launch_bounds__(kThreads, 1) selinv_kernel(SelinvArgs a) {
                         mma_sub<false>(C + p * kLdc, kLdc, R, pw, C + k0 * kLdc, kLdc, S1, LDS, K);
                         __syncthreads();
                     }
+                    const bool band = D.kind == TILE_DIAG_BAND;
                     for (int idx = threadIdx.x; idx < kPb * kPb; idx += kThreads) {
-                        const int i = idx & (kPb - 1), j = idx / kPb;
+                        const int i = band ? idx / kPb : idx & (kPb - 1);
+                        const int j = band ? idx & (kPb - 1) : idx / kPb;
                         double v = 0.0;
                         if (i < pw && j < pw && i >= j)
                             v = diag_at(DT, D, nb, logical_col(O, a.saind, p + i), logical_col(O, a.saind, p + j));
-                        S0[i + j * kPb] = v;
+                        S0[i + j * (kPb + 1)] = v;
                     }
                     __syncthreads();
-                    if (threadIdx.x < pw) sv[threadIdx.x] = 1.0 / S0[threadIdx.x * (kPb + 1)];
+                    if (threadIdx.x < pw) sv[threadIdx.x] = 1.0 / S0[threadIdx.x * (kPb + 2)];
                     __syncthreads();
-                    trsm_rows_dir<true>(C + p * kLdc, kLdc, R, pw, S0, kPb, sv);
+                    trsm_rows_dir<true>(C + p * kLdc, kLdc, R, pw, S0, kPb + 1, sv);
                     __syncthreads();
                 }
                 double* T = Sg + O.off;
@@ -1426,9 +1428,8 @@ __global__ void __launch_bounds__(kThreads, 1) selinv_kernel(SelinvArgs a) {
                 // packed lower triangle of L_kk in the staging area: (r, c) at c*nb - c(c-1)/2 + r - c
                 double* Lp = S0;
                 const double* DT = Lf + D.off;
-                for_rc(nb, nb, [&](int r, int c) {
-                    if (r >= c) Lp[c * nb - c * (c - 1) / 2 + (r - c)] = diag_at(DT, D, nb, r, c);
-                });
+                read_diag_rows(DT, D, nb, 0, nb,
+                               [&](int r, int c, double v) { Lp[c * nb - c * (c - 1) / 2 + (r - c)] = v; });
                 __syncthreads();
                 for (int c = w - 1; c >= 0; --c) {
                     const double* Lc = Lp + c * nb - c * (c - 1) / 2 - c;  // Lc[i] = L[i][c]
