@@ -34,7 +34,7 @@ constexpr int kNbMax = 128;
 constexpr int kLdc = kNbMax + 1;   // shared-memory leading dimension of the tile buffer
 constexpr int kKc = 32;            // inner-dimension chunk staged per step
 constexpr int kPb = kPanelW;       // panel width of the blocked TRSM
-constexpr int kStage = kKc * (kNbMax + 8);          // doubles per staging buffer
+constexpr int kStage = kKc * (kNbMax + 9);          // doubles per staging buffer (odd ld)
 constexpr int kCbuf = kLdc * kNbMax + 16;           // tile buffer (+ overrun pad)
 constexpr int kSmemDoubles = kCbuf + 2 * kStage + kNbMax;
 constexpr size_t kSmemBytes = kSmemDoubles * sizeof(double) + 64;
@@ -1277,6 +1277,29 @@ __device__ __forceinline__ double sym_at(const double* T, const DTile& d, int nb
     return r >= c ? diag_at(T, d, nb, r, c) : diag_at(T, d, nb, c, r);
 }
 
+// S[r + k*ld] = get(r, k) for r < R, zero for R <= r < Rp, k < K; consecutive threads on
+// consecutive r (RFAST) or consecutive k -- whichever is contiguous in the source -- with
+// four loads in flight per thread.
+template <bool RFAST, class Get>
+__device__ void stage_gather(double* S, int ld, int R, int Rp, int K, Get get) {
+    const int n = Rp * K;
+    for (int b = threadIdx.x; b < n; b += 4 * kThreads) {
+        double v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int j = b + u * kThreads;
+            const int r = RFAST ? j % Rp : j / K, k = RFAST ? j / Rp : j % K;
+            v[u] = (j < n && r < R) ? get(r, k) : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int j = b + u * kThreads;
+            const int r = RFAST ? j % Rp : j / K, k = RFAST ? j / Rp : j % K;
+            if (j < n) S[r + k * ld] = v[u];
+        }
+    }
+}
+
 __global__ void __launch_bounds__(kThreads, 1) selinv_kernel(SelinvArgs a) {
     extern __shared__ double smem[];
     double* C = smem;
@@ -1287,7 +1310,8 @@ __global__ void __launch_bounds__(kThreads, 1) selinv_kernel(SelinvArgs a) {
     __shared__ int s_ok;
     const long long total = (long long)a.ntasks * a.batch;
     const int nb = a.nb;
-    constexpr int LDS = kNbMax + 8;
+    constexpr int LDS = kNbMax + 9;  // odd: column-wise staging stores hit distinct banks
+    __shared__ int16_t s_idx[2][kNbMax];  // stored-column indices of a contribution's tiles
     for (;;) {
         if (threadIdx.x == 0) s_slot = (long long)atomicAdd(&a.hdr->head, 1ULL);
         __syncthreads();
@@ -1319,32 +1343,34 @@ __global__ void __launch_bounds__(kThreads, 1) selinv_kernel(SelinvArgs a) {
                 const double* ST = Sg + St.off;
                 const int16_t* si_S = a.sinv + (size_t)cn.stile * nb;
                 const int16_t* si_L = a.sinv + (size_t)cn.ltile * nb;
+                // stored-column indices used by every chunk: Sigma's for the inner rows i
+                // (MJ) or the output rows (JM), L's for the output's stored columns
+                for (int q = threadIdx.x; q < nb; q += kThreads) {
+                    s_idx[0][q] = si_S[q];
+                    s_idx[1][q] = q < sw ? si_L[logical_col(O, a.saind, q)] : (int16_t)-1;
+                }
+                __syncthreads();
                 for (int i0 = Lt.r0; i0 < Lt.r1; i0 += kKc) {
                     const int K = min(kKc, Lt.r1 - i0);
                     const int Rp = ((R + 3) & ~3) + 4, Cp = ((sw + 3) & ~3) + 4;
-                    for_rc(Rp, K, [&](int r, int kk) {
-                        double v = 0.0;
-                        if (r < R) {
-                            const int gr = t.r0 + r, i = i0 + kk;
-                            if (cn.mode == SCON_MJ) {
-                                const int sidx = si_S[i];
-                                if (sidx >= 0) v = __ldcg(ST + gr + (size_t)sidx * nb);
-                            } else if (cn.mode == SCON_JM) {
-                                const int sidx = si_S[gr];
-                                if (sidx >= 0) v = __ldcg(ST + i + (size_t)sidx * nb);
-                            } else {
-                                v = sym_at(ST, St, nb, gr, i);
-                            }
-                        }
-                        S0[r + kk * LDS] = v;
-                    });
-                    for_rc(Cp, K, [&](int c, int kk) {
-                        double v = 0.0;
-                        if (c < sw) {
-                            const int sl = si_L[logical_col(O, a.saind, c)];
-                            if (sl >= 0) v = __ldcg(LT + (i0 + kk) + (size_t)sl * nb);
-                        }
-                        S1[c + kk * LDS] = v;
+                    if (cn.mode == SCON_MJ) {  // Sigma(m, j): output rows contiguous
+                        stage_gather<true>(S0, LDS, R, Rp, K, [&](int r, int kk) {
+                            const int sidx = s_idx[0][i0 + kk];
+                            return sidx >= 0 ? __ldcg(ST + t.r0 + r + (size_t)sidx * nb) : 0.0;
+                        });
+                    } else if (cn.mode == SCON_JM) {  // Sigma(j, m)^T: inner rows contiguous
+                        stage_gather<false>(S0, LDS, R, Rp, K, [&](int r, int kk) {
+                            const int sidx = s_idx[0][t.r0 + r];
+                            return sidx >= 0 ? __ldcg(ST + i0 + kk + (size_t)sidx * nb) : 0.0;
+                        });
+                    } else {
+                        stage_gather<true>(S0, LDS, R, Rp, K,
+                                           [&](int r, int kk) { return sym_at(ST, St, nb, t.r0 + r, i0 + kk); });
+                    }
+                    // L(j, k) rows i0.. of the output's stored columns: rows contiguous
+                    stage_gather<false>(S1, LDS, sw, Cp, K, [&](int c, int kk) {
+                        const int sl = s_idx[1][c];
+                        return sl >= 0 ? __ldcg(LT + (i0 + kk) + (size_t)sl * nb) : 0.0;
                     });
                     __syncthreads();
                     mma_sub<false>(C, kLdc, R, sw, S0, LDS, S1, LDS, K);  // C = -sum Sigma L
@@ -1403,20 +1429,19 @@ __global__ void __launch_bounds__(kThreads, 1) selinv_kernel(SelinvArgs a) {
                 const bool contig = Tt.c0 >= 0;
                 const int M = contig ? Tt.sw : w;   // rows/cols of the Z block
                 const int16_t* si = a.sinv + (size_t)cn.ltile * nb;
+                for (int q = threadIdx.x; q < nb; q += kThreads) s_idx[0][q] = contig ? (int16_t)q : si[q];
+                __syncthreads();
                 for (int i0 = Tt.r0; i0 < Tt.r1; i0 += kKc) {
                     const int K = min(kKc, Tt.r1 - i0);
                     const int Mp = ((M + 3) & ~3) + 4;
-                    for_rc(Mp, K, [&](int r, int kk) {
-                        double vs = 0.0, vl = 0.0;
-                        if (r < M) {
-                            const int sidx = contig ? r : si[r];
-                            if (sidx >= 0) {
-                                vs = __ldcg(ST + (i0 + kk) + (size_t)sidx * nb);
-                                vl = __ldcg(LT + (i0 + kk) + (size_t)sidx * nb);
-                            }
-                        }
-                        S0[r + kk * LDS] = vs;
-                        S1[r + kk * LDS] = vl;
+                    // rows i0.. of the stored columns: contiguous along the inner index
+                    stage_gather<false>(S0, LDS, M, Mp, K, [&](int r, int kk) {
+                        const int sidx = s_idx[0][r];
+                        return sidx >= 0 ? __ldcg(ST + (i0 + kk) + (size_t)sidx * nb) : 0.0;
+                    });
+                    stage_gather<false>(S1, LDS, M, Mp, K, [&](int r, int kk) {
+                        const int sidx = s_idx[0][r];
+                        return sidx >= 0 ? __ldcg(LT + (i0 + kk) + (size_t)sidx * nb) : 0.0;
                     });
                     __syncthreads();
                     double* Cz = contig ? C + Tt.c0 * (1 + kLdc) : C;
