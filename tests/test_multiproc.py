@@ -41,3 +41,13 @@ def test_two_gloo_ranks_shard_and_reduce():
     assert out[0][:2] == (0, 63) and out[1][:2] == (64, 127)     # disjoint contiguous seed ranges
     for r in range(world):
         assert out[r][2] == [11.0, 10.0, 1.0, 2.0]                # element-wise max over ranks
+
+
+def test_parallel_oracle_baseline_small():
+    # the bench's CPU baseline: one oracle process per core, all started together
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    sys.path.insert(0, root)
+    import bench
+    walls = bench.oracle_parallel(3000, 2, rounds=2)
+    assert len(walls) == 2 and all(w > 0.0 for w in walls)
