@@ -55,6 +55,10 @@ extern "C" {
 #define STC_ERR_UNSUPPORTED (-6)     /* option or size outside what is built      */
 #define STC_ERR_BUFFER_TOO_SMALL (-7)
 
+/* A short English description of a return code (STC_OK or STC_ERR_*); a static string,
+ * never NULL ("unknown error" for any other value).  Host only. */
+const char* stc_strerror(int code);
+
 /* ---- routes (Sec. 5.1) ------------------------------------------------- */
 #define STC_ROUTE_AUTO (-1)
 #define STC_ROUTE_DENSE 0       /* every active tile stored as a full n_b x n_b block  */

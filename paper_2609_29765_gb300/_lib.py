@@ -23,8 +23,6 @@ STC_ERR_CUDA = -4
 STC_ERR_TIMEOUT = -5
 STC_ERR_UNSUPPORTED = -6
 STC_ERR_BUFFER_TOO_SMALL = -7
-ERRORS = {0: "ok", -1: "invalid argument", -2: "invalid pattern", -3: "out of memory",
-          -4: "CUDA error", -5: "device wait timeout", -6: "unsupported", -7: "buffer too small"}
 
 STC_ROUTE_AUTO, STC_ROUTE_DENSE, STC_ROUTE_SEMISPARSE, STC_ROUTE_SUPERNODAL = -1, 0, 1, 2
 STC_ORDER_AUTO, STC_ORDER_NATURAL, STC_ORDER_GIVEN, STC_ORDER_ND, STC_ORDER_RCM = 0, 1, 2, 3, 4
@@ -39,13 +37,18 @@ EXPORTED = [
     "stc_logdet", "stc_solve", "stc_factor_to_csc", "stc_fp64_peak_probe", "stc_factorize_noalloc",
     "stc_selinv", "stc_logdet_backward", "stc_sym_outer_backward", "stc_quad_form",
     "stc_group_create", "stc_group_workspace_bytes", "stc_factorize_group", "stc_group_destroy",
+    "stc_strerror",
 ]
 STC_NOALLOC_SCRATCH_BYTES = 4 << 20
 
 
+def stc_strerror(code) -> str:
+    return lib().stc_strerror(int(code)).decode()
+
+
 class StcError(RuntimeError):
     def __init__(self, code, where=""):
-        super().__init__("%s: %s (%d)" % (where, ERRORS.get(code, "error"), code))
+        super().__init__("%s: %s (%d)" % (where, stc_strerror(code), code))
         self.code = code
 
 
@@ -84,6 +87,8 @@ def lib():
         L = C.CDLL(_build.LIB)
         L.stc_options_default.argtypes = [C.POINTER(stc_options)]
         L.stc_options_default.restype = None
+        L.stc_strerror.argtypes = [C.c_int]
+        L.stc_strerror.restype = C.c_char_p
         L.stc_analyze.argtypes = [C.c_int64, _vp, _vp, _vp, C.POINTER(stc_options), C.POINTER(_vp)]
         L.stc_analyze.restype = C.c_int
         L.stc_plan_info_get.argtypes = [_vp, C.POINTER(stc_plan_info)]

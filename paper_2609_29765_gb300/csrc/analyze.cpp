@@ -821,6 +821,20 @@ stc::TaskSet* stc_plan::taskset(int32_t slices, bool bl_order) {
 // ---------------------------------------------------------------------------
 // Public entry points (host side).
 // ---------------------------------------------------------------------------
+extern "C" const char* stc_strerror(int code) {
+    switch (code) {
+        case STC_OK: return "success";
+        case STC_ERR_INVALID_ARG: return "invalid argument";
+        case STC_ERR_INVALID_PATTERN: return "invalid pattern (not lower CSC with sorted rows and a diagonal)";
+        case STC_ERR_OUT_OF_MEMORY: return "out of memory";
+        case STC_ERR_CUDA: return "CUDA runtime error";
+        case STC_ERR_TIMEOUT: return "device dependency wait exceeded its limit";
+        case STC_ERR_UNSUPPORTED: return "unsupported option or size";
+        case STC_ERR_BUFFER_TOO_SMALL: return "buffer too small";
+        default: return "unknown error";
+    }
+}
+
 extern "C" void stc_options_default(stc_options* o) {
     if (!o) return;
     std::memset(o, 0, sizeof(*o));

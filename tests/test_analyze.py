@@ -258,3 +258,13 @@ def test_chunk_row_extents_vs_oracle_structure(case, route):
     t = F.tile_map(kw["nb"])
     ext = P.export("chunk_extents")
     assert np.array_equal(ext, _chunk_extents_brute(F, t, kw["nb"], n, route == "dense"))
+
+
+def test_strerror_names_every_code():
+    codes = [L.STC_OK, L.STC_ERR_INVALID_ARG, L.STC_ERR_INVALID_PATTERN, L.STC_ERR_OUT_OF_MEMORY,
+             L.STC_ERR_CUDA, L.STC_ERR_TIMEOUT, L.STC_ERR_UNSUPPORTED, L.STC_ERR_BUFFER_TOO_SMALL]
+    names = [L.stc_strerror(c) for c in codes]
+    assert len(set(names)) == len(codes) and all(names)
+    assert L.stc_strerror(-99) == "unknown error" and L.stc_strerror(7) == "unknown error"
+    with pytest.raises(L.StcError, match="invalid argument"):
+        L.check(L.STC_ERR_INVALID_ARG, "here")
