@@ -204,6 +204,14 @@ int stc_factorize_group(stc_group* group, const double* const* d_values, void* c
                         int32_t* const* d_info, void* d_work, void* stream);
 void stc_group_destroy(stc_group* group);
 
+/* The same in one call: a group of the nplans plans (batch[p] value sets each) is
+ * created, run on `stream` and destroyed; its workspace comes from the stream-ordered
+ * allocator (cudaMallocAsync) and is released before returning.  Synchronous: returns
+ * after the factorization has finished, with its status (STC_OK, STC_ERR_TIMEOUT, or an
+ * error of group creation or of CUDA).  Buffers as for stc_factorize_group. */
+int stc_factorize_mixed(int32_t nplans, const stc_plan* const* plans, const double* const* d_values,
+                        const int64_t* batch, void* const* d_factor, int32_t* const* d_info, void* stream);
+
 /* Synchronize `stream` and return the device status word of d_work: STC_OK or
  * STC_ERR_TIMEOUT (a dependency wait gave up), or STC_ERR_CUDA. */
 int stc_sync_status(const void* d_work, void* stream);

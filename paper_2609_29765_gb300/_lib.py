@@ -37,7 +37,7 @@ EXPORTED = [
     "stc_logdet", "stc_solve", "stc_factor_to_csc", "stc_fp64_peak_probe", "stc_factorize_noalloc",
     "stc_selinv", "stc_logdet_backward", "stc_sym_outer_backward", "stc_quad_form",
     "stc_group_create", "stc_group_workspace_bytes", "stc_factorize_group", "stc_group_destroy",
-    "stc_strerror",
+    "stc_strerror", "stc_factorize_mixed",
 ]
 STC_NOALLOC_SCRATCH_BYTES = 4 << 20
 
@@ -123,6 +123,9 @@ def lib():
         L.stc_group_workspace_bytes.restype = C.c_size_t
         L.stc_factorize_group.argtypes = [_vp, C.POINTER(_vp), C.POINTER(_vp), C.POINTER(_vp), _vp, _vp]
         L.stc_factorize_group.restype = C.c_int
+        L.stc_factorize_mixed.argtypes = [C.c_int32, C.POINTER(_vp), C.POINTER(_vp), C.POINTER(C.c_int64),
+                                          C.POINTER(_vp), C.POINTER(_vp), _vp]
+        L.stc_factorize_mixed.restype = C.c_int
         L.stc_group_destroy.argtypes = [_vp]
         L.stc_group_destroy.restype = None
         L.stc_selinv.argtypes = [_vp, _vp, C.c_int64, _vp, _vp, _vp]
@@ -301,6 +304,16 @@ def stc_factorize_group(group, d_values, d_factor, d_info, d_work, stream=None):
     pf = (C.c_void_p * n)(*[_dev_ptr(t).value for t in d_factor])
     pi = (C.c_void_p * n)(*[_dev_ptr(t).value for t in d_info])
     return lib().stc_factorize_group(group, pv, pf, pi, _dev_ptr(d_work), _stream(stream))
+
+
+def stc_factorize_mixed(plans, d_values, batches, d_factor, d_info, stream=None):
+    n = len(plans)
+    pp = (C.c_void_p * n)(*[p.value if isinstance(p, C.c_void_p) else p for p in plans])
+    pv = (C.c_void_p * n)(*[_dev_ptr(t).value for t in d_values])
+    bat = (C.c_int64 * n)(*[int(b) for b in batches])
+    pf = (C.c_void_p * n)(*[_dev_ptr(t).value for t in d_factor])
+    pi = (C.c_void_p * n)(*[_dev_ptr(t).value for t in d_info])
+    return lib().stc_factorize_mixed(n, pp, pv, bat, pf, pi, _stream(stream))
 
 
 def stc_group_destroy(group):

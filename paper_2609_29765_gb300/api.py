@@ -258,6 +258,23 @@ class Group:
         return L.stc_sync_status(self._ws)
 
 
+def factorize_mixed(plans, values_list):
+    """Several patterns in one launch and one call (stc_factorize_mixed, synchronous):
+    values_list[p] is CUDA float64 [batch_p, nnzA_p]; returns one Factor per plan."""
+    torch = _torch()
+    dev = values_list[0].device
+    facs, infos, vals = [], [], []
+    for P, v in zip(plans, values_list):
+        if v.dim() != 2 or v.shape[1] != P.nnzA or v.dtype != torch.float64:
+            raise ValueError("values must be float64 [batch_p, nnzA_p]")
+        vals.append(v.contiguous())
+        facs.append(torch.empty(P.factor_bytes(v.shape[0]) // 8, dtype=torch.float64, device=dev))
+        infos.append(torch.empty(v.shape[0], dtype=torch.int32, device=dev))
+    L.check(L.stc_factorize_mixed([P.h for P in plans], vals, [v.shape[0] for v in vals], facs, infos),
+            "stc_factorize_mixed")
+    return [Factor(P, f, i, v.shape[0]) for P, f, i, v in zip(plans, facs, infos, vals)]
+
+
 # ---------------------------------------------------------------------------
 # Differentiation: torch.autograd.Function wrappers.  The forward and backward
 # arithmetic runs in libstc.so; torch only carries the tensors and the chain rule of

@@ -5,7 +5,7 @@ import pytest
 from oracle import oracle as O
 from paper_2609_29765_gb300 import _lib as L
 from paper_2609_29765_gb300 import inputs as I
-from paper_2609_29765_gb300.api import GraphedFactorize, Group, Plan
+from paper_2609_29765_gb300.api import GraphedFactorize, Group, Plan, factorize_mixed
 from paper_2609_29765_gb300.tune import autotune
 
 torch = pytest.importorskip("torch")
@@ -30,9 +30,11 @@ def test_group_mixed_patterns_match_single_launch_and_oracle(route):
     G = Group(plans, [v.shape[0] for v in vals])
     facs = G.factorize(vals)
     assert G.status() == L.STC_OK
-    for P, v, f, (n, Ap, Ai) in zip(plans, vals, facs, pats):
+    once = factorize_mixed(plans, vals)                   # the one-call form
+    for P, v, f, g, (n, Ap, Ai) in zip(plans, vals, facs, once, pats):
         ref = P.factorize(v)
         assert torch.equal(f.to_csc(), ref.to_csc())     # same tasks, same arithmetic
+        assert torch.equal(g.to_csc(), ref.to_csc())
         assert int(f.info.abs().sum()) == 0
         F = O.OracleFactor(n, Ap, Ai, P.export("perm"))
         Lo, _ = F.factor(v[-1].cpu().numpy())
