@@ -254,6 +254,12 @@ int stc_logdet_backward(const stc_plan* plan, const void* d_factor, int64_t batc
  * with u, v [batch][n] in the original ordering; scale [batch] or NULL (= 1).
  * u = v = x gives d(x^T A x)/d a_e; u = A^{-1} b, v = A^{-1} g, scale = -1 gives the
  * adjoint of the solve x = A^{-1} b for an upstream gradient g on x. */
+/* d(x^T A x)/d a_e = gout[b] (2 - delta_ij) x_i x_j for every stored A entry e = (i, j)
+ * (stc_sym_outer_backward with u = v = x, scale = gout): x [batch][n] in the original
+ * ordering; gout [batch] or NULL (= 1); d_gvalues [batch][nnzA], added to when
+ * accumulate != 0. */
+int stc_quad_backward(const stc_plan* plan, int64_t batch, const double* d_x, const double* d_gout,
+                      double* d_gvalues, int accumulate, void* stream);
 int stc_sym_outer_backward(const stc_plan* plan, int64_t batch, const double* d_u,
                            const double* d_v, const double* d_scale, double* d_gvalues,
                            int accumulate, void* stream);

@@ -37,7 +37,7 @@ EXPORTED = [
     "stc_logdet", "stc_solve", "stc_factor_to_csc", "stc_fp64_peak_probe", "stc_factorize_noalloc",
     "stc_selinv", "stc_logdet_backward", "stc_sym_outer_backward", "stc_quad_form",
     "stc_group_create", "stc_group_workspace_bytes", "stc_factorize_group", "stc_group_destroy",
-    "stc_strerror", "stc_factorize_mixed",
+    "stc_strerror", "stc_factorize_mixed", "stc_quad_backward",
 ]
 STC_NOALLOC_SCRATCH_BYTES = 4 << 20
 
@@ -126,6 +126,8 @@ def lib():
         L.stc_factorize_mixed.argtypes = [C.c_int32, C.POINTER(_vp), C.POINTER(_vp), C.POINTER(C.c_int64),
                                           C.POINTER(_vp), C.POINTER(_vp), _vp]
         L.stc_factorize_mixed.restype = C.c_int
+        L.stc_quad_backward.argtypes = [_vp, C.c_int64, _vp, _vp, _vp, C.c_int, _vp]
+        L.stc_quad_backward.restype = C.c_int
         L.stc_group_destroy.argtypes = [_vp]
         L.stc_group_destroy.restype = None
         L.stc_selinv.argtypes = [_vp, _vp, C.c_int64, _vp, _vp, _vp]
@@ -314,6 +316,11 @@ def stc_factorize_mixed(plans, d_values, batches, d_factor, d_info, stream=None)
     pf = (C.c_void_p * n)(*[_dev_ptr(t).value for t in d_factor])
     pi = (C.c_void_p * n)(*[_dev_ptr(t).value for t in d_info])
     return lib().stc_factorize_mixed(n, pp, pv, bat, pf, pi, _stream(stream))
+
+
+def stc_quad_backward(plan, batch, d_x, d_gout, d_gvalues, accumulate, stream=None):
+    return lib().stc_quad_backward(plan, int(batch), _dev_ptr(d_x), _dev_ptr(d_gout), _dev_ptr(d_gvalues),
+                                   int(accumulate), _stream(stream))
 
 
 def stc_group_destroy(group):

@@ -20,7 +20,7 @@ OUT = os.path.join(PKG, "_build")
 LIB = os.path.join(OUT, "libstc.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
-SOURCES_CU = ["replay.cu", "mixed.cu"]
+SOURCES_CU = ["replay.cu", "compose.cu"]
 SOURCES_CPP = ["analyze.cpp"]
 
 

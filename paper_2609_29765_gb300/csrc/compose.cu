@@ -1,7 +1,10 @@
-// mixed.cu -- several patterns, each with its own batch of value sets, factorized by one
-// persistent launch in a single call: a group is created, run and destroyed around the
-// caller's buffers (the batching of Sec. 1 and 2 over uneven patterns).  Host code only;
-// the kernel is the replay kernel behind stc_factorize_group.
+// compose.cu -- entry points composed from the others (host code only).
+//  * stc_factorize_mixed: several patterns, each with its own batch of value sets,
+//    factorized by one persistent launch in a single call: a group is created, run and
+//    destroyed around the caller's buffers (the batching of Sec. 1 and 2 over uneven
+//    patterns); the kernel is the replay kernel behind stc_factorize_group.
+//  * stc_quad_backward: the gradient of the quadratic form x^T A x, the symmetric outer
+//    product of x with itself.
 #include <cuda_runtime.h>
 
 #include "stc.h"
@@ -25,4 +28,9 @@ extern "C" int stc_factorize_mixed(int32_t nplans, const stc_plan* const* plans,
     const bool freed = cudaFreeAsync(ws, st) == cudaSuccess && cudaStreamSynchronize(st) == cudaSuccess;
     stc_group_destroy(g);
     return status != STC_OK ? status : (freed ? STC_OK : STC_ERR_CUDA);
+}
+
+extern "C" int stc_quad_backward(const stc_plan* plan, int64_t batch, const double* d_x, const double* d_gout,
+                                 double* d_gvalues, int accumulate, void* stream) {
+    return stc_sym_outer_backward(plan, batch, d_x, d_x, d_gout, d_gvalues, accumulate, stream);
 }

@@ -195,6 +195,9 @@ def test_quad_form_and_outer_backward_vs_numpy():
     g = torch.empty(2, len(Ai), dtype=torch.float64, device="cuda")
     sc = dev(np.array([1.0, -0.5]))
     assert L.stc_sym_outer_backward(P.h, 2, dev(x), dev(x), sc, g, 0) == L.STC_OK
+    gq = torch.empty_like(g)
+    assert L.stc_quad_backward(P.h, 2, dev(x), sc, gq, 0) == L.STC_OK    # u = v = x form
+    assert torch.equal(gq, g)
     col = np.repeat(np.arange(n), np.diff(Ap))
     for bb in range(2):
         A = full_sym(n, Ap, Ai, vals[bb])
