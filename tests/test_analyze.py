@@ -268,3 +268,33 @@ def test_strerror_names_every_code():
     assert L.stc_strerror(-99) == "unknown error" and L.stc_strerror(7) == "unknown error"
     with pytest.raises(L.StcError, match="invalid argument"):
         L.check(L.STC_ERR_INVALID_ARG, "here")
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_random_patterns_symbolic_and_extents_vs_oracle(seed):
+    # random sizes, densities, tile sizes and orderings: every symbolic export and the
+    # 16-column row extents against the oracle and brute force
+    rng = np.random.default_rng(1000 + seed)
+    n = int(rng.integers(20, 260))
+    Ap, Ai, _ = I.random_spd(n, float(rng.uniform(0.005, 0.08)), seed)
+    nb = int(rng.choice([8, 16, 24, 32, 64]))
+    kind = ["natural", "rcm", "given"][seed % 3]
+    perm = rng.permutation(n) if kind == "given" else None
+    route = "dense" if seed % 4 == 0 else "semisparse"
+    P = Plan(n, Ap, Ai, nb=nb, ordering=kind if perm is None else "auto", perm=perm, route=route)
+    operm = P.export("perm")
+    assert np.array_equal(np.sort(operm), np.arange(n))
+    if perm is not None:
+        assert np.array_equal(operm, perm)
+    F = O.OracleFactor(n, Ap, Ai, operm)
+    assert np.array_equal(P.export("etree"), F.parent)
+    assert np.array_equal(P.export("Lp"), F.Lp)
+    assert np.array_equal(P.export("Li"), F.Li)
+    t = F.tile_map(nb)
+    T = P.export("tiles")
+    ref = np.stack([t["I"], t["J"], t["nact"], t["aoff"], t["contig"], t["full"], t["kd"],
+                    t["r0"], t["r1"]], axis=1)
+    assert np.array_equal(T, ref)
+    assert np.array_equal(P.export("aind"), t["aind"])
+    assert np.array_equal(P.export("tasks"), t["tasks"])
+    assert np.array_equal(P.export("chunk_extents"), _chunk_extents_brute(F, t, nb, n, route == "dense"))
