@@ -778,6 +778,21 @@ stc::TaskSet* stc_plan::taskset(int32_t slices, bool bl_order) {
         fin[i] = t;
         key[i] = std::max(first, kdep + 1e-6);
         ts->fma += std::accumulate(mt.ucost.begin(), mt.ucost.end(), 0.0) + mt.fcost;
+        {
+            // the POTRF cost of the model is the banded-Cholesky estimate w (kd+1)^2 / 2;
+            // the kernel updates, after column j, the min(kd, w-1-j) rows below it
+            double fc = mt.fcost;
+            if (tasks[i].kind == stc::TASK_DIAG || tasks[i].kind == stc::TASK_POTRF) {
+                const stc::DTile& Dt = tiles[tasks[i].tile];
+                const int64_t kdd = std::min<int64_t>(Dt.kd, Dt.sw - 1);
+                fc = 0.0;
+                for (int64_t j = 0; j < Dt.sw; ++j) {
+                    const double m = double(std::min<int64_t>(kdd, Dt.sw - 1 - j));
+                    fc += m * (m + 1) / 2 + m;
+                }
+            }
+            ts->fma_exec += std::accumulate(mt.ucost.begin(), mt.ucost.end(), 0.0) + fc;
+        }
         const int32_t o = tasks[i].tile;
         if (mt.npub > 0) tile_avail[o] = std::min(tile_avail[o], tf + (t - tf) / mt.npub);
         tile_fin[o] = std::max(tile_fin[o], fin[i]);
@@ -1033,7 +1048,7 @@ static int analyze_impl(int64_t n, const int64_t* Ap, const int64_t* Ai, const d
             P->acol[p] = (int32_t)j;
         }
     stc::TaskSet* ts = P->taskset(1);
-    P->flops_tile = 2.0 * ts->fma;
+    P->flops_tile = 2.0 * ts->fma_exec;
     P->analyze_seconds =
         std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     *out = P.release();

@@ -143,7 +143,8 @@ struct TaskSet {
     std::vector<double> qkey;     // modelled start of each task (queue order)
     double period = 0.0;          // modelled time per block column
     double par = 0.0;             // modelled average parallelism (work / makespan)
-    double fma = 0.0;             // executed FMAs
+    double fma = 0.0;             // modelled FMAs (queue-order cost model)
+    double fma_exec = 0.0;        // FMAs the kernels execute (exact POTRF count)
     std::map<int64_t, uint64_t*> d_queue;  // per batch: merged (task << 32 | item) order
     // device copies
     DTask* d_tasks = nullptr;
