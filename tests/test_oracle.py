@@ -9,10 +9,15 @@ Pins used (none of them re-types the oracle's own formula):
 * hand-derived task lists and ND orderings;
 * a dense numpy tile executor driven by the oracle's Algorithm-1 task list, which must
   reproduce numpy's Cholesky (pins the order and completeness of the task list);
-* central finite differences for gradients.
+* central finite differences for gradients;
+* exact rational arithmetic on small integer matrices (cofactor determinant, Cramer's rule);
+* the block-determinant identity through the Schur complement of the border;
+* closed-form theta derivatives of the border-free spatio-temporal log-determinant.
 """
 import json
+import math
 import os
+from fractions import Fraction
 
 import numpy as np
 import pytest
@@ -142,6 +147,67 @@ def test_logdet_fem3d_unit_conductance_closed_form():
     assert abs(F.logdet(Lx) - ref) <= 1e-10 * abs(ref)
 
 
+def _det_cofactor(M):
+    """Exact determinant of a small matrix of Fractions by Laplace expansion along row 0."""
+    m = len(M)
+    if m == 1:
+        return M[0][0]
+    tot = Fraction(0)
+    for c in range(m):
+        if M[0][c] != 0:
+            minor = [row[:c] + row[c + 1:] for row in M[1:]]
+            tot += (-1) ** c * M[0][c] * _det_cofactor(minor)
+    return tot
+
+
+@pytest.mark.parametrize("n,seed", [(3, 0), (5, 1), (7, 2), (8, 3)])
+def test_logdet_and_solve_vs_exact_rational_arithmetic(n, seed):
+    # integer SPD matrix (strictly diagonally dominant, random sparsity): the determinant by
+    # cofactor expansion and the solution by Cramer's rule, both in exact rationals
+    rng = np.random.default_rng(seed)
+    A = np.zeros((n, n), dtype=np.int64)
+    for i in range(n):
+        for j in range(i):
+            if rng.uniform() < 0.6:
+                A[i, j] = A[j, i] = int(rng.integers(-5, 6))
+    A[np.arange(n), np.arange(n)] = np.abs(A).sum(axis=1) + rng.integers(1, 4, n)
+    b = rng.integers(-9, 10, n)
+    Ap, Ai, Ax = I.lower_csc(sp.csc_matrix(A.astype(float)))
+    F = O.OracleFactor(n, Ap, Ai, rng.permutation(n))
+    Lx, info = F.factor(Ax)
+    assert info == 0
+    Mq = [[Fraction(int(v)) for v in row] for row in A]
+    det = _det_cofactor(Mq)
+    assert det > 0
+    assert abs(F.logdet(Lx) - math.log(det)) <= 1e-13 * max(1.0, math.log(det))
+    x = F.solve(Lx, b.astype(float))
+    for i in range(n):
+        Mi = [row[:i] + [Fraction(int(b[r]))] + row[i + 1:] for r, row in enumerate(Mq)]
+        xi = _det_cofactor(Mi) / det
+        assert abs(x[i] - float(xi)) <= 1e-13 * max(1.0, abs(float(xi)))
+
+
+def test_logdet_bordered_block_determinant():
+    # logdet Q = logdet Q_ff + logdet(Q_bb - Q_bf Q_ff^-1 Q_fb): the field block is factored
+    # on its own (border rows dropped), the 2x2 Schur complement is built from field solves
+    # and its determinant taken by the 2x2 formula
+    Ap, Ai, Ax, coords = I.laplace2d_bordered(20, 20, 2)
+    n = len(Ap) - 1
+    nf = n - 2
+    Q = full_sym(n, Ap, Ai, Ax)
+    Qff, Qfb, Qbb = Q[:nf, :nf], Q[:nf, nf:].toarray(), Q[nf:, nf:].toarray()
+    Fa = O.OracleFactor(n, Ap, Ai, O.nd_lattice(coords))
+    full = Fa.logdet(Fa.factor(Ax)[0])
+    fp, fi, fx = I.lower_csc(Qff)
+    Ff = O.OracleFactor(nf, fp, fi, O.nd_lattice(coords[:nf]))
+    Lf, info = Ff.factor(fx)
+    assert info == 0
+    Z = np.stack([Ff.solve(Lf, Qfb[:, k]) for k in range(2)], axis=1)
+    S = Qbb - Qfb.T @ Z
+    ref = Ff.logdet(Lf) + math.log(S[0, 0] * S[1, 1] - S[0, 1] * S[1, 0])
+    assert abs(full - ref) <= 1e-12 * abs(ref)
+
+
 # --------------------------------------------------------------------------- solve
 def test_solve_matches_dense_and_residual():
     Ap, Ai, Ax, coords = I.laplace2d_bordered(16, 16, 3)
@@ -198,6 +264,28 @@ def test_grad_logdet_finite_differences_and_dense_inverse():
         xp[e] += h; xm[e] -= h
         fp = F.logdet(F.factor(xp)[0]); fm = F.logdet(F.factor(xm)[0])
         assert abs((fp - fm) / (2 * h) - g[e]) <= 1e-6 * max(1.0, abs(g[e]))
+
+
+def test_theta_gradient_closed_form_without_border():
+    # d logdet Q(theta)/d theta = sum_ij (d logdet/d a_ij)(d a_ij/d theta) on the lower
+    # pattern; border-free closed forms: d/dtau = n/tau, d/drho = -nx ny 2 rho/(1-rho^2),
+    # d/dkappa = nt [ny sum_a 2k/(k2+mu_a) + nx sum_b 2k/(k2+mu_b)]
+    nx, ny, nt = 9, 7, 5
+    Ap, Ai, coords = I.stcov_pattern(nx, ny, nt, 0)
+    n = len(Ap) - 1
+    F = O.OracleFactor(n, Ap, Ai, O.nd_lattice(coords, 16))
+    for tau, rho, kap in [(2.0, 0.6, 0.7), (0.3, 0.9, 1.5)]:
+        th = (tau, rho, kap)
+        Lx, info = F.factor(I.stcov_values(th, nx, ny, nt, 0))
+        assert info == 0
+        g = F.grad_logdet(F.selinv(Lx))
+        got = I.stcov_dtheta(th, nx, ny, nt, 0) @ g
+        mux = 2 - 2 * np.cos(np.arange(1, nx + 1) * np.pi / (nx + 1))
+        muy = 2 - 2 * np.cos(np.arange(1, ny + 1) * np.pi / (ny + 1))
+        k2 = kap * kap
+        ref = [n / tau, -nx * ny * 2 * rho / (1 - rho * rho),
+               nt * (ny * np.sum(2 * kap / (k2 + mux)) + nx * np.sum(2 * kap / (k2 + muy)))]
+        assert np.allclose(got, ref, rtol=1e-11, atol=1e-10), (got, ref)
 
 
 # --------------------------------------------------------------------------- symbolic
