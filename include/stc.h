@@ -82,7 +82,8 @@ typedef struct stc_options {
                              the k-th pivot (copied during analyze)                    */
     int32_t row_slices;   /* rows of an off-diagonal tile split into this many device
                              tasks (1,2,4,8); 0 = chosen per call from the batch size  */
-    int32_t reserved0;
+    int32_t host_threads; /* host threads stc_analyze may use; 0 = all hardware threads
+                             (at most 32).  The plan does not depend on this count.   */
     int64_t spin_limit;   /* polls before a device dependency wait gives up with
                              STC_ERR_TIMEOUT; 0 = default (about 10 s)                 */
     double gate_rho_dense;   /* selector gates (Table 5); 0 = default 0.90 */

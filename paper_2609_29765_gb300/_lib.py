@@ -55,7 +55,7 @@ class StcError(RuntimeError):
 class stc_options(C.Structure):
     _fields_ = [("nb", C.c_int32), ("force_route", C.c_int32), ("ordering", C.c_int32),
                 ("nd_leaf", C.c_int32), ("perm", C.POINTER(C.c_int64)), ("row_slices", C.c_int32),
-                ("reserved0", C.c_int32), ("spin_limit", C.c_int64), ("gate_rho_dense", C.c_double),
+                ("host_threads", C.c_int32), ("spin_limit", C.c_int64), ("gate_rho_dense", C.c_double),
                 ("gate_phi_fill", C.c_double), ("gate_rho_semi", C.c_double),
                 ("gate_sigma_skew", C.c_double), ("queue_skew", C.c_double)]
 

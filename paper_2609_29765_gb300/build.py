@@ -57,7 +57,7 @@ def build(verbose: bool = False) -> str:
     for s in SOURCES_CPP:
         o = os.path.join(OUT, s + ".o")
         objs.append(o)
-        cmds.append(["g++", "-O2", "-std=c++17", "-fPIC", "-I", INC, "-c",
+        cmds.append(["g++", "-O2", "-std=c++17", "-fPIC", "-pthread", "-I", INC, "-c",
                      os.path.join(CSRC, s), "-o", o])
 
     def run(c):
@@ -71,7 +71,7 @@ def build(verbose: bool = False) -> str:
     with ThreadPoolExecutor(max_workers=len(cmds)) as ex:
         list(ex.map(run, cmds))
     tmp = LIB + ".tmp%d" % os.getpid()
-    run([nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"])
+    run([nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart", "-lpthread"])
     os.replace(tmp, LIB)
     return LIB
 

@@ -14,13 +14,16 @@
 // 1994, the pipeline cited in Sec. 5.4).
 #include <algorithm>
 #include <array>
+#include <atomic>
 #include <chrono>
 #include <climits>
 #include <cmath>
 #include <cstring>
+#include <exception>
 #include <new>
 #include <numeric>
 #include <limits>
+#include <thread>
 
 #include "plan.hpp"
 
@@ -32,6 +35,45 @@ using std::vector;
 namespace {
 
 constexpr int kMaxNb = 128;
+
+// Runs f(chunk, worker) for every chunk in [0, nchunks) on up to `threads` threads
+// (worker in [0, threads)); chunks are handed out in increasing order.  Every caller
+// writes each output element from exactly one chunk, so results do not depend on the
+// thread count.  An exception in a worker is rethrown here after all workers joined.
+template <class F>
+void parallel_chunks(int threads, int64_t nchunks, F&& f) {
+    const int nt = int(std::max<int64_t>(1, std::min<int64_t>(threads, nchunks)));
+    if (nt == 1) {
+        for (int64_t c = 0; c < nchunks; ++c) f(c, 0);
+        return;
+    }
+    std::atomic<int64_t> next{0};
+    std::atomic<bool> failed{false};
+    std::exception_ptr err;
+    std::mutex emu;
+    auto work = [&](int w) {
+        try {
+            for (int64_t c; !failed.load(std::memory_order_relaxed) && (c = next.fetch_add(1)) < nchunks;)
+                f(c, w);
+        } catch (...) {
+            std::lock_guard<std::mutex> g(emu);
+            if (!err) err = std::current_exception();
+            failed = true;
+        }
+    };
+    vector<std::thread> pool;
+    pool.reserve(nt - 1);
+    try {
+        for (int w = 1; w < nt; ++w) pool.emplace_back(work, w);
+    } catch (...) {
+        failed = true;  // could not start a thread: the started ones stop, then rethrow
+        for (auto& th : pool) th.join();
+        throw;
+    }
+    work(0);
+    for (auto& th : pool) th.join();
+    if (err) std::rethrow_exception(err);
+}
 
 int validate_pattern(int64_t n, const int64_t* Ap, const int64_t* Ai) {
     if (n <= 0 || !Ap || !Ai) return STC_ERR_INVALID_ARG;
@@ -220,39 +262,73 @@ void permuted_rows(int64_t n, const int64_t* Ap, const int64_t* Ai, const vector
         }
 }
 
-// Liu's elimination tree and the structure of L from row subtrees.
+// Liu's elimination tree and the structure of L from row subtrees.  The structure of row
+// i of L is the row subtree of i: the etree paths from the columns of row i of A up to i.
+// Rows are walked in chunks of consecutive rows, twice: once to count each chunk's
+// entries per column, once to write them, at offsets that put every column's rows in
+// ascending order (the chunks' counts are prefix-summed in chunk order).
 void symbolic(int64_t n, const vector<int64_t>& rp, const vector<int32_t>& rc,
-              vector<int64_t>& parent, vector<int64_t>& Lp, vector<int32_t>& Li) {
+              vector<int64_t>& parent, vector<int64_t>& Lp, stc::RowIndexVec& Li, int threads) {
     parent.assign(n, -1);
-    vector<int64_t> anc(n, -1);
-    for (int64_t i = 0; i < n; ++i)
-        for (int64_t p = rp[i]; p < rp[i + 1]; ++p) {
-            int64_t j = rc[p];
-            while (j != -1 && j < i) {
-                int64_t nxt = anc[j];
-                anc[j] = i;
-                if (nxt == -1) parent[j] = i;
-                j = nxt;
+    {
+        vector<int64_t> anc(n, -1);
+        for (int64_t i = 0; i < n; ++i)
+            for (int64_t p = rp[i]; p < rp[i + 1]; ++p) {
+                int64_t j = rc[p];
+                while (j != -1 && j < i) {
+                    int64_t nxt = anc[j];
+                    anc[j] = i;
+                    if (nxt == -1) parent[j] = i;
+                    j = nxt;
+                }
             }
-        }
-    // pass 1: column counts; pass 2: fill (rows arrive in ascending order)
-    vector<int64_t> mark(n, -1), cnt(n, 1);
-    for (int64_t i = 0; i < n; ++i) {
-        mark[i] = i;
-        for (int64_t p = rp[i]; p < rp[i + 1]; ++p)
-            for (int64_t j = rc[p]; mark[j] != i; j = parent[j]) { mark[j] = i; cnt[j]++; }
     }
+    const int64_t nch = std::max<int64_t>(1, std::min<int64_t>(int64_t(threads) * 8, n / 512));
+    const int nw = int(std::min<int64_t>(threads, nch));
+    // per chunk: (column, entries of the chunk's rows in it), then (column, first slot)
+    vector<vector<std::pair<int32_t, int64_t>>> touch(nch);
+    vector<vector<int32_t>> mark(nw);
+    vector<vector<int64_t>> acc(nw);
+    auto walk = [&](int64_t c, int w, bool fill) {
+        vector<int32_t>& mk = mark[w];
+        vector<int64_t>& ct = acc[w];
+        if (mk.empty()) { mk.assign(n, -1); ct.assign(n, 0); }
+        const int64_t i0 = c * n / nch, i1 = (c + 1) * n / nch;
+        vector<std::pair<int32_t, int64_t>>& tl = touch[c];
+        if (fill)
+            for (const auto& e : tl) ct[e.first] = e.second;
+        for (int64_t i = i0; i < i1; ++i) {
+            mk[i] = (int32_t)i;  // row ids differ between chunks: no reset within a walk
+            if (fill) Li[Lp[i]] = (int32_t)i;  // the diagonal heads column i
+            for (int64_t p = rp[i]; p < rp[i + 1]; ++p)
+                for (int64_t j = rc[p]; mk[j] != i; j = parent[j]) {
+                    mk[j] = (int32_t)i;
+                    if (fill) Li[ct[j]++] = (int32_t)i;
+                    else if (ct[j]++ == 0) tl.push_back({(int32_t)j, 0});
+                }
+        }
+        for (auto& e : tl) {
+            if (!fill) e.second = ct[e.first];
+            ct[e.first] = 0;
+        }
+    };
+    parallel_chunks(nw, nch, [&](int64_t c, int w) { walk(c, w, false); });
+    vector<int64_t> cnt(n, 1);  // the diagonal
+    for (const auto& tl : touch)
+        for (const auto& e : tl) cnt[e.first] += e.second;
     Lp.assign(n + 1, 0);
     for (int64_t j = 0; j < n; ++j) Lp[j + 1] = Lp[j] + cnt[j];
-    Li.assign(Lp[n], 0);
-    vector<int64_t> f(Lp.begin(), Lp.end() - 1);
-    std::fill(mark.begin(), mark.end(), -1);
-    for (int64_t i = 0; i < n; ++i) {
-        Li[f[i]++] = (int32_t)i;  // diagonal: the first entry of column i (rows < i never land here)
-        mark[i] = i;
-        for (int64_t p = rp[i]; p < rp[i + 1]; ++p)
-            for (int64_t j = rc[p]; mark[j] != i; j = parent[j]) { mark[j] = i; Li[f[j]++] = (int32_t)i; }
-    }
+    for (int64_t j = 0; j < n; ++j) cnt[j] = Lp[j] + 1;  // next free slot below the diagonal
+    for (auto& tl : touch)
+        for (auto& e : tl) {
+            const int64_t start = cnt[e.first];
+            cnt[e.first] += e.second;
+            e.second = start;
+        }
+    Li.clear();
+    Li.resize(Lp[n]);  // uninitialised: the second walk writes every entry
+    for (auto& mk : mark) std::fill(mk.begin(), mk.end(), -1);  // the second walk marks again
+    parallel_chunks(nw, nch, [&](int64_t c, int w) { walk(c, w, true); });
 }
 
 }  // namespace
@@ -279,12 +355,8 @@ int stored_col(const stc_plan& P, const stc::DTile& t, int lc) {
     return (e != a + t.sw && *e == lc) ? int(e - a) : -1;
 }
 
-int64_t entry_offset(const stc_plan& P, int64_t r, int64_t c) {  // r >= c, permuted
+int64_t tile_entry_offset(const stc_plan& P, const stc::DTile& T, int lr, int lc) {
     const int64_t nb = P.nb;
-    int t = P.tile_id(r / nb, c / nb);
-    if (t < 0) return -1;
-    const stc::DTile& T = P.tiles[t];
-    int lr = int(r % nb), lc = int(c % nb);
     if (T.kind == stc::TILE_DIAG_DENSE) return T.off + lr + (int64_t)lc * nb;
     if (T.kind == stc::TILE_DIAG_BAND) {
         if (lr - lc > T.kd) return -1;
@@ -295,114 +367,171 @@ int64_t entry_offset(const stc_plan& P, int64_t r, int64_t c) {  // r >= c, perm
     return T.off + lr + (int64_t)s * nb;
 }
 
-int build_tiles(stc_plan& P) {
-    const int64_t n = P.n, nb = P.nb, nt = P.nt;
+int64_t entry_offset(const stc_plan& P, int64_t r, int64_t c) {  // r >= c, permuted
+    const int64_t nb = P.nb;
+    int t = P.tile_id(r / nb, c / nb);
+    if (t < 0) return -1;
+    return tile_entry_offset(P, P.tiles[t], int(r % nb), int(c % nb));
+}
+
+// The tiles of one block column, with offsets into the column's own lists; build_tiles
+// merges the columns in order.
+struct ColTiles {
+    vector<stc::DTile> tiles;   // aoff / xoff relative to this column's saind / cext
+    vector<int64_t> size;       // stored doubles of each tile
+    vector<int32_t> nact;
+    vector<int64_t> aoff;       // offset of each tile's active columns in `aind`
+    vector<int16_t> aind, saind, cext;
+    vector<int8_t> contig, full;
+};
+
+struct TileScratch {            // per worker
+    struct Acc { uint64_t m[2]; int r0, r1, kd; int32_t ext; };
+    vector<int32_t> slot;
+    vector<int64_t> touched;
+    vector<int16_t> clo, chi;   // per tile of the column: row extent of each column
+    vector<Acc> acc;
+    vector<int16_t> cols;
+};
+
+void build_block_column(const stc_plan& P, int64_t J, bool dense, TileScratch& S, ColTiles& out) {
+    const int64_t n = P.n, nb = P.nb;
+    if (S.slot.empty()) S.slot.assign(P.nt, -1);
+    S.touched.clear();
+    S.acc.clear();
+    S.clo.clear();
+    S.chi.clear();
+    const int64_t c0 = J * nb, c1 = std::min(n, (J + 1) * nb);
+    for (int64_t j = c0; j < c1; ++j)
+        for (int64_t q = P.Lp[j]; q < P.Lp[j + 1]; ++q) {
+            int64_t i = P.Li[q], I = i / nb;
+            if (S.slot[I] < 0) {
+                S.slot[I] = (int32_t)S.acc.size();
+                S.acc.push_back(TileScratch::Acc{{0, 0}, INT_MAX, -1, -1, (int32_t)S.clo.size()});
+                S.clo.resize(S.clo.size() + nb, (int16_t)nb);
+                S.chi.resize(S.chi.size() + nb, 0);
+                S.touched.push_back(I);
+            }
+            TileScratch::Acc& a = S.acc[S.slot[I]];
+            int lr = int(i - I * nb), lc = int(j - c0);
+            a.m[lc >> 6] |= 1ull << (lc & 63);
+            a.r0 = std::min(a.r0, lr);
+            a.r1 = std::max(a.r1, lr + 1);
+            S.clo[a.ext + lc] = (int16_t)std::min<int>(S.clo[a.ext + lc], lr);
+            S.chi[a.ext + lc] = (int16_t)std::max<int>(S.chi[a.ext + lc], lr + 1);
+            if (I == J) a.kd = std::max(a.kd, lr - lc);
+        }
+    std::sort(S.touched.begin(), S.touched.end());
+    for (int64_t I : S.touched) {
+        const TileScratch::Acc& a = S.acc[S.slot[I]];
+        S.slot[I] = -1;
+        stc::DTile t{};
+        t.I = (int32_t)I; t.J = (int32_t)J;
+        vector<int16_t>& cols = S.cols;
+        cols.clear();
+        for (int c = 0; c < nb; ++c)
+            if (a.m[c >> 6] >> (c & 63) & 1) cols.push_back((int16_t)c);
+        const int cnt = (int)cols.size();
+        const bool contiguous = cols.back() - cols.front() + 1 == cnt;
+        out.nact.push_back(cnt);
+        out.aoff.push_back((int64_t)out.aind.size());
+        out.aind.insert(out.aind.end(), cols.begin(), cols.end());
+        out.contig.push_back(contiguous);
+        out.full.push_back(cnt == nb);
+        t.pd_slot = -1;
+        t.aoff = -1;
+        t.xoff = -1;
+        int64_t size;
+        if (I == J) {
+            t.sw = int(c1 - c0);
+            t.c0 = 0;
+            t.r0 = 0; t.r1 = int(nb);
+            if (dense) {
+                t.kind = stc::TILE_DIAG_DENSE;
+                t.kd = int(nb - 1);
+                size = nb * nb;
+            } else {
+                t.kind = stc::TILE_DIAG_BAND;
+                t.kd = std::max(a.kd, 0);
+                size = (int64_t)(t.kd + 1) * nb;
+            }
+            t.pd_slot = (int32_t)J;
+        } else {
+            t.kind = stc::TILE_OFF;
+            t.kd = -1;
+            if (dense) {
+                t.sw = int(nb); t.c0 = 0; t.r0 = 0; t.r1 = int(nb);
+            } else {
+                t.sw = cnt;
+                t.r0 = a.r0; t.r1 = a.r1;
+                if (contiguous) {
+                    t.c0 = cols.front();
+                } else {
+                    t.c0 = -1;
+                    t.aoff = (int32_t)out.saind.size();
+                    out.saind.insert(out.saind.end(), cols.begin(), cols.end());
+                }
+            }
+            size = (int64_t)t.sw * nb;
+            // row extents of each kExtW stored columns (dense route: all n_b columns)
+            t.xoff = (int32_t)(out.cext.size() / 2);
+            for (int s0 = 0; s0 < t.sw; s0 += stc::kExtW) {
+                int lo = int(nb), hi = 0;
+                for (int s = s0; s < std::min(t.sw, s0 + stc::kExtW); ++s) {
+                    const int lc = dense ? s : cols[s];
+                    lo = std::min<int>(lo, S.clo[a.ext + lc]);
+                    hi = std::max<int>(hi, S.chi[a.ext + lc]);
+                }
+                out.cext.push_back((int16_t)lo);
+                out.cext.push_back((int16_t)hi);
+            }
+        }
+        t.nfinal = 1;
+        out.tiles.push_back(t);
+        out.size.push_back(size);
+    }
+}
+
+// Tile map of L (Sec. 4): block columns are built in parallel, then laid out in order
+// (block-column-major, I ascending, 32-byte aligned tiles).
+int build_tiles(stc_plan& P, int threads) {
+    const int64_t nt = P.nt;
     const bool dense = P.route_exec == STC_ROUTE_DENSE;
     P.colstart.assign(nt + 1, 0);
     P.diag_tile.assign(nt, -1);
-    vector<int32_t> slot(nt, -1);
-    vector<int64_t> touched;
-    struct Acc { uint64_t m[2]; int r0, r1, kd; int32_t ext; };
-    vector<int16_t> clo, chi;  // per tile slot of this block column: column row extents
-    vector<Acc> acc;
+    vector<ColTiles> col(nt);
+    const int nw = int(std::max<int64_t>(1, std::min<int64_t>(threads, nt)));
+    vector<TileScratch> scratch(nw);
+    const int64_t per = std::max<int64_t>(1, nt / (int64_t(nw) * 16));  // block columns per chunk
+    parallel_chunks(nw, (nt + per - 1) / per, [&](int64_t c, int w) {
+        for (int64_t J = c * per; J < std::min(nt, (c + 1) * per); ++J)
+            build_block_column(P, J, dense, scratch[w], col[J]);
+    });
+    scratch.clear();
     int64_t off = 0;
     for (int64_t J = 0; J < nt; ++J) {
+        ColTiles& C = col[J];
         P.colstart[J] = (int32_t)P.tiles.size();
-        touched.clear();
-        acc.clear();
-        clo.clear();
-        chi.clear();
-        const int64_t c0 = J * nb, c1 = std::min(n, (J + 1) * nb);
-        for (int64_t j = c0; j < c1; ++j)
-            for (int64_t q = P.Lp[j]; q < P.Lp[j + 1]; ++q) {
-                int64_t i = P.Li[q], I = i / nb;
-                if (slot[I] < 0) {
-                    slot[I] = (int32_t)acc.size();
-                    acc.push_back(Acc{{0, 0}, INT_MAX, -1, -1, (int32_t)clo.size()});
-                    clo.resize(clo.size() + nb, (int16_t)nb);
-                    chi.resize(chi.size() + nb, 0);
-                    touched.push_back(I);
-                }
-                Acc& a = acc[slot[I]];
-                int lr = int(i - I * nb), lc = int(j - c0);
-                a.m[lc >> 6] |= 1ull << (lc & 63);
-                a.r0 = std::min(a.r0, lr);
-                a.r1 = std::max(a.r1, lr + 1);
-                clo[a.ext + lc] = (int16_t)std::min<int>(clo[a.ext + lc], lr);
-                chi[a.ext + lc] = (int16_t)std::max<int>(chi[a.ext + lc], lr + 1);
-                if (I == J) a.kd = std::max(a.kd, lr - lc);
-            }
-        std::sort(touched.begin(), touched.end());
-        for (int64_t I : touched) {
-            const Acc& a = acc[slot[I]];
-            slot[I] = -1;
-            stc::DTile t{};
-            t.I = (int32_t)I; t.J = (int32_t)J;
-            vector<int16_t> cols;
-            for (int c = 0; c < nb; ++c)
-                if (a.m[c >> 6] >> (c & 63) & 1) cols.push_back((int16_t)c);
-            const int cnt = (int)cols.size();
-            const bool contiguous = cols.back() - cols.front() + 1 == cnt;
-            P.nact.push_back(cnt);
-            P.aoff_struct.push_back((int64_t)P.aind_struct.size());
-            P.aind_struct.insert(P.aind_struct.end(), cols.begin(), cols.end());
-            P.contig.push_back(contiguous);
-            P.full.push_back(cnt == nb);
-            t.pd_slot = -1;
-            t.aoff = -1;
-            t.xoff = -1;
-            int64_t size;
-            if (I == J) {
-                t.sw = int(c1 - c0);
-                t.c0 = 0;
-                t.r0 = 0; t.r1 = int(nb);
-                if (dense) {
-                    t.kind = stc::TILE_DIAG_DENSE;
-                    t.kd = int(nb - 1);
-                    size = nb * nb;
-                } else {
-                    t.kind = stc::TILE_DIAG_BAND;
-                    t.kd = std::max(a.kd, 0);
-                    size = (int64_t)(t.kd + 1) * nb;
-                }
-                t.pd_slot = (int32_t)J;
-                P.diag_tile[J] = (int32_t)P.tiles.size();
-            } else {
-                t.kind = stc::TILE_OFF;
-                t.kd = -1;
-                if (dense) {
-                    t.sw = int(nb); t.c0 = 0; t.r0 = 0; t.r1 = int(nb);
-                } else {
-                    t.sw = cnt;
-                    t.r0 = a.r0; t.r1 = a.r1;
-                    if (contiguous) {
-                        t.c0 = cols.front();
-                    } else {
-                        t.c0 = -1;
-                        t.aoff = (int32_t)P.saind.size();
-                        P.saind.insert(P.saind.end(), cols.begin(), cols.end());
-                    }
-                }
-                size = (int64_t)t.sw * nb;
-                // row extents of each kExtW stored columns (dense route: all n_b columns)
-                t.xoff = (int32_t)(P.cext.size() / 2);
-                for (int s0 = 0; s0 < t.sw; s0 += stc::kExtW) {
-                    int lo = int(nb), hi = 0;
-                    for (int s = s0; s < std::min(t.sw, s0 + stc::kExtW); ++s) {
-                        const int lc = dense ? s : cols[s];
-                        lo = std::min<int>(lo, clo[a.ext + lc]);
-                        hi = std::max<int>(hi, chi[a.ext + lc]);
-                    }
-                    P.cext.push_back((int16_t)lo);
-                    P.cext.push_back((int16_t)hi);
-                }
-            }
+        const int32_t sbase = (int32_t)P.saind.size(), xbase = (int32_t)(P.cext.size() / 2);
+        const int64_t abase = (int64_t)P.aind_struct.size();
+        for (size_t k = 0; k < C.tiles.size(); ++k) {
+            stc::DTile t = C.tiles[k];
+            if (t.aoff >= 0) t.aoff += sbase;
+            if (t.xoff >= 0) t.xoff += xbase;
+            if (t.I == t.J) P.diag_tile[J] = (int32_t)P.tiles.size();
             t.off = off;
-            off += (size + 3) / 4 * 4;  // 32-byte aligned tiles
-            P.stored_entries += size;
-            t.nfinal = 1;
+            off += (C.size[k] + 3) / 4 * 4;  // 32-byte aligned tiles
+            P.stored_entries += C.size[k];
+            P.aoff_struct.push_back(abase + C.aoff[k]);
             P.tiles.push_back(t);
         }
+        P.nact.insert(P.nact.end(), C.nact.begin(), C.nact.end());
+        P.aind_struct.insert(P.aind_struct.end(), C.aind.begin(), C.aind.end());
+        P.contig.insert(P.contig.end(), C.contig.begin(), C.contig.end());
+        P.full.insert(P.full.end(), C.full.begin(), C.full.end());
+        P.saind.insert(P.saind.end(), C.saind.begin(), C.saind.end());
+        P.cext.insert(P.cext.end(), C.cext.begin(), C.cext.end());
+        C = ColTiles();  // release the column's lists
     }
     P.colstart[nt] = (int32_t)P.tiles.size();
     P.partial_off = off;
@@ -883,6 +1012,10 @@ static int analyze_impl(int64_t n, const int64_t* Ap, const int64_t* Ai, const d
     if (opt.gate_rho_semi == 0) opt.gate_rho_semi = 0.15;
     if (opt.gate_sigma_skew == 0) opt.gate_sigma_skew = 20.0;
 
+    int threads = opt.host_threads;
+    if (threads <= 0) threads = int(std::min<unsigned>(32, std::max<unsigned>(1, std::thread::hardware_concurrency())));
+    threads = std::min(threads, 256);
+
     auto P = std::make_unique<stc_plan>();
     P->n = n; P->nb = opt.nb; P->nt = (n + opt.nb - 1) / opt.nb; P->nnzA = Ap[n];
     P->opt = opt;
@@ -918,15 +1051,15 @@ static int analyze_impl(int64_t n, const int64_t* Ap, const int64_t* Ai, const d
     vector<int64_t> rp;
     vector<int32_t> rcv;
     permuted_rows(n, Ap, Ai, iperm, rp, rcv);
-    symbolic(n, rp, rcv, P->parent, P->Lp, P->Li);
+    symbolic(n, rp, rcv, P->parent, P->Lp, P->Li, threads);
     if (ord == STC_ORDER_AUTO) ord = STC_ORDER_RCM;
     // AUTO without coordinates: keep the natural order when RCM does not reduce the fill
     if (opt.ordering == STC_ORDER_AUTO && !coords) {
         vector<int64_t> idp(n), par2, Lp2;
-        vector<int32_t> Li2;
+        stc::RowIndexVec Li2;
         std::iota(idp.begin(), idp.end(), 0);
         permuted_rows(n, Ap, Ai, idp, rp, rcv);
-        symbolic(n, rp, rcv, par2, Lp2, Li2);
+        symbolic(n, rp, rcv, par2, Lp2, Li2, threads);
         if (Lp2[n] <= P->Lp[n]) {
             P->perm = idp; iperm = idp; P->parent.swap(par2); P->Lp.swap(Lp2); P->Li.swap(Li2);
             ord = STC_ORDER_NATURAL;
@@ -941,7 +1074,7 @@ static int analyze_impl(int64_t n, const int64_t* Ap, const int64_t* Ai, const d
 
     // ---- features and selector (Sec. 5.1): computed on the structural tile map ----
     P->route_exec = STC_ROUTE_SEMISPARSE;
-    rc = build_tiles(*P);  // structural pass (semisparse storage)
+    rc = build_tiles(*P, threads);  // structural pass (semisparse storage)
     if (rc) return rc;
     {
         double sum = 0; int64_t cnt = 0;
@@ -965,33 +1098,57 @@ static int analyze_impl(int64_t n, const int64_t* Ap, const int64_t* Ai, const d
     if (P->route_exec == STC_ROUTE_DENSE) {  // rebuild storage as full tiles
         P->tiles.clear(); P->nact.clear(); P->aoff_struct.clear(); P->aind_struct.clear();
         P->contig.clear(); P->full.clear(); P->saind.clear(); P->stored_entries = 0;
-        rc = build_tiles(*P);
+        rc = build_tiles(*P, threads);
         if (rc) return rc;
     }
     build_alg1(*P);
 
     // ---- value map (a1), padding identity, CSC map of L ----
+    // columns of A (and of L below) in chunks of kColChunk, each chunk's entries written once
+    constexpr int64_t kColChunk = 2048;
+    const int64_t ncc = (n + kColChunk - 1) / kColChunk;
+    std::atomic<bool> unmapped{false};
     P->value_map.resize(P->nnzA);
-    for (int64_t j = 0; j < n; ++j)
-        for (int64_t p = Ap[j]; p < Ap[j + 1]; ++p) {
-            int64_t a = iperm[Ai[p]], b = iperm[j];
-            int64_t off = entry_offset(*P, std::max(a, b), std::min(a, b));
-            if (off < 0) return STC_ERR_INVALID_PATTERN;
-            P->value_map[p] = off;
-        }
+    P->vdiag.resize(P->nnzA);
+    P->arow.resize(P->nnzA);
+    P->acol.resize(P->nnzA);
+    parallel_chunks(threads, ncc, [&](int64_t c, int) {
+        for (int64_t j = c * kColChunk; j < std::min(n, (c + 1) * kColChunk); ++j)
+            for (int64_t p = Ap[j]; p < Ap[j + 1]; ++p) {
+                int64_t a = iperm[Ai[p]], b = iperm[j];
+                int64_t off = entry_offset(*P, std::max(a, b), std::min(a, b));
+                if (off < 0) unmapped = true;
+                P->value_map[p] = off;
+                P->vdiag[p] = Ai[p] == j;
+                P->arow[p] = (int32_t)Ai[p];
+                P->acol[p] = (int32_t)j;
+            }
+    });
+    if (unmapped) return STC_ERR_INVALID_PATTERN;
     {
         const stc::DTile& D = P->tiles[P->diag_tile[P->nt - 1]];
         for (int64_t r = D.sw; r < P->nb; ++r)
             P->pad_diag.push_back(D.kind == stc::TILE_DIAG_BAND ? D.off + D.kd + r * (D.kd + 1)
                                                                  : D.off + r + r * P->nb);
     }
+    // rows of a column ascend, so its tiles are met in order: a cursor replaces the lookup
     P->csc_map.resize(P->Lp[n]);
-    for (int64_t j = 0; j < n; ++j)
-        for (int64_t q = P->Lp[j]; q < P->Lp[j + 1]; ++q) {
-            int64_t off = entry_offset(*P, P->Li[q], j);
-            if (off < 0) return STC_ERR_INVALID_PATTERN;
-            P->csc_map[q] = off;
+    parallel_chunks(threads, P->nt, [&](int64_t J, int) {
+        const int32_t tend = P->colstart[J + 1];
+        for (int64_t j = J * P->nb; j < std::min(n, (J + 1) * P->nb); ++j) {
+            int32_t t = P->colstart[J];
+            for (int64_t q = P->Lp[j]; q < P->Lp[j + 1]; ++q) {
+                const int64_t r = P->Li[q], I = r / P->nb;
+                while (t < tend && P->tiles[t].I < I) ++t;
+                int64_t off = -1;
+                if (t < tend && P->tiles[t].I == I)
+                    off = tile_entry_offset(*P, P->tiles[t], int(r - I * P->nb), int(j - J * P->nb));
+                if (off < 0) unmapped = true;
+                P->csc_map[q] = off;
+            }
         }
+    });
+    if (unmapped) return STC_ERR_INVALID_PATTERN;
     // ---- selected inverse: stored-index lookup, tasks in reverse block-column order ----
     P->sinv.assign(P->tiles.size() * (size_t)P->nb, (int16_t)-1);
     for (size_t t = 0; t < P->tiles.size(); ++t) {
@@ -1038,15 +1195,6 @@ static int analyze_impl(int64_t n, const int64_t* Ap, const int64_t* Ai, const d
         d.cend = (int32_t)P->scons.size();
         P->stasks.push_back(d);
     }
-    P->vdiag.resize(P->nnzA);
-    P->arow.resize(P->nnzA);
-    P->acol.resize(P->nnzA);
-    for (int64_t j = 0; j < n; ++j)
-        for (int64_t p = Ap[j]; p < Ap[j + 1]; ++p) {
-            P->vdiag[p] = Ai[p] == j;
-            P->arow[p] = (int32_t)Ai[p];
-            P->acol[p] = (int32_t)j;
-        }
     stc::TaskSet* ts = P->taskset(1);
     P->flops_tile = 2.0 * ts->fma_exec;
     P->analyze_seconds =

@@ -5,11 +5,30 @@
 #include <map>
 #include <memory>
 #include <mutex>
+#include <new>
+#include <type_traits>
+#include <utility>
 #include <vector>
 
 #include "stc.h"
 
 namespace stc {
+
+// Allocator that leaves elements uninitialised on a value-less resize: for large index
+// arrays that are written in full, in parallel, right after they are sized.
+template <class T>
+struct UninitAlloc : std::allocator<T> {
+    template <class U> struct rebind { using other = UninitAlloc<U>; };
+    UninitAlloc() = default;
+    template <class U> UninitAlloc(const UninitAlloc<U>&) noexcept {}
+    template <class U> void construct(U* p) noexcept(std::is_nothrow_default_constructible<U>::value) {
+        ::new (static_cast<void*>(p)) U;
+    }
+    template <class U, class... A> void construct(U* p, A&&... a) {
+        ::new (static_cast<void*>(p)) U(std::forward<A>(a)...);
+    }
+};
+using RowIndexVec = std::vector<int32_t, UninitAlloc<int32_t>>;
 
 // ---------------------------------------------------------------------------
 // Device-side descriptors (plain old data, uploaded as arrays).
@@ -168,7 +187,7 @@ struct stc_plan {
     std::vector<int64_t> perm;     // perm[k] = original index of pivot k
     std::vector<int64_t> parent;   // elimination tree of the permuted matrix
     std::vector<int64_t> Lp;       // symbolic structure of L (permuted), CSC
-    std::vector<int32_t> Li;
+    stc::RowIndexVec Li;
     // tiles (block-column-major: J ascending, I ascending)
     std::vector<stc::DTile> tiles;
     std::vector<int32_t> nact;         // |A| (structural active columns)

@@ -298,3 +298,30 @@ def test_random_patterns_symbolic_and_extents_vs_oracle(seed):
     assert np.array_equal(P.export("aind"), t["aind"])
     assert np.array_equal(P.export("tasks"), t["tasks"])
     assert np.array_equal(P.export("chunk_extents"), _chunk_extents_brute(F, t, nb, n, route == "dense"))
+
+
+def _plan_exports(P):
+    names = ["perm", "etree", "Lp", "Li", "tiles", "aind", "tasks", "value_map", "tile_offsets",
+             "chunk_extents"]
+    return {k: P.export(k) for k in names}
+
+
+@pytest.mark.parametrize("case", ["fem", "band", "random"])
+def test_plan_independent_of_host_threads(case):
+    # the analysis runs its symbolic factorization, tile map and maps on several host
+    # threads; every output must be the same for any thread count
+    if case == "fem":
+        Ap, Ai, Ax, coords = I.fem3d(16, 16, 16)
+        kw = dict(coords=coords, nb=32, route="dense")
+    elif case == "band":
+        Ap, Ai = I.band_pattern(6000, 40)
+        coords, kw = None, dict(nb=64, ordering="natural")
+    else:
+        Ap, Ai, _ = I.random_spd(5000, 0.0008, 11)
+        coords, kw = None, dict(nb=48, ordering="rcm")
+    n = len(Ap) - 1
+    ref = _plan_exports(Plan(n, Ap, Ai, host_threads=1, **kw))
+    for t in (2, 3, 8):
+        got = _plan_exports(Plan(n, Ap, Ai, host_threads=t, **kw))
+        for k in ref:
+            assert np.array_equal(got[k], ref[k]), (t, k)
