@@ -7,15 +7,15 @@
  *   analyze   -- once per sparsity pattern, on the host (Sec. 3 ordering and symbolic
  *                factorization; Sec. 5.1 selector; Sec. 5.2 per-tile metadata, task list
  *                of Algorithm 1 and per-task scatter maps).  The interface splits a
- *                once-per-pattern analyze from a repeated factorize (Sec. 6.7).
+ *                once-per-pattern analyze from a repeated factorize (Sec. 6.6).
  *   factorize -- per call, on the GPU: replay of the POTRF / SYRK / TRSM / GEMM tile
  *                tasks (Algorithm 1 executed as in Algorithm 2, with device-side
  *                dependency counters in place of the progress matrix P, Sec. 5.3) on
  *                dense tiles and on active-column tiles (Sec. 4).
  *   logdet, solve -- consume the factor where it sits (Sec. 5.4 log-determinant reuse;
- *                Sec. 6.8 solves).
+ *                Sec. 6.7 solves).
  *   logdet_backward / quad_backward -- adjoints; no counterpart in the paper (it leaves
- *                selected inversion to separate work, Sec. 6.3): Takahashi selected
+ *                selected inversion to separate work, Sec. 6.2): Takahashi selected
  *                inverse on the same tile map.
  *
  * Conventions (every entry point):
@@ -233,7 +233,7 @@ int stc_factor_to_csc(const stc_plan* plan, const void* d_factor, int64_t batch,
 
 /* Selected inverse Sigma = (P A P^T)^{-1} on every stored entry of the tile storage
  * (no counterpart in the paper, which leaves selected inversion to separate work,
- * Sec. 6.3: Takahashi's recurrence on the same tile map, walked in reverse block-column
+ * Sec. 6.2: Takahashi's recurrence on the same tile map, walked in reverse block-column
  * order by one persistent kernel).  Sigma is exact on the structural entries of L;
  * stored entries the symbolic factor proves zero hold unspecified finite values.
  *   d_factor: a factor from stc_factorize; d_sigma: stc_factor_bytes(plan,batch) bytes

@@ -11,10 +11,10 @@ What it computes, with the paper's section for each step:
   column structure of L (Sec. 3 symbolic factorization; Sec. 5.4 symbolic pipeline).
 * ``.factor(Ax)``   -- left-looking column Cholesky, FP64 (exact factorization; Sec. 5.2
   at column granularity).
-* ``.logdet / .solve`` -- 2 sum log L_jj; x = P^T L^-T L^-1 P b (Sec. 6.8).
+* ``.logdet / .solve`` -- 2 sum log L_jj; x = P^T L^-T L^-1 P b (Sec. 6.7).
 * ``.selinv / .grad_logdet`` -- Takahashi selected inverse and d logdet/d a_ij
   = (2 - delta_ij) Sigma_ij (not in the paper: it leaves selected inversion to separate
-  work, Sec. 6.3; textbook recurrence).
+  work, Sec. 6.2; textbook recurrence).
 * ``.tile_map(nb) / .task_list(nb)`` -- Sec. 4 active-column tiles and Algorithm 1.
 * ``features / select_route`` -- phi, rho, sigma and the selector of Sec. 5.1, with the
   precedence dense (rho>=0.90) > supernodal (phi>2.0) > semisparse (rho>=0.15 or

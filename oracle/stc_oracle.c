@@ -23,13 +23,13 @@
  *                      x -= L[j:,k] L_jk for each k<j with L_jk != 0, ascending;
  *                      L_jj = sqrt(x_0), L[j+1:,j] = x[1:]/L_jj.
  *   orc_logdet         2 * sum_j log L_jj  (log-determinant reused from the factor,
- *                      Sec. 5.4 and Sec. 6.8).
- *   orc_solve          x = P^T L^-T L^-1 P b  (solves consume the factor, Sec. 6.8).
+ *                      Sec. 5.4 and Sec. 6.7).
+ *   orc_solve          x = P^T L^-T L^-1 P b  (solves consume the factor, Sec. 6.7).
  *   orc_selinv         Takahashi recurrence for Sigma = A_p^{-1} on pattern(L):
  *                      Sigma_ij = delta_ij/L_jj^2 - (1/L_jj) sum_{k in struct(L_:j),k>j}
  *                                 L_kj Sigma_ik,   j = n-1..0.
  *                      (The paper leaves selected inversion to separate work,
- *                      Sec. 6.3; this is the textbook recurrence, Takahashi 1973.)
+ *                      Sec. 6.2; this is the textbook recurrence, Takahashi 1973.)
  *   orc_grad_logdet    d logdet / d a_ij = (2 - delta_ij) Sigma_ij on the lower CSC
  *                      entries of the ORIGINAL matrix.
  *   orc_tile_map       uniform n_b grid over L (Sec. 4): active tiles, active-column
