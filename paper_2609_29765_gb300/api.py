@@ -58,11 +58,11 @@ class Plan:
             L.stc_plan_destroy(self.h)
             self.h = None
 
-    property
+    @property
     def route(self) -> str:
         return ROUTE_NAMES[self.info["route_executed"]]
 
-    property
+    @property
     def route_selected(self) -> str:
         return ROUTE_NAMES[self.info["route_selected"]]
 
@@ -287,13 +287,13 @@ def _autograd():
     class LogdetFn(torch.autograd.Function):
         """logdet(A_b) for values [batch, nnzA]; backward = selected inverse."""
 
-        staticmethod
+        @staticmethod
         def forward(ctx, values, plan):
             fac = plan.factorize(values.detach())
             ctx.plan, ctx.fac = plan, fac
             return fac.logdet()
 
-        staticmethod
+        @staticmethod
         def backward(ctx, gout):
             g = ctx.fac.logdet_backward(gout.contiguous())
             return g, None
@@ -301,7 +301,7 @@ def _autograd():
     class QuadFn(torch.autograd.Function):
         """x_b^T A_b x_b; gradients for the values and for x."""
 
-        staticmethod
+        @staticmethod
         def forward(ctx, values, x, plan):
             values = values.detach().contiguous()
             x = x.detach().contiguous()
@@ -311,7 +311,7 @@ def _autograd():
             ctx.plan = plan
             return out
 
-        staticmethod
+        @staticmethod
         def backward(ctx, gout):
             values, x = ctx.saved_tensors
             plan = ctx.plan
@@ -329,7 +329,7 @@ def _autograd():
     class SolveFn(torch.autograd.Function):
         """x = A_b^{-1} b_b; backward: g_b = A^{-1} g_x, g_A = -(2-delta)/2 (x_i g_j + x_j g_i)."""
 
-        staticmethod
+        @staticmethod
         def forward(ctx, values, b, plan):
             fac = plan.factorize(values.detach())
             x = fac.solve(b.detach().contiguous())
@@ -337,7 +337,7 @@ def _autograd():
             ctx.save_for_backward(x)
             return x
 
-        staticmethod
+        @staticmethod
         def backward(ctx, gx):
             (x,) = ctx.saved_tensors
             g = ctx.fac.solve(gx.contiguous())
