@@ -284,7 +284,9 @@ void symbolic(int64_t n, const vector<int64_t>& rp, const vector<int32_t>& rc,
             }
     }
     const int64_t nch = std::max<int64_t>(1, std::min<int64_t>(int64_t(threads) * 8, n / 512));
-    const int nw = int(std::min<int64_t>(threads, nch));
+    // each worker holds 12 n bytes of scratch: at most ~1 GiB in total
+    const int64_t mem_cap = std::max<int64_t>(1, (int64_t(1) << 30) / (12 * n));
+    const int nw = int(std::min<int64_t>(std::min<int64_t>(threads, nch), mem_cap));
     // per chunk: (column, entries of the chunk's rows in it), then (column, first slot)
     vector<vector<std::pair<int32_t, int64_t>>> touch(nch);
     vector<vector<int32_t>> mark(nw);
