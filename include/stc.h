@@ -135,6 +135,26 @@ typedef struct stc_plan_info {
                                      past the stored width and for diagonal tiles.  The
                                      tile products skip rows outside these extents (the
                                      paper computes on full-height columns, Sec. 4.1). */
+/* The non-uniform supernodal tiling of Sec. 5.4 (host plan; built on first request from
+ * the plan's ordering and symbolic factor; the numeric phase still runs on the tile
+ * routes).  Fundamental supernodes, relaxed by amalgamation along contiguous etree
+ * links (width <= 4 always; <= 16 / <= 48 / wider while explicit zeros stay below
+ * 80 % / 10 % / 5 % of the panel's lower trapezoid; merged width <= 128), wider
+ * supernodes cut into 128-column panels. */
+#define STC_EXPORT_SN_NODES 10  /* [nsn][4]: first column, width, rows, panel offset in a
+                                   per-item arena (doubles; rows x width column-major) */
+#define STC_EXPORT_SN_ROWS 11   /* concatenated row lists (permuted indices): each
+                                   supernode's own columns, then the rows below, ascending */
+#define STC_EXPORT_SN_CELLS 12  /* [ncells][4]: column supernode I, row supernode J, and
+                                   the run [r0, r1) of I's row list that J owns; the
+                                   diagonal cell (I, I, 0, width) first for each I       */
+#define STC_EXPORT_SN_TASKS 13  /* [ntasks][4], left-looking order (for each supernode J:
+                                   its updates, its factor, its TRSMs):
+                                   (0, diagonal cell of J, -1, -1)  FACTOR (POTRF)
+                                   (1, cell (K,J), -1, -1)          TRSM against J's factor
+                                   (2, cell (K,J), cell (K,I), cell (J,I))
+                                                                    UPDATE L_KJ -= L_KI L_JI^T,
+                                   rows and columns placed by sorted-subset scatter    */
 
 /* Fill *opt with defaults (nb 128, auto route, auto ordering, ND leaf 64). */
 void stc_options_default(stc_options* opt);

@@ -27,7 +27,8 @@ STC_ERR_BUFFER_TOO_SMALL = -7
 STC_ROUTE_AUTO, STC_ROUTE_DENSE, STC_ROUTE_SEMISPARSE, STC_ROUTE_SUPERNODAL = -1, 0, 1, 2
 STC_ORDER_AUTO, STC_ORDER_NATURAL, STC_ORDER_GIVEN, STC_ORDER_ND, STC_ORDER_RCM = 0, 1, 2, 3, 4
 (STC_EXPORT_PERM, STC_EXPORT_ETREE, STC_EXPORT_LP, STC_EXPORT_LI, STC_EXPORT_TILES, STC_EXPORT_AIND,
- STC_EXPORT_TASKS, STC_EXPORT_VALUE_MAP, STC_EXPORT_TILE_OFFSETS, STC_EXPORT_CHUNK_EXTENTS) = range(10)
+ STC_EXPORT_TASKS, STC_EXPORT_VALUE_MAP, STC_EXPORT_TILE_OFFSETS, STC_EXPORT_CHUNK_EXTENTS,
+ STC_EXPORT_SN_NODES, STC_EXPORT_SN_ROWS, STC_EXPORT_SN_CELLS, STC_EXPORT_SN_TASKS) = range(14)
 
 # every symbol include/stc.h declares
 EXPORTED = [

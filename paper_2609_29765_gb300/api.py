@@ -70,13 +70,15 @@ class Plan:
         code = {"perm": L.STC_EXPORT_PERM, "etree": L.STC_EXPORT_ETREE, "Lp": L.STC_EXPORT_LP,
                 "Li": L.STC_EXPORT_LI, "tiles": L.STC_EXPORT_TILES, "aind": L.STC_EXPORT_AIND,
                 "tasks": L.STC_EXPORT_TASKS, "value_map": L.STC_EXPORT_VALUE_MAP,
-                "tile_offsets": L.STC_EXPORT_TILE_OFFSETS, "chunk_extents": L.STC_EXPORT_CHUNK_EXTENTS}[what]
+                "tile_offsets": L.STC_EXPORT_TILE_OFFSETS, "chunk_extents": L.STC_EXPORT_CHUNK_EXTENTS,
+                "sn_nodes": L.STC_EXPORT_SN_NODES, "sn_rows": L.STC_EXPORT_SN_ROWS,
+                "sn_cells": L.STC_EXPORT_SN_CELLS, "sn_tasks": L.STC_EXPORT_SN_TASKS}[what]
         a = L.stc_plan_export(self.h, code)
         if what == "tiles":
             return a.reshape(-1, 9)
         if what == "chunk_extents":
             return a.reshape(-1, 8, 2)
-        if what == "tasks":
+        if what in ("tasks", "sn_nodes", "sn_cells", "sn_tasks"):
             return a.reshape(-1, 4)
         return a
 

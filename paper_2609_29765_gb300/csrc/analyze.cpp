@@ -1232,7 +1232,7 @@ extern "C" int stc_plan_info_get(const stc_plan* P, stc_plan_info* o) {
     return STC_OK;
 }
 
-extern "C" int stc_plan_export(const stc_plan* P, int what, void* buf, size_t* bytes) {
+static int plan_export_impl(const stc_plan* P, int what, void* buf, size_t* bytes) {
     if (!P || !bytes) return STC_ERR_INVALID_ARG;
     vector<int64_t> tmp;
     const void* src = nullptr;
@@ -1301,6 +1301,27 @@ extern "C" int stc_plan_export(const stc_plan* P, int what, void* buf, size_t* b
             src = tmp.data(); sz = tmp.size() * 8;
             break;
         }
+        case STC_EXPORT_SN_NODES:
+        case STC_EXPORT_SN_ROWS:
+        case STC_EXPORT_SN_CELLS:
+        case STC_EXPORT_SN_TASKS: {
+            const stc::SnPlan& S = P->supernodal();
+            const int64_t nsn = (int64_t)S.first.size() - 1;
+            if (what == STC_EXPORT_SN_NODES) {
+                for (int64_t s = 0; s < nsn; ++s) {
+                    const int64_t f[4] = {S.first[s], S.first[s + 1] - S.first[s], S.rptr[s + 1] - S.rptr[s], S.off[s]};
+                    tmp.insert(tmp.end(), f, f + 4);
+                }
+            } else if (what == STC_EXPORT_SN_ROWS) {
+                tmp.assign(S.rows.begin(), S.rows.end());
+            } else if (what == STC_EXPORT_SN_CELLS) {
+                tmp.assign(S.cells.begin(), S.cells.end());
+            } else {
+                tmp.assign(S.tasks.begin(), S.tasks.end());
+            }
+            src = tmp.data(); sz = tmp.size() * 8;
+            break;
+        }
         default: return STC_ERR_INVALID_ARG;
     }
     if (!buf) { *bytes = sz; return STC_OK; }
@@ -1308,4 +1329,14 @@ extern "C" int stc_plan_export(const stc_plan* P, int what, void* buf, size_t* b
     if (sz) std::memcpy(buf, src, sz);
     *bytes = sz;
     return STC_OK;
+}
+
+extern "C" int stc_plan_export(const stc_plan* P, int what, void* buf, size_t* bytes) {
+    try {
+        return plan_export_impl(P, what, buf, bytes);
+    } catch (const std::bad_alloc&) {
+        return STC_ERR_OUT_OF_MEMORY;
+    } catch (...) {
+        return STC_ERR_INVALID_PATTERN;
+    }
 }

@@ -173,6 +173,27 @@ struct TaskSet {
     int device = -1;
 };
 
+// Non-uniform supernodal tiling (Sec. 5.4), host plan.  Supernode s owns the columns
+// [first[s], first[s+1]) and the rows rows[rptr[s] .. rptr[s+1]) (its own columns first,
+// ascending); its panel is a dense column-major rows x width block at arena offset off[s].
+// A cell (I, J, r0, r1) is the run [r0, r1) of column supernode I's rows owned by row
+// supernode J; cells of I are cells[cptr[I] .. cptr[I+1]), the diagonal cell first.
+enum : int32_t { SN_FACTOR = 0, SN_TRSM = 1, SN_UPDATE = 2 };
+struct SnPlan {
+    std::vector<int32_t> first;
+    std::vector<int64_t> rptr;
+    std::vector<int32_t> rows;
+    std::vector<int64_t> off;
+    int64_t arena = 0;           // doubles per item
+    std::vector<int32_t> cells;  // 4 per cell: I, J, r0, r1
+    std::vector<int32_t> cptr;
+    // 4 per task: SN_FACTOR (kind, diagonal cell, -1, -1); SN_TRSM (kind, cell, -1, -1);
+    // SN_UPDATE (kind, target cell (K,J), source cells (K,I) and (J,I))
+    std::vector<int32_t> tasks;
+    int64_t stored = 0;          // lower-trapezoid entries of all panels
+    int64_t zeros = 0;           // of which structurally zero (relaxation)
+};
+
 }  // namespace stc
 
 // The opaque plan of the public ABI.
@@ -218,6 +239,11 @@ struct stc_plan {
     std::map<int32_t, std::unique_ptr<stc::TaskSet>> tasksets;
     stc::DevPlanArrays dev;
     std::mutex mu;
+
+    // supernodal layout, built on first use from the symbolic factor
+    mutable std::unique_ptr<stc::SnPlan> sn;
+    mutable std::mutex sn_mu;
+    const stc::SnPlan& supernodal() const;
 
     int tile_id(int64_t I, int64_t J) const;  // -1 if not active
     // built on demand (host); bl_order: queue by bottom level (longest path to the end of
