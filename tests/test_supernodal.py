@@ -229,3 +229,21 @@ def test_supernodal_tasks_reproduce_oracle_factor(case):
         assert np.all(M[s][lower & ~covered[s]] == 0.0), (name, s)  # explicit zeros stay zero
     ld = 2 * sum(np.sum(np.log(np.diag(M[s][:nodes[s, 1], :nodes[s, 1]]))) for s in range(len(nodes)))
     assert abs(ld - F.logdet(Lx)) <= 1e-12 * abs(F.logdet(Lx))
+
+
+@pytest.mark.parametrize("seed", range(10))
+def test_supernodal_random_patterns(seed):
+    rng = np.random.default_rng(900 + seed)
+    n = int(rng.integers(20, 600))
+    Ap, Ai, Ax = I.random_spd(n, float(rng.uniform(0.002, 0.08)), 40 + seed)
+    kind = ["rcm", "natural", "given"][seed % 3]
+    perm = rng.permutation(n) if kind == "given" else None
+    P = Plan(n, Ap, Ai, nb=32, ordering=kind if perm is None else "auto", perm=perm)
+    nodes, R, M = _execute(n, P, Ap, Ai, Ax)
+    F = O.OracleFactor(n, Ap, Ai, P.export("perm"))
+    Lx, info = F.factor(Ax)
+    assert info == 0
+    snof = np.repeat(np.arange(len(nodes)), nodes[:, 1])
+    got = np.concatenate([M[snof[j]][np.searchsorted(R[snof[j]], F.Li[F.Lp[j]:F.Lp[j + 1]]), j - nodes[snof[j], 0]]
+                          for j in range(n)])
+    assert np.max(np.abs(got - Lx)) <= 1e-12 * np.max(np.abs(Lx))
