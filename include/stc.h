@@ -181,6 +181,18 @@ int stc_plan_upload(stc_plan* plan);
 
 void stc_plan_destroy(stc_plan* plan);
 
+/* Save / load an analysed plan (the analysis is what the repeated factorizations reuse,
+ * Sec. 6.6; a saved plan lets a later process skip stc_analyze).
+ * stc_plan_save writes a self-contained host blob (magic, version, size, FNV-1a
+ * checksum, then every host array of the plan, native little-endian); buf == NULL reads
+ * the size into *bytes; STC_ERR_BUFFER_TOO_SMALL if *bytes is short.  stc_plan_load
+ * builds a new plan from such a blob (the caller keeps the buffer and destroys the plan
+ * with stc_plan_destroy); task sets and device copies are rebuilt on first use.  A
+ * truncated, corrupted or inconsistent blob gives STC_ERR_INVALID_PATTERN, another
+ * format version STC_ERR_UNSUPPORTED, and no plan. */
+int stc_plan_save(const stc_plan* plan, void* buf, size_t* bytes);
+int stc_plan_load(const void* buf, size_t bytes, stc_plan** plan_out);
+
 /* Bytes of caller-owned device memory:
  *   factor    -- the tile-stored factor of `batch` items (item stride = value at batch 1)
  *   workspace -- dependency counters, queue head and status word used by factorize,

@@ -38,7 +38,7 @@ EXPORTED = [
     "stc_logdet", "stc_solve", "stc_factor_to_csc", "stc_fp64_peak_probe", "stc_factorize_noalloc",
     "stc_selinv", "stc_logdet_backward", "stc_sym_outer_backward", "stc_quad_form",
     "stc_group_create", "stc_group_workspace_bytes", "stc_factorize_group", "stc_group_destroy",
-    "stc_strerror", "stc_factorize_mixed", "stc_quad_backward",
+    "stc_strerror", "stc_factorize_mixed", "stc_quad_backward", "stc_plan_save", "stc_plan_load",
 ]
 STC_NOALLOC_SCRATCH_BYTES = 4 << 20
 
@@ -100,6 +100,10 @@ def lib():
         L.stc_plan_upload.restype = C.c_int
         L.stc_plan_destroy.argtypes = [_vp]
         L.stc_plan_destroy.restype = None
+        L.stc_plan_save.argtypes = [_vp, _vp, C.POINTER(C.c_size_t)]
+        L.stc_plan_save.restype = C.c_int
+        L.stc_plan_load.argtypes = [_vp, C.c_size_t, C.POINTER(_vp)]
+        L.stc_plan_load.restype = C.c_int
         L.stc_factor_bytes.argtypes = [_vp, C.c_int64]
         L.stc_factor_bytes.restype = C.c_size_t
         L.stc_workspace_bytes.argtypes = [_vp, C.c_int64]
@@ -205,6 +209,21 @@ def stc_plan_export(plan, what: int) -> np.ndarray:
     out = np.empty(sz.value // 8, dtype=np.int64)
     check(lib().stc_plan_export(plan, int(what), _host_ptr(out), C.byref(sz)), "stc_plan_export")
     return out
+
+
+def stc_plan_save(plan) -> bytes:
+    sz = C.c_size_t(0)
+    check(lib().stc_plan_save(plan, None, C.byref(sz)), "stc_plan_save")
+    buf = C.create_string_buffer(sz.value)
+    check(lib().stc_plan_save(plan, buf, C.byref(sz)), "stc_plan_save")
+    return buf.raw[:sz.value]
+
+
+def stc_plan_load(blob: bytes):
+    """Returns (status, plan_handle)."""
+    h = C.c_void_p()
+    rc = lib().stc_plan_load(blob, len(blob), C.byref(h))
+    return rc, h
 
 
 def stc_plan_upload(plan):

@@ -47,11 +47,28 @@ class Plan:
         self.h = None
         rc, h = L.stc_analyze(n, colptr, rowind, coords, o)
         L.check(rc, "stc_analyze")
+        self._adopt(h)
+
+    def _adopt(self, h):
         self.h = h
         i = L.stc_plan_info_get(h)
         self.info = {f: getattr(i, f) for f, _ in L.stc_plan_info._fields_ if not f.startswith("reserved")}
         self.n, self.nnzA, self.nnzL = int(i.n), int(i.nnzA), int(i.nnzL)
         self._ws = {}
+
+    def save(self) -> bytes:
+        """The analysed plan as a self-contained blob (stc_plan_save)."""
+        return L.stc_plan_save(self.h)
+
+    @classmethod
+    def load(cls, blob: bytes) -> "Plan":
+        """A plan from a blob of `save`, without re-running the analysis (stc_plan_load)."""
+        rc, h = L.stc_plan_load(bytes(blob))
+        L.check(rc, "stc_plan_load")
+        P = cls.__new__(cls)
+        P._perm_keep = None
+        P._adopt(h)
+        return P
 
     def __del__(self):
         if getattr(self, "h", None):

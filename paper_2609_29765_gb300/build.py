@@ -21,7 +21,7 @@ LIB = os.path.join(OUT, "libstc.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 SOURCES_CU = ["replay.cu", "compose.cu"]
-SOURCES_CPP = ["analyze.cpp", "supernodal.cpp"]
+SOURCES_CPP = ["analyze.cpp", "supernodal.cpp", "plan_io.cpp"]
 
 
 def _nvcc() -> str:

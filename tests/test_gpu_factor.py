@@ -194,3 +194,17 @@ def test_invalid_device_arguments():
     assert L.lib().stc_factorize(P.h, None, 1, None, None, None, None) == L.STC_ERR_INVALID_ARG
     b = torch.zeros(1, 1, 50, dtype=torch.float64, device="cuda")
     assert L.stc_solve(P.h, f, 1, 1, b, b, w) == L.STC_ERR_INVALID_ARG
+
+
+def test_loaded_plan_factorizes_identically():
+    # a plan saved and loaded again (stc_plan_save / stc_plan_load) holds the same arrays,
+    # so its factors are bit-identical to the original plan's
+    Ap, Ai, coords, vals = c1_batch(2)
+    n = len(Ap) - 1
+    P = Plan(n, Ap, Ai, coords=coords, nb=64)
+    Q = Plan.load(P.save())
+    a = P.factorize(dev(vals))
+    b = Q.factorize(dev(vals))
+    assert b.status() == L.STC_OK
+    assert torch.equal(a.data, b.data)
+    assert torch.equal(a.logdet(), b.logdet())

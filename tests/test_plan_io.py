@@ -1,0 +1,91 @@
+"""Saving and loading analysed plans (stc_plan_save / stc_plan_load), on the CPU.
+
+A loaded plan must be the same plan: re-saving it gives the identical blob (the blob
+holds every host array), every export and the plan info match the original, and the
+task sets and supernodal layout it rebuilds on demand match.  Truncated, corrupted and
+foreign blobs are refused.
+"""
+import numpy as np
+import pytest
+
+from paper_2609_29765_gb300 import _lib as L
+from paper_2609_29765_gb300 import build as B
+from paper_2609_29765_gb300 import inputs as I
+from paper_2609_29765_gb300.api import Plan
+
+EXPORTS = ["perm", "etree", "Lp", "Li", "tiles", "aind", "tasks", "value_map", "tile_offsets",
+           "chunk_extents", "sn_nodes", "sn_rows", "sn_cells", "sn_tasks"]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if B.stale():
+        B.build()
+    L.lib()
+
+
+def _plans():
+    Ap, Ai, Ax, coords = I.laplace2d_bordered()
+    yield "config1_nd", Plan(len(Ap) - 1, Ap, Ai, coords=coords, nb=64)
+    Ap, Ai, Ax, coords = I.fem3d(10, 9, 8)
+    yield "fem_dense_route", Plan(len(Ap) - 1, Ap, Ai, coords=coords, nb=32, route="dense", nd_leaf=32)
+    Ap, Ai = I.band_pattern(3000, 70)
+    yield "band_slices", Plan(3000, Ap, Ai, nb=64, ordering="natural", row_slices=4)
+    Ap, Ai, _ = I.random_spd(700, 0.005, 2)
+    yield "random_given", Plan(700, Ap, Ai, nb=24, perm=np.random.default_rng(1).permutation(700))
+
+
+PLANS = list(_plans())
+
+
+@pytest.mark.parametrize("case", PLANS, ids=lambda c: c[0])
+def test_round_trip_is_the_same_plan(case):
+    _, P = case
+    blob = P.save()
+    Q = Plan.load(blob)
+    assert Q.save() == blob
+    assert Q.info == P.info
+    for k in EXPORTS:
+        assert np.array_equal(Q.export(k), P.export(k)), k
+    assert Q.factor_bytes(3) == P.factor_bytes(3) and Q.workspace_bytes(5) == P.workspace_bytes(5)
+    assert Q.route == P.route and Q.route_selected == P.route_selected
+
+
+def test_refuses_truncated_corrupted_and_foreign_blobs():
+    _, P = PLANS[0]
+    blob = P.save()
+    for bad in (blob[:10], blob[:-1], blob[:len(blob) // 2]):
+        assert L.stc_plan_load(bad)[0] == L.STC_ERR_INVALID_PATTERN
+    flipped = bytearray(blob)
+    flipped[len(blob) // 3] ^= 0x40
+    assert L.stc_plan_load(bytes(flipped))[0] == L.STC_ERR_INVALID_PATTERN
+    foreign = bytearray(blob)
+    foreign[0:8] = b"NOTAPLAN"
+    assert L.stc_plan_load(bytes(foreign))[0] == L.STC_ERR_INVALID_PATTERN
+    newer = bytearray(blob)
+    newer[8] = 99  # format version
+    assert L.stc_plan_load(bytes(newer))[0] == L.STC_ERR_UNSUPPORTED
+    with pytest.raises(L.StcError):
+        Plan.load(blob[:-8])
+
+
+def test_save_size_query_and_short_buffer():
+    _, P = PLANS[2]
+    sz = L.C.c_size_t(0)
+    assert L.lib().stc_plan_save(P.h, None, L.C.byref(sz)) == L.STC_OK
+    assert sz.value == len(P.save())
+    short = L.C.c_size_t(sz.value - 1)
+    buf = L.C.create_string_buffer(sz.value)
+    assert L.lib().stc_plan_save(P.h, buf, L.C.byref(short)) == L.STC_ERR_BUFFER_TOO_SMALL
+    assert short.value == sz.value
+
+
+def test_loaded_plan_survives_the_original():
+    Ap, Ai = I.band_pattern(2000, 40)
+    P = Plan(2000, Ap, Ai, nb=32, ordering="natural")
+    ref = {k: P.export(k) for k in ("tiles", "value_map", "tasks")}
+    blob = P.save()
+    del P
+    Q = Plan.load(blob)
+    for k, v in ref.items():
+        assert np.array_equal(Q.export(k), v)
