@@ -1,6 +1,7 @@
 """GPU parity: factorize / logdet / solve through the C ABI against the CPU oracle.
 
-Tolerances (FP64 throughout, see the design doc for the derivation):
+Tolerances (FP64 throughout; the factor bound is the forward error of two exact
+Cholesky factorizations that differ only in summation order, ~kappa * c * u * |L|):
   * factor entries: |L_gpu - L_oracle| <= 1e-11 * max |L_:j| per column (two exact
     factorizations differing only in summation order);
   * residual ||L L^T - A_p||_F / ||A_p||_F <= 1e-12 (the spec gate);
