@@ -175,6 +175,34 @@ int stc_plan_info_get(const stc_plan* plan, stc_plan_info* out);
  * read the size in bytes into *bytes; STC_ERR_BUFFER_TOO_SMALL if *bytes is short. */
 int stc_plan_export(const stc_plan* plan, int what, void* buf, size_t* bytes);
 
+/* Copy one array of the device task list that stc_factorize replays (Algorithm 1's tasks
+ * grouped per output tile, Sec. 5.2-5.3) with `slices` row slices per off-diagonal tile
+ * (1, 2, 4 or 8; bl_order != 0: queued by bottom level, as for one or two value sets),
+ * so that host-side checks can execute it.  Every entry is widened to int64.  The set is
+ * built on first request, as on the first factorization that uses it. */
+#define STC_TASKSET_TASKS 0     /* [ntasks][12] in queue order: kind (0 DIAG = SYRKs + POTRF,
+                                   1 OFF = GEMMs + TRSM of a row slice, 2 SYRK row slice,
+                                   3 POTRF), output tile, diagonal tile, update range
+                                   [ubeg, uend), row slice [rs0, rs1), TRSM rows [tr0, tr1),
+                                   POTRF's wait count, slice index, slice height          */
+#define STC_TASKSET_UPDS 1      /* [nupds][10]: a, b (operand tiles), kmap (pair offset in
+                                   the imap, -1 = contiguous inner range), klen, ka0, kb0
+                                   (first stored column of a / b when contiguous), ra0, ra1
+                                   (output rows), oc0, oc1 (output stored columns; SYRK
+                                   slice: oc0 = first column)                               */
+#define STC_TASKSET_IMAP 2      /* [npairs][2]: stored column of a and of b per inner index */
+#define STC_TASKSET_TILES 3     /* [ntiles][13]: offset, I, J, kind (0 off-diagonal, 1 dense
+                                   diagonal, 2 banded diagonal), stored width, first
+                                   logical column if contiguous else -1, offset in the
+                                   stored-column list, storage kd, row extent r0, r1,
+                                   completion target, logdet slot, extent-pair offset    */
+#define STC_TASKSET_SAIND 4     /* stored-column lists of indexed tiles                      */
+#define STC_TASKSET_CEXT 5      /* (lo, hi) row extent per 16 stored columns                 */
+#define STC_TASKSET_CSC_MAP 6   /* [nnzL] factor offset of each structural entry of L        */
+#define STC_TASKSET_PAD_DIAG 7  /* factor offsets set to 1.0 (padding of the ragged tile)    */
+int stc_plan_export_taskset(const stc_plan* plan, int32_t slices, int bl_order, int what, void* buf,
+                            size_t* bytes);
+
 /* Upload the plan's device metadata to the current CUDA device now (synchronous).
  * Optional: every device call does it on first use. */
 int stc_plan_upload(stc_plan* plan);

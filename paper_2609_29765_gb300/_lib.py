@@ -39,7 +39,10 @@ EXPORTED = [
     "stc_selinv", "stc_logdet_backward", "stc_sym_outer_backward", "stc_quad_form",
     "stc_group_create", "stc_group_workspace_bytes", "stc_factorize_group", "stc_group_destroy",
     "stc_strerror", "stc_factorize_mixed", "stc_quad_backward", "stc_plan_save", "stc_plan_load",
+    "stc_plan_export_taskset",
 ]
+(STC_TASKSET_TASKS, STC_TASKSET_UPDS, STC_TASKSET_IMAP, STC_TASKSET_TILES, STC_TASKSET_SAIND,
+ STC_TASKSET_CEXT, STC_TASKSET_CSC_MAP, STC_TASKSET_PAD_DIAG) = range(8)
 STC_NOALLOC_SCRATCH_BYTES = 4 << 20
 
 
@@ -100,6 +103,8 @@ def lib():
         L.stc_plan_upload.restype = C.c_int
         L.stc_plan_destroy.argtypes = [_vp]
         L.stc_plan_destroy.restype = None
+        L.stc_plan_export_taskset.argtypes = [_vp, C.c_int32, C.c_int, C.c_int, _vp, C.POINTER(C.c_size_t)]
+        L.stc_plan_export_taskset.restype = C.c_int
         L.stc_plan_save.argtypes = [_vp, _vp, C.POINTER(C.c_size_t)]
         L.stc_plan_save.restype = C.c_int
         L.stc_plan_load.argtypes = [_vp, C.c_size_t, C.POINTER(_vp)]
@@ -208,6 +213,16 @@ def stc_plan_export(plan, what: int) -> np.ndarray:
     check(lib().stc_plan_export(plan, int(what), None, C.byref(sz)), "stc_plan_export")
     out = np.empty(sz.value // 8, dtype=np.int64)
     check(lib().stc_plan_export(plan, int(what), _host_ptr(out), C.byref(sz)), "stc_plan_export")
+    return out
+
+
+def stc_plan_export_taskset(plan, slices: int, bl_order: bool, what: int) -> np.ndarray:
+    sz = C.c_size_t(0)
+    check(lib().stc_plan_export_taskset(plan, int(slices), int(bl_order), int(what), None, C.byref(sz)),
+          "stc_plan_export_taskset")
+    out = np.empty(sz.value // 8, dtype=np.int64)
+    check(lib().stc_plan_export_taskset(plan, int(slices), int(bl_order), int(what), _host_ptr(out), C.byref(sz)),
+          "stc_plan_export_taskset")
     return out
 
 

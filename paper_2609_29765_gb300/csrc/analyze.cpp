@@ -1331,6 +1331,61 @@ static int plan_export_impl(const stc_plan* P, int what, void* buf, size_t* byte
     return STC_OK;
 }
 
+static int taskset_export_impl(const stc_plan* P, int32_t slices, int bl_order, int what, void* buf,
+                               size_t* bytes) {
+    if (!P || !bytes) return STC_ERR_INVALID_ARG;
+    if (slices != 1 && slices != 2 && slices != 4 && slices != 8) return STC_ERR_INVALID_ARG;
+    // task sets are built on demand under the plan's lock, as on the first factorization
+    const stc::TaskSet* ts = const_cast<stc_plan*>(P)->taskset(slices, bl_order != 0);
+    vector<int64_t> tmp;
+    switch (what) {
+        case STC_TASKSET_TASKS:
+            for (const stc::DTask& t : ts->tasks) {
+                const int64_t f[12] = {t.kind, t.tile, t.diag, t.ubeg, t.uend, t.rs0, t.rs1,
+                                       t.tr0, t.tr1, t.own_wait, t.slice, ts->slice_h};
+                tmp.insert(tmp.end(), f, f + 12);
+            }
+            break;
+        case STC_TASKSET_UPDS:
+            for (const stc::DUpd& u : ts->upds) {
+                const int64_t f[10] = {u.a, u.b, u.kmap, u.klen, u.ka0, u.kb0, u.ra0, u.ra1, u.oc0, u.oc1};
+                tmp.insert(tmp.end(), f, f + 10);
+            }
+            break;
+        case STC_TASKSET_IMAP: tmp.assign(ts->imap.begin(), ts->imap.end()); break;
+        case STC_TASKSET_TILES:
+            for (size_t t = 0; t < P->tiles.size(); ++t) {
+                const stc::DTile& T = P->tiles[t];
+                const int64_t f[13] = {T.off, T.I, T.J, T.kind, T.sw, T.c0, T.aoff, T.kd, T.r0, T.r1,
+                                       ts->nfinal[t], T.pd_slot, T.xoff};
+                tmp.insert(tmp.end(), f, f + 13);
+            }
+            break;
+        case STC_TASKSET_SAIND: tmp.assign(P->saind.begin(), P->saind.end()); break;
+        case STC_TASKSET_CEXT: tmp.assign(P->cext.begin(), P->cext.end()); break;
+        case STC_TASKSET_CSC_MAP: tmp.assign(P->csc_map.begin(), P->csc_map.end()); break;
+        case STC_TASKSET_PAD_DIAG: tmp.assign(P->pad_diag.begin(), P->pad_diag.end()); break;
+        default: return STC_ERR_INVALID_ARG;
+    }
+    const size_t sz = tmp.size() * 8;
+    if (!buf) { *bytes = sz; return STC_OK; }
+    if (*bytes < sz) { *bytes = sz; return STC_ERR_BUFFER_TOO_SMALL; }
+    if (sz) std::memcpy(buf, tmp.data(), sz);
+    *bytes = sz;
+    return STC_OK;
+}
+
+extern "C" int stc_plan_export_taskset(const stc_plan* P, int32_t slices, int bl_order, int what, void* buf,
+                                       size_t* bytes) {
+    try {
+        return taskset_export_impl(P, slices, bl_order, what, buf, bytes);
+    } catch (const std::bad_alloc&) {
+        return STC_ERR_OUT_OF_MEMORY;
+    } catch (...) {
+        return STC_ERR_INVALID_PATTERN;
+    }
+}
+
 extern "C" int stc_plan_export(const stc_plan* P, int what, void* buf, size_t* bytes) {
     try {
         return plan_export_impl(P, what, buf, bytes);

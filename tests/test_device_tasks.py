@@ -1,0 +1,261 @@
+"""The device task list, executed on the host (no GPU).
+
+`stc_plan_export_taskset` hands out the arrays the factorization kernel replays: tasks in
+queue order, their updates (operand tiles, inner-dimension maps, row and column ranges),
+the tiles with their stored columns and 16-column row extents.  This file runs that list
+with numpy, one task after another in queue order (a topological order of the DAG), the
+way the kernel does it: SYRK / GEMM products chunked by 16 inner columns and cut to the
+chunk's row extents, the TRSM of a row slice by 32-column panels cut to the panel's row
+extents.  It checks that
+
+* the result equals the oracle's factor on every structural entry of L (so the update
+  lists are complete and the inner-dimension maps pair the right columns), and
+* every row or column the extents let the kernel skip is exactly zero in the operand
+  (so skipping is exact, reading 13).
+
+Row slices 1, 2, 4 and 8 and both queue orders are covered.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2609_29765_gb300 import _lib as L
+from paper_2609_29765_gb300 import build as B
+from paper_2609_29765_gb300 import inputs as I
+from paper_2609_29765_gb300.api import Plan
+
+KC = 16      # inner chunk of the tile products
+PANEL = 32   # TRSM panel width
+DIAG, OFF, SYRK, POTRF = 0, 1, 2, 3
+T_OFF, T_DENSE, T_BAND = 0, 1, 2
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if B.stale():
+        B.build()
+    L.lib()
+
+
+class Replay:
+    def __init__(self, P, slices, bl):
+        ex = lambda w: L.stc_plan_export_taskset(P.h, slices, bl, w)
+        self.nb = P.info["nb"]
+        self.tasks = ex(L.STC_TASKSET_TASKS).reshape(-1, 12)
+        self.upds = ex(L.STC_TASKSET_UPDS).reshape(-1, 10)
+        self.imap = ex(L.STC_TASKSET_IMAP).reshape(-1, 2)
+        self.tiles = ex(L.STC_TASKSET_TILES).reshape(-1, 13)
+        self.saind = ex(L.STC_TASKSET_SAIND)
+        self.cext = ex(L.STC_TASKSET_CEXT).reshape(-1, 2)
+        self.csc_map = ex(L.STC_TASKSET_CSC_MAP)
+        self.pad = ex(L.STC_TASKSET_PAD_DIAG)
+        self.value_map = P.export("value_map")
+        self.fdoubles = P.factor_bytes(1) // 8
+        self.skipped_checks = 0
+
+    # ---- storage
+    def off_view(self, F, t):
+        off, sw = self.tiles[t, 0], self.tiles[t, 4]
+        return F[off:off + self.nb * sw].reshape(sw, self.nb).T  # [row, stored column]
+
+    def diag_full(self, F, t):
+        nb = self.nb
+        off, kind, kd = self.tiles[t, 0], self.tiles[t, 3], self.tiles[t, 7]
+        if kind == T_DENSE:
+            return np.tril(F[off:off + nb * nb].reshape(nb, nb).T)
+        D = np.zeros((nb, nb))
+        for r in range(nb):
+            for c in range(max(0, r - kd), r + 1):
+                D[r, c] = F[off + (kd + c - r) + r * (kd + 1)]
+        return D
+
+    def diag_store(self, F, t, D, rows=None):
+        nb = self.nb
+        off, kind, kd = self.tiles[t, 0], self.tiles[t, 3], self.tiles[t, 7]
+        rows = range(nb) if rows is None else rows
+        for r in rows:
+            for c in range(0, r + 1):
+                if kind == T_DENSE:
+                    F[off + r + c * nb] = D[r, c]
+                elif r - c <= kd:
+                    F[off + (kd + c - r) + r * (kd + 1)] = D[r, c]
+                else:
+                    assert D[r, c] == 0.0, "fill outside the band of a diagonal tile"
+
+    def logical(self, t, s):
+        c0, aoff = self.tiles[t, 5], self.tiles[t, 6]
+        s = np.asarray(s)
+        return c0 + s if c0 >= 0 else self.saind[aoff + s]
+
+    def ext(self, t, s0, s1):
+        xoff = self.tiles[t, 12]
+        if xoff < 0:
+            return 0, self.nb
+        q = np.arange(s0 // 16, s1 // 16 + 1)
+        return int(self.cext[xoff + q, 0].min()), int(self.cext[xoff + q, 1].max())
+
+    def inner(self, u, k0, K, b):
+        _, _, kmap, _, ka0, kb0 = u[:6]
+        if kmap < 0:
+            return np.arange(k0, k0 + K) + (kb0 if b else ka0)
+        return self.imap[kmap + k0:kmap + k0 + K, 1 if b else 0]
+
+    def assert_zero_outside(self, M, lo, hi, what):
+        assert np.all(M[:lo] == 0.0) and np.all(M[hi:] == 0.0), what
+        self.skipped_checks += 1
+
+    # ---- tasks
+    def potrf(self, F, t):
+        nb, sw = self.nb, self.tiles[t, 4]
+        D = self.diag_full(F, t)
+        S = D[:sw, :sw]
+        Lw = np.linalg.cholesky(S + np.tril(S, -1).T)
+        D[:sw, :sw] = Lw
+        self.diag_store(F, t, D)
+
+    def syrk_into(self, F, D, u, r0, d0, rb):
+        A = self.off_view(F, u[0])
+        for k0 in range(0, u[3], KC):
+            K = min(KC, u[3] - k0)
+            idx = self.inner(u, k0, K, False)
+            lo, hi = self.ext(u[0], idx[0], idx[-1])
+            self.assert_zero_outside(A[:, idx], lo, hi, "SYRK operand outside its extent")
+            q0, e0, e1 = max(r0, lo), max(d0, lo), min(rb, hi)
+            if e0 >= e1:
+                continue
+            U = A[e0:e1, idx] @ A[q0:e1, idx].T
+            D[e0:e1, q0:e1] -= np.tril(U, e0 - q0)  # lower part only (column <= row)
+
+    def off_task(self, F, tk):
+        kind, o, dk, ub, ue, rs0, rs1, tr0, tr1 = tk[:9]
+        nb = self.nb
+        Ot = self.off_view(F, o)
+        sw = self.tiles[o, 4]
+        X = Ot[rs0:rs1].copy()
+        oc0 = self.tiles[o, 5]
+        for u in self.upds[ub:ue]:
+            A, Bt = self.off_view(F, u[0]), self.off_view(F, u[1])
+            for k0 in range(0, u[3], KC):
+                K = min(KC, u[3] - k0)
+                ia, ib = self.inner(u, k0, K, False), self.inner(u, k0, K, True)
+                alo, ahi = self.ext(u[0], ia[0], ia[-1])
+                blo, bhi = self.ext(u[1], ib[0], ib[-1])
+                self.assert_zero_outside(A[:, ia], alo, ahi, "GEMM A outside its extent")
+                self.assert_zero_outside(Bt[:, ib], blo, bhi, "GEMM B outside its extent")
+                e0, e1 = max(u[6], alo), min(u[7], ahi)
+                c0, c1 = u[8], u[9]
+                if oc0 >= 0:
+                    c0, c1 = max(c0, blo - oc0), min(c1, bhi - oc0)
+                if e0 >= e1 or c0 >= c1:
+                    continue
+                rows_b = self.logical(o, np.arange(c0, c1))
+                X[e0 - rs0:e1 - rs0, c0:c1] -= A[e0:e1, ia] @ Bt[np.ix_(rows_b, ib)].T
+        # TRSM against L_kk restricted to the stored columns, by panels
+        Lk = self.diag_full(F, dk)
+        lc = self.logical(o, np.arange(sw))
+        Ls = Lk[np.ix_(lc, lc)]
+        for p in range(0, sw, PANEL):
+            pw = min(PANEL, sw - p)
+            lo, hi = self.ext(o, p, p + pw - 1)
+            y0, y1 = max(tr0, lo), min(tr1, hi)
+            panel = X[:, p:p + pw]
+            keep = np.zeros(rs1 - rs0, dtype=bool)
+            keep[max(y0 - rs0, 0):max(y1 - rs0, 0)] = True
+            assert np.all(panel[~keep] == 0.0), "TRSM rows outside the panel's extent are not zero"
+            if y0 < y1:
+                Lpp = Ls[p:p + pw, p:p + pw]
+                X[y0 - rs0:y1 - rs0, p:p + pw] = np.linalg.solve(Lpp, X[y0 - rs0:y1 - rs0, p:p + pw].T).T
+            pn = p + pw
+            if pn >= sw or y0 >= y1:
+                continue
+            for k0 in range(p, pn, KC):
+                K = min(KC, pn - k0)
+                lo, hi = self.ext(o, k0, k0 + K - 1)
+                x0, x1 = max(tr0, lo), min(tr1, hi)
+                if x0 < x1:
+                    X[x0 - rs0:x1 - rs0, pn:] -= X[x0 - rs0:x1 - rs0, k0:k0 + K] @ Ls[pn:, k0:k0 + K].T
+        Ot[rs0:rs1] = X
+
+    def run(self, values):
+        F = np.zeros(self.fdoubles)
+        F[self.value_map] = values
+        F[self.pad] = 1.0
+        nb = self.nb
+        for tk in self.tasks:
+            kind, t = tk[0], tk[1]
+            if kind == DIAG:
+                D = self.diag_full(F, t)
+                for u in self.upds[tk[3]:tk[4]]:
+                    self.syrk_into(F, D, u, u[8], u[6], u[7])
+                self.diag_store(F, t, D)
+                self.potrf(F, t)
+            elif kind == SYRK:
+                rs0, rs1 = tk[5], tk[6]
+                D = self.diag_full(F, t)
+                for u in self.upds[tk[3]:tk[4]]:
+                    assert rs0 <= u[6] and u[7] <= rs1
+                    self.syrk_into(F, D, u, u[8], u[6], u[7])
+                self.diag_store(F, t, D, rows=range(rs0, rs1))
+            elif kind == POTRF:
+                self.potrf(F, t)
+            else:
+                self.off_task(F, tk)
+        return F[self.csc_map]
+
+
+def _cases():
+    Ap, Ai, Ax, coords = I.laplace2d_bordered(16, 16, 2)
+    yield "bordered_nd_nb16", Ap, Ai, Ax, dict(coords=coords, nb=16, route="semisparse", nd_leaf=16)
+    yield "bordered_nd_dense_nb32", Ap, Ai, Ax, dict(coords=coords, nb=32, route="dense", nd_leaf=16)
+    Ap, Ai, Ax = I.band(700, 40, 1)
+    yield "band_nb32", Ap, Ai, Ax, dict(nb=32, ordering="natural")
+    yield "band_nb128", Ap, Ai, Ax, dict(nb=128, ordering="natural")
+    Ap, Ai, coords = I.stcov_pattern(7, 6, 5, 3)
+    Ax = I.stcov_values((2.0, 0.7, 0.5), 7, 6, 5, 3)
+    yield "stcov_nd_nb16", Ap, Ai, Ax, dict(coords=coords, nb=16, nd_leaf=20)
+    Ap, Ai, Ax = I.random_spd(400, 0.008, 5)
+    yield "random_rcm_nb8", Ap, Ai, Ax, dict(nb=8, ordering="rcm")
+    yield "random_rcm_nb24", Ap, Ai, Ax, dict(nb=24, ordering="rcm")
+    Ap, Ai, Ax, coords = I.fem3d(7, 6, 6)
+    yield "fem_dense_nb16", Ap, Ai, Ax, dict(coords=coords, nb=16, route="dense", nd_leaf=20)
+
+
+CASES = list(_cases())
+
+
+@pytest.mark.parametrize("slices,bl", [(1, False), (2, False), (4, False), (8, False), (2, True)])
+@pytest.mark.parametrize("case", CASES, ids=lambda c: c[0])
+def test_device_task_list_reproduces_oracle(case, slices, bl):
+    name, Ap, Ai, Ax, kw = case
+    n = len(Ap) - 1
+    P = Plan(n, Ap, Ai, **kw)
+    R = Replay(P, slices, bl)
+    got = R.run(Ax)
+    F = O.OracleFactor(n, Ap, Ai, P.export("perm"))
+    Lo, info = F.factor(Ax)
+    assert info == 0
+    col = np.repeat(np.arange(n), np.diff(F.Lp))
+    scale = np.maximum.reduceat(np.abs(Lo), F.Lp[:-1])[col]
+    assert np.max(np.abs(got - Lo) / scale) <= 1e-12, name
+    assert R.skipped_checks > 0
+
+
+def test_queue_order_is_topological():
+    # every tile a task reads (update operands, the diagonal tile of a TRSM) is complete,
+    # i.e. all of its producing tasks come earlier in the queue; a POTRF comes after the
+    # SYRK slices of its tile
+    Ap, Ai, Ax, coords = I.laplace2d_bordered(16, 16, 2)
+    P = Plan(len(Ap) - 1, Ap, Ai, coords=coords, nb=16)
+    for slices, bl in ((1, False), (2, False), (4, True), (8, False)):
+        R = Replay(P, slices, bl)
+        last = {}
+        for i, tk in enumerate(R.tasks):
+            last[tk[1]] = i
+        for i, tk in enumerate(R.tasks):
+            for u in R.upds[tk[3]:tk[4]]:
+                assert last[u[0]] < i and last[u[1]] < i, (slices, bl, i)
+            if tk[0] == OFF:
+                assert last[tk[2]] < i
+            if tk[0] == POTRF:
+                slices_of_tile = [j for j, t2 in enumerate(R.tasks) if t2[1] == tk[1] and t2[0] == SYRK]
+                assert len(slices_of_tile) == tk[9] and all(j < i for j in slices_of_tile)
