@@ -155,6 +155,22 @@ typedef struct stc_plan_info {
                                    (2, cell (K,J), cell (K,I), cell (J,I))
                                                                     UPDATE L_KJ -= L_KI L_JI^T,
                                    rows and columns placed by sorted-subset scatter    */
+/* The same plan in device form (the input of a supernodal executor, shaped like the
+ * tile route's tasks): one task per diagonal cell (all its updates, then POTRF) and per
+ * row slice of <= 64 rows of an off-diagonal cell (all its updates, then the TRSM
+ * against the diagonal cell), in left-looking order.  Cell c's entry (i, k) lies at
+ * arena offset off + i + k * ld.  An update subtracts A B^T, A = rows [ar0, ar1) of cell
+ * a, B = all rows of cell b (inner dimension: the klen columns of their supernode), at
+ * target rows maps[rmap + i] (cell-local, i counted from row 0 of a) and target columns
+ * maps[cmap + j]; a diagonal task keeps the lower part. */
+#define STC_EXPORT_SN_DEV_CELLS 14  /* [ncells][7]: off, ld, h, w, I, J, row slices        */
+#define STC_EXPORT_SN_DEV_TASKS 15  /* [ntasks][8]: kind (0 diagonal, 1 off-diagonal slice),
+                                       cell, diagonal cell, update range [ubeg, uend),
+                                       rows [rs0, rs1), slice                             */
+#define STC_EXPORT_SN_DEV_UPDS 16   /* [nupds][7]: a, b, ar0, ar1, rmap, cmap, klen       */
+#define STC_EXPORT_SN_DEV_MAPS 17   /* the row / column position maps (int16 widened)     */
+#define STC_EXPORT_SN_VALUE_MAP 18  /* [nnzA] arena offset of each entry of A             */
+#define STC_EXPORT_SN_CSC_MAP 19    /* [nnzL] arena offset of each structural entry of L  */
 
 /* Fill *opt with defaults (nb 128, auto route, auto ordering, ND leaf 64). */
 void stc_options_default(stc_options* opt);

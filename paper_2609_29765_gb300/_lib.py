@@ -28,7 +28,9 @@ STC_ROUTE_AUTO, STC_ROUTE_DENSE, STC_ROUTE_SEMISPARSE, STC_ROUTE_SUPERNODAL = -1
 STC_ORDER_AUTO, STC_ORDER_NATURAL, STC_ORDER_GIVEN, STC_ORDER_ND, STC_ORDER_RCM = 0, 1, 2, 3, 4
 (STC_EXPORT_PERM, STC_EXPORT_ETREE, STC_EXPORT_LP, STC_EXPORT_LI, STC_EXPORT_TILES, STC_EXPORT_AIND,
  STC_EXPORT_TASKS, STC_EXPORT_VALUE_MAP, STC_EXPORT_TILE_OFFSETS, STC_EXPORT_CHUNK_EXTENTS,
- STC_EXPORT_SN_NODES, STC_EXPORT_SN_ROWS, STC_EXPORT_SN_CELLS, STC_EXPORT_SN_TASKS) = range(14)
+ STC_EXPORT_SN_NODES, STC_EXPORT_SN_ROWS, STC_EXPORT_SN_CELLS, STC_EXPORT_SN_TASKS,
+ STC_EXPORT_SN_DEV_CELLS, STC_EXPORT_SN_DEV_TASKS, STC_EXPORT_SN_DEV_UPDS, STC_EXPORT_SN_DEV_MAPS,
+ STC_EXPORT_SN_VALUE_MAP, STC_EXPORT_SN_CSC_MAP) = range(20)
 
 # every symbol include/stc.h declares
 EXPORTED = [

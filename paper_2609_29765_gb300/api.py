@@ -89,7 +89,10 @@ class Plan:
                 "tasks": L.STC_EXPORT_TASKS, "value_map": L.STC_EXPORT_VALUE_MAP,
                 "tile_offsets": L.STC_EXPORT_TILE_OFFSETS, "chunk_extents": L.STC_EXPORT_CHUNK_EXTENTS,
                 "sn_nodes": L.STC_EXPORT_SN_NODES, "sn_rows": L.STC_EXPORT_SN_ROWS,
-                "sn_cells": L.STC_EXPORT_SN_CELLS, "sn_tasks": L.STC_EXPORT_SN_TASKS}[what]
+                "sn_cells": L.STC_EXPORT_SN_CELLS, "sn_tasks": L.STC_EXPORT_SN_TASKS,
+                "sn_dev_cells": L.STC_EXPORT_SN_DEV_CELLS, "sn_dev_tasks": L.STC_EXPORT_SN_DEV_TASKS,
+                "sn_dev_upds": L.STC_EXPORT_SN_DEV_UPDS, "sn_dev_maps": L.STC_EXPORT_SN_DEV_MAPS,
+                "sn_value_map": L.STC_EXPORT_SN_VALUE_MAP, "sn_csc_map": L.STC_EXPORT_SN_CSC_MAP}[what]
         a = L.stc_plan_export(self.h, code)
         if what == "tiles":
             return a.reshape(-1, 9)
@@ -97,6 +100,10 @@ class Plan:
             return a.reshape(-1, 8, 2)
         if what in ("tasks", "sn_nodes", "sn_cells", "sn_tasks"):
             return a.reshape(-1, 4)
+        if what in ("sn_dev_cells", "sn_dev_upds"):
+            return a.reshape(-1, 7)
+        if what == "sn_dev_tasks":
+            return a.reshape(-1, 8)
         return a
 
     def factor_bytes(self, batch: int = 1) -> int:

@@ -1304,7 +1304,13 @@ static int plan_export_impl(const stc_plan* P, int what, void* buf, size_t* byte
         case STC_EXPORT_SN_NODES:
         case STC_EXPORT_SN_ROWS:
         case STC_EXPORT_SN_CELLS:
-        case STC_EXPORT_SN_TASKS: {
+        case STC_EXPORT_SN_TASKS:
+        case STC_EXPORT_SN_DEV_CELLS:
+        case STC_EXPORT_SN_DEV_TASKS:
+        case STC_EXPORT_SN_DEV_UPDS:
+        case STC_EXPORT_SN_DEV_MAPS:
+        case STC_EXPORT_SN_VALUE_MAP:
+        case STC_EXPORT_SN_CSC_MAP: {
             const stc::SnPlan& S = P->supernodal();
             const int64_t nsn = (int64_t)S.first.size() - 1;
             if (what == STC_EXPORT_SN_NODES) {
@@ -1316,8 +1322,29 @@ static int plan_export_impl(const stc_plan* P, int what, void* buf, size_t* byte
                 tmp.assign(S.rows.begin(), S.rows.end());
             } else if (what == STC_EXPORT_SN_CELLS) {
                 tmp.assign(S.cells.begin(), S.cells.end());
-            } else {
+            } else if (what == STC_EXPORT_SN_TASKS) {
                 tmp.assign(S.tasks.begin(), S.tasks.end());
+            } else if (what == STC_EXPORT_SN_DEV_CELLS) {
+                for (const stc::SnDevCell& c : S.dcells) {
+                    const int64_t f[7] = {c.off, c.ld, c.h, c.w, c.I, c.J, c.nslices};
+                    tmp.insert(tmp.end(), f, f + 7);
+                }
+            } else if (what == STC_EXPORT_SN_DEV_TASKS) {
+                for (const stc::SnDevTask& t : S.dtasks) {
+                    const int64_t f[8] = {t.kind, t.cell, t.diag, t.ubeg, t.uend, t.rs0, t.rs1, t.slice};
+                    tmp.insert(tmp.end(), f, f + 8);
+                }
+            } else if (what == STC_EXPORT_SN_DEV_UPDS) {
+                for (const stc::SnDevUpd& u : S.dupds) {
+                    const int64_t f[7] = {u.a, u.b, u.ar0, u.ar1, u.rmap, u.cmap, u.klen};
+                    tmp.insert(tmp.end(), f, f + 7);
+                }
+            } else if (what == STC_EXPORT_SN_DEV_MAPS) {
+                tmp.assign(S.maps.begin(), S.maps.end());
+            } else if (what == STC_EXPORT_SN_VALUE_MAP) {
+                tmp.assign(S.value_map.begin(), S.value_map.end());
+            } else {
+                tmp.assign(S.csc_map.begin(), S.csc_map.end());
             }
             src = tmp.data(); sz = tmp.size() * 8;
             break;

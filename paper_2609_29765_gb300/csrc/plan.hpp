@@ -2,6 +2,7 @@
 // and the CUDA kernels (replay.cu).  Not part of the public ABI (include/stc.h).
 #pragma once
 #include <cstdint>
+#include <functional>
 #include <map>
 #include <memory>
 #include <mutex>
@@ -179,6 +180,31 @@ struct TaskSet {
 // A cell (I, J, r0, r1) is the run [r0, r1) of column supernode I's rows owned by row
 // supernode J; cells of I are cells[cptr[I] .. cptr[I+1]), the diagonal cell first.
 enum : int32_t { SN_FACTOR = 0, SN_TRSM = 1, SN_UPDATE = 2 };
+enum : int32_t { SN_T_DIAG = 0, SN_T_OFF = 1 };
+constexpr int kSnSliceH = 64;
+struct SnDevCell {
+    int64_t off;     // arena offset of the cell's first row (column 0 of its supernode)
+    int32_t ld;      // rows of the column supernode's panel (leading dimension)
+    int32_t h, w;    // rows of the cell, columns of its supernode
+    int32_t I, J;    // column supernode, row supernode
+    int32_t nslices; // device tasks that write it
+};
+struct SnDevTask {
+    int32_t kind;    // SN_T_DIAG or SN_T_OFF
+    int32_t cell;    // target cell
+    int32_t diag;    // diagonal cell of the target's column supernode
+    int32_t ubeg, uend;
+    int32_t rs0, rs1;  // rows of the target cell written
+    int32_t slice;
+};
+struct SnDevUpd {
+    int32_t a, b;      // source cells (K,I) and (J,I); a == b for a diagonal target
+    int32_t ar0, ar1;  // rows of a used
+    int32_t rmap;      // offset in maps: target row of each row of a (from row 0 of a)
+    int32_t cmap;      // offset in maps: target column of each row of b
+    int32_t klen;      // inner length (columns of supernode I)
+    int32_t pad;
+};
 struct SnPlan {
     std::vector<int32_t> first;
     std::vector<int64_t> rptr;
@@ -192,6 +218,20 @@ struct SnPlan {
     std::vector<int32_t> tasks;
     int64_t stored = 0;          // lower-trapezoid entries of all panels
     int64_t zeros = 0;           // of which structurally zero (relaxation)
+
+    // Device form (the executor's input; the same shape as the tile route's tasks): one
+    // task per diagonal cell (its updates, then POTRF) and per row slice of <= kSnSliceH
+    // rows of an off-diagonal cell (its updates, then the TRSM against the diagonal
+    // cell), in left-looking order.  An update subtracts A B^T, A = rows [ar0, ar1) of
+    // cell a, B = all rows of cell b, inner dimension the klen columns of their column
+    // supernode, from the target at rows rmap[i] (cell-local) and columns cmap[j]
+    // (columns of the target's column supernode); a diagonal task keeps the lower part.
+    std::vector<SnDevCell> dcells;
+    std::vector<SnDevTask> dtasks;
+    std::vector<SnDevUpd> dupds;
+    std::vector<int16_t> maps;
+    std::vector<int64_t> value_map;  // per A entry: arena offset (permuted lower entry)
+    std::vector<int64_t> csc_map;    // per structural L entry: arena offset
 };
 
 }  // namespace stc
@@ -244,6 +284,9 @@ struct stc_plan {
     mutable std::unique_ptr<stc::SnPlan> sn;
     mutable std::mutex sn_mu;
     const stc::SnPlan& supernodal() const;
+    void build_device_form(stc::SnPlan& S, const std::vector<int32_t>& snof,
+                           const std::vector<std::vector<int32_t>>& byrow,
+                           const std::function<int32_t(int32_t, int32_t)>& cell_of) const;
 
     int tile_id(int64_t I, int64_t J) const;  // -1 if not active
     // built on demand (host); bl_order: queue by bottom level (longest path to the end of

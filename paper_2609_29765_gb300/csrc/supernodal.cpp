@@ -18,6 +18,7 @@
 //     FACTOR (POTRF) of J's diagonal cell, then the TRSM of each cell below it.
 // Only the host plan exists: the plans still execute on the semisparse tile route.
 #include <algorithm>
+#include <functional>
 #include <memory>
 #include <mutex>
 #include <stdexcept>
@@ -169,6 +170,133 @@ const stc::SnPlan& stc_plan::supernodal() const {
         for (int32_t c = S->cptr[J] + 1; c < S->cptr[J + 1]; ++c)
             S->tasks.insert(S->tasks.end(), {stc::SN_TRSM, c, -1, -1});
     }
+    build_device_form(*S, snof, byrow, cell_of);
     sn = std::move(S);
     return *sn;
+}
+
+void stc_plan::build_device_form(stc::SnPlan& S, const vector<int32_t>& snof,
+                                 const vector<vector<int32_t>>& byrow,
+                                 const std::function<int32_t(int32_t, int32_t)>& cell_of) const {
+    const int32_t nsn = (int32_t)S.first.size() - 1;
+    const int32_t ncell = (int32_t)(S.cells.size() / 4);
+    auto nrows = [&](int32_t s) { return (int32_t)(S.rptr[s + 1] - S.rptr[s]); };
+    auto width = [&](int32_t s) { return S.first[s + 1] - S.first[s]; };
+    auto cell_rows = [&](int32_t c) {  // global row indices of cell c
+        const int32_t I = S.cells[4 * c];
+        return S.rows.data() + S.rptr[I] + S.cells[4 * c + 2];
+    };
+    auto height = [&](int32_t c) { return S.cells[4 * c + 3] - S.cells[4 * c + 2]; };
+    S.dcells.resize(ncell);
+    for (int32_t c = 0; c < ncell; ++c) {
+        const int32_t I = S.cells[4 * c], h = height(c);
+        stc::SnDevCell& d = S.dcells[c];
+        d.off = S.off[I] + S.cells[4 * c + 2];
+        d.ld = nrows(I);
+        d.h = h;
+        d.w = width(I);
+        d.I = I;
+        d.J = S.cells[4 * c + 1];
+        d.nslices = (I == d.J) ? 1 : (h + stc::kSnSliceH - 1) / stc::kSnSliceH;
+    }
+    // column map of a source cell (J,I): its rows as columns of J (one per cell)
+    vector<int32_t> cmap_of(ncell, -1);
+    auto cmap = [&](int32_t c) {
+        if (cmap_of[c] < 0) {
+            const int32_t J = S.cells[4 * c + 1];
+            cmap_of[c] = (int32_t)S.maps.size();
+            const int32_t* r = cell_rows(c);
+            for (int32_t i = 0; i < height(c); ++i) S.maps.push_back((int16_t)(r[i] - S.first[J]));
+        }
+        return cmap_of[c];
+    };
+    for (int32_t J = 0; J < nsn; ++J) {
+        const int32_t dJ = S.cptr[J];
+        // diagonal cell: every (J,I) SYRK-like update, then POTRF
+        stc::SnDevTask t{};
+        t.kind = stc::SN_T_DIAG; t.cell = dJ; t.diag = dJ; t.rs0 = 0; t.rs1 = width(J); t.slice = 0;
+        t.ubeg = (int32_t)S.dupds.size();
+        for (int32_t cJI : byrow[J]) {
+            stc::SnDevUpd u{};
+            u.a = cJI; u.b = cJI; u.ar0 = 0; u.ar1 = height(cJI);
+            u.cmap = cmap(cJI);
+            u.rmap = u.cmap;
+            u.klen = width(S.cells[4 * cJI]);
+            S.dupds.push_back(u);
+        }
+        t.uend = (int32_t)S.dupds.size();
+        S.dtasks.push_back(t);
+        // off-diagonal cells (K,J): row slices, GEMM-like updates from every I with cells
+        // (K,I) and (J,I), then TRSM
+        for (int32_t cKJ = S.cptr[J] + 1; cKJ < S.cptr[J + 1]; ++cKJ) {
+            const int32_t K = S.cells[4 * cKJ + 1], h = height(cKJ);
+            const int32_t* tr = cell_rows(cKJ);
+            // per source I: the cell (K,I), its row map into (K,J), and (J,I)
+            struct Src { int32_t cKI, cJI, rmap, klen; };
+            vector<Src> srcs;
+            for (int32_t cJI : byrow[J]) {
+                const int32_t I = S.cells[4 * cJI];
+                const int32_t cKI = cell_of(I, K);
+                if (cKI < 0) continue;
+                Src x{cKI, cJI, (int32_t)S.maps.size(), width(I)};
+                const int32_t* r = cell_rows(cKI);
+                for (int32_t i = 0, q = 0; i < height(cKI); ++i) {
+                    while (q < h && tr[q] < r[i]) ++q;
+                    if (q >= h || tr[q] != r[i]) throw std::logic_error("supernodal row map: not a subset");
+                    S.maps.push_back((int16_t)q);
+                }
+                srcs.push_back(x);
+            }
+            const int32_t nsl = S.dcells[cKJ].nslices;
+            for (int32_t sl = 0; sl < nsl; ++sl) {
+                stc::SnDevTask o{};
+                o.kind = stc::SN_T_OFF; o.cell = cKJ; o.diag = dJ; o.slice = sl;
+                o.rs0 = sl * stc::kSnSliceH; o.rs1 = std::min(h, o.rs0 + stc::kSnSliceH);
+                o.ubeg = (int32_t)S.dupds.size();
+                for (const Src& x : srcs) {
+                    const int16_t* m = S.maps.data() + x.rmap;
+                    const int32_t hk = height(x.cKI);
+                    const int32_t a0 = (int32_t)(std::lower_bound(m, m + hk, (int16_t)o.rs0) - m);
+                    const int32_t a1 = (int32_t)(std::lower_bound(m, m + hk, (int16_t)o.rs1) - m);
+                    if (a0 >= a1) continue;
+                    stc::SnDevUpd u{};
+                    u.a = x.cKI; u.b = x.cJI; u.ar0 = a0; u.ar1 = a1;
+                    u.rmap = x.rmap; u.cmap = cmap(x.cJI); u.klen = x.klen;
+                    S.dupds.push_back(u);
+                }
+                o.uend = (int32_t)S.dupds.size();
+                S.dtasks.push_back(o);
+            }
+        }
+    }
+    // value and CSC maps into the arena
+    vector<int64_t> iperm(n);
+    for (int64_t k = 0; k < n; ++k) iperm[perm[k]] = k;
+    auto arena_off = [&](int64_t r, int64_t c) -> int64_t {  // r >= c, permuted
+        const int32_t s = snof[c];
+        const int32_t* b = S.rows.data() + S.rptr[s];
+        const int32_t* e = S.rows.data() + S.rptr[s + 1];
+        const int32_t* x = std::lower_bound(b, e, (int32_t)r);
+        if (x == e || *x != r) throw std::logic_error("entry outside the supernodal panels");
+        return S.off[s] + (x - b) + (c - S.first[s]) * (int64_t)(e - b);
+    };
+    S.value_map.resize(nnzA);
+    for (int64_t p = 0; p < nnzA; ++p) {
+        const int64_t a = iperm[arow[p]], b = iperm[acol[p]];
+        S.value_map[p] = arena_off(std::max(a, b), std::min(a, b));
+    }
+    // a column's structure is an ascending subset of its supernode's rows: one merge walk
+    S.csc_map.resize(Lp[n]);
+    for (int32_t s = 0; s < nsn; ++s) {
+        const int32_t* R = S.rows.data() + S.rptr[s];
+        const int64_t m = nrows(s);
+        for (int64_t j = S.first[s]; j < S.first[s + 1]; ++j) {
+            int64_t x = 0;
+            for (int64_t q = Lp[j]; q < Lp[j + 1]; ++q) {
+                while (x < m && R[x] < Li[q]) ++x;
+                if (x >= m || R[x] != Li[q]) throw std::logic_error("entry outside the supernodal panels");
+                S.csc_map[q] = S.off[s] + x + (j - S.first[s]) * m;
+            }
+        }
+    }
 }

@@ -14,7 +14,8 @@ from paper_2609_29765_gb300 import inputs as I
 from paper_2609_29765_gb300.api import Plan
 
 EXPORTS = ["perm", "etree", "Lp", "Li", "tiles", "aind", "tasks", "value_map", "tile_offsets",
-           "chunk_extents", "sn_nodes", "sn_rows", "sn_cells", "sn_tasks"]
+           "chunk_extents", "sn_nodes", "sn_rows", "sn_cells", "sn_tasks", "sn_dev_cells", "sn_dev_tasks",
+           "sn_dev_upds", "sn_dev_maps", "sn_value_map", "sn_csc_map"]
 
 
 @pytest.fixture(scope="module", autouse=True)

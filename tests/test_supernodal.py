@@ -247,3 +247,61 @@ def test_supernodal_random_patterns(seed):
     got = np.concatenate([M[snof[j]][np.searchsorted(R[snof[j]], F.Li[F.Lp[j]:F.Lp[j + 1]]), j - nodes[snof[j], 0]]
                           for j in range(n)])
     assert np.max(np.abs(got - Lx)) <= 1e-12 * np.max(np.abs(Lx))
+    got2 = _execute_device_form(n, P, Ax)
+    assert np.max(np.abs(got2 - Lx)) <= 1e-12 * np.max(np.abs(Lx))
+
+
+def _execute_device_form(n, P, values):
+    """Run the supernodal plan's device form with numpy, task by task in queue order,
+    as a supernodal executor would: load the target rows, subtract every update through
+    its row and column maps, then POTRF (diagonal cell) or TRSM (off-diagonal slice)."""
+    cells = P.export("sn_dev_cells")
+    tasks = P.export("sn_dev_tasks")
+    upds = P.export("sn_dev_upds")
+    maps = P.export("sn_dev_maps")
+    nodes = P.export("sn_nodes")
+    arena = np.zeros(int(nodes[-1, 3] + nodes[-1, 1] * nodes[-1, 2]) + 4)
+    arena[P.export("sn_value_map")] = values
+
+    def view(c):  # cell c as an h x w matrix view into the arena
+        off, ld, h, w = cells[c, :4]
+        return np.lib.stride_tricks.as_strided(arena[off:], shape=(h, w), strides=(8, 8 * ld))
+
+    for kind, c, d, ub, ue, rs0, rs1, _ in tasks:
+        X = view(c)[rs0:rs1].copy()
+        for a, b, ar0, ar1, rmap, cmap, klen in upds[ub:ue]:
+            assert cells[a, 3] == klen and cells[b, 3] == klen and cells[a, 4] == cells[b, 4]
+            U = view(a)[ar0:ar1] @ view(b).T
+            rr = maps[rmap + ar0:rmap + ar1] - rs0
+            cc = maps[cmap:cmap + cells[b, 2]]
+            assert np.all((rr >= 0) & (rr < rs1 - rs0)) and np.all((cc >= 0) & (cc < cells[c, 3]))
+            if kind == 0:
+                U = np.where(rr[:, None] >= cc[None, :], U, 0.0)
+            np.subtract.at(X, (rr[:, None], cc[None, :]), U)
+        if kind == 0:
+            S = np.tril(X)
+            X = np.linalg.cholesky(S + np.tril(S, -1).T)
+        else:
+            Ljj = view(d)
+            X = np.linalg.solve(np.tril(Ljj), X.T).T
+        view(c)[rs0:rs1] = X
+    return arena[P.export("sn_csc_map")]
+
+
+@pytest.mark.parametrize("case", CASES, ids=lambda c: c[0])
+def test_supernodal_device_form_reproduces_oracle(case):
+    name, Ap, Ai, Ax, kw = case
+    n, P = _plan(case)
+    got = _execute_device_form(n, P, Ax)
+    F = O.OracleFactor(n, Ap, Ai, P.export("perm"))
+    Lx, info = F.factor(Ax)
+    assert info == 0
+    assert np.max(np.abs(got - Lx)) <= 1e-12 * np.max(np.abs(Lx)), name
+    # off-diagonal slices hold at most 64 rows, every cell fits 128 x 128
+    cells = P.export("sn_dev_cells")
+    tasks = P.export("sn_dev_tasks")
+    off = tasks[:, 0] == 1
+    assert np.all(tasks[off, 6] - tasks[off, 5] <= 64)
+    assert np.all(cells[:, 2] <= 128) and np.all(cells[:, 3] <= 128)
+    # one task per diagonal cell and per slice of each off-diagonal cell
+    assert len(tasks) == cells[:, 6].sum()
