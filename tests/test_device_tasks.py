@@ -259,3 +259,41 @@ def test_queue_order_is_topological():
             if tk[0] == POTRF:
                 slices_of_tile = [j for j, t2 in enumerate(R.tasks) if t2[1] == tk[1] and t2[0] == SYRK]
                 assert len(slices_of_tile) == tk[9] and all(j < i for j in slices_of_tile)
+
+
+def _spd_from_pattern(n, rows, cols, seed):
+    import scipy.sparse as sp
+    rng = np.random.default_rng(seed)
+    M = sp.coo_matrix((rng.uniform(-1, 1, len(rows)), (rows, cols)), shape=(n, n)).tocsc()
+    M = M + M.T
+    M = M + sp.diags(np.asarray(abs(M).sum(axis=1)).ravel() + 1.0)
+    return I.lower_csc(M)
+
+
+EDGE = [
+    ("n=1", 1, [], []),
+    ("n=2", 2, [1], [0]),
+    ("diagonal", 50, [], []),
+    ("n=7 single ragged tile", 7, [3, 6, 5], [0, 2, 1]),
+    ("dense", 40, *[list(x) for x in np.tril_indices(40, -1)]),
+    ("n=64 tridiagonal (multiple of n_b)", 64, list(range(1, 64)), list(range(63))),
+    ("disconnected blocks", 30, [1, 2, 20, 25], [0, 1, 18, 19]),
+    ("one dense last row", 33, [32] * 32, list(range(32))),
+]
+
+
+@pytest.mark.parametrize("nb", [8, 32, 128])
+@pytest.mark.parametrize("edge", EDGE, ids=lambda e: e[0])
+def test_edge_patterns(edge, nb):
+    # degenerate sizes and structures: both routes, two orderings, three slice counts
+    name, n, r, c = edge
+    Ap, Ai, Ax = _spd_from_pattern(n, np.array(r, dtype=int), np.array(c, dtype=int), 0)
+    for route in ("semisparse", "dense"):
+        for ordering in ("natural", "rcm"):
+            P = Plan(n, Ap, Ai, nb=nb, route=route, ordering=ordering)
+            F = O.OracleFactor(n, Ap, Ai, P.export("perm"))
+            Lo, info = F.factor(Ax)
+            assert info == 0
+            for slices, bl in ((1, False), (2, False), (8, True)):
+                got = Replay(P, slices, bl).run(Ax)
+                assert np.max(np.abs(got - Lo)) <= 1e-12 * np.max(np.abs(Lo)), (name, route, ordering, slices)
