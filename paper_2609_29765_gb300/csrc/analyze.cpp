@@ -623,7 +623,6 @@ stc::TaskSet* stc_plan::taskset(int32_t slices, bool bl_order) {
     vector<Meta> meta;
     vector<vector<int32_t>> producers(tiles.size());
     ts->nfinal.assign(tiles.size(), 0);
-    vector<int> ca, cb;
     // executed FMAs of the chunked products, with the same extent skipping as the kernel
     auto ext = [&](const stc::DTile& T, int s0, int s1, int& lo, int& hi) {
         if (T.xoff < 0) { lo = 0; hi = NB; return; }
@@ -633,22 +632,23 @@ stc::TaskSet* stc_plan::taskset(int32_t slices, bool bl_order) {
             hi = std::max<int>(hi, cext[2 * (T.xoff + q) + 1]);
         }
     };
-    auto inner_range = [&](const stc::DUpd& u, int k0, int K, bool b, int& s0, int& s1) {
+    auto inner_range = [&](const vector<int16_t>& im, const stc::DUpd& u, int k0, int K, bool b, int& s0,
+                           int& s1) {
         if (u.kmap < 0) {
             s0 = (b ? u.kb0 : u.ka0) + k0;
             s1 = s0 + K - 1;
         } else {
-            s0 = ts->imap[2 * (u.kmap + k0) + (b ? 1 : 0)];
-            s1 = ts->imap[2 * (u.kmap + k0 + K - 1) + (b ? 1 : 0)];
+            s0 = im[2 * (u.kmap + k0) + (b ? 1 : 0)];
+            s1 = im[2 * (u.kmap + k0 + K - 1) + (b ? 1 : 0)];
         }
     };
-    auto syrk_cost = [&](const stc::DUpd& u, int r0, int d0, int rb) {  // rows [d0,rb), cols [r0,rb)
+    auto syrk_cost = [&](const vector<int16_t>& im, const stc::DUpd& u, int r0, int d0, int rb) {  // rows [d0,rb), cols [r0,rb)
         const stc::DTile& A = tiles[u.a];
         double c = 0.0;
         for (int k0 = 0; k0 < u.klen; k0 += kChunk) {
             const int K = std::min(kChunk, u.klen - k0);
             int s0, s1, lo, hi;
-            inner_range(u, k0, K, false, s0, s1);
+            inner_range(im, u, k0, K, false, s0, s1);
             ext(A, s0, s1, lo, hi);
             const int e0 = std::max(d0, lo), e1 = std::min(rb, hi);
             if (e0 >= e1) continue;
@@ -657,16 +657,16 @@ stc::TaskSet* stc_plan::taskset(int32_t slices, bool bl_order) {
         }
         return c;
     };
-    auto gemm_cost = [&](const stc::DUpd& u, const stc::DTile& O) {
+    auto gemm_cost = [&](const vector<int16_t>& im, const stc::DUpd& u, const stc::DTile& O) {
         const stc::DTile& A = tiles[u.a];
         const stc::DTile& B = tiles[u.b];
         double c = 0.0;
         for (int k0 = 0; k0 < u.klen; k0 += kChunk) {
             const int K = std::min(kChunk, u.klen - k0);
             int s0, s1, alo, ahi, blo, bhi;
-            inner_range(u, k0, K, false, s0, s1);
+            inner_range(im, u, k0, K, false, s0, s1);
             ext(A, s0, s1, alo, ahi);
-            inner_range(u, k0, K, true, s0, s1);
+            inner_range(im, u, k0, K, true, s0, s1);
             ext(B, s0, s1, blo, bhi);
             const int e0 = std::max(u.ra0, alo), e1 = std::min(u.ra1, ahi);
             int c0 = u.oc0, c1 = u.oc1;
@@ -698,7 +698,17 @@ stc::TaskSet* stc_plan::taskset(int32_t slices, bool bl_order) {
         double w = D.sw, kd = std::min<double>(D.kd, w - 1);
         return (D.kind == stc::TILE_DIAG_BAND) ? w * (kd + 1) * (kd + 1) / 2 : w * w * w / 6;
     };
-    for (int64_t k = 0; k < NT; ++k) {
+    // tasks of each block column are built independently (in parallel), then laid out in
+    // block-column order with their update and map offsets shifted
+    struct Local {
+        vector<stc::DTask> tasks;
+        vector<Meta> meta;
+        vector<stc::DUpd> upds;
+        vector<int16_t> imap;
+    };
+    vector<Local> loc(NT);
+    auto build_col = [&](int64_t k, Local& Lk) {
+        vector<int> ca, cb;
         const int32_t dk = diag_tile[k];
         const stc::DTile& D = tiles[dk];
         const bool has_syrk = rowstart[k + 1] > rowstart[k];
@@ -707,23 +717,22 @@ stc::TaskSet* stc_plan::taskset(int32_t slices, bool bl_order) {
             stc::DTask t{};
             Meta mt;
             t.kind = stc::TASK_DIAG; t.tile = dk; t.diag = dk;
-            t.ubeg = (int32_t)ts->upds.size();
+            t.ubeg = (int32_t)Lk.upds.size();
             for (int32_t a = rowstart[k]; a < rowstart[k + 1]; ++a) {
                 const int32_t at = rowtiles[a];
                 const stc::DTile& A = tiles[at];
                 stc::DUpd u{};
                 u.a = at; u.b = at; u.kmap = -1; u.klen = A.sw; u.ka0 = 0; u.kb0 = 0;
                 u.ra0 = A.r0; u.ra1 = A.r1; u.oc0 = A.r0; u.oc1 = A.r1;
-                ts->upds.push_back(u);
-                mt.srcs.push_back(at); mt.nsrc.push_back(1); mt.ucost.push_back(syrk_cost(u, A.r0, A.r0, A.r1));
+                Lk.upds.push_back(u);
+                mt.srcs.push_back(at); mt.nsrc.push_back(1); mt.ucost.push_back(syrk_cost(Lk.imap, u, A.r0, A.r0, A.r1));
             }
-            t.uend = (int32_t)ts->upds.size();
+            t.uend = (int32_t)Lk.upds.size();
             t.rs0 = 0; t.rs1 = NB; t.tr0 = 0; t.tr1 = NB;
             mt.fcost = potrf_cost(D);
             mt.npub = diag_groups(D);
-            producers[dk].push_back((int32_t)tasks.size());
-            tasks.push_back(t);
-            meta.push_back(mt);
+                        Lk.tasks.push_back(t);
+            Lk.meta.push_back(mt);
             ts->nfinal[dk] = diag_groups(D);
         } else {
             // TASK_SYRK row slices of (k,k), then TASK_POTRF.  Row r of the lower
@@ -754,7 +763,7 @@ stc::TaskSet* stc_plan::taskset(int32_t slices, bool bl_order) {
                 Meta mt;
                 t.kind = stc::TASK_SYRK; t.tile = dk; t.diag = dk;
                 t.rs0 = rs0; t.rs1 = rs1; t.tr0 = rs0; t.tr1 = rs1;
-                t.ubeg = (int32_t)ts->upds.size();
+                t.ubeg = (int32_t)Lk.upds.size();
                 for (int32_t a = rowstart[k]; a < rowstart[k + 1]; ++a) {
                     const int32_t at = rowtiles[a];
                     const stc::DTile& A = tiles[at];
@@ -763,27 +772,25 @@ stc::TaskSet* stc_plan::taskset(int32_t slices, bool bl_order) {
                     stc::DUpd u{};
                     u.a = at; u.b = at; u.kmap = -1; u.klen = A.sw; u.ka0 = 0; u.kb0 = 0;
                     u.ra0 = ra; u.ra1 = rb; u.oc0 = A.r0; u.oc1 = rb;
-                    ts->upds.push_back(u);
+                    Lk.upds.push_back(u);
                     mt.srcs.push_back(at); mt.nsrc.push_back(1);
-                    mt.ucost.push_back(syrk_cost(u, A.r0, ra, rb));
+                    mt.ucost.push_back(syrk_cost(Lk.imap, u, A.r0, ra, rb));
                 }
-                t.uend = (int32_t)ts->upds.size();
+                t.uend = (int32_t)Lk.upds.size();
                 if (t.uend == t.ubeg) continue;  // rows untouched by any SYRK
-                producers[dk].push_back((int32_t)tasks.size());
-                tasks.push_back(t);
-                meta.push_back(mt);
+                                Lk.tasks.push_back(t);
+                Lk.meta.push_back(mt);
                 ++nsl;
             }
             stc::DTask p{};
             Meta mp;
-            p.kind = stc::TASK_POTRF; p.tile = dk; p.diag = dk; p.ubeg = p.uend = (int32_t)ts->upds.size();
+            p.kind = stc::TASK_POTRF; p.tile = dk; p.diag = dk; p.ubeg = p.uend = (int32_t)Lk.upds.size();
             p.rs0 = 0; p.rs1 = NB; p.tr0 = 0; p.tr1 = NB; p.own_wait = nsl;
             mp.final_tile = nsl > 0 ? dk : -1;
             mp.fcost = potrf_cost(D);
             mp.npub = diag_groups(D);
-            producers[dk].push_back((int32_t)tasks.size());
-            tasks.push_back(p);
-            meta.push_back(mp);
+                        Lk.tasks.push_back(p);
+            Lk.meta.push_back(mp);
             ts->nfinal[dk] = nsl + diag_groups(D);
         }
         // OFF(m,k) row slices: GEMM from every n in N(k) & N(m), n < k, then TRSM
@@ -799,7 +806,7 @@ stc::TaskSet* stc_plan::taskset(int32_t slices, bool bl_order) {
                 Meta ms;
                 s.kind = stc::TASK_OFF; s.tile = o; s.diag = dk; s.slice = rs0 / h;
                 s.rs0 = rs0; s.rs1 = rs1; s.tr0 = tr0; s.tr1 = tr1;
-                s.ubeg = (int32_t)ts->upds.size();
+                s.ubeg = (int32_t)Lk.upds.size();
                 int32_t a = rowstart[k], b = rowstart[m];
                 while (a < rowstart[k + 1] && b < rowstart[m + 1]) {
                     const int32_t kt = rowtiles[a], mtile = rowtiles[b];
@@ -812,7 +819,7 @@ stc::TaskSet* stc_plan::taskset(int32_t slices, bool bl_order) {
                     stc::DUpd u{};
                     u.a = mtile; u.b = kt;
                     u.ra0 = std::max(tr0, A.r0); u.ra1 = std::min(tr1, A.r1);
-                    size_t imap_mark = ts->imap.size();
+                    size_t imap_mark = Lk.imap.size();
                     if (A.c0 >= 0 && B.c0 >= 0) {
                         const int lo = std::max(A.c0, B.c0), hi = std::min(A.c0 + A.sw, B.c0 + B.sw);
                         u.kmap = -1; u.klen = std::max(0, hi - lo);
@@ -820,11 +827,11 @@ stc::TaskSet* stc_plan::taskset(int32_t slices, bool bl_order) {
                     } else {
                         stored_cols(*this, A, ca);
                         stored_cols(*this, B, cb);
-                        u.kmap = (int32_t)(ts->imap.size() / 2);
+                        u.kmap = (int32_t)(Lk.imap.size() / 2);
                         int x = 0, y = 0, len = 0;
                         while (x < (int)ca.size() && y < (int)cb.size()) {
                             if (ca[x] == cb[y]) {
-                                ts->imap.push_back((int16_t)x); ts->imap.push_back((int16_t)y);
+                                Lk.imap.push_back((int16_t)x); Lk.imap.push_back((int16_t)y);
                                 ++len; ++x; ++y;
                             } else if (ca[x] < cb[y]) ++x; else ++y;
                         }
@@ -837,25 +844,61 @@ stc::TaskSet* stc_plan::taskset(int32_t slices, bool bl_order) {
                         u.oc0 = 0; u.oc1 = O.sw;
                     }
                     if (u.klen <= 0 || u.ra0 >= u.ra1 || u.oc0 >= u.oc1) {
-                        ts->imap.resize(imap_mark);
+                        Lk.imap.resize(imap_mark);
                         continue;
                     }
-                    ts->upds.push_back(u);
+                    Lk.upds.push_back(u);
                     ms.srcs.push_back(mtile); ms.srcs.push_back(kt); ms.nsrc.push_back(2);
-                    ms.ucost.push_back(gemm_cost(u, O));
+                    ms.ucost.push_back(gemm_cost(Lk.imap, u, O));
                 }
-                s.uend = (int32_t)ts->upds.size();
+                s.uend = (int32_t)Lk.upds.size();
                 ms.final_tile = dk;
                 ms.fcost = trsm_cost(O, tr0, tr1);
                 ms.trsm = true;
                 ms.npub = (O.sw + kPanel - 1) / kPanel;
-                producers[o].push_back((int32_t)tasks.size());
-                tasks.push_back(s);
-                meta.push_back(ms);
+                                Lk.tasks.push_back(s);
+                Lk.meta.push_back(ms);
                 for (int q = 0; q * kPanel < O.sw; ++q)
                     ts->nfinal[o] |= (int32_t)(1u << (q * stc::kMaxSlices + s.slice));
             }
         }
+    };
+    {
+        int nth = opt.host_threads;
+        if (nth <= 0) nth = int(std::min<unsigned>(32, std::max<unsigned>(1, std::thread::hardware_concurrency())));
+        const int64_t per = std::max<int64_t>(1, NT / (int64_t(nth) * 16));
+        parallel_chunks(nth, (NT + per - 1) / per, [&](int64_t c, int) {
+            for (int64_t k = c * per; k < std::min<int64_t>(NT, (c + 1) * per); ++k) build_col(k, loc[k]);
+        });
+    }
+    {
+        size_t nt_ = 0, nu = 0, nm = 0;
+        for (const Local& Lk : loc) {
+            nt_ += Lk.tasks.size();
+            nu += Lk.upds.size();
+            nm += Lk.imap.size();
+        }
+        tasks.reserve(nt_);
+        meta.reserve(nt_);
+        ts->upds.reserve(nu);
+        ts->imap.reserve(nm);
+    }
+    for (int64_t k = 0; k < NT; ++k) {
+        Local& Lk = loc[k];
+        const int32_t ubase = (int32_t)ts->upds.size(), mbase = (int32_t)(ts->imap.size() / 2);
+        for (stc::DUpd& u : Lk.upds)
+            if (u.kmap >= 0) u.kmap += mbase;
+        for (size_t i = 0; i < Lk.tasks.size(); ++i) {
+            stc::DTask t = Lk.tasks[i];
+            t.ubeg += ubase;
+            t.uend += ubase;
+            producers[t.tile].push_back((int32_t)tasks.size());
+            tasks.push_back(t);
+            meta.push_back(std::move(Lk.meta[i]));
+        }
+        ts->upds.insert(ts->upds.end(), Lk.upds.begin(), Lk.upds.end());
+        ts->imap.insert(ts->imap.end(), Lk.imap.begin(), Lk.imap.end());
+        Lk = Local();
     }
     // Queue order: earliest start on unbounded workers.  Tiles are published in steps
     // (an off-diagonal slice per TRSM panel, a diagonal tile per kPanel factored
