@@ -39,7 +39,8 @@ constexpr int kMaxNb = 128;
 // Runs f(chunk, worker) for every chunk in [0, nchunks) on up to `threads` threads
 // (worker in [0, threads)); chunks are handed out in increasing order.  Every caller
 // writes each output element from exactly one chunk, so results do not depend on the
-// thread count.  An exception in a worker is rethrown here after all workers joined.
+// thread count (nor on how many threads could be started).  An exception in a worker is
+// rethrown here after all workers joined.
 template <class F>
 void parallel_chunks(int threads, int64_t nchunks, F&& f) {
     const int nt = int(std::max<int64_t>(1, std::min<int64_t>(threads, nchunks)));
@@ -62,13 +63,11 @@ void parallel_chunks(int threads, int64_t nchunks, F&& f) {
         }
     };
     vector<std::thread> pool;
-    pool.reserve(nt - 1);
     try {
+        pool.reserve(nt - 1);
         for (int w = 1; w < nt; ++w) pool.emplace_back(work, w);
     } catch (...) {
-        failed = true;  // could not start a thread: the started ones stop, then rethrow
-        for (auto& th : pool) th.join();
-        throw;
+        // no more threads to be had: the ones started and this thread share the chunks
     }
     work(0);
     for (auto& th : pool) th.join();
