@@ -244,21 +244,45 @@ void order_rcm(int64_t n, const int64_t* Ap, const int64_t* Ai, vector<int64_t>&
 
 // Strict lower part of A_p = P A P^T as row lists: row r holds columns c < r.
 void permuted_rows(int64_t n, const int64_t* Ap, const int64_t* Ai, const vector<int64_t>& iperm,
-                   vector<int64_t>& rp, vector<int32_t>& rc) {
+                   vector<int64_t>& rp, vector<int32_t>& rc, int threads) {
+    // columns in chunks, walked twice (count, then write at offsets prefix-summed in chunk
+    // order, so each row lists its columns in the order of a serial column sweep)
+    const int64_t nch = std::max<int64_t>(1, std::min<int64_t>(int64_t(threads) * 8, n / 2048));
+    const int64_t mem_cap = std::max<int64_t>(1, (int64_t(1) << 30) / (8 * n));
+    const int nw = int(std::min<int64_t>(std::min<int64_t>(threads, nch), mem_cap));
+    vector<vector<std::pair<int32_t, int64_t>>> touch(nch);
+    vector<vector<int64_t>> acc(nw);
+    auto walk = [&](int64_t c, int w, bool fill) {
+        vector<int64_t>& ct = acc[w];
+        if (ct.empty()) ct.assign(n, 0);
+        vector<std::pair<int32_t, int64_t>>& tl = touch[c];
+        if (fill)
+            for (const auto& e : tl) ct[e.first] = e.second;
+        for (int64_t j = c * n / nch; j < (c + 1) * n / nch; ++j)
+            for (int64_t p = Ap[j] + 1; p < Ap[j + 1]; ++p) {
+                const int64_t a = iperm[Ai[p]], b = iperm[j], r = std::max(a, b);
+                if (fill) rc[ct[r]++] = (int32_t)std::min(a, b);
+                else if (ct[r]++ == 0) tl.push_back({(int32_t)r, 0});
+            }
+        for (auto& e : tl) {
+            if (!fill) e.second = ct[e.first];
+            ct[e.first] = 0;
+        }
+    };
+    parallel_chunks(nw, nch, [&](int64_t c, int w) { walk(c, w, false); });
     rp.assign(n + 1, 0);
-    for (int64_t j = 0; j < n; ++j)
-        for (int64_t p = Ap[j] + 1; p < Ap[j + 1]; ++p) {
-            int64_t a = iperm[Ai[p]], b = iperm[j];
-            rp[std::max(a, b) + 1]++;
-        }
+    for (const auto& tl : touch)
+        for (const auto& e : tl) rp[e.first + 1] += e.second;
     for (int64_t i = 0; i < n; ++i) rp[i + 1] += rp[i];
-    rc.assign(rp[n], 0);
-    vector<int64_t> f(rp.begin(), rp.end() - 1);
-    for (int64_t j = 0; j < n; ++j)
-        for (int64_t p = Ap[j] + 1; p < Ap[j + 1]; ++p) {
-            int64_t a = iperm[Ai[p]], b = iperm[j];
-            rc[f[std::max(a, b)]++] = (int32_t)std::min(a, b);
+    vector<int64_t> next(rp.begin(), rp.end() - 1);
+    for (auto& tl : touch)
+        for (auto& e : tl) {
+            const int64_t start = next[e.first];
+            next[e.first] += e.second;
+            e.second = start;
         }
+    rc.assign(rp[n], 0);
+    parallel_chunks(nw, nch, [&](int64_t c, int w) { walk(c, w, true); });
 }
 
 // Liu's elimination tree and the structure of L from row subtrees.  The structure of row
@@ -1094,7 +1118,7 @@ static int analyze_impl(int64_t n, const int64_t* Ap, const int64_t* Ai, const d
     // ---- symbolic factorization ----
     vector<int64_t> rp;
     vector<int32_t> rcv;
-    permuted_rows(n, Ap, Ai, iperm, rp, rcv);
+    permuted_rows(n, Ap, Ai, iperm, rp, rcv, threads);
     symbolic(n, rp, rcv, P->parent, P->Lp, P->Li, threads);
     if (ord == STC_ORDER_AUTO) ord = STC_ORDER_RCM;
     // AUTO without coordinates: keep the natural order when RCM does not reduce the fill
@@ -1102,7 +1126,7 @@ static int analyze_impl(int64_t n, const int64_t* Ap, const int64_t* Ai, const d
         vector<int64_t> idp(n), par2, Lp2;
         stc::RowIndexVec Li2;
         std::iota(idp.begin(), idp.end(), 0);
-        permuted_rows(n, Ap, Ai, idp, rp, rcv);
+        permuted_rows(n, Ap, Ai, idp, rp, rcv, threads);
         symbolic(n, rp, rcv, par2, Lp2, Li2, threads);
         if (Lp2[n] <= P->Lp[n]) {
             P->perm = idp; iperm = idp; P->parent.swap(par2); P->Lp.swap(Lp2); P->Li.swap(Li2);
