@@ -90,10 +90,12 @@ typedef struct stc_options {
     double gate_phi_fill;    /* 0 = default 2.0  */
     double gate_rho_semi;    /* 0 = default 0.15 */
     double gate_sigma_skew;  /* 0 = default 20   */
-    double queue_skew;       /* batched factorize: 0 (default) queues the items in
-                                lockstep (slot = task * batch + item); > 0 queues item b's
-                                tasks as if it started b/batch x queue_skew block-column
-                                periods late (a merged order built once per batch size)  */
+    int32_t replay_ctas;     /* CTAs of the persistent device kernels (factorize, solve,
+                                selected inverse); 0 = chosen from the batch and the SM
+                                count.  1 = serial replay: one CTA executes the task queue
+                                strictly in queue order, the reference schedule that a
+                                parallel run must reproduce bit for bit (race check).   */
+    int32_t reserved1;
 } stc_options;
 
 typedef struct stc_plan stc_plan;

@@ -63,7 +63,7 @@ class stc_options(C.Structure):
                 ("nd_leaf", C.c_int32), ("perm", C.POINTER(C.c_int64)), ("row_slices", C.c_int32),
                 ("host_threads", C.c_int32), ("spin_limit", C.c_int64), ("gate_rho_dense", C.c_double),
                 ("gate_phi_fill", C.c_double), ("gate_rho_semi", C.c_double),
-                ("gate_sigma_skew", C.c_double), ("queue_skew", C.c_double)]
+                ("gate_sigma_skew", C.c_double), ("replay_ctas", C.c_int32), ("reserved1", C.c_int32)]
 
 
 class stc_plan_info(C.Structure):

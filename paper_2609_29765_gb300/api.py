@@ -30,7 +30,7 @@ class Plan:
     """Symbolic plan of one sparsity pattern (lower CSC, original order)."""
 
     def __init__(self, n, colptr, rowind, coords=None, nb=128, route="auto", ordering="auto",
-                 perm=None, nd_leaf=64, row_slices=0, spin_limit=0, queue_skew=0.0, host_threads=0):
+                 perm=None, nd_leaf=64, row_slices=0, spin_limit=0, replay_ctas=0, host_threads=0):
         o = L.stc_options_default()
         o.nb = int(nb)
         o.force_route = ROUTES[route]
@@ -38,7 +38,7 @@ class Plan:
         o.nd_leaf = int(nd_leaf)
         o.row_slices = int(row_slices)
         o.spin_limit = int(spin_limit)
-        o.queue_skew = float(queue_skew)
+        o.replay_ctas = int(replay_ctas)
         o.host_threads = int(host_threads)
         self._perm_keep = None
         if perm is not None:

@@ -1075,6 +1075,7 @@ static int analyze_impl(int64_t n, const int64_t* Ap, const int64_t* Ai, const d
     if (opt.row_slices != 0 && opt.row_slices != 1 && opt.row_slices != 2 && opt.row_slices != 4 &&
         opt.row_slices != 8)
         return STC_ERR_INVALID_ARG;
+    if (opt.replay_ctas < 0) return STC_ERR_INVALID_ARG;
     if (opt.gate_rho_dense == 0) opt.gate_rho_dense = 0.90;
     if (opt.gate_phi_fill == 0) opt.gate_phi_fill = 2.0;
     if (opt.gate_rho_semi == 0) opt.gate_rho_semi = 0.15;

@@ -165,7 +165,6 @@ struct TaskSet {
     double par = 0.0;             // modelled average parallelism (work / makespan)
     double fma = 0.0;             // modelled FMAs (queue-order cost model)
     double fma_exec = 0.0;        // FMAs the kernels execute (exact POTRF count)
-    std::map<int64_t, uint64_t*> d_queue;  // per batch: merged (task << 32 | item) order
     // device copies
     DTask* d_tasks = nullptr;
     DUpd* d_upds = nullptr;

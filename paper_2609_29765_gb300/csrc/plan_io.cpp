@@ -25,7 +25,7 @@ using std::vector;
 namespace {
 
 constexpr char kMagic[8] = {'S', 'T', 'C', 'P', 'L', 'A', 'N', '1'};
-constexpr uint32_t kVersion = 1;
+constexpr uint32_t kVersion = 2;
 constexpr size_t kHeader = 8 + 4 + 4 + 8 + 8;
 
 uint64_t fnv1a(const unsigned char* p, size_t n) {
@@ -107,47 +107,98 @@ struct GetAdapter {  // Reader with the Writer's put/vec names
     template <class T, class A> void vec(vector<T, A>& v) { r.vec(v); }
 };
 
-// Lengths every loaded array must have for the plan's dimensions (the kernels index
-// them without further checks).
+// A loaded plan is handed to kernels that index its arrays without further checks, so
+// every length, index and offset is checked against the plan's dimensions: each tile's
+// whole footprint (from its kind, stored width and band) lies inside the tile area, the
+// partials fit the item stride, every stored-column index, extent, map entry and tile id
+// is in range, perm is a permutation and the etree and L's structure are well formed.
+// The checksum only catches damage in transit; this catches a blob that is intact but
+// inconsistent (edited, or written by a build with another layout).
+bool in(int64_t v, int64_t lo, int64_t hi) { return v >= lo && v < hi; }
+
 bool consistent(const stc_plan& P) {
-    const int64_t n = P.n, nt = P.nt;
+    const int64_t n = P.n, nt = P.nt, nb = P.nb;
     const size_t nT = P.tiles.size();
-    if (n <= 0 || P.nb < 8 || P.nb > stc::kMaxNb || P.nb % 8 || nt != (n + P.nb - 1) / P.nb) return false;
+    if (n <= 0 || nb < 8 || nb > stc::kMaxNb || nb % 8 || nt != (n + nb - 1) / nb) return false;
+    if (P.nnzA < n || P.npartials != nt || P.partial_off < 0 || P.partial_off + P.npartials > P.factor_doubles)
+        return false;
     if ((int64_t)P.perm.size() != n || (int64_t)P.parent.size() != n) return false;
+    {
+        vector<char> seen(n, 0);
+        for (int64_t v : P.perm) {
+            if (!in(v, 0, n) || seen[v]) return false;
+            seen[v] = 1;
+        }
+    }
+    for (int64_t j = 0; j < n; ++j)
+        if (P.parent[j] != -1 && !in(P.parent[j], j + 1, n)) return false;
     if ((int64_t)P.Lp.size() != n + 1 || P.Lp[0] != 0 || (int64_t)P.Li.size() != P.Lp[n]) return false;
+    for (int64_t j = 0; j < n; ++j) {
+        if (P.Lp[j + 1] <= P.Lp[j] || P.Li[P.Lp[j]] != j) return false;  // diagonal first
+        for (int64_t q = P.Lp[j] + 1; q < P.Lp[j + 1]; ++q)
+            if (!in(P.Li[q], P.Li[q - 1] + 1, n)) return false;
+    }
     if (P.nact.size() != nT || P.aoff_struct.size() != nT || P.contig.size() != nT || P.full.size() != nT)
         return false;
+    for (size_t t = 0; t < nT; ++t)
+        if (P.nact[t] < 0 || P.nact[t] > nb || P.aoff_struct[t] < 0 ||
+            (size_t)P.aoff_struct[t] + (size_t)P.nact[t] > P.aind_struct.size())
+            return false;
     if ((int64_t)P.colstart.size() != nt + 1 || (int64_t)P.diag_tile.size() != nt) return false;
-    if ((int64_t)P.rowstart.size() != nt + 1 || P.colstart[nt] != (int32_t)nT) return false;
+    if ((int64_t)P.rowstart.size() != nt + 1 || P.colstart[0] != 0 || P.colstart[nt] != (int32_t)nT) return false;
+    if (P.rowstart[0] != 0 || (size_t)P.rowstart[nt] != P.rowtiles.size()) return false;
+    for (int64_t k = 0; k < nt; ++k)
+        if (P.colstart[k + 1] < P.colstart[k] || P.rowstart[k + 1] < P.rowstart[k]) return false;
     if ((int64_t)P.value_map.size() != P.nnzA || (int64_t)P.vdiag.size() != P.nnzA ||
         (int64_t)P.arow.size() != P.nnzA || (int64_t)P.acol.size() != P.nnzA)
         return false;
-    if ((int64_t)P.csc_map.size() != P.Lp[n] || P.sinv.size() != nT * (size_t)P.nb) return false;
+    for (int64_t e = 0; e < P.nnzA; ++e)
+        if (!in(P.arow[e], 0, n) || !in(P.acol[e], 0, n) || (P.vdiag[e] != 0 && P.vdiag[e] != 1)) return false;
+    if ((int64_t)P.csc_map.size() != P.Lp[n] || P.sinv.size() != nT * (size_t)nb) return false;
+    for (int16_t v : P.sinv)
+        if (!in(v, -1, nb)) return false;
+    for (int16_t v : P.saind)
+        if (!in(v, 0, nb)) return false;
+    for (int16_t v : P.cext)
+        if (!in(v, 0, nb + 1)) return false;
     if (P.route_exec != STC_ROUTE_DENSE && P.route_exec != STC_ROUTE_SEMISPARSE) return false;
     for (const stc::DTile& T : P.tiles) {
-        if (T.off < 0 || T.off >= P.partial_off || T.I < 0 || T.J < 0 || T.I >= nt || T.J >= nt) return false;
-        if (T.sw < 0 || T.sw > P.nb || T.r0 < 0 || T.r1 > P.nb) return false;
-        if (T.aoff >= 0 && (size_t)T.aoff + (size_t)T.sw > P.saind.size()) return false;
-        if (T.xoff >= 0 && 2 * ((size_t)T.xoff + ((size_t)T.sw + stc::kExtW - 1) / stc::kExtW) > P.cext.size())
+        if (!in(T.I, 0, nt) || !in(T.J, 0, nt) || T.I < T.J) return false;
+        if (T.sw < 0 || T.sw > nb || T.r0 < 0 || T.r1 > nb || T.r0 > T.r1) return false;
+        int64_t size;
+        if (T.kind == stc::TILE_OFF) {
+            if (T.I == T.J || T.pd_slot != -1) return false;
+            size = nb * (int64_t)T.sw;
+            if (T.c0 >= 0 ? T.c0 + (int64_t)T.sw > nb : (T.aoff < 0 || (size_t)T.aoff + (size_t)T.sw > P.saind.size()))
+                return false;
+            if (T.xoff >= 0 && 2 * ((size_t)T.xoff + ((size_t)T.sw + stc::kExtW - 1) / stc::kExtW) > P.cext.size())
+                return false;
+        } else if (T.kind == stc::TILE_DIAG_DENSE || T.kind == stc::TILE_DIAG_BAND) {
+            if (T.I != T.J || !in(T.pd_slot, 0, P.npartials) || T.xoff >= 0) return false;
+            if (!in(T.kd, 0, nb)) return false;
+            size = T.kind == stc::TILE_DIAG_DENSE ? nb * nb : nb * (int64_t)(T.kd + 1);
+        } else {
             return false;
+        }
+        if (T.off < 0 || T.off + size > P.partial_off) return false;
     }
     for (int32_t t : P.rowtiles)
-        if (t < 0 || (size_t)t >= nT) return false;
+        if (!in(t, 0, (int64_t)nT)) return false;
     for (int32_t t : P.diag_tile)
-        if (t < 0 || (size_t)t >= nT) return false;
+        if (!in(t, 0, (int64_t)nT) || P.tiles[t].kind == stc::TILE_OFF) return false;
     for (const stc::DSTask& t : P.stasks)
-        if (t.tile < 0 || (size_t)t.tile >= nT || t.diag < 0 || (size_t)t.diag >= nT || t.cbeg < 0 ||
-            t.cend < t.cbeg || (size_t)t.cend > P.scons.size())
+        if (!in(t.tile, 0, (int64_t)nT) || !in(t.diag, 0, (int64_t)nT) || t.cbeg < 0 || t.cend < t.cbeg ||
+            (size_t)t.cend > P.scons.size() || t.r0 < 0 || t.r1 > nb || t.r0 > t.r1)
             return false;
     for (const stc::DSCon& c : P.scons)
-        if (c.ltile < 0 || (size_t)c.ltile >= nT || c.stile < 0 || (size_t)c.stile >= nT) return false;
+        if (!in(c.ltile, 0, (int64_t)nT) || !in(c.stile, 0, (int64_t)nT) || !in(c.mode, 0, 4)) return false;
     for (int64_t v : P.pad_diag)
-        if (v < 0 || v >= P.partial_off) return false;
+        if (!in(v, 0, P.partial_off)) return false;
     for (int64_t v : P.value_map)
-        if (v < 0 || v >= P.partial_off) return false;
+        if (!in(v, 0, P.partial_off)) return false;
     for (int64_t v : P.csc_map)
-        if (v < 0 || v >= P.partial_off) return false;
-    return P.partial_off <= P.factor_doubles;
+        if (!in(v, 0, P.partial_off)) return false;
+    return true;
 }
 
 }  // namespace

@@ -23,6 +23,7 @@
 #include <climits>
 #include <cstdio>
 #include <cstring>
+#include <stdexcept>
 
 #include "plan.hpp"
 
@@ -1601,15 +1602,41 @@ void free_dev(stc_plan* P) {
         if (ts->d_upds) cudaFree(ts->d_upds);
         if (ts->d_imap) cudaFree(ts->d_imap);
         if (ts->d_tiles) cudaFree(ts->d_tiles);
-        for (auto& q : ts->d_queue) cudaFree(q.second);
-        ts->d_queue.clear();
         ts->d_tasks = nullptr; ts->d_upds = nullptr; ts->d_imap = nullptr; ts->d_tiles = nullptr;
         ts->device = -1;
     }
 }
 
+// Host allocation failures while a task set or a device copy is prepared come back as
+// STC_ERR_OUT_OF_MEMORY instead of unwinding through the C ABI.
+template <class F>
+int no_throw(F&& f) {
+    try {
+        return f();
+    } catch (const std::bad_alloc&) {
+        return STC_ERR_OUT_OF_MEMORY;
+    } catch (const std::length_error&) {
+        return STC_ERR_OUT_OF_MEMORY;
+    } catch (...) {
+        return STC_ERR_INVALID_ARG;
+    }
+}
+
+// The plan's device task list for `slices` row slices (built on the host on first use).
+int get_taskset(stc_plan* P, int32_t slices, bool bl_order, TaskSet** out) {
+    *out = nullptr;
+    return no_throw([&] {
+        *out = P->taskset(slices, bl_order);
+        return STC_OK;
+    });
+}
+
 // Device copies of the plan's arrays on the current device (synchronous on first use).
+int ensure_plan_impl(stc_plan* P, int dev);
 int ensure_plan(stc_plan* P, int dev) {
+    return no_throw([&] { return ensure_plan_impl(P, dev); });
+}
+int ensure_plan_impl(stc_plan* P, int dev) {
     std::lock_guard<std::mutex> g(P->mu);
     if (P->dev.device == dev) return STC_OK;
     if (P->dev.device >= 0) free_dev(P);
@@ -1636,7 +1663,11 @@ int ensure_plan(stc_plan* P, int dev) {
     return STC_OK;
 }
 
+int ensure_taskset_impl(stc_plan* P, TaskSet* ts, int dev);
 int ensure_taskset(stc_plan* P, TaskSet* ts, int dev) {
+    return no_throw([&] { return ensure_taskset_impl(P, ts, dev); });
+}
+int ensure_taskset_impl(stc_plan* P, TaskSet* ts, int dev) {
     std::lock_guard<std::mutex> g(P->mu);
     if (ts->device == dev) return STC_OK;
     std::vector<DTile> tiles = P->tiles;
@@ -1652,41 +1683,6 @@ int ensure_taskset(stc_plan* P, TaskSet* ts, int dev) {
     return STC_OK;
 }
 
-// Merged queue for a batch: item b's tasks keep their earliest-start order and are
-// keyed as if the item started b/batch * skew block-column periods late.  Built on the
-// host and uploaded once per batch size (synchronous), then cached with the task set.
-int ensure_queue(stc_plan* P, TaskSet* ts, int64_t batch, uint64_t** out) {
-    *out = nullptr;
-    const double skew = P->opt.queue_skew;
-    if (batch <= 1 || !(skew > 0.0) || batch >= (1LL << 28)) return STC_OK;
-    std::lock_guard<std::mutex> g(P->mu);
-    auto it = ts->d_queue.find(batch);
-    if (it != ts->d_queue.end()) { *out = it->second; return STC_OK; }
-    const size_t T = ts->tasks.size();
-    std::vector<uint64_t> q;
-    q.reserve(T * (size_t)batch);
-    typedef std::pair<double, int64_t> E;
-    std::priority_queue<E, std::vector<E>, std::greater<E>> h;
-    std::vector<size_t> pos((size_t)batch, 0);
-    auto phi = [&](int64_t b) { return skew * ts->period * double(b) / double(batch); };
-    for (int64_t b = 0; b < batch; ++b) h.push(E(ts->qkey[0] + phi(b), b));
-    while (!h.empty()) {
-        const int64_t b = h.top().second;
-        h.pop();
-        q.push_back(qpack(0, (int)pos[b], b));
-        if (++pos[b] < T) h.push(E(ts->qkey[pos[b]] + phi(b), b));
-    }
-    uint64_t* d = nullptr;
-    if (cudaMalloc((void**)&d, q.size() * sizeof(uint64_t)) != cudaSuccess) return STC_ERR_OUT_OF_MEMORY;
-    if (cudaMemcpy(d, q.data(), q.size() * sizeof(uint64_t), cudaMemcpyHostToDevice) != cudaSuccess) {
-        cudaFree(d);
-        return STC_ERR_CUDA;
-    }
-    ts->d_queue[batch] = d;
-    *out = d;
-    return STC_OK;
-}
-
 // Two CTAs per SM hide one CTA's waits behind the other's arithmetic when many items
 // are in flight; with few items every task is on the critical path and gets an SM alone.
 long long batch_total(const ReplayLaunch& L) {
@@ -1694,7 +1690,14 @@ long long batch_total(const ReplayLaunch& L) {
     for (int j = 0; j < L.njobs; ++j) b += L.job[j].batch;
     return b;
 }
-long long replay_ctas(int sms, long long batch) { return batch >= 16 ? 2LL * sms : (long long)sms; }
+long long default_ctas(int sms, long long batch) { return batch >= 16 ? 2LL * sms : (long long)sms; }
+// Grid of a persistent kernel: the plan's replay_ctas option when set (1 = serial replay
+// in queue order, the race check's reference schedule), else `dflt`; never more CTAs
+// than slots.
+int grid_of(const stc_plan* P, long long dflt, long long slots) {
+    const long long g = P->opt.replay_ctas > 0 ? (long long)P->opt.replay_ctas : dflt;
+    return (int)std::max<long long>(1, std::min<long long>(g, slots));
+}
 
 void fill_job(ReplayArgs& a, const stc_plan* P, const TaskSet* ts, void* d_factor, int* counters, int32_t* d_info,
               int64_t batch, WorkHeader* hdr) {
@@ -1714,7 +1717,7 @@ size_t solve_ws(const stc_plan* P, int64_t chains) {
     return sizeof(WorkHeader) + flags + (size_t)chains * P->nt * P->nb * sizeof(double);
 }
 
-int32_t pick_slices(stc_plan* P, int64_t batch, int sms) {
+int32_t pick_slices_impl(stc_plan* P, int64_t batch, int sms) {
     if (P->opt.row_slices > 0) return P->opt.row_slices;
     // Split heavy tiles so the chain POTRF -> TRSM -> SYRK of consecutive block columns
     // is spread over several SMs (the per-SM FP64 rate is low), but no further than the
@@ -1729,8 +1732,50 @@ int32_t pick_slices(stc_plan* P, int64_t batch, int sms) {
     return P->nb < 96 ? std::max(1, s / 2) : s;
 }
 
+// The task set a factorization of `batch` value sets replays (slice count from the batch,
+// bottom-level order for one or two value sets).
+int pick_taskset(stc_plan* P, int64_t batch, int sms, bool bl_order, TaskSet** out) {
+    *out = nullptr;
+    return no_throw([&] {
+        *out = P->taskset(pick_slices_impl(P, batch, sms), bl_order);
+        return STC_OK;
+    });
+}
+
 inline cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 
+}  // namespace
+}  // namespace stc
+
+// ---------------------------------------------------------------------------
+// Allocation-free factorization: the replay kernel's scratch (WorkHeader + per-tile
+// counters) comes from this fixed array instead of a caller workspace.  Host code
+// must not pass `g_noalloc_scratch` itself to a kernel (on the host that name is only
+// a stand-in for the device object); the device address is looked up once per device.
+// ---------------------------------------------------------------------------
+namespace stc {
+namespace {
+static __device__ __align__(256) unsigned char g_noalloc_scratch[STC_NOALLOC_SCRATCH_BYTES];
+
+struct NoallocSlot {
+    void* ptr = nullptr;
+    bool ready = false;
+};
+NoallocSlot g_noalloc[64];
+std::mutex g_noalloc_mu;
+
+int noalloc_scratch(int dev, void** out) {
+    std::lock_guard<std::mutex> g(g_noalloc_mu);
+    NoallocSlot& s = g_noalloc[dev];
+    if (!s.ready) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return STC_ERR_CUDA;
+        s.ptr = p;
+        s.ready = true;
+    }
+    *out = s.ptr;
+    return STC_OK;
+}
 }  // namespace
 }  // namespace stc
 
@@ -1742,7 +1787,13 @@ extern "C" int stc_plan_upload(stc_plan* P) {
     int rc = device_info(&dev, &sms);
     if (rc) return rc;
     if ((rc = ensure_plan(P, dev))) return rc;
-    return ensure_taskset(P, P->taskset(1), dev);
+    TaskSet* ts = nullptr;
+    if ((rc = get_taskset(P, 1, false, &ts))) return rc;
+    if ((rc = ensure_taskset(P, ts, dev))) return rc;
+    // resolve the allocation-free entry point's scratch array now, so that the module
+    // holding it is loaded on this device before the caller reserves the rest of its memory
+    void* scratch = nullptr;
+    return noalloc_scratch(dev, &scratch);
 }
 
 extern "C" void stc_plan_destroy(stc_plan* P) {
@@ -1790,10 +1841,9 @@ extern "C" int stc_factorize_scattered(const stc_plan* Pc, int64_t batch, void* 
     if ((rc = device_info(&dev, &sms))) return rc;
     if ((rc = ensure_plan(P, dev))) return rc;
     // one or two value sets: the item's own DAG width decides, so the critical path goes first
-    TaskSet* ts = P->taskset(pick_slices(P, batch, sms), batch <= 2);
+    TaskSet* ts = nullptr;
+    if ((rc = pick_taskset(P, batch, sms, batch <= 2, &ts))) return rc;
     if ((rc = ensure_taskset(P, ts, dev))) return rc;
-    uint64_t* queue = nullptr;
-    if ((rc = ensure_queue(P, ts, batch, &queue))) return rc;
     cudaStream_t st = S(stream);
     if (cudaMemsetAsync(d_work, 0, factorize_ws(P, batch), st) != cudaSuccess) return STC_ERR_CUDA;
     if (cudaMemsetAsync(d_info, 0, (size_t)batch * sizeof(int32_t), st) != cudaSuccess) return STC_ERR_CUDA;
@@ -1801,10 +1851,10 @@ extern "C" int stc_factorize_scattered(const stc_plan* Pc, int64_t batch, void* 
     fill_job(Lc.job[0], P, ts, d_factor, (int*)((char*)d_work + sizeof(WorkHeader)), d_info, batch,
              (WorkHeader*)d_work);
     Lc.njobs = 1;
-    Lc.queue = queue;
+    Lc.queue = nullptr;
     Lc.hdr = (WorkHeader*)d_work;
     Lc.total = (long long)ts->tasks.size() * batch;
-    const int grid = (int)std::max<long long>(1, std::min<long long>(replay_ctas(sms, batch_total(Lc)), Lc.total));
+    const int grid = grid_of(P, default_ctas(sms, batch_total(Lc)), Lc.total);
     replay_kernel<<<grid, kThreads, kRSmemBytes, st>>>(Lc);
     return cudaGetLastError() == cudaSuccess ? STC_OK : STC_ERR_CUDA;
 }
@@ -1857,7 +1907,8 @@ extern "C" int stc_solve(const stc_plan* Pc, const void* d_factor, int64_t batch
     int dev, sms, rc;
     if ((rc = device_info(&dev, &sms))) return rc;
     if ((rc = ensure_plan(P, dev))) return rc;
-    TaskSet* ts = P->taskset(1);
+    TaskSet* ts = nullptr;
+    if ((rc = get_taskset(P, 1, false, &ts))) return rc;
     if ((rc = ensure_taskset(P, ts, dev))) return rc;
     const long long chains = batch * nrhs;
     cudaStream_t st = S(stream);
@@ -1873,7 +1924,7 @@ extern "C" int stc_solve(const stc_plan* Pc, const void* d_factor, int64_t batch
     a.chains = chains; a.nrhs = nrhs; a.nt = (int)P->nt; a.nb = (int)P->nb; a.n = P->n;
     a.spin = P->opt.spin_limit > 0 ? P->opt.spin_limit : kDefaultSpin;
     const long long total = 2LL * P->nt * chains;
-    const int grid = (int)std::max<long long>(1, std::min<long long>(sms, total));
+    const int grid = grid_of(P, sms, total);
     solve_kernel<<<grid, kThreads, kSolveSmem, st>>>(a);
     return cudaGetLastError() == cudaSuccess ? STC_OK : STC_ERR_CUDA;
 }
@@ -1911,7 +1962,8 @@ extern "C" int stc_selinv(const stc_plan* Pc, const void* d_factor, int64_t batc
     int dev, sms, rc;
     if ((rc = device_info(&dev, &sms))) return rc;
     if ((rc = ensure_plan(P, dev))) return rc;
-    TaskSet* ts = P->taskset(1);
+    TaskSet* ts = nullptr;
+    if ((rc = get_taskset(P, 1, false, &ts))) return rc;
     if ((rc = ensure_taskset(P, ts, dev))) return rc;
     cudaStream_t st = S(stream);
     if (cudaMemsetAsync(d_sigma, 0, stc_factor_bytes(P, batch), st) != cudaSuccess) return STC_ERR_CUDA;
@@ -1924,7 +1976,7 @@ extern "C" int stc_selinv(const stc_plan* Pc, const void* d_factor, int64_t batc
     a.ntasks = (int)P->stasks.size(); a.batch = batch; a.nb = (int)P->nb;
     a.spin = P->opt.spin_limit > 0 ? P->opt.spin_limit : kDefaultSpin;
     const long long total = (long long)a.ntasks * batch;
-    const int grid = (int)std::max<long long>(1, std::min<long long>(sms, total));
+    const int grid = grid_of(P, sms, total);
     selinv_kernel<<<grid, kThreads, kSmemBytes, st>>>(a);
     return cudaGetLastError() == cudaSuccess ? STC_OK : STC_ERR_CUDA;
 }
@@ -2000,7 +2052,8 @@ extern "C" int stc_group_create(int32_t nplans, const stc_plan* const* plans, co
     for (int p = 0; p < nplans; ++p) {
         stc_plan* P = const_cast<stc_plan*>(plans[p]);
         if ((rc = ensure_plan(P, dev))) return rc;
-        TaskSet* ts = P->taskset(pick_slices(P, btot, sms));
+        TaskSet* ts = nullptr;
+        if ((rc = pick_taskset(P, btot, sms, false, &ts))) return rc;
         if ((rc = ensure_taskset(P, ts, dev))) return rc;
         g->plans.push_back(P);
         g->batch.push_back(batch[p]);
@@ -2065,7 +2118,7 @@ extern "C" int stc_factorize_group(stc_group* g, const double* const* d_values, 
     Lc.queue = g->d_queue;
     Lc.hdr = (WorkHeader*)d_work;
     Lc.total = g->total;
-    const int grid = (int)std::max<long long>(1, std::min<long long>(replay_ctas(sms, batch_total(Lc)), Lc.total));
+    const int grid = grid_of(g->plans[0], default_ctas(sms, batch_total(Lc)), Lc.total);
     replay_kernel<<<grid, kThreads, kRSmemBytes, st>>>(Lc);
     return cudaGetLastError() == cudaSuccess ? STC_OK : STC_ERR_CUDA;
 }
@@ -2081,38 +2134,6 @@ extern "C" void stc_group_destroy(stc_group* g) {
     }
     delete g;
 }
-
-// ---------------------------------------------------------------------------
-// Allocation-free factorization: the replay kernel's scratch (WorkHeader + per-tile
-// counters) comes from this fixed array instead of a caller workspace.  Host code
-// must not pass `g_noalloc_scratch` itself to a kernel (on the host that name is only
-// a stand-in for the device object); the device address is looked up once per device.
-// ---------------------------------------------------------------------------
-namespace stc {
-namespace {
-static __device__ __align__(256) unsigned char g_noalloc_scratch[STC_NOALLOC_SCRATCH_BYTES];
-
-struct NoallocSlot {
-    void* ptr = nullptr;
-    bool ready = false;
-};
-NoallocSlot g_noalloc[64];
-std::mutex g_noalloc_mu;
-
-int noalloc_scratch(int dev, void** out) {
-    std::lock_guard<std::mutex> g(g_noalloc_mu);
-    NoallocSlot& s = g_noalloc[dev];
-    if (!s.ready) {
-        void* p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return STC_ERR_CUDA;
-        s.ptr = p;
-        s.ready = true;
-    }
-    *out = s.ptr;
-    return STC_OK;
-}
-}  // namespace
-}  // namespace stc
 
 extern "C" int stc_factorize_noalloc(const stc_plan* Pc, const double* d_values, int64_t batch, void* d_factor,
                                      int32_t* d_info, int32_t* d_status, void* stream) {
@@ -2143,7 +2164,7 @@ extern "C" int stc_factorize_noalloc(const stc_plan* Pc, const double* d_values,
     Lc.queue = nullptr;
     Lc.hdr = (WorkHeader*)scratch;
     Lc.total = (long long)ts->tasks.size() * batch;
-    const int grid = (int)std::max<long long>(1, std::min<long long>(replay_ctas(sms, batch_total(Lc)), Lc.total));
+    const int grid = grid_of(P, default_ctas(sms, batch_total(Lc)), Lc.total);
     replay_kernel<<<grid, kThreads, kRSmemBytes, st>>>(Lc);
     if (cudaGetLastError() != cudaSuccess) return STC_ERR_CUDA;
     if (d_status && cudaMemcpyAsync(d_status, &Lc.hdr->status, sizeof(int32_t), cudaMemcpyDeviceToDevice, st) !=

@@ -210,6 +210,9 @@ def test_unsupported_options_rejected():
     o = L.stc_options_default()
     o.row_slices = 3
     assert L.stc_analyze(10, Ap, Ai, None, o)[0] == L.STC_ERR_INVALID_ARG
+    o = L.stc_options_default()
+    o.replay_ctas = -1
+    assert L.stc_analyze(10, Ap, Ai, None, o)[0] == L.STC_ERR_INVALID_ARG
 
 
 def test_export_buffer_too_small():

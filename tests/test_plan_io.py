@@ -90,3 +90,72 @@ def test_loaded_plan_survives_the_original():
     Q = Plan.load(blob)
     for k, v in ref.items():
         assert np.array_equal(Q.export(k), v)
+
+
+def _fnv1a(b: bytes) -> int:
+    h = 1469598103934665603
+    for c in b:
+        h = ((h ^ c) * 1099511628211) & 0xFFFFFFFFFFFFFFFF
+    return h
+
+
+def _tiles_and_scalars(blob):
+    """Byte offsets of the tile array and of two scalars in a saved blob (the format of
+    plan_io.cpp: 32-byte header, scalars, then each array as a u64 count + elements)."""
+    import struct
+    so = L.C.sizeof(L.stc_options)
+    sc = 32 + 32 + so + 12 + 32           # n..nnzA, options, 3 x int32, 4 doubles
+    npartials_at, partial_off_at = sc + 16, sc + 24
+    pos = 32 + 32 + so + 12 + 32 + 32 + 32 + 16
+    perm_at = None
+    for esize in (8, 8, 8, 4):            # perm, parent, Lp, Li
+        (cnt,) = struct.unpack_from("<Q", blob, pos)
+        if perm_at is None:
+            perm_at = pos + 8
+        pos += 8 + cnt * esize
+    (ntiles,) = struct.unpack_from("<Q", blob, pos)
+    return pos + 8, ntiles, npartials_at, partial_off_at, perm_at
+
+
+def test_refuses_intact_but_inconsistent_blobs():
+    # a blob with a valid checksum whose contents disagree with the plan's dimensions
+    # (an edited blob, or one written by a build with another layout) must never reach
+    # a kernel: each edit below is re-checksummed and must still be refused
+    import struct
+    Ap, Ai, _ = I.tridiag(300, 0)
+    P = Plan(300, Ap, Ai, nb=32, ordering="natural", route="semisparse")
+    blob = P.save()
+    tiles_at, ntiles, np_at, po_at, perm_at = _tiles_and_scalars(blob)
+    assert ntiles == P.info["ntiles"]
+    (npartials,) = struct.unpack_from("<q", blob, np_at)
+    (partial_off,) = struct.unpack_from("<q", blob, po_at)
+    assert npartials == P.info["nt"]
+    T = P.export("tiles")
+    off_tile = int(np.nonzero(T[:, 0] != T[:, 1])[0][-1])
+    diag_tile = int(np.nonzero(T[:, 0] == T[:, 1])[0][-1])
+
+    def resign(b):
+        b = bytearray(b)
+        b[24:32] = struct.pack("<Q", _fnv1a(bytes(b[32:])))
+        return bytes(b)
+
+    assert Plan.load(resign(blob)).save() == blob  # re-signing alone changes nothing
+
+    def edited(tile, field_at, fmt, value):
+        b = bytearray(blob)
+        struct.pack_into(fmt, b, tiles_at + 56 * tile + field_at, value)
+        return resign(b)
+
+    bad = {
+        "footprint past the tile area": edited(off_tile, 0, "<q", partial_off - 1),
+        "negative offset": edited(off_tile, 0, "<q", -8),
+        "unknown tile kind": edited(diag_tile, 16, "<i", 7),
+        "logdet slot out of range": edited(diag_tile, 48, "<i", npartials),
+        "band wider than the tile": edited(diag_tile, 32, "<i", 32),
+        "stored width past the tile": edited(off_tile, 20, "<i", 33),
+    }
+    b = bytearray(blob)
+    b[perm_at:perm_at + 8] = b[perm_at + 8:perm_at + 16]   # perm[0] = perm[1]
+    bad["perm not a permutation"] = resign(b)
+    for what, blob2 in bad.items():
+        assert L.stc_plan_load(blob2)[0] == L.STC_ERR_INVALID_PATTERN, what
