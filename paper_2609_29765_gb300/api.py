@@ -14,7 +14,8 @@ import numpy as np
 
 from . import _lib as L
 
-ROUTES = {"auto": L.STC_ROUTE_AUTO, "dense": L.STC_ROUTE_DENSE, "semisparse": L.STC_ROUTE_SEMISPARSE}
+ROUTES = {"auto": L.STC_ROUTE_AUTO, "dense": L.STC_ROUTE_DENSE, "semisparse": L.STC_ROUTE_SEMISPARSE,
+          "supernodal": L.STC_ROUTE_SUPERNODAL}
 ROUTE_NAMES = {L.STC_ROUTE_DENSE: "dense", L.STC_ROUTE_SEMISPARSE: "semisparse",
                L.STC_ROUTE_SUPERNODAL: "supernodal"}
 ORDERINGS = {"auto": L.STC_ORDER_AUTO, "natural": L.STC_ORDER_NATURAL, "given": L.STC_ORDER_GIVEN,

@@ -1070,7 +1070,7 @@ static int analyze_impl(int64_t n, const int64_t* Ap, const int64_t* Ai, const d
     if (opt.nd_leaf <= 0) opt.nd_leaf = 64;
     if (opt.nb < 8 || opt.nb > kMaxNb || opt.nb % 8) return STC_ERR_UNSUPPORTED;
     if (opt.force_route != STC_ROUTE_AUTO && opt.force_route != STC_ROUTE_DENSE &&
-        opt.force_route != STC_ROUTE_SEMISPARSE)
+        opt.force_route != STC_ROUTE_SEMISPARSE && opt.force_route != STC_ROUTE_SUPERNODAL)
         return STC_ERR_INVALID_ARG;
     if (opt.row_slices != 0 && opt.row_slices != 1 && opt.row_slices != 2 && opt.row_slices != 4 &&
         opt.row_slices != 8)
@@ -1161,7 +1161,9 @@ static int analyze_impl(int64_t n, const int64_t* Ap, const int64_t* Ai, const d
         else sel = STC_ROUTE_SUPERNODAL;
         P->route_selected = sel;
         int ex = opt.force_route != STC_ROUTE_AUTO ? opt.force_route : sel;
-        if (ex == STC_ROUTE_SUPERNODAL) ex = STC_ROUTE_SEMISPARSE;
+        // the selector's supernodal choice executes on the semisparse tile route unless the
+        // supernodal route is asked for explicitly
+        if (ex == STC_ROUTE_SUPERNODAL && opt.force_route != STC_ROUTE_SUPERNODAL) ex = STC_ROUTE_SEMISPARSE;
         P->route_exec = ex;
     }
     if (P->route_exec == STC_ROUTE_DENSE) {  // rebuild storage as full tiles
@@ -1266,6 +1268,10 @@ static int analyze_impl(int64_t n, const int64_t* Ap, const int64_t* Ai, const d
     }
     stc::TaskSet* ts = P->taskset(1);
     P->flops_tile = 2.0 * ts->fma_exec;
+    if (P->route_exec == STC_ROUTE_SUPERNODAL) {  // Sec. 5.4 layout, built now: it sizes the factor
+        const stc::SnPlan& S = P->supernodal();
+        P->flops_tile = 2.0 * S.fma_exec;
+    }
     P->analyze_seconds =
         std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     *out = P.release();
@@ -1283,12 +1289,23 @@ extern "C" int stc_analyze(int64_t n, const int64_t* colptr, const int64_t* rowi
     }
 }
 
+static int plan_info_impl(const stc_plan* P, stc_plan_info* o);
 extern "C" int stc_plan_info_get(const stc_plan* P, stc_plan_info* o) {
+    try {
+        return plan_info_impl(P, o);
+    } catch (const std::bad_alloc&) {
+        return STC_ERR_OUT_OF_MEMORY;
+    } catch (...) {
+        return STC_ERR_INVALID_ARG;
+    }
+}
+static int plan_info_impl(const stc_plan* P, stc_plan_info* o) {
     if (!P || !o) return STC_ERR_INVALID_ARG;
     std::memset(o, 0, sizeof(*o));
     o->n = P->n; o->nb = P->nb; o->nt = P->nt; o->ntiles = (int64_t)P->tiles.size();
-    o->nnzA = P->nnzA; o->nnzL = P->Lp[P->n]; o->stored_entries = P->stored_entries;
-    o->factor_doubles = P->factor_doubles;
+    o->nnzA = P->nnzA; o->nnzL = P->Lp[P->n];
+    o->stored_entries = P->route_exec == STC_ROUTE_SUPERNODAL ? P->supernodal().stored : P->stored_entries;
+    o->factor_doubles = P->item_doubles();
     o->route_selected = P->route_selected; o->route_executed = P->route_exec;
     o->ordering = P->ordering;
     o->phi = P->phi; o->rho = P->rho; o->sigma = P->sigma;

@@ -231,6 +231,30 @@ struct SnPlan {
     std::vector<int16_t> maps;
     std::vector<int64_t> value_map;  // per A entry: arena offset (permuted lower entry)
     std::vector<int64_t> csc_map;    // per structural L entry: arena offset
+    std::vector<int32_t> cell_cmap;  // per cell: offset in maps of its rows as columns of
+                                     // its row supernode (-1 for diagonal cells)
+    std::vector<int32_t> rptr_cells, row_cells;  // per row supernode J: cells (J, I), I < J
+    double fma_exec = 0.0;           // FMAs of the device form (updates, POTRF, TRSM)
+    int32_t nsn() const { return (int32_t)first.size() - 1; }
+    // item layout of the supernodal route: the arena, then one logdet partial per supernode
+    int64_t poff() const { return (arena + 31) / 32 * 32; }
+    int64_t item_doubles() const { return (poff() + nsn() + 31) / 32 * 32; }
+};
+
+// Device copies of a supernodal plan (uploaded on first use per device).
+struct SnDev {
+    SnDevCell* cells = nullptr;
+    SnDevTask* tasks = nullptr;
+    SnDevUpd* upds = nullptr;
+    int16_t* maps = nullptr;
+    int32_t* first = nullptr;       // nsn + 1
+    int32_t* cell_cmap = nullptr;
+    int32_t* cptr = nullptr;        // nsn + 1: cells of column supernode I (diagonal first)
+    int32_t* rptr_cells = nullptr;  // nsn + 1
+    int32_t* row_cells = nullptr;
+    int64_t* value_map = nullptr;
+    int64_t* csc_map = nullptr;
+    int device = -1;
 };
 
 }  // namespace stc
@@ -279,9 +303,15 @@ struct stc_plan {
     stc::DevPlanArrays dev;
     std::mutex mu;
 
-    // supernodal layout, built on first use from the symbolic factor
+    // supernodal layout, built on first use from the symbolic factor (at analysis when the
+    // plan executes on the supernodal route)
     mutable std::unique_ptr<stc::SnPlan> sn;
     mutable std::mutex sn_mu;
+    stc::SnDev sndev;
+    // item stride, logdet partials offset and count of the route the plan executes
+    int64_t item_doubles() const { return route_exec == STC_ROUTE_SUPERNODAL ? supernodal().item_doubles() : factor_doubles; }
+    int64_t logdet_off() const { return route_exec == STC_ROUTE_SUPERNODAL ? supernodal().poff() : partial_off; }
+    int64_t nlogdet() const { return route_exec == STC_ROUTE_SUPERNODAL ? supernodal().nsn() : npartials; }
     const stc::SnPlan& supernodal() const;
     void build_device_form(stc::SnPlan& S, const std::vector<int32_t>& snof,
                            const std::vector<std::vector<int32_t>>& byrow,

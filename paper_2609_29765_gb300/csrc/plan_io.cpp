@@ -161,7 +161,9 @@ bool consistent(const stc_plan& P) {
         if (!in(v, 0, nb)) return false;
     for (int16_t v : P.cext)
         if (!in(v, 0, nb + 1)) return false;
-    if (P.route_exec != STC_ROUTE_DENSE && P.route_exec != STC_ROUTE_SEMISPARSE) return false;
+    if (P.route_exec != STC_ROUTE_DENSE && P.route_exec != STC_ROUTE_SEMISPARSE &&
+        P.route_exec != STC_ROUTE_SUPERNODAL)
+        return false;
     for (const stc::DTile& T : P.tiles) {
         if (!in(T.I, 0, nt) || !in(T.J, 0, nt) || T.I < T.J) return false;
         if (T.sw < 0 || T.sw > nb || T.r0 < 0 || T.r1 > nb || T.r0 > T.r1) return false;

@@ -1231,6 +1231,392 @@ __global__ void __launch_bounds__(kThreads, 1) solve_kernel(SolveArgs a) {
     }
 }
 
+// ---------------------------------------------------------------------------
+// Supernodal route (Sec. 5.4): the same persistent executor over non-uniform cells.
+// Each supernode owns a dense column-major panel (its rows x its columns, at most 128
+// columns); a cell is the run of the panel's rows owned by one row supernode (at most
+// 128 rows).  A device task is a diagonal cell (its SYRK-like updates, then POTRF) or a
+// row slice of <= 64 rows of an off-diagonal cell (its GEMM-like updates, then the TRSM
+// against the diagonal cell).  An update subtracts A B^T, A = rows [ar0, ar1) of the
+// source cell (K,I), B = the source cell (J,I), inner dimension the dense columns of I,
+// and scatters the product into the target through sorted-subset row and column maps
+// (each row of A lands on one target row, each row of B on one target column).  A
+// cell's completion counter counts its finished slices.
+// ---------------------------------------------------------------------------
+struct SnArgs {
+    const SnDevCell* cells;
+    const SnDevTask* tasks;
+    const SnDevUpd* upds;
+    const int16_t* maps;
+    const int32_t* first;    // first column of each supernode
+    double* factor;          // item 0
+    long long fstride;       // doubles per item
+    long long poff;          // offset of the logdet partials (one per supernode)
+    int* counters;           // [batch][ncells]
+    int ncells;
+    int* info;
+    WorkHeader* hdr;
+    int ntasks;
+    long long batch;
+    long long spin;
+};
+
+// C(rm[r], cm[c]) -= sum_k A(r,k) B(c,k) for r < R, c < Cn: the tile product of
+// mma_tiles with the result scattered through row and column maps (shared memory, each
+// map injective).  PACKED: C is a packed lower triangle of width pnb; LOWER: only
+// r >= c (rm and cm ascending, so the mapped entry is in the lower triangle).
+template <bool LOWER, int TR, int TC, bool PACKED>
+__device__ void mma_scatter_tiles(double* __restrict__ C, int ldc, int R, int Cn, const double* __restrict__ A,
+                                  int lda, const double* __restrict__ B, int ldb, int K, const int* rm,
+                                  const int* cm, int pnb) {
+    const int MR = (R + TR - 1) / TR, MC = (Cn + TC - 1) / TC;
+    const int count = LOWER ? MR * (MR + 1) / 2 : MR * MC;
+    for (int mt = threadIdx.x; mt < count; mt += kThreads) {
+        int ri, cj;
+        if (LOWER) {
+            int r = (int)((sqrtf(8.0f * mt + 1.0f) - 1.0f) * 0.5f);
+            while (r * (r + 1) / 2 > mt) --r;
+            while ((r + 1) * (r + 2) / 2 <= mt) ++r;
+            ri = r;
+            cj = mt - r * (r + 1) / 2;
+        } else {
+            ri = mt % MR;
+            cj = mt / MR;
+        }
+        const int r0 = ri * TR, c0 = cj * TC;
+        int ci[TR][TC];
+        double acc[TR][TC];
+#pragma unroll
+        for (int i = 0; i < TR; ++i)
+#pragma unroll
+            for (int j = 0; j < TC; ++j) {
+                const int r = r0 + i, c = c0 + j;
+                const bool live = r < R && c < Cn && (!LOWER || r >= c);
+                ci[i][j] = live ? (PACKED ? pk(pnb, rm[r], cm[c]) : rm[r] + cm[c] * ldc) : -1;
+                acc[i][j] = live ? C[ci[i][j]] : 0.0;
+            }
+        const double* a = A + r0;
+        const double* b = B + c0;
+#pragma unroll 4
+        for (int k = 0; k < K; ++k) {
+            double av[TR], bv[TC];
+#pragma unroll
+            for (int i = 0; i < TR; ++i) av[i] = a[i];
+#pragma unroll
+            for (int j = 0; j < TC; ++j) bv[j] = b[j];
+#pragma unroll
+            for (int i = 0; i < TR; ++i)
+#pragma unroll
+                for (int j = 0; j < TC; ++j) acc[i][j] = fma(-av[i], bv[j], acc[i][j]);
+            a += lda;
+            b += ldb;
+        }
+#pragma unroll
+        for (int i = 0; i < TR; ++i)
+#pragma unroll
+            for (int j = 0; j < TC; ++j)
+                if (ci[i][j] >= 0) C[ci[i][j]] = acc[i][j];
+    }
+}
+
+template <bool LOWER, bool PACKED>
+__device__ __forceinline__ void mma_scatter(double* C, int ldc, int R, int Cn, const double* A, int lda,
+                                            const double* B, int ldb, int K, const int* rm, const int* cm,
+                                            int pnb) {
+    const int m4 = (R + 3) >> 2, n4 = (Cn + 3) >> 2;
+    const int c44 = LOWER ? m4 * (m4 + 1) / 2 : m4 * n4;
+    if (c44 >= (kThreads * 3) / 4)
+        mma_scatter_tiles<LOWER, 4, 4, PACKED>(C, ldc, R, Cn, A, lda, B, ldb, K, rm, cm, pnb);
+    else
+        mma_scatter_tiles<LOWER, 2, 2, PACKED>(C, ldc, R, Cn, A, lda, B, ldb, K, rm, cm, pnb);
+}
+
+// Rows [r0, r0 + R) and inner columns [k0, k0 + K) of a cell into S[r + k * ld], zero
+// rows up to the next multiple of 4 (+4), as the micro-tiles read them.
+__device__ __forceinline__ void sn_stage(double* S, int ld, const double* F, const SnDevCell& c, int r0, int R,
+                                         int k0, int K) {
+    const int Rp = ((R + 3) & ~3) + 4;
+    const double* base = F + c.off + r0 + (size_t)k0 * c.ld;
+    for_rc(Rp, K, [&](int r, int k) { S[r + k * ld] = r < R ? __ldcg(base + r + (size_t)k * c.ld) : 0.0; });
+}
+
+__global__ void __launch_bounds__(kThreads, 2) sn_replay_kernel(const __grid_constant__ SnArgs a) {
+    extern __shared__ double smem[];
+    double* C = smem;              // row-slice buffer (ld kRLd) or packed diagonal cell
+    double* S0 = C + kRCbuf;       // staging, kRKc columns of ld kRStLd
+    double* S1 = S0 + kRStage;
+    double* sv = S1 + kRStage;     // kNbMax doubles
+    __shared__ int s_rm[kNbMax], s_cm[kNbMax];
+    __shared__ long long s_slot;
+    __shared__ int s_ok;
+    const long long total = (long long)a.ntasks * a.batch;
+    for (;;) {
+        if (threadIdx.x == 0) s_slot = (long long)atomicAdd(&a.hdr->head, 1ULL);
+        __syncthreads();
+        const long long slot = s_slot;
+        __syncthreads();
+        if (slot >= total) break;
+        const int ti = (int)(slot / a.batch);
+        const long long item = slot % a.batch;
+        const SnDevTask t = a.tasks[ti];
+        const SnDevCell O = a.cells[t.cell];
+        double* F = a.factor + item * a.fstride;
+        int* cnt = a.counters + item * a.ncells;
+        if (threadIdx.x == 0) s_ok = (*(volatile int*)&a.hdr->status == STC_OK);
+        __syncthreads();
+        if (t.kind == SN_T_DIAG) {
+            const int w = O.w;
+            if (s_ok) {
+                // lower triangle of the diagonal cell -> packed triangle of width w
+                for_rc(w, w, [&](int r, int c) {
+                    if (r >= c) C[pk(w, r, c)] = __ldcg(F + O.off + r + (size_t)c * O.ld);
+                });
+                __syncthreads();
+                for (int ui = t.ubeg; ui < t.uend && s_ok; ++ui) {
+                    const SnDevUpd u = a.upds[ui];
+                    const SnDevCell A = a.cells[u.a];
+                    if (threadIdx.x == 0) s_ok = wait_counter(cnt + u.a, A.nslices, a.spin, &a.hdr->status);
+                    for (int i = threadIdx.x; i < A.h; i += kThreads) s_rm[i] = a.maps[u.rmap + i];
+                    __syncthreads();
+                    if (!s_ok) break;
+                    for (int k0 = 0; k0 < u.klen; k0 += kRKc) {
+                        const int K = min(kRKc, u.klen - k0);
+                        sn_stage(S0, kRStLd, F, A, 0, A.h, k0, K);
+                        __syncthreads();
+                        mma_scatter<true, true>(C, 0, A.h, A.h, S0, kRStLd, S0, kRStLd, K, s_rm, s_rm, w);
+                        __syncthreads();
+                    }
+                }
+                if (s_ok) {
+                    int bad;
+                    double ls;
+                    potrf_packed(C, w, w, w - 1, S0, &bad, &ls, [](int) {});
+                    for_rc(w, w, [&](int r, int c) {
+                        if (r >= c) __stcg(F + O.off + r + (size_t)c * O.ld, C[pk(w, r, c)]);
+                    });
+                    if (threadIdx.x == 0) {
+                        if (bad >= 0) record_info(a.info + item, a.first[O.I] + bad + 1);
+                        F[a.poff + O.I] = bad >= 0 ? __longlong_as_double(0x7ff8000000000000LL) : ls;
+                    }
+                }
+            }
+        } else {
+            const int R = t.rs1 - t.rs0, w = O.w;
+            if (s_ok) {
+                for_rc(R, w, [&](int r, int c) { C[r + c * kRLd] = __ldcg(F + O.off + t.rs0 + r + (size_t)c * O.ld); });
+                __syncthreads();
+                for (int ui = t.ubeg; ui < t.uend && s_ok; ++ui) {
+                    const SnDevUpd u = a.upds[ui];
+                    const SnDevCell A = a.cells[u.a];
+                    const SnDevCell B = a.cells[u.b];
+                    const int Ra = u.ar1 - u.ar0;
+                    if (threadIdx.x == 0)
+                        s_ok = wait_counter(cnt + u.a, A.nslices, a.spin, &a.hdr->status) &&
+                               wait_counter(cnt + u.b, B.nslices, a.spin, &a.hdr->status);
+                    for (int i = threadIdx.x; i < Ra; i += kThreads) s_rm[i] = a.maps[u.rmap + u.ar0 + i] - t.rs0;
+                    for (int j = threadIdx.x; j < B.h; j += kThreads) s_cm[j] = a.maps[u.cmap + j];
+                    __syncthreads();
+                    if (!s_ok) break;
+                    for (int k0 = 0; k0 < u.klen; k0 += kRKc) {
+                        const int K = min(kRKc, u.klen - k0);
+                        sn_stage(S0, kRStLd, F, A, u.ar0, Ra, k0, K);
+                        sn_stage(S1, kRStLd, F, B, 0, B.h, k0, K);
+                        __syncthreads();
+                        mma_scatter<false, false>(C, kRLd, Ra, B.h, S0, kRStLd, S1, kRStLd, K, s_rm, s_cm, 0);
+                        __syncthreads();
+                    }
+                }
+                if (s_ok) {
+                    const SnDevCell D = a.cells[t.diag];
+                    if (threadIdx.x == 0) s_ok = wait_counter(cnt + t.diag, 1, a.spin, &a.hdr->status);
+                    __syncthreads();
+                    if (s_ok) {
+                        // X <- X L_JJ^{-T}, right-looking by panels of kPb columns
+                        const double* DT = F + D.off;
+                        for (int p = 0; p < w; p += kPb) {
+                            const int pw = min(kPb, w - p);
+                            for (int idx = threadIdx.x; idx < kPb * kPb; idx += kThreads) {
+                                const int i = idx & (kPb - 1), j = idx / kPb;
+                                S0[i + j * (kPb + 1)] =
+                                    (i < pw && j < pw && i >= j) ? __ldcg(DT + p + i + (size_t)(p + j) * D.ld) : 0.0;
+                            }
+                            __syncthreads();
+                            if (threadIdx.x < pw) sv[threadIdx.x] = 1.0 / S0[threadIdx.x * (kPb + 2)];
+                            __syncthreads();
+                            trsm_rows(C + p * kRLd, kRLd, R, pw, S0, kPb + 1, sv);
+                            __syncthreads();
+                            const int pn = p + pw, Cn = w - pn;
+                            if (Cn <= 0) continue;
+                            for (int k0 = p; k0 < pn; k0 += kRKc) {
+                                const int K = min(kRKc, pn - k0);
+                                const int Cp = ((Cn + 3) & ~3) + 4;
+                                for_rc(Cp, K, [&](int c, int k) {
+                                    S1[c + k * kRStLd] = c < Cn ? __ldcg(DT + pn + c + (size_t)(k0 + k) * D.ld) : 0.0;
+                                });
+                                __syncthreads();
+                                mma_sub<false>(C + pn * kRLd, kRLd, R, Cn, C + k0 * kRLd, kRLd, S1, kRStLd, K);
+                                __syncthreads();
+                            }
+                        }
+                        for_rc(R, w, [&](int r, int c) { __stcg(F + O.off + t.rs0 + r + (size_t)c * O.ld, C[r + c * kRLd]); });
+                    }
+                }
+            }
+        }
+        __threadfence();
+        __syncthreads();
+        if (threadIdx.x == 0) red_release_add(cnt + t.cell, 1);
+    }
+}
+
+// Supernodal solve.  One persistent kernel over every (item, rhs) chain; step J < nsn is
+// the forward block of supernode J:  y_J = L_JJ^{-1} ((P b)_J - sum_I L_(J,I) y_I) over
+// the cells (J, I) that row supernode J owns; step nsn + i is the backward block of
+// J = nsn-1-i:  z_J = L_JJ^{-T} (y_J - sum_K L_(K,J)^T z_K) over the cells below J's
+// diagonal; z is scattered to x = P^T z.
+struct SnSolveArgs {
+    const SnDevCell* cells;
+    const int16_t* maps;
+    const int32_t* cell_cmap;
+    const int32_t* first;
+    const int32_t* cptr;       // cells of column supernode J: [cptr[J], cptr[J+1]), diagonal first
+    const int32_t* rptr_cells; // cells owned by row supernode J
+    const int32_t* row_cells;
+    const int32_t* perm;
+    const double* factor;
+    long long fstride;
+    const double* b;           // [chains][n]
+    double* x;                 // [chains][n]
+    double* y;                 // workspace [chains][n]
+    int* done;                 // workspace [chains][2*nsn]
+    WorkHeader* hdr;
+    long long chains, nrhs;
+    int nsn;
+    long long n, spin;
+};
+
+__global__ void __launch_bounds__(kThreads, 1) sn_solve_kernel(SnSolveArgs a) {
+    extern __shared__ double smem[];
+    double* Ls = smem;                              // diagonal block, L(r,c) at r + c*kLdc
+    __shared__ double v[kNbMax], ys[kNbMax], sdinv[kNbMax];
+    __shared__ double part[kThreads];
+    __shared__ long long s_slot;
+    __shared__ int s_ok;
+    const long long total = 2LL * a.nsn * a.chains;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (;;) {
+        if (threadIdx.x == 0) s_slot = (long long)atomicAdd(&a.hdr->head, 1ULL);
+        __syncthreads();
+        const long long slot = s_slot;
+        __syncthreads();
+        if (slot >= total) break;
+        const int ti = (int)(slot / a.chains);
+        const long long ch = slot % a.chains;
+        const long long item = ch / a.nrhs;
+        const double* F = a.factor + item * a.fstride;
+        double* y = a.y + ch * a.n;
+        int* done = a.done + ch * 2LL * a.nsn;
+        const bool fwd = ti < a.nsn;
+        const int J = fwd ? ti : a.nsn - 1 - (ti - a.nsn);
+        const SnDevCell D = a.cells[a.cptr[J]];
+        const int w = D.w, c0 = a.first[J];
+        if (threadIdx.x == 0) {
+            s_ok = (*(volatile int*)&a.hdr->status == STC_OK);
+            if (s_ok && !fwd) s_ok = wait_counter(done + J, 1, a.spin, &a.hdr->status);
+        }
+        __syncthreads();
+        if (s_ok) {
+            // diagonal block, scaled to the unit lower triangle M = L diag(L)^{-1}
+            for_rc(kNbMax, kNbMax, [&](int r, int c) { Ls[r + c * kLdc] = 0.0; });
+            __syncthreads();
+            for_rc(w, w, [&](int r, int c) {
+                if (r >= c) Ls[r + c * kLdc] = __ldcg(F + D.off + r + (size_t)c * D.ld);
+            });
+            __syncthreads();
+            for (int c = threadIdx.x; c < w; c += kThreads) sdinv[c] = 1.0 / Ls[c * (kLdc + 1)];
+            for (int r = threadIdx.x; r < kNbMax; r += kThreads) {
+                v[r] = 0.0;
+                if (r < w) v[r] = fwd ? a.b[ch * a.n + a.perm[c0 + r]] : __ldcg(y + c0 + r);
+            }
+            __syncthreads();
+            for_rc(w, w, [&](int r, int c) { if (r > c) Ls[r + c * kLdc] *= sdinv[c]; });
+            __syncthreads();
+            if (fwd) {
+                // v[map[i]] -= sum_k L_(J,I)[i][k] y_I[k], cells in ascending I
+                for (int q = a.rptr_cells[J]; q < a.rptr_cells[J + 1] && s_ok; ++q) {
+                    const int cid = a.row_cells[q];
+                    const SnDevCell T = a.cells[cid];
+                    if (threadIdx.x == 0) s_ok = wait_counter(done + T.I, 1, a.spin, &a.hdr->status);
+                    __syncthreads();
+                    if (!s_ok) break;
+                    const int cI = a.first[T.I];
+                    for (int k = threadIdx.x; k < T.w; k += kThreads) ys[k] = __ldcg(y + cI + k);
+                    __syncthreads();
+                    // two threads per row (T.h <= 128), halves of the inner range
+                    const int i = threadIdx.x >> 1, hf = threadIdx.x & 1;
+                    double s0 = 0.0, s1 = 0.0;
+                    if (i < T.h) {
+                        const double* Lr = F + T.off + i;
+                        int k = hf;
+                        for (; k + 2 < T.w; k += 4) {
+                            s0 = fma(__ldcg(Lr + (size_t)k * T.ld), ys[k], s0);
+                            s1 = fma(__ldcg(Lr + (size_t)(k + 2) * T.ld), ys[k + 2], s1);
+                        }
+                        if (k < T.w) s0 = fma(__ldcg(Lr + (size_t)k * T.ld), ys[k], s0);
+                    }
+                    double sacc = s0 + s1;
+                    sacc += __shfl_xor_sync(0xffffffffu, sacc, 1);
+                    if (i < T.h && hf == 0) v[a.maps[a.cell_cmap[cid] + i]] -= sacc;
+                    __syncthreads();
+                }
+            } else {
+                // v[k] -= sum_i L_(K,J)[i][k] z_K[map[i]], cells below the diagonal, last first
+                for (int q = a.cptr[J + 1] - 1; q > a.cptr[J] && s_ok; --q) {
+                    const SnDevCell T = a.cells[q];
+                    if (threadIdx.x == 0) s_ok = wait_counter(done + a.nsn + T.J, 1, a.spin, &a.hdr->status);
+                    __syncthreads();
+                    if (!s_ok) break;
+                    const int cK = a.first[T.J];
+                    const int16_t* m = a.maps + a.cell_cmap[q];
+                    for (int i = threadIdx.x; i < T.h; i += kThreads) ys[i] = __ldcg(y + cK + m[i]);
+                    __syncthreads();
+                    for (int k = warp; k < T.w; k += kThreads / 32) {
+                        const double* Lc = F + T.off + (size_t)k * T.ld;
+                        double d = 0.0;
+                        for (int i = lane; i < T.h; i += 32) d = fma(__ldcg(Lc + i), ys[i], d);
+#pragma unroll
+                        for (int o = 16; o > 0; o >>= 1) d += __shfl_down_sync(0xffffffffu, d, o);
+                        if (lane == 0) part[k] = d;
+                    }
+                    __syncthreads();
+                    for (int k = threadIdx.x; k < T.w; k += kThreads) v[k] -= part[k];
+                    __syncthreads();
+                }
+            }
+            if (s_ok) {
+                DTile Dt{};
+                Dt.kd = w - 1;
+                if (fwd) {
+                    diag_solve<false>(v, Ls, Dt, kNbMax, w);
+                    for (int i = threadIdx.x; i < w; i += kThreads) v[i] *= sdinv[i];
+                    __syncthreads();
+                } else {
+                    for (int i = threadIdx.x; i < w; i += kThreads) v[i] *= sdinv[i];
+                    __syncthreads();
+                    diag_solve<true>(v, Ls, Dt, kNbMax, w);
+                }
+                for (int i = threadIdx.x; i < w; i += kThreads) {
+                    __stcg(y + c0 + i, v[i]);
+                    if (!fwd) a.x[ch * a.n + a.perm[c0 + i]] = v[i];
+                }
+            }
+        }
+        __threadfence();
+        __syncthreads();
+        if (threadIdx.x == 0) red_release_add(done + (fwd ? J : a.nsn + J), 1);
+    }
+}
+
 // DFMA throughput probe: 8 independent FMA chains per thread.
 __global__ void fp64_probe_kernel(double* out, long long iters, double a, double b) {
     double c[8];
@@ -1572,6 +1958,12 @@ int device_info(int* dev, int* sms) {
             return STC_ERR_CUDA;
         if (cudaFuncSetAttribute(solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSolveSmem) != cudaSuccess)
             return STC_ERR_CUDA;
+        if (cudaFuncSetAttribute(sn_replay_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRSmemBytes) !=
+            cudaSuccess)
+            return STC_ERR_CUDA;
+        if (cudaFuncSetAttribute(sn_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSolveSmem) !=
+            cudaSuccess)
+            return STC_ERR_CUDA;
         d.attr_set = true;
     }
     *sms = d.sms;
@@ -1596,6 +1988,12 @@ void free_dev(stc_plan* P) {
     for (void* p : ptrs)
         if (p) cudaFree(p);
     d = DevPlanArrays{};
+    SnDev& q = P->sndev;
+    void* sptrs[] = {q.cells, q.tasks, q.upds, q.maps, q.first, q.cell_cmap, q.cptr, q.rptr_cells, q.row_cells,
+                     q.value_map, q.csc_map};
+    for (void* p : sptrs)
+        if (p) cudaFree(p);
+    q = SnDev{};
     for (auto& kv : P->tasksets) {
         TaskSet* ts = kv.second.get();
         if (ts->d_tasks) cudaFree(ts->d_tasks);
@@ -1683,6 +2081,37 @@ int ensure_taskset_impl(stc_plan* P, TaskSet* ts, int dev) {
     return STC_OK;
 }
 
+// Device copies of the supernodal layout (synchronous on first use per device).
+int ensure_sn_impl(stc_plan* P, int dev) {
+    const SnPlan& S = P->supernodal();
+    std::lock_guard<std::mutex> g(P->mu);
+    SnDev& d = P->sndev;
+    if (d.device == dev) return STC_OK;
+    if (d.device >= 0) return STC_ERR_UNSUPPORTED;  // one device per plan's supernodal copy
+    int rc;
+    std::vector<int32_t> cptr(S.cptr.begin(), S.cptr.end());
+    std::vector<int16_t> maps = S.maps;
+    if (maps.empty()) maps.push_back(0);
+    std::vector<int32_t> rc_list = S.row_cells;
+    if (rc_list.empty()) rc_list.push_back(0);
+    if ((rc = upload(&d.cells, S.dcells))) return rc;
+    if ((rc = upload(&d.tasks, S.dtasks))) return rc;
+    if ((rc = upload(&d.upds, S.dupds))) return rc;
+    if ((rc = upload(&d.maps, maps))) return rc;
+    if ((rc = upload(&d.first, S.first))) return rc;
+    if ((rc = upload(&d.cell_cmap, S.cell_cmap))) return rc;
+    if ((rc = upload(&d.cptr, cptr))) return rc;
+    if ((rc = upload(&d.rptr_cells, S.rptr_cells))) return rc;
+    if ((rc = upload(&d.row_cells, rc_list))) return rc;
+    if ((rc = upload(&d.value_map, S.value_map))) return rc;
+    if ((rc = upload(&d.csc_map, S.csc_map))) return rc;
+    d.device = dev;
+    return STC_OK;
+}
+int ensure_sn(stc_plan* P, int dev) {
+    return no_throw([&] { return ensure_sn_impl(P, dev); });
+}
+
 // Two CTAs per SM hide one CTA's waits behind the other's arithmetic when many items
 // are in flight; with few items every task is on the critical path and gets an SM alone.
 long long batch_total(const ReplayLaunch& L) {
@@ -1709,12 +2138,20 @@ void fill_job(ReplayArgs& a, const stc_plan* P, const TaskSet* ts, void* d_facto
     a.spin = P->opt.spin_limit > 0 ? P->opt.spin_limit : kDefaultSpin;
 }
 
+bool is_sn(const stc_plan* P) { return P->route_exec == STC_ROUTE_SUPERNODAL; }
+// completion counters per item: one per tile, or one per supernodal cell
+size_t counters_per_item(const stc_plan* P) { return is_sn(P) ? P->supernodal().dcells.size() : P->tiles.size(); }
 size_t factorize_ws(const stc_plan* P, int64_t batch) {
-    return sizeof(WorkHeader) + (size_t)batch * P->tiles.size() * sizeof(int);
+    return sizeof(WorkHeader) + (size_t)batch * counters_per_item(P) * sizeof(int);
+}
+// solve: a done flag per (chain, forward/backward step) and a y vector per chain
+size_t solve_flags(const stc_plan* P, int64_t chains) {
+    const size_t steps = is_sn(P) ? (size_t)P->supernodal().nsn() : (size_t)P->nt;
+    return ((size_t)chains * 2 * steps * sizeof(int) + 255) / 256 * 256;
 }
 size_t solve_ws(const stc_plan* P, int64_t chains) {
-    size_t flags = ((size_t)chains * 2 * P->nt * sizeof(int) + 255) / 256 * 256;
-    return sizeof(WorkHeader) + flags + (size_t)chains * P->nt * P->nb * sizeof(double);
+    const size_t ylen = is_sn(P) ? (size_t)P->n : (size_t)(P->nt * P->nb);
+    return sizeof(WorkHeader) + solve_flags(P, chains) + (size_t)chains * ylen * sizeof(double);
 }
 
 int32_t pick_slices_impl(stc_plan* P, int64_t batch, int sms) {
@@ -1743,6 +2180,52 @@ int pick_taskset(stc_plan* P, int64_t batch, int sms, bool bl_order, TaskSet** o
 }
 
 inline cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+// Supernodal factorization: the persistent kernel over (task, item) slots, every item of
+// a task in lockstep (the left-looking task order is topological).
+int sn_factorize_scattered(stc_plan* P, int64_t batch, void* d_factor, void* d_work, int32_t* d_info, void* stream,
+                           int dev, int sms) {
+    int rc;
+    if ((rc = ensure_sn(P, dev))) return rc;
+    const SnPlan& Sp = P->supernodal();
+    cudaStream_t st = S(stream);
+    if (cudaMemsetAsync(d_work, 0, factorize_ws(P, batch), st) != cudaSuccess) return STC_ERR_CUDA;
+    if (cudaMemsetAsync(d_info, 0, (size_t)batch * sizeof(int32_t), st) != cudaSuccess) return STC_ERR_CUDA;
+    SnArgs a{};
+    a.cells = P->sndev.cells; a.tasks = P->sndev.tasks; a.upds = P->sndev.upds; a.maps = P->sndev.maps;
+    a.first = P->sndev.first; a.factor = (double*)d_factor; a.fstride = Sp.item_doubles(); a.poff = Sp.poff();
+    a.hdr = (WorkHeader*)d_work; a.counters = (int*)((char*)d_work + sizeof(WorkHeader));
+    a.ncells = (int)Sp.dcells.size(); a.info = d_info; a.ntasks = (int)Sp.dtasks.size(); a.batch = batch;
+    a.spin = P->opt.spin_limit > 0 ? P->opt.spin_limit : kDefaultSpin;
+    const long long total = (long long)a.ntasks * batch;
+    const int grid = grid_of(P, default_ctas(sms, batch), total);
+    sn_replay_kernel<<<grid, kThreads, kRSmemBytes, st>>>(a);
+    return cudaGetLastError() == cudaSuccess ? STC_OK : STC_ERR_CUDA;
+}
+
+int sn_solve(stc_plan* P, const void* d_factor, int64_t batch, int64_t nrhs, const double* d_b, double* d_x,
+             void* d_work, void* stream, int dev, int sms) {
+    int rc;
+    if ((rc = ensure_sn(P, dev))) return rc;
+    const SnPlan& Sp = P->supernodal();
+    const long long chains = batch * nrhs;
+    cudaStream_t st = S(stream);
+    const size_t flags = solve_flags(P, chains);
+    if (cudaMemsetAsync(d_work, 0, sizeof(WorkHeader) + flags, st) != cudaSuccess) return STC_ERR_CUDA;
+    SnSolveArgs a{};
+    a.cells = P->sndev.cells; a.maps = P->sndev.maps; a.cell_cmap = P->sndev.cell_cmap; a.first = P->sndev.first;
+    a.cptr = P->sndev.cptr; a.rptr_cells = P->sndev.rptr_cells; a.row_cells = P->sndev.row_cells;
+    a.perm = P->dev.perm; a.factor = (const double*)d_factor; a.fstride = Sp.item_doubles();
+    a.b = d_b; a.x = d_x; a.hdr = (WorkHeader*)d_work;
+    a.done = (int*)((char*)d_work + sizeof(WorkHeader));
+    a.y = (double*)((char*)d_work + sizeof(WorkHeader) + flags);
+    a.chains = chains; a.nrhs = nrhs; a.nsn = Sp.nsn(); a.n = P->n;
+    a.spin = P->opt.spin_limit > 0 ? P->opt.spin_limit : kDefaultSpin;
+    const long long total = 2LL * a.nsn * chains;
+    const int grid = grid_of(P, sms, total);
+    sn_solve_kernel<<<grid, kThreads, kSolveSmem, st>>>(a);
+    return cudaGetLastError() == cudaSuccess ? STC_OK : STC_ERR_CUDA;
+}
 
 }  // namespace
 }  // namespace stc
@@ -1790,6 +2273,7 @@ extern "C" int stc_plan_upload(stc_plan* P) {
     TaskSet* ts = nullptr;
     if ((rc = get_taskset(P, 1, false, &ts))) return rc;
     if ((rc = ensure_taskset(P, ts, dev))) return rc;
+    if (is_sn(P) && (rc = ensure_sn(P, dev))) return rc;
     // resolve the allocation-free entry point's scratch array now, so that the module
     // holding it is loaded on this device before the caller reserves the rest of its memory
     void* scratch = nullptr;
@@ -1810,7 +2294,7 @@ extern "C" void stc_plan_destroy(stc_plan* P) {
 
 extern "C" size_t stc_factor_bytes(const stc_plan* P, int64_t batch) {
     if (!P || batch < 0) return 0;
-    return (size_t)batch * (size_t)P->factor_doubles * sizeof(double);
+    return (size_t)batch * (size_t)P->item_doubles() * sizeof(double);
 }
 
 extern "C" size_t stc_workspace_bytes(const stc_plan* P, int64_t batch) {
@@ -1825,11 +2309,16 @@ extern "C" int stc_scatter_values(const stc_plan* Pc, const double* d_values, in
     int dev, sms, rc;
     if ((rc = device_info(&dev, &sms))) return rc;
     if ((rc = ensure_plan(P, dev))) return rc;
+    if (is_sn(P) && (rc = ensure_sn(P, dev))) return rc;
     cudaStream_t st = S(stream);
     if (cudaMemsetAsync(d_factor, 0, stc_factor_bytes(P, batch), st) != cudaSuccess) return STC_ERR_CUDA;
     const int blocks = std::max(1, std::min<int>(sms * 8, (int)((P->nnzA + 255) / 256)));
-    scatter_kernel<<<blocks, 256, 0, st>>>(d_values, P->nnzA, batch, P->dev.value_map, (double*)d_factor,
-                                           P->factor_doubles, P->dev.pad_diag, (int)P->pad_diag.size());
+    if (is_sn(P))  // the supernodal arena has no padding
+        scatter_kernel<<<blocks, 256, 0, st>>>(d_values, P->nnzA, batch, P->sndev.value_map, (double*)d_factor,
+                                               P->item_doubles(), nullptr, 0);
+    else
+        scatter_kernel<<<blocks, 256, 0, st>>>(d_values, P->nnzA, batch, P->dev.value_map, (double*)d_factor,
+                                               P->factor_doubles, P->dev.pad_diag, (int)P->pad_diag.size());
     return cudaGetLastError() == cudaSuccess ? STC_OK : STC_ERR_CUDA;
 }
 
@@ -1840,6 +2329,7 @@ extern "C" int stc_factorize_scattered(const stc_plan* Pc, int64_t batch, void* 
     int dev, sms, rc;
     if ((rc = device_info(&dev, &sms))) return rc;
     if ((rc = ensure_plan(P, dev))) return rc;
+    if (is_sn(P)) return sn_factorize_scattered(P, batch, d_factor, d_work, d_info, stream, dev, sms);
     // one or two value sets: the item's own DAG width decides, so the critical path goes first
     TaskSet* ts = nullptr;
     if ((rc = pick_taskset(P, batch, sms, batch <= 2, &ts))) return rc;
@@ -1880,8 +2370,16 @@ extern "C" int stc_logdet(const stc_plan* P, const void* d_factor, int64_t batch
     if (!P || !d_factor || !d_logdet || batch <= 0) return STC_ERR_INVALID_ARG;
     const int wpb = 8;
     const long long blocks = (batch + wpb - 1) / wpb;
-    logdet_kernel<<<(unsigned)blocks, 32 * wpb, 0, S(stream)>>>((const double*)d_factor, P->factor_doubles,
-                                                                P->partial_off, (int)P->npartials, batch, d_logdet);
+    int64_t stride, poff, np;
+    if (no_throw([&] {
+            stride = P->item_doubles();
+            poff = P->logdet_off();
+            np = P->nlogdet();
+            return STC_OK;
+        }))
+        return STC_ERR_OUT_OF_MEMORY;
+    logdet_kernel<<<(unsigned)blocks, 32 * wpb, 0, S(stream)>>>((const double*)d_factor, stride, poff, (int)np, batch,
+                                                                d_logdet);
     return cudaGetLastError() == cudaSuccess ? STC_OK : STC_ERR_CUDA;
 }
 
@@ -1892,10 +2390,11 @@ extern "C" int stc_factor_to_csc(const stc_plan* Pc, const void* d_factor, int64
     int dev, sms, rc;
     if ((rc = device_info(&dev, &sms))) return rc;
     if ((rc = ensure_plan(P, dev))) return rc;
+    if (is_sn(P) && (rc = ensure_sn(P, dev))) return rc;
     const long long nnzl = P->Lp[P->n];
     const int blocks = std::max(1, std::min<int>(sms * 8, (int)((nnzl + 255) / 256)));
-    to_csc_kernel<<<blocks, 256, 0, S(stream)>>>((const double*)d_factor, P->factor_doubles, batch, P->dev.csc_map,
-                                                 nnzl, d_Lx);
+    to_csc_kernel<<<blocks, 256, 0, S(stream)>>>((const double*)d_factor, P->item_doubles(), batch,
+                                                 is_sn(P) ? P->sndev.csc_map : P->dev.csc_map, nnzl, d_Lx);
     return cudaGetLastError() == cudaSuccess ? STC_OK : STC_ERR_CUDA;
 }
 
@@ -1907,12 +2406,13 @@ extern "C" int stc_solve(const stc_plan* Pc, const void* d_factor, int64_t batch
     int dev, sms, rc;
     if ((rc = device_info(&dev, &sms))) return rc;
     if ((rc = ensure_plan(P, dev))) return rc;
+    if (is_sn(P)) return sn_solve(P, d_factor, batch, nrhs, d_b, d_x, d_work, stream, dev, sms);
     TaskSet* ts = nullptr;
     if ((rc = get_taskset(P, 1, false, &ts))) return rc;
     if ((rc = ensure_taskset(P, ts, dev))) return rc;
     const long long chains = batch * nrhs;
     cudaStream_t st = S(stream);
-    const size_t flags = ((size_t)chains * 2 * P->nt * sizeof(int) + 255) / 256 * 256;
+    const size_t flags = solve_flags(P, chains);
     if (cudaMemsetAsync(d_work, 0, sizeof(WorkHeader) + flags, st) != cudaSuccess) return STC_ERR_CUDA;
     SolveArgs a{};
     a.tiles = ts->d_tiles; a.saind = P->dev.saind; a.rowstart = P->dev.srow_beg; a.rowtiles = P->dev.srow_tiles;
@@ -1959,6 +2459,7 @@ extern "C" int stc_selinv(const stc_plan* Pc, const void* d_factor, int64_t batc
                           void* stream) {
     stc_plan* P = const_cast<stc_plan*>(Pc);
     if (!P || !d_factor || !d_sigma || !d_work || batch <= 0 || d_factor == d_sigma) return STC_ERR_INVALID_ARG;
+    if (is_sn(P)) return STC_ERR_UNSUPPORTED;  // selected inverse on the tile routes only
     int dev, sms, rc;
     if ((rc = device_info(&dev, &sms))) return rc;
     if ((rc = ensure_plan(P, dev))) return rc;
@@ -2046,6 +2547,7 @@ extern "C" int stc_group_create(int32_t nplans, const stc_plan* const* plans, co
     int64_t btot = 0;
     for (int p = 0; p < nplans; ++p) {
         if (!plans[p] || batch[p] <= 0 || batch[p] >= (1LL << 28)) return STC_ERR_INVALID_ARG;
+        if (is_sn(plans[p])) return STC_ERR_UNSUPPORTED;  // mixed batches of tile-route plans
         btot += batch[p];
     }
     size_t off = sizeof(WorkHeader);
@@ -2139,6 +2641,7 @@ extern "C" int stc_factorize_noalloc(const stc_plan* Pc, const double* d_values,
                                      int32_t* d_info, int32_t* d_status, void* stream) {
     stc_plan* P = const_cast<stc_plan*>(Pc);
     if (!P || !d_values || !d_factor || !d_info || batch <= 0) return STC_ERR_INVALID_ARG;
+    if (is_sn(P)) return STC_ERR_UNSUPPORTED;  // tile routes only
     const size_t need = factorize_ws(P, batch);
     if (need > (size_t)STC_NOALLOC_SCRATCH_BYTES) return STC_ERR_UNSUPPORTED;
     int dev, sms, rc;

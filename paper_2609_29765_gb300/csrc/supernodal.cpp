@@ -16,7 +16,7 @@
 //   * the left-looking task list of Sec. 5.4: for each supernode J in order, every
 //     UPDATE L_KJ -= L_KI L_JI^T from the supernodes I < J with a cell (J, I), then the
 //     FACTOR (POTRF) of J's diagonal cell, then the TRSM of each cell below it.
-// Only the host plan exists: the plans still execute on the semisparse tile route.
+// Plans analysed for the supernodal route execute this layout on the GPU (replay.cu).
 #include <algorithm>
 #include <functional>
 #include <memory>
@@ -269,6 +269,26 @@ void stc_plan::build_device_form(stc::SnPlan& S, const vector<int32_t>& snof,
             }
         }
     }
+    // per-cell column maps (every off-diagonal cell (J, I) is a source of J's diagonal
+    // task, so each has one), the cells owned by each row supernode, and the FMAs the
+    // device form executes: updates (lower half on a diagonal target), POTRF, TRSM
+    S.cell_cmap = cmap_of;
+    S.rptr_cells.assign(nsn + 1, 0);
+    for (int32_t J = 0; J < nsn; ++J) {
+        S.rptr_cells[J + 1] = S.rptr_cells[J] + (int32_t)byrow[J].size();
+        S.row_cells.insert(S.row_cells.end(), byrow[J].begin(), byrow[J].end());
+    }
+    double fma = 0.0;
+    for (const stc::SnDevTask& t : S.dtasks) {
+        const double w = S.dcells[t.cell].w;
+        for (int32_t u = t.ubeg; u < t.uend; ++u) {
+            const stc::SnDevUpd& x = S.dupds[u];
+            const double ra = x.ar1 - x.ar0, hb = S.dcells[x.b].h;
+            fma += (t.kind == stc::SN_T_DIAG ? ra * (ra + 1) / 2 : ra * hb) * x.klen;
+        }
+        fma += t.kind == stc::SN_T_DIAG ? w * (w + 1) * (w + 2) / 6 : double(t.rs1 - t.rs0) * w * (w + 1) / 2;
+    }
+    S.fma_exec = fma;
     // value and CSC maps into the arena
     vector<int64_t> iperm(n);
     for (int64_t k = 0; k < n; ++k) iperm[perm[k]] = k;

@@ -34,6 +34,8 @@ def _plans():
     yield "band_slices", Plan(3000, Ap, Ai, nb=64, ordering="natural", row_slices=4)
     Ap, Ai, _ = I.random_spd(700, 0.005, 2)
     yield "random_given", Plan(700, Ap, Ai, nb=24, perm=np.random.default_rng(1).permutation(700))
+    Ap, Ai, Ax, coords = I.laplace2d_bordered(16, 16, 2)
+    yield "supernodal_route", Plan(len(Ap) - 1, Ap, Ai, coords=coords, nb=32, route="supernodal")
 
 
 PLANS = list(_plans())
