@@ -38,7 +38,19 @@ N, BW, NB = 200_000, 200, 128
 SMS, DFMA_PER_CLK, MAX_MHZ = 152, 2, 2070.0
 # nominal FP64 ALU peak from unit counts and the maximum SM clock (TFLOP/s)
 PEAK_FP64_NOMINAL = SMS * DFMA_PER_CLK * 2 * MAX_MHZ * 1e6 / 1e12
-HBM_GBS = 6678.5  # measured copy bandwidth of the GB300s (MEASURED_PEAKS.json)
+
+
+def _hbm_peak():
+    """Measured copy bandwidth of the GB300s (MEASURED_PEAKS.json, written by the
+    pool's driver), else the recipe's fallback figure."""
+    try:
+        v = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"])
+        return v, "measured (MEASURED_PEAKS.json hbm_gbs)"
+    except (OSError, ValueError, KeyError, TypeError):
+        return 6800.0, "fallback 6.8 TB/s"
+
+
+HBM_GBS, HBM_SOURCE = _hbm_peak()
 
 
 def parse():
@@ -55,8 +67,8 @@ def parse():
                    help="row slices per off-diagonal tile (0: the library's choice)")
     p.add_argument("--workloads", default="c1,c3,c4,c5",
                    help="other workloads measured after the headline, comma list or 'none'")
-    p.add_argument("--full-workloads", action="store_true",
-                   help="the other workloads at their full batch sizes (minutes)")
+    p.add_argument("--small-workloads", action="store_true",
+                   help="the other workloads at reduced batch sizes (a quick check, not the configured sizes)")
     return p.parse_args()
 
 
@@ -264,11 +276,11 @@ def measure_workloads(args):
     from paper_2609_29765_gb300.api import Group, Plan
 
     want = [] if args.workloads == "none" else args.workloads.split(",")
-    full = args.full_workloads
+    small = args.small_workloads
     dev = lambda a: torch.as_tensor(np.ascontiguousarray(a), device="cuda")
     out = {}
 
-    def plain_and_batched(P, vals, reps_b, reps_p, with_solve):
+    def plain_and_batched(P, vals, reps_b, reps_p, with_solve, warm_b=1):
         batch = vals.shape[0]
         fac = torch.empty(P.factor_bytes(batch) // 8, dtype=torch.float64, device="cuda")
         info = torch.empty(batch, dtype=torch.int32, device="cuda")
@@ -282,55 +294,75 @@ def measure_workloads(args):
             L.check(L.stc_logdet(P.h, fac, bt, ld), "logdet")
             if with_solve:
                 L.check(L.stc_solve(P.h, fac, bt, 1, b[:bt], x[:bt], ws), "solve")
-        ms_b = _events_ms(lambda: run(batch), reps_b, 1)
-        ms_f = _events_ms(lambda: L.check(L.stc_factorize(P.h, vals, batch, fac, ws, info)), reps_b, 0)
         ms_p = _events_ms(lambda: run(1), reps_p, 1)
+        # the batched launch is warmed up on a few items (same kernels, same plan upload)
+        _events_ms(lambda: run(min(batch, 8)), warm_b, 0)
+        ms_b = _events_ms(lambda: run(batch), reps_b, 0)
         L.check(L.stc_sync_status(ws), "device status")
-        assert int(info.abs().sum()) == 0
+        assert int(info.abs().sum()) == 0 and bool(torch.isfinite(ld[:batch]).all())
+        ms_f = _events_ms(lambda: L.check(L.stc_factorize(P.h, vals, batch, fac, ws, info)), reps_b, 0)
+        L.check(L.stc_sync_status(ws), "device status")
+        del fac, b, x
         return ms_b, ms_f, ms_p
 
     if "c1" in want:
         Ap, Ai, _, coords = I.laplace2d_bordered(seed=0)
         n = len(Ap) - 1
-        P = Plan(n, Ap, Ai, coords=coords, nb=64)
         batch = 1024
         vals = dev(_distinct_values(lambda s: I.laplace2d_bordered(seed=s)[2], batch, 16))
-        ms_b, ms_f, ms_p = plain_and_batched(P, vals, 5, 50, True)
         out["c1"] = {"workload": "n=1,026 32x32 Laplacian + 0.1 I + 2 border rows, ND, n_b=64; factor+logdet+solve",
-                     "route": P.route, "route_selected": P.route_selected,
-                     "plain": {"value": 1e3 / ms_p, "unit": UNIT, "us_per_call": 1e3 * ms_p},
-                     "batched": {"value": batch * 1e3 / ms_b, "unit": UNIT, "batch": batch,
-                                 "values": "16 distinct value sets (seeds 0..15) cycled"},
-                     "note": "latency-bound: roofline fraction not meaningful"}
+                     "note": "latency-bound: roofline fraction not meaningful",
+                     "values": "16 distinct value sets (seeds 0..15) cycled"}
+        for route in ("semisparse", "supernodal"):
+            P = Plan(n, Ap, Ai, coords=coords, nb=64, route=route)
+            ms_b, ms_f, ms_p = plain_and_batched(P, vals, 5, 50, True)
+            out["c1"][route] = {"route_selected": P.route_selected,
+                                "plain": {"value": 1e3 / ms_p, "unit": UNIT, "us_per_call": 1e3 * ms_p},
+                                "batched": {"value": batch * 1e3 / ms_b, "unit": UNIT, "batch": batch}}
         del vals
-    c3_plan = None
-    if "c3" in want or "c5" in want:
-        Ap, Ai, coords = I.stcov_pattern()
-        c3_plan = Plan(len(Ap) - 1, Ap, Ai, coords=coords, nb=64, route="semisparse")
     if "c3" in want:
-        P = c3_plan
-        batch = 128 if full else 16
+        Ap, Ai, coords = I.stcov_pattern()
+        n = len(Ap) - 1
+        batch = 16 if small else 256
         th = I.stcov_thetas(batch, 0)
-        vals = dev(_distinct_values(lambda s: I.stcov_values(th[s]), batch, 16 if full else 4))
-        ms_b, ms_f, ms_p = plain_and_batched(P, vals, 1 if full else 2, 2, False)
-        fa = P.info["flops_alg"]
+        distinct = 4 if small else 16
+        vals = dev(_distinct_values(lambda s: I.stcov_values(th[s]), batch, distinct))
         out["c3"] = {"workload": "tau AR1(rho) x SPDE 9-point 60x60, 50 steps, + 20 border rows, n=180,020, "
-                                 "ND, n_b=64; factor+logdet",
-                     "route": P.route, "route_selected": P.route_selected,
-                     "plain": {"value": 1e3 / ms_p, "unit": UNIT, "ms_per_call": ms_p},
-                     "batched": {"value": batch * 1e3 / ms_b, "unit": UNIT, "batch": batch,
-                                 "values": "%d distinct theta draws cycled" % (16 if full else 4),
-                                 "note": "one launch of %d of the 256 theta sets (factors: %.0f GB)"
-                                         % (batch, P.factor_bytes(batch) / 1e9)},
-                     "roofline_replay": dict(_fp64(fa * batch, ms_f), bound="alu", peak=PEAK_FP64_NOMINAL,
-                                             work="sum_j c_j^2 = %.4g flops per factorization" % fa,
-                                             ms=ms_f)}
-        del vals
+                                 "ND; factor+logdet", "values": "%d distinct theta draws cycled" % distinct}
+        # the supernodal route (the selector's choice) holds all 256 theta sets in one launch
+        P = Plan(n, Ap, Ai, coords=coords, nb=64, route="supernodal")
+        ms_b, ms_f, ms_p = plain_and_batched(P, vals, 1, 2, False)
+        fa, fx = P.info["flops_alg"], P.info["flops_tile"]
+        out["c3"]["supernodal"] = {
+            "route_selected": P.route_selected,
+            "plain": {"value": 1e3 / ms_p, "unit": UNIT, "ms_per_call": ms_p},
+            "batched": {"value": batch * 1e3 / ms_b, "unit": UNIT, "batch": batch,
+                        "note": "one persistent launch of all %d theta sets (factors: %.0f GB)"
+                                % (batch, P.factor_bytes(batch) / 1e9)},
+            "roofline_replay": dict(_fp64(fa * batch, ms_f), bound="alu", peak=PEAK_FP64_NOMINAL,
+                                    work="sum_j c_j^2 = %.4g flops per factorization (executed %.4g)" % (fa, fx),
+                                    ms=ms_f),
+            "analyze_seconds": P.info["analyze_seconds"]}
+        del P
+        torch.cuda.empty_cache()
+        # the semisparse tile route on the same pattern (its factors take 1.8 GB per set)
+        P = Plan(n, Ap, Ai, coords=coords, nb=64, route="semisparse")
+        bt = 16
+        ms_b, ms_f, ms_p = plain_and_batched(P, vals[:bt], 1, 2, False)
+        out["c3"]["semisparse"] = {
+            "plain": {"value": 1e3 / ms_p, "unit": UNIT, "ms_per_call": ms_p},
+            "batched": {"value": bt * 1e3 / ms_b, "unit": UNIT, "batch": bt},
+            "roofline_replay": dict(_fp64(fa * bt, ms_f), bound="alu", peak=PEAK_FP64_NOMINAL, ms=ms_f,
+                                    work="sum_j c_j^2 = %.4g flops per factorization (executed %.4g)"
+                                         % (fa, P.info["flops_tile"]))}
+        del vals, P
+        torch.cuda.empty_cache()
     if "c5" in want:
-        P = c3_plan
-        batch = 64 if full else 8
+        Ap, Ai, coords = I.stcov_pattern()
+        P = Plan(len(Ap) - 1, Ap, Ai, coords=coords, nb=64, route="semisparse")
+        batch = 8 if small else 64
         th = I.stcov_thetas(batch, 0)
-        distinct = 16 if full else 4
+        distinct = 4 if small else 16
         vals = dev(_distinct_values(lambda s: I.stcov_values(th[s]), batch, distinct))
         xs = dev(np.stack([I.rhs(P.n, s)[0] for s in range(batch)]))
         fac = torch.empty(P.factor_bytes(batch) // 8, dtype=torch.float64, device="cuda")
@@ -343,30 +375,31 @@ def measure_workloads(args):
         ws = P.workspace(batch)
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
 
-        def grad_step(rec=False):
+        def grad_step(bt, rec=False):
             if rec:
                 ev[0].record()
-            L.check(L.stc_factorize(P.h, vals, batch, fac, ws, info), "factorize")
-            L.check(L.stc_logdet(P.h, fac, batch, ld), "logdet")
+            L.check(L.stc_factorize(P.h, vals[:bt], bt, fac, ws, info), "factorize")
+            L.check(L.stc_logdet(P.h, fac, bt, ld), "logdet")
             if rec:
                 ev[1].record()
-            L.check(L.stc_logdet_backward(P.h, fac, batch, None, g, 0, sig, ws), "logdet_backward")
+            L.check(L.stc_logdet_backward(P.h, fac, bt, None, g[:bt], 0, sig, ws), "logdet_backward")
             if rec:
                 ev[2].record()
-            L.check(L.stc_quad_form(P.h, batch, vals, xs, q), "quad_form")
-            L.check(L.stc_sym_outer_backward(P.h, batch, xs, xs, neg, g, 1), "outer_backward")
+            L.check(L.stc_quad_form(P.h, bt, vals[:bt], xs[:bt], q), "quad_form")
+            L.check(L.stc_sym_outer_backward(P.h, bt, xs[:bt], xs[:bt], neg, g[:bt], 1), "outer_backward")
             if rec:
                 ev[3].record()
-        grad_step()
+        grad_step(min(batch, 4))       # warm-up on a few items (same kernels and plan upload)
         torch.cuda.synchronize()
-        grad_step(True)
+        grad_step(batch, True)
         torch.cuda.synchronize()
         L.check(L.stc_sync_status(ws), "device status")
         assert int(info.abs().sum()) == 0
         ms_tot = ev[0].elapsed_time(ev[3])
         ms_bwd = ev[1].elapsed_time(ev[2])
         fa = P.info["flops_alg"]
-        out["c5"] = {"workload": "d/dQ [logdet Q(theta) - x^T Q(theta) x] on the n=180,020 pattern above",
+        out["c5"] = {"workload": "d/dQ [logdet Q(theta) - x^T Q(theta) x] on the n=180,020 pattern above, "
+                                 "semisparse route",
                      "gradients": {"value": batch * 1e3 / ms_tot, "unit": "gradients/s", "batch": batch,
                                    "values": "%d distinct theta draws cycled" % distinct,
                                    "step": "factorize+logdet+selected inverse+gather+quad form+outer product",
@@ -376,11 +409,11 @@ def measure_workloads(args):
                                              ms=ms_bwd),
                      "gradient_w_r_t": "the nnzA values of Q; the 3-parameter theta chain is a host-side "
                                        "contraction outside the step"}
-        del vals, fac, sig, g
-    c3_plan = None
+        del vals, fac, sig, g, P
+        torch.cuda.empty_cache()
     if "c4" in want:
-        plans, vals, nfl = [], [], []
-        per = 8 if full else 2
+        plans, vals = [], []
+        per = 2 if small else 8
         for m in (32, 48, 64):
             vs = [I.fem3d(m, m, m, seed=s)[2] for s in range(per)]
             Ap, Ai, _, coords = I.fem3d(m, m, m, seed=0)
@@ -394,20 +427,30 @@ def measure_workloads(args):
         ms_p = _events_ms(lambda: L.check(L.stc_factorize(P64.h, vals[2][:1], 1, fac, ws, info)), 1, 1)
         L.check(L.stc_sync_status(ws), "device status")
         del fac
+        Ap, Ai, _, coords = I.fem3d(64, 64, 64, seed=0)
+        Psn = Plan(len(Ap) - 1, Ap, Ai, coords=coords, nb=64, route="supernodal")
+        fac = torch.empty(Psn.factor_bytes(1) // 8, dtype=torch.float64, device="cuda")
+        ws = Psn.workspace(1)
+        ms_sn = _events_ms(lambda: L.check(L.stc_factorize(Psn.h, vals[2][:1], 1, fac, ws, info)), 1, 1)
+        L.check(L.stc_sync_status(ws), "device status")
+        del fac
         G = Group(plans, [per] * 3)
         ms_g = _events_ms(lambda: G.factorize(vals), 1, 1)
         L.check(G.status(), "group status")
         fl = sum(P.info["flops_alg"] for P in plans) * per
         ft = sum(P.info["flops_tile"] for P in plans) * per
-        out["c4"] = {"workload": "7-point lognormal-conductance FEM + 1e-3 I, ND, n_b=64, forced dense route",
+        out["c4"] = {"workload": "7-point lognormal-conductance FEM + 1e-3 I, ND, n_b=64",
                      "route_selected": P64.route_selected,
-                     "plain_64cubed": {"value": 1e3 / ms_p, "unit": UNIT, "ms_per_call": ms_p, "n": P64.n,
-                                       **_fp64(P64.info["flops_alg"], ms_p),
-                                       "tile_tflops": P64.info["flops_tile"] / (ms_p * 1e-3) / 1e12},
-                     "mixed_batch": {"value": 3 * per * 1e3 / ms_g, "unit": UNIT,
-                                     "items": "32^3, 48^3, 64^3 x %d each, one persistent launch" % per,
-                                     "ms": ms_g, **_fp64(fl, ms_g),
-                                     "tile_tflops": ft / (ms_g * 1e-3) / 1e12}}
+                     "plain_64cubed_dense": {"value": 1e3 / ms_p, "unit": UNIT, "ms_per_call": ms_p, "n": P64.n,
+                                             **_fp64(P64.info["flops_alg"], ms_p),
+                                             "tile_tflops": P64.info["flops_tile"] / (ms_p * 1e-3) / 1e12},
+                     "plain_64cubed_supernodal": {"value": 1e3 / ms_sn, "unit": UNIT, "ms_per_call": ms_sn,
+                                                  **_fp64(Psn.info["flops_alg"], ms_sn),
+                                                  "executed_tflops": Psn.info["flops_tile"] / (ms_sn * 1e-3) / 1e12},
+                     "mixed_batch_dense": {"value": 3 * per * 1e3 / ms_g, "unit": UNIT,
+                                           "items": "32^3, 48^3, 64^3 x %d each, one persistent launch" % per,
+                                           "ms": ms_g, **_fp64(fl, ms_g),
+                                           "tile_tflops": ft / (ms_g * 1e-3) / 1e12}}
         del G, vals
     torch.cuda.empty_cache()
     return out
@@ -431,14 +474,16 @@ def run_ours(args):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cores = host_cores()
-        wall = oracle_parallel(args.n, cores)[0]
+        walls = oracle_parallel(args.n, cores, rounds=4)
+        wall = min(walls[1:])          # minimum of 3 after a warm-up round, as the paper times
         rate = cores / wall
-        t = oracle_sample(args.n, 2, seed0=0)
+        t = oracle_sample(args.n, 4, seed0=0)
         cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": "%d value sets of the workload at once (factor+logdet+solve), one single-threaded "
-                         "oracle process per host core, %.1f s wall" % (cores, wall),
-               "single_thread": {"value": len(t) / sum(t), "unit": UNIT, "cores": 1,
-                                 "sample": "2 value sets, one after the other, %.1f s" % sum(t)}}
+                         "oracle process per host core; minimum of 3 rounds after a warm-up round, %.1f s wall"
+                         % (cores, wall),
+               "single_thread": {"value": 1.0 / min(t[1:]), "unit": UNIT, "cores": 1,
+                                 "sample": "one value set, minimum of 3 after a warm-up, %.2f s" % min(t[1:])}}
 
     n, batch = args.n, args.batch
     Ap, Ai = I.band_pattern(n, BW)
@@ -631,11 +676,13 @@ def run_ours(args):
         "kernels": {
             "scatter_kernel": {"ms": ms_scatter, "bound": "hbm", "unit": "GB/s",
                                "achieved": scat_bytes / (ms_scatter * 1e-3) / 1e9,
-                               "peak": HBM_GBS, "frac": scat_bytes / (ms_scatter * 1e-3) / 1e9 / HBM_GBS,
+                               "peak": HBM_GBS, "peak_source": HBM_SOURCE,
+                               "frac": scat_bytes / (ms_scatter * 1e-3) / 1e9 / HBM_GBS,
                                "work": "zero-fill of the factor + values read + map read + scattered writes"},
             "solve_kernel": {"ms": ms_solve, "bound": "hbm", "unit": "GB/s",
                              "achieved": solve_bytes / (ms_solve * 1e-3) / 1e9,
-                             "peak": HBM_GBS, "frac": solve_bytes / (ms_solve * 1e-3) / 1e9 / HBM_GBS,
+                             "peak": HBM_GBS, "peak_source": HBM_SOURCE,
+                             "frac": solve_bytes / (ms_solve * 1e-3) / 1e9 / HBM_GBS,
                              "work": "factor tiles read twice (forward + backward) + b, x"},
             "logdet_kernel": {"ms": ms_logdet},
         },

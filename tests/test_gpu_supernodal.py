@@ -22,11 +22,13 @@ pytestmark = pytest.mark.gpu
 
 
 def _batch(Ap, Ai, Ax, count, seed):
+    """Item 0 is Ax; item b scales every off-diagonal entry by one factor s_b in [0.3, 1],
+    i.e. (1 - s_b) D + s_b A, a convex combination of SPD matrices, so it stays SPD."""
     n = len(Ap) - 1
     col = np.repeat(np.arange(n), np.diff(Ap))
     off = Ai != col
     rng = np.random.default_rng(seed)
-    return np.stack([Ax] + [np.where(off, Ax * rng.uniform(-1, 1, len(Ax)), Ax) for _ in range(count - 1)])
+    return np.stack([Ax] + [np.where(off, Ax * rng.uniform(0.3, 1.0), Ax) for _ in range(count - 1)])
 
 
 @pytest.mark.parametrize("case", CASES, ids=lambda c: c[0])
