@@ -56,15 +56,18 @@ extern "C" {
 #define STC_ERR_BUFFER_TOO_SMALL (-7)
 
 /* A short English description of a return code (STC_OK or STC_ERR_*); a static string,
- * never NULL ("unknown error" for any other value).  Host only. */
+ * never NULL ("unknown error" for any other value).  Host only; no counterpart in the
+ * paper. */
 const char* stc_strerror(int code);
 
 /* ---- routes (Sec. 5.1) ------------------------------------------------- */
 #define STC_ROUTE_AUTO (-1)
 #define STC_ROUTE_DENSE 0       /* every active tile stored as a full n_b x n_b block  */
 #define STC_ROUTE_SEMISPARSE 1  /* active-column tiles + banded-packed diagonal tiles */
-#define STC_ROUTE_SUPERNODAL 2  /* selector result only: the supernodal route is not
-                                   built; such plans execute on the semisparse route  */
+#define STC_ROUTE_SUPERNODAL 2  /* non-uniform supernodal panels (Sec. 5.4).  Executed
+                                   when asked for with force_route; a plan whose selector
+                                   picks it under STC_ROUTE_AUTO executes on the
+                                   semisparse route (route_executed says which)        */
 
 /* ---- orderings (Sec. 3) ------------------------------------------------ */
 #define STC_ORDER_AUTO 0     /* ND when coordinates are given, else best of RCM/natural */
@@ -75,7 +78,7 @@ const char* stc_strerror(int code);
 
 typedef struct stc_options {
     int32_t nb;           /* tile size n_b; 0 = 128.  Built range 8..128, multiple of 8 */
-    int32_t force_route;  /* STC_ROUTE_AUTO, STC_ROUTE_DENSE or STC_ROUTE_SEMISPARSE   */
+    int32_t force_route;  /* STC_ROUTE_AUTO, _DENSE, _SEMISPARSE or _SUPERNODAL        */
     int32_t ordering;     /* STC_ORDER_*                                               */
     int32_t nd_leaf;      /* ND leaf size; 0 = 64                                      */
     const int64_t* perm;  /* host [n], for STC_ORDER_GIVEN: perm[k] = original index of
@@ -105,17 +108,19 @@ typedef struct stc_plan_info {
     int64_t ntiles;             /* active tiles (diagonal included)                   */
     int64_t nnzA;               /* stored lower entries of A                          */
     int64_t nnzL;               /* structural non-zeros of L (diagonal included)      */
-    int64_t stored_entries;     /* doubles stored for L in tiles (per item)           */
+    int64_t stored_entries;     /* doubles stored for L (tiles, or the lower trapezoids
+                                   of the supernodal panels), per item               */
     int64_t factor_doubles;     /* per-item factor footprint incl. logdet partials    */
     int32_t route_selected;     /* selector's choice (STC_ROUTE_*)                    */
-    int32_t route_executed;     /* route the plan runs (dense or semisparse)          */
+    int32_t route_executed;     /* route the plan runs (dense, semisparse, supernodal) */
     int32_t ordering;           /* ordering used (STC_ORDER_*)                        */
     int32_t reserved0;
     double phi, rho, sigma;     /* routing features (Sec. 5.1)                        */
     int64_t ntasks_alg1;        /* Algorithm 1 tasks                                  */
     int64_t n_potrf, n_syrk, n_trsm, n_gemm;
     double flops_alg;           /* sum_j c_j^2 (c_j = column count of L)              */
-    double flops_tile;          /* flops the tile kernels execute (row slice = 1)     */
+    double flops_tile;          /* flops the device kernels execute (tile routes: row
+                                   slice = 1; supernodal: updates, POTRF and TRSM)   */
     double analyze_seconds;     /* host wall time of stc_analyze                      */
 } stc_plan_info;
 
@@ -174,10 +179,14 @@ typedef struct stc_plan_info {
 #define STC_EXPORT_SN_VALUE_MAP 18  /* [nnzA] arena offset of each entry of A             */
 #define STC_EXPORT_SN_CSC_MAP 19    /* [nnzL] arena offset of each structural entry of L  */
 
-/* Fill *opt with defaults (nb 128, auto route, auto ordering, ND leaf 64). */
+/* Fill *opt with defaults (nb 128, auto route, auto ordering, ND leaf 64; selector gates
+ * of Table 5: rho_dense 0.90, phi 2.0, rho_semi 0.15, sigma 20). */
 void stc_options_default(stc_options* opt);
 
-/* Symbolic analysis (host only; no GPU needed).
+/* Symbolic analysis (host only; no GPU needed): the once-per-pattern analyze of Sec. 6.6
+ * -- ordering and symbolic factorization (Sec. 3), features and selector (Sec. 5.1),
+ * per-tile metadata, Algorithm 1's task list and the scatter maps (Sec. 5.2), and on the
+ * supernodal route the supernodal layout (Sec. 5.4).
  *   n, colptr[n+1], rowind[nnz]: lower CSC pattern of A (original order).
  *   coords: optional host [n][3] lattice coordinates for geometric ND (integral values;
  *           rows with a NaN coordinate are set-aside dense rows, ordered last); NULL ok.
@@ -187,10 +196,16 @@ void stc_options_default(stc_options* opt);
 int stc_analyze(int64_t n, const int64_t* colptr, const int64_t* rowind,
                 const double* coords, const stc_options* opt, stc_plan** plan_out);
 
+/* The plan's summary (the quantities the paper reports per matrix: features and route,
+ * Sec. 5.1 and Table 1; nnz(L) and stored entries, App. C; task counts and flops).
+ * Named stc_plan_info_get because stc_plan_info names its struct.  *out written. */
 int stc_plan_info_get(const stc_plan* plan, stc_plan_info* out);
 
-/* Copy one symbolic array (STC_EXPORT_*) into host memory.  Call with buf == NULL to
- * read the size in bytes into *bytes; STC_ERR_BUFFER_TOO_SMALL if *bytes is short. */
+/* Copy one symbolic array (STC_EXPORT_*: the ordering and etree of Sec. 3, the tile map
+ * and active-column lists of Sec. 4.1, kd of Sec. 4.3, Algorithm 1's tasks, the
+ * supernodal layout of Sec. 5.4) into host memory, for bit-exact checks.  Call with
+ * buf == NULL to read the size in bytes into *bytes; STC_ERR_BUFFER_TOO_SMALL if *bytes
+ * is short. */
 int stc_plan_export(const stc_plan* plan, int what, void* buf, size_t* bytes);
 
 /* Copy one array of the device task list that stc_factorize replays (Algorithm 1's tasks
@@ -221,10 +236,13 @@ int stc_plan_export(const stc_plan* plan, int what, void* buf, size_t* bytes);
 int stc_plan_export_taskset(const stc_plan* plan, int32_t slices, int bl_order, int what, void* buf,
                             size_t* bytes);
 
-/* Upload the plan's device metadata to the current CUDA device now (synchronous).
- * Optional: every device call does it on first use. */
+/* Upload the plan's device metadata (tile or supernodal descriptors, task list, value
+ * and CSC maps: the per-task offsets resolved at analysis, Sec. 5.2) to the current CUDA
+ * device now (synchronous), and load the library's device module there.  Optional:
+ * every device call does it on first use. */
 int stc_plan_upload(stc_plan* plan);
 
+/* Free a plan, its device copies and its own workspace (no-op on NULL). */
 void stc_plan_destroy(stc_plan* plan);
 
 /* Save / load an analysed plan (the analysis is what the repeated factorizations reuse,
@@ -239,28 +257,45 @@ void stc_plan_destroy(stc_plan* plan);
 int stc_plan_save(const stc_plan* plan, void* buf, size_t* bytes);
 int stc_plan_load(const void* buf, size_t bytes, stc_plan** plan_out);
 
-/* Bytes of caller-owned device memory:
- *   factor    -- the tile-stored factor of `batch` items (item stride = value at batch 1)
+/* Bytes of caller-owned device memory (Sec. 3: the factor is allocated once from the
+ * symbolic analysis, every tile's offset resolved in advance):
+ *   factor    -- the factor of `batch` items in the route's storage (tiles, or supernodal
+ *                panels), then one logdet partial per diagonal tile / supernode; item
+ *                stride = the value at batch 1
  *   workspace -- dependency counters, queue head and status word used by factorize,
- *                solve and logdet_backward (contents need not be initialised). */
+ *                solve, selinv and logdet_backward (contents need not be initialised).
+ *
+ * Workspace convention (factorize, factorize_scattered, solve, selinv, logdet_backward):
+ * d_work == NULL uses a workspace owned by the plan instead, allocated on the first such
+ * call and grown when a larger one is needed (that call synchronizes the device, so
+ * make it before any stream capture); it is freed with the plan, every call on the plan
+ * shares it, and calls that overlap on the GPU race on it.  Its status word is read with
+ * stc_plan_sync_status.  The paper's interface passes no workspace (Sec. 6.6); a caller
+ * that owns its memory passes d_work to keep calls on several streams independent. */
 size_t stc_factor_bytes(const stc_plan* plan, int64_t batch);
 size_t stc_workspace_bytes(const stc_plan* plan, int64_t batch);
 
-/* Numeric factorization of `batch` value sets of the plan's pattern, one persistent
- * kernel walking the task DAG (Algorithm 2 with per-tile counters).
+/* Numeric factorization (Sec. 6.6's repeated factorize; Algorithm 1's tasks executed as
+ * in Algorithm 2, Sec. 5.3, with per-tile counters in place of the progress matrix P;
+ * on the supernodal route the left-looking supernodal tasks of Sec. 5.4) of `batch`
+ * value sets of the plan's pattern by one persistent kernel walking the task DAG.
  *   d_values [batch][nnzA] FP64 in the original CSC order of the analyzed pattern;
  *   d_factor stc_factor_bytes(plan,batch) bytes (written); d_work
- *   stc_workspace_bytes(plan,batch) bytes; d_info [batch] int32 (written).
+ *   stc_workspace_bytes(plan,batch) bytes, or NULL (see above); d_info [batch] int32
+ *   (written).
  * A wait that exceeds spin_limit sets the workspace status to STC_ERR_TIMEOUT and the
  * kernel finishes (results then undefined); read it with stc_sync_status. */
 int stc_factorize(const stc_plan* plan, const double* d_values, int64_t batch,
                   void* d_factor, void* d_work, int32_t* d_info, void* stream);
 
 /* The two halves of stc_factorize, for callers that time or overlap them separately:
- *   stc_scatter_values      -- a1: zero the factor, copy d_values into tile storage
- *                              through the plan's value map, set the padding diagonal;
- *   stc_factorize_scattered -- a2..a9: the persistent task-DAG replay on a factor that
- *                              stc_scatter_values filled (same arguments as above). */
+ *   stc_scatter_values      -- the value upload of Sec. 6.7 (A's entries placed into the
+ *                              factor storage allocated in Sec. 3): zero the factor,
+ *                              copy d_values through the plan's value map, set the
+ *                              padding diagonal of a ragged last tile to 1;
+ *   stc_factorize_scattered -- Algorithm 2's task replay (Sec. 5.3; Sec. 5.4 on the
+ *                              supernodal route) on a factor that stc_scatter_values
+ *                              filled (same arguments as stc_factorize). */
 int stc_scatter_values(const stc_plan* plan, const double* d_values, int64_t batch,
                        void* d_factor, void* stream);
 int stc_factorize_scattered(const stc_plan* plan, int64_t batch, void* d_factor, void* d_work,
@@ -268,7 +303,10 @@ int stc_factorize_scattered(const stc_plan* plan, int64_t batch, void* d_factor,
 
 /* Mixed batches: several plans (patterns of different sizes), each with its own batch of
  * value sets, factorized by ONE persistent kernel launch whose queue merges the plans'
- * task lists in earliest-start order (up to STC_GROUP_MAX_PLANS plans).
+ * task lists in earliest-start order (up to STC_GROUP_MAX_PLANS plans).  No counterpart
+ * in the paper beyond its motivation: INLA factorizes many matrices per fit (Sec. 1, 2),
+ * and Algorithm 2's executor takes any ready task, whichever matrix it belongs to.
+ * Tile-route plans only (a supernodal plan gives STC_ERR_UNSUPPORTED).
  *   stc_group_create: host + device set-up (synchronous; uploads the plans and the merged
  *     queue); plans must outlive the group; batch[p] in 1 .. 2^28-1.
  *   stc_factorize_group: d_values[p], d_factor[p], d_info[p] are host arrays of device
@@ -292,20 +330,34 @@ int stc_factorize_mixed(int32_t nplans, const stc_plan* const* plans, const doub
                         const int64_t* batch, void* const* d_factor, int32_t* const* d_info, void* stream);
 
 /* Synchronize `stream` and return the device status word of d_work: STC_OK or
- * STC_ERR_TIMEOUT (a dependency wait gave up), or STC_ERR_CUDA. */
+ * STC_ERR_TIMEOUT (a dependency wait gave up), or STC_ERR_CUDA.  The failure reporting
+ * that replaces a hung spin-wait on P (Sec. 5.3 waits without a limit). */
 int stc_sync_status(const void* d_work, void* stream);
+/* The same for the plan's own workspace (calls made with d_work == NULL);
+ * STC_ERR_INVALID_ARG if no call has used it yet. */
+int stc_plan_sync_status(const stc_plan* plan, void* stream);
 
-/* logdet(A_b) = 2 sum_j log L_jj for every item b; d_logdet [batch] FP64. */
+/* logdet(A_b) = 2 sum_j log L_jj for every item b, from the factor where it sits (Sec.
+ * 5.4: the log-determinant is reused from the factorization; Sec. 6.7 returns it from
+ * the device factor): the factorization leaves sum log L_jj of each diagonal tile or
+ * supernode in the item's partials, summed here in a fixed order.  d_factor from
+ * stc_factorize; d_logdet [batch] FP64 (written; NaN for an item whose info != 0). */
 int stc_logdet(const stc_plan* plan, const void* d_factor, int64_t batch,
                double* d_logdet, void* stream);
 
-/* x = A^{-1} b for `nrhs` right-hand sides per item; d_b, d_x [batch][nrhs][n] FP64
- * (original ordering).  d_x may not alias d_b. d_work: stc_workspace_bytes(plan,batch*nrhs). */
+/* x = A^{-1} b = P^T L^{-T} L^{-1} P b for `nrhs` right-hand sides per item (Sec. 6.7:
+ * the solves consume the factor where it sits on the device): forward substitution over
+ * block rows (or supernodes), then backward, one persistent kernel over every (item,
+ * rhs) chain with per-block completion flags.  d_b, d_x [batch][nrhs][n] FP64 (original
+ * ordering; d_x written, may not alias d_b); d_work stc_workspace_bytes(plan,
+ * batch*nrhs) bytes or NULL (see above). */
 int stc_solve(const stc_plan* plan, const void* d_factor, int64_t batch, int64_t nrhs,
               const double* d_b, double* d_x, void* d_work, void* stream);
 
-/* Copy L's values out of tile storage into CSC order (STC_EXPORT_LP / LI layout):
- * d_Lx [batch][nnzL] FP64. */
+/* Copy L's values out of the factor storage into CSC order (STC_EXPORT_LP / LI layout),
+ * the "factor returned" form of Sec. 6.7 (Table 6 reports the factor kept on the device
+ * and returned to the caller): d_factor from stc_factorize; d_Lx [batch][nnzL] FP64
+ * (written). */
 int stc_factor_to_csc(const stc_plan* plan, const void* d_factor, int64_t batch,
                       double* d_Lx, void* stream);
 
@@ -316,19 +368,25 @@ int stc_factor_to_csc(const stc_plan* plan, const void* d_factor, int64_t batch,
  * stored entries the symbolic factor proves zero hold unspecified finite values.
  *   d_factor: a factor from stc_factorize; d_sigma: stc_factor_bytes(plan,batch) bytes
  *   (written, same layout as the factor, must not alias it); d_work:
- *   stc_workspace_bytes(plan,batch) bytes. */
+ *   stc_workspace_bytes(plan,batch) bytes or NULL (see above).
+ * Tile routes only: a supernodal plan gives STC_ERR_UNSUPPORTED. */
 int stc_selinv(const stc_plan* plan, const void* d_factor, int64_t batch, void* d_sigma,
                void* d_work, void* stream);
 
-/* Adjoint of logdet: d_gvalues[b][e] (+)= gout[b] * d logdet(A_b) / d a_e for every stored
- * lower entry e of A (original CSC order), i.e. (2 - delta_ij) (A^{-1})_ij, A symmetric
- * parametrised by its lower triangle.  d_gout [batch] or NULL (= 1); accumulate != 0 adds
- * to d_gvalues.  Runs stc_selinv into d_sigma (scratch, stc_factor_bytes) first. */
+/* Adjoint of logdet (no counterpart in the paper: the gradient d logdet / dA = A^{-1}
+ * needs the selected inversion Sec. 6.2 leaves to separate work): d_gvalues[b][e] (+)=
+ * gout[b] * d logdet(A_b) / d a_e for every stored lower entry e of A (original CSC
+ * order), i.e. (2 - delta_ij) (A^{-1})_ij, A symmetric parametrised by its lower
+ * triangle.  d_gout [batch] or NULL (= 1); accumulate != 0 adds to d_gvalues.  Runs
+ * stc_selinv into d_sigma first (scratch of stc_factor_bytes(plan,batch) bytes, or NULL
+ * for one owned by the plan, grown and shared like the plan's workspace); d_work as for
+ * stc_selinv. */
 int stc_logdet_backward(const stc_plan* plan, const void* d_factor, int64_t batch,
                         const double* d_gout, double* d_gvalues, int accumulate, void* d_sigma,
                         void* d_work, void* stream);
 
-/* Symmetric outer-product adjoint, for quadratic forms and solves:
+/* Symmetric outer-product adjoint, for quadratic forms and solves (no counterpart in the
+ * paper; the adjoint of x^T A x and of x = A^{-1} b with respect to A's lower values):
  *   d_gvalues[b][e] (+)= scale[b] * (2 - delta_ij)/2 * (u_i v_j + u_j v_i),  e = (i, j)
  * with u, v [batch][n] in the original ordering; scale [batch] or NULL (= 1).
  * u = v = x gives d(x^T A x)/d a_e; u = A^{-1} b, v = A^{-1} g, scale = -1 gives the
@@ -343,7 +401,9 @@ int stc_sym_outer_backward(const stc_plan* plan, int64_t batch, const double* d_
                            const double* d_v, const double* d_scale, double* d_gvalues,
                            int accumulate, void* stream);
 
-/* out[b] = x_b^T A_b x_b from the lower CSC values (d_values [batch][nnzA], d_x [batch][n]). */
+/* out[b] = x_b^T A_b x_b from the lower CSC values (d_values [batch][nnzA], d_x [batch][n]);
+ * the Gaussian quadratic form beside logdet in an INLA objective (Sec. 1), no
+ * counterpart in the paper's interface. */
 int stc_quad_form(const stc_plan* plan, int64_t batch, const double* d_values,
                   const double* d_x, double* d_out, void* stream);
 
@@ -371,12 +431,16 @@ int stc_fp64_peak_probe(double* d_scratch, int64_t scratch_doubles, int64_t iter
  *   d_info [batch] outputs as for stc_factorize; d_status: optional device int32 that
  *   receives STC_OK or STC_ERR_TIMEOUT when the kernel ends (NULL = not reported).
  * Preconditions: stc_plan_upload(plan) was called on the current device (otherwise
- * STC_ERR_INVALID_ARG: uploading would allocate).  The first call on each device looks
- * up the array's device address (cudaGetSymbolAddress); make that first call before
- * any stream capture.  Every call on a device shares the one array and clears the part
- * it uses on `stream` before its kernel starts; calls whose kernels overlap on the GPU
- * (different streams, or several threads) race on it and give undefined results, so
- * serialise them. */
+ * STC_ERR_INVALID_ARG: uploading would allocate).  stc_plan_upload also loads the
+ * library's device module on that device and looks up the array's device address
+ * (cudaGetSymbolAddress), so the array is placed there at that moment: call it before
+ * reserving the rest of the GPU's memory and before any stream capture.  Every call on a
+ * device shares the one array and clears the part it uses on `stream` before its kernel
+ * starts; calls whose kernels overlap on the GPU (different streams, or several threads)
+ * race on it and give undefined results, so serialise them.  It replays the unsliced
+ * task list with every item of a task in lockstep (no per-batch choice of row slices or
+ * queue order), so its speed can differ from stc_factorize's; its results are the same
+ * to rounding.  Tile routes only (a supernodal plan gives STC_ERR_UNSUPPORTED). */
 #define STC_NOALLOC_SCRATCH_BYTES (4u << 20)
 int stc_factorize_noalloc(const stc_plan* plan, const double* d_values, int64_t batch,
                           void* d_factor, int32_t* d_info, int32_t* d_status, void* stream);

@@ -41,7 +41,7 @@ EXPORTED = [
     "stc_selinv", "stc_logdet_backward", "stc_sym_outer_backward", "stc_quad_form",
     "stc_group_create", "stc_group_workspace_bytes", "stc_factorize_group", "stc_group_destroy",
     "stc_strerror", "stc_factorize_mixed", "stc_quad_backward", "stc_plan_save", "stc_plan_load",
-    "stc_plan_export_taskset",
+    "stc_plan_export_taskset", "stc_plan_sync_status",
 ]
 (STC_TASKSET_TASKS, STC_TASKSET_UPDS, STC_TASKSET_IMAP, STC_TASKSET_TILES, STC_TASKSET_SAIND,
  STC_TASKSET_CEXT, STC_TASKSET_CSC_MAP, STC_TASKSET_PAD_DIAG) = range(8)
@@ -123,6 +123,8 @@ def lib():
         L.stc_factorize_scattered.restype = C.c_int
         L.stc_sync_status.argtypes = [_vp, _vp]
         L.stc_sync_status.restype = C.c_int
+        L.stc_plan_sync_status.argtypes = [_vp, _vp]
+        L.stc_plan_sync_status.restype = C.c_int
         L.stc_logdet.argtypes = [_vp, _vp, C.c_int64, _vp, _vp]
         L.stc_logdet.restype = C.c_int
         L.stc_solve.argtypes = [_vp, _vp, C.c_int64, C.c_int64, _vp, _vp, _vp, _vp]
@@ -276,6 +278,10 @@ def stc_factorize_scattered(plan, batch, d_factor, d_work, d_info, stream=None):
 
 def stc_sync_status(d_work, stream=None):
     return lib().stc_sync_status(_dev_ptr(d_work), _stream(stream))
+
+
+def stc_plan_sync_status(plan, stream=None):
+    return lib().stc_plan_sync_status(plan, _stream(stream))
 
 
 def stc_logdet(plan, d_factor, batch, d_logdet, stream=None):

@@ -308,6 +308,13 @@ struct stc_plan {
     mutable std::unique_ptr<stc::SnPlan> sn;
     mutable std::mutex sn_mu;
     stc::SnDev sndev;
+    // library-owned workspace and selected-inverse scratch, for calls that pass none
+    // (allocated on first such call, grown as needed, freed with the plan)
+    void* own_ws = nullptr;
+    size_t own_ws_bytes = 0;
+    void* own_sig = nullptr;
+    size_t own_sig_bytes = 0;
+    std::mutex own_mu;
     // item stride, logdet partials offset and count of the route the plan executes
     int64_t item_doubles() const { return route_exec == STC_ROUTE_SUPERNODAL ? supernodal().item_doubles() : factor_doubles; }
     int64_t logdet_off() const { return route_exec == STC_ROUTE_SUPERNODAL ? supernodal().poff() : partial_off; }

@@ -1994,6 +1994,13 @@ void free_dev(stc_plan* P) {
     for (void* p : sptrs)
         if (p) cudaFree(p);
     q = SnDev{};
+    {
+        std::lock_guard<std::mutex> g(P->own_mu);
+        if (P->own_ws) cudaFree(P->own_ws);
+        if (P->own_sig) cudaFree(P->own_sig);
+        P->own_ws = P->own_sig = nullptr;
+        P->own_ws_bytes = P->own_sig_bytes = 0;
+    }
     for (auto& kv : P->tasksets) {
         TaskSet* ts = kv.second.get();
         if (ts->d_tasks) cudaFree(ts->d_tasks);
@@ -2110,6 +2117,28 @@ int ensure_sn_impl(stc_plan* P, int dev) {
 }
 int ensure_sn(stc_plan* P, int dev) {
     return no_throw([&] { return ensure_sn_impl(P, dev); });
+}
+
+// The plan's own workspace (sigma = false) or selected-inverse scratch (sigma = true) of
+// at least `bytes`, for callers that pass a NULL buffer.  Growing it frees the old buffer
+// (cudaFree waits for the device) and allocates a new one, so the first call of a size
+// synchronizes; calls that use it must not overlap on the GPU.
+int own_buffer(stc_plan* P, bool sigma, size_t bytes, void** out) {
+    std::lock_guard<std::mutex> g(P->own_mu);
+    void*& ptr = sigma ? P->own_sig : P->own_ws;
+    size_t& have = sigma ? P->own_sig_bytes : P->own_ws_bytes;
+    if (have < bytes) {
+        if (ptr) cudaFree(ptr);
+        ptr = nullptr;
+        have = 0;
+        if (cudaMalloc(&ptr, std::max<size_t>(bytes, 256)) != cudaSuccess) {
+            ptr = nullptr;
+            return STC_ERR_OUT_OF_MEMORY;
+        }
+        have = std::max<size_t>(bytes, 256);
+    }
+    *out = ptr;
+    return STC_OK;
 }
 
 // Two CTAs per SM hide one CTA's waits behind the other's arithmetic when many items
@@ -2325,10 +2354,11 @@ extern "C" int stc_scatter_values(const stc_plan* Pc, const double* d_values, in
 extern "C" int stc_factorize_scattered(const stc_plan* Pc, int64_t batch, void* d_factor, void* d_work,
                                        int32_t* d_info, void* stream) {
     stc_plan* P = const_cast<stc_plan*>(Pc);
-    if (!P || !d_factor || !d_work || !d_info || batch <= 0) return STC_ERR_INVALID_ARG;
+    if (!P || !d_factor || !d_info || batch <= 0) return STC_ERR_INVALID_ARG;
     int dev, sms, rc;
     if ((rc = device_info(&dev, &sms))) return rc;
     if ((rc = ensure_plan(P, dev))) return rc;
+    if (!d_work && (rc = own_buffer(P, false, stc_workspace_bytes(P, batch), &d_work))) return rc;
     if (is_sn(P)) return sn_factorize_scattered(P, batch, d_factor, d_work, d_info, stream, dev, sms);
     // one or two value sets: the item's own DAG width decides, so the critical path goes first
     TaskSet* ts = nullptr;
@@ -2351,7 +2381,7 @@ extern "C" int stc_factorize_scattered(const stc_plan* Pc, int64_t batch, void* 
 
 extern "C" int stc_factorize(const stc_plan* P, const double* d_values, int64_t batch, void* d_factor,
                              void* d_work, int32_t* d_info, void* stream) {
-    if (!P || !d_values || !d_factor || !d_work || !d_info || batch <= 0) return STC_ERR_INVALID_ARG;
+    if (!P || !d_values || !d_factor || !d_info || batch <= 0) return STC_ERR_INVALID_ARG;
     int rc = stc_scatter_values(P, d_values, batch, d_factor, stream);
     if (rc) return rc;
     return stc_factorize_scattered(P, batch, d_factor, d_work, d_info, stream);
@@ -2363,6 +2393,18 @@ extern "C" int stc_sync_status(const void* d_work, void* stream) {
     WorkHeader h;
     if (cudaMemcpy(&h, d_work, sizeof(h), cudaMemcpyDeviceToHost) != cudaSuccess) return STC_ERR_CUDA;
     return h.status;
+}
+
+extern "C" int stc_plan_sync_status(const stc_plan* Pc, void* stream) {
+    stc_plan* P = const_cast<stc_plan*>(Pc);
+    if (!P) return STC_ERR_INVALID_ARG;
+    void* w;
+    {
+        std::lock_guard<std::mutex> g(P->own_mu);
+        w = P->own_ws;
+    }
+    if (!w) return STC_ERR_INVALID_ARG;  // no call has used the plan's own workspace yet
+    return stc_sync_status(w, stream);
 }
 
 extern "C" int stc_logdet(const stc_plan* P, const void* d_factor, int64_t batch, double* d_logdet,
@@ -2401,11 +2443,12 @@ extern "C" int stc_factor_to_csc(const stc_plan* Pc, const void* d_factor, int64
 extern "C" int stc_solve(const stc_plan* Pc, const void* d_factor, int64_t batch, int64_t nrhs, const double* d_b,
                          double* d_x, void* d_work, void* stream) {
     stc_plan* P = const_cast<stc_plan*>(Pc);
-    if (!P || !d_factor || !d_b || !d_x || !d_work || batch <= 0 || nrhs <= 0 || d_b == d_x)
+    if (!P || !d_factor || !d_b || !d_x || batch <= 0 || nrhs <= 0 || d_b == d_x)
         return STC_ERR_INVALID_ARG;
     int dev, sms, rc;
     if ((rc = device_info(&dev, &sms))) return rc;
     if ((rc = ensure_plan(P, dev))) return rc;
+    if (!d_work && (rc = own_buffer(P, false, stc_workspace_bytes(P, batch * nrhs), &d_work))) return rc;
     if (is_sn(P)) return sn_solve(P, d_factor, batch, nrhs, d_b, d_x, d_work, stream, dev, sms);
     TaskSet* ts = nullptr;
     if ((rc = get_taskset(P, 1, false, &ts))) return rc;
@@ -2458,11 +2501,12 @@ extern "C" int stc_fp64_peak_probe(double* d_scratch, int64_t scratch_doubles, i
 extern "C" int stc_selinv(const stc_plan* Pc, const void* d_factor, int64_t batch, void* d_sigma, void* d_work,
                           void* stream) {
     stc_plan* P = const_cast<stc_plan*>(Pc);
-    if (!P || !d_factor || !d_sigma || !d_work || batch <= 0 || d_factor == d_sigma) return STC_ERR_INVALID_ARG;
+    if (!P || !d_factor || !d_sigma || batch <= 0 || d_factor == d_sigma) return STC_ERR_INVALID_ARG;
     if (is_sn(P)) return STC_ERR_UNSUPPORTED;  // selected inverse on the tile routes only
     int dev, sms, rc;
     if ((rc = device_info(&dev, &sms))) return rc;
     if ((rc = ensure_plan(P, dev))) return rc;
+    if (!d_work && (rc = own_buffer(P, false, stc_workspace_bytes(P, batch), &d_work))) return rc;
     TaskSet* ts = nullptr;
     if ((rc = get_taskset(P, 1, false, &ts))) return rc;
     if ((rc = ensure_taskset(P, ts, dev))) return rc;
@@ -2485,9 +2529,15 @@ extern "C" int stc_selinv(const stc_plan* Pc, const void* d_factor, int64_t batc
 extern "C" int stc_logdet_backward(const stc_plan* Pc, const void* d_factor, int64_t batch, const double* d_gout,
                                    double* d_gvalues, int accumulate, void* d_sigma, void* d_work, void* stream) {
     stc_plan* P = const_cast<stc_plan*>(Pc);
-    if (!P || !d_gvalues) return STC_ERR_INVALID_ARG;
-    int rc = stc_selinv(P, d_factor, batch, d_sigma, d_work, stream);
-    if (rc) return rc;
+    if (!P || !d_gvalues || batch <= 0) return STC_ERR_INVALID_ARG;
+    int rc;
+    if (!d_sigma) {
+        int dev, sms;
+        if ((rc = device_info(&dev, &sms))) return rc;
+        if ((rc = ensure_plan(P, dev))) return rc;
+        if ((rc = own_buffer(P, true, stc_factor_bytes(P, batch), &d_sigma))) return rc;
+    }
+    if ((rc = stc_selinv(P, d_factor, batch, d_sigma, d_work, stream))) return rc;
     int sms = g_dev[P->dev.device].sms;
     const int blocks = std::max(1, std::min<int>(sms * 8, (int)((P->nnzA + 255) / 256)));
     grad_gather_kernel<<<blocks, 256, 0, S(stream)>>>((const double*)d_sigma, P->factor_doubles, batch,

@@ -209,3 +209,27 @@ def test_loaded_plan_factorizes_identically():
     assert b.status() == L.STC_OK
     assert torch.equal(a.data, b.data)
     assert torch.equal(a.logdet(), b.logdet())
+
+
+def test_null_workspace_uses_the_plans_own():
+    # d_work == NULL (and d_sigma == NULL in logdet_backward) runs on buffers owned by the
+    # plan; results are bit-identical to the caller-owned ones
+    Ap, Ai, coords, vals = c1_batch(3)
+    n = len(Ap) - 1
+    P = Plan(n, Ap, Ai, coords=coords, nb=64)
+    assert L.stc_plan_sync_status(P.h) == L.STC_ERR_INVALID_ARG   # not used yet
+    v = dev(vals)
+    ref = P.factorize(v)
+    fac = torch.empty_like(ref.data)
+    info = torch.empty(3, dtype=torch.int32, device="cuda")
+    assert L.stc_factorize(P.h, v, 3, fac, None, info) == L.STC_OK
+    assert L.stc_plan_sync_status(P.h) == L.STC_OK
+    assert torch.equal(fac, ref.data) and torch.equal(info, ref.info)
+    b = dev(np.random.default_rng(4).standard_normal((3, 2, n)))
+    x = torch.empty_like(b)
+    assert L.stc_solve(P.h, fac, 3, 2, b, x, None) == L.STC_OK
+    assert torch.equal(x, ref.solve(b))
+    g = torch.empty(3, P.nnzA, dtype=torch.float64, device="cuda")
+    assert L.stc_logdet_backward(P.h, fac, 3, None, g, 0, None, None) == L.STC_OK
+    assert L.stc_plan_sync_status(P.h) == L.STC_OK
+    assert torch.equal(g, ref.logdet_backward())
