@@ -1003,7 +1003,7 @@ struct SolveArgs {
 constexpr int kSolveWarps = kThreads / 32;
 constexpr int kSolvePre = kNbMax / 2;  // tile entries per thread held across a wait (forward)
 static_assert(kNbMax <= 128 && kThreads == 256, "the solve's register prefetch covers 128 x 128 tiles");
-constexpr size_t kSolveSmem = (size_t)kLdc * kNbMax * sizeof(double);
+constexpr size_t kSolveSmem = (size_t)kLdc * kNbMax * sizeof(double);  // >= (nb + 1) nb and (kd + 1) nb
 
 // Diagonal-block substitution with the unit lower triangular M = L diag(L)^{-1} (Ls
 // holds M, its columns scaled beforehand, off the dependency chain), panels of 32: warp 0
@@ -1072,17 +1072,134 @@ __device__ void diag_solve(double* v, const double* Ls, const DTile& D, int nb, 
     }
 }
 
+// ---- one-dimensional TMA (cp.async.bulk) into shared memory, completion on an mbarrier
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(unsigned long long* bar) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+// src and dst 16-byte aligned, bytes a multiple of 16
+__device__ __forceinline__ void tma_load_1d(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+// Bounded wait for the mbarrier phase `parity` to complete; false after `limit` polls.
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity, long long limit) {
+    for (long long it = 0; it <= limit; ++it) {
+        unsigned done;
+        asm volatile(
+            "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+            : "=r"(done)
+            : "r"(smem_u32(bar)), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+// L_kk[r][c] (r >= c) from a diagonal tile staged in shared memory: a banded tile in its
+// storage layout (entry at kd + c + r kd: consecutive rows and consecutive columns both
+// land in distinct banks), a dense tile column-major with leading dimension nb + 1.
+struct DiagView {
+    const double* d;
+    int kd, ld;
+    bool band;
+    __device__ __forceinline__ double at(int r, int c) const {
+        if (band) return (r - c > kd) ? 0.0 : d[kd + c + r * kd];
+        return d[r + c * ld];
+    }
+};
+
+// v <- L^{-1} v (forward) or v <- L^{-T} v (backward) for a diagonal tile held in shared
+// memory, panels of 32.  Inside a panel warp 0 solves with the unit triangle
+// M = L diag(L)^{-1} (its entries scaled as they are loaded into registers, so a step of
+// the dependency chain is one shuffle and one FMA); the rows below (forward) or columns
+// above (backward) are then updated by one thread each with the true L.
+template <bool BACK>
+__device__ void diag_solve_tile(double* v, const DiagView& L, int nb, const double* dinv) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int np = (nb + 31) / 32;
+    if (BACK) {
+        for (int c = threadIdx.x; c < nb; c += kThreads) v[c] *= dinv[c];
+        __syncthreads();
+    }
+    for (int qi = 0; qi < np; ++qi) {
+        const int p = BACK ? (np - 1 - qi) * 32 : qi * 32;
+        const int pw = min(32, nb - p);
+        if (warp == 0) {
+            double Lr[32];
+            double vi = 0.0;
+#pragma unroll
+            for (int l = 0; l < 32; ++l) {
+                // forward: row p+lane, columns p+l < row; backward: column p+lane, rows p+l > it
+                double x = 0.0;
+                if (lane < pw && l < pw && (BACK ? l > lane : l < lane))
+                    x = BACK ? L.at(p + l, p + lane) * dinv[p + lane] : L.at(p + lane, p + l) * dinv[p + l];
+                Lr[l] = x;
+            }
+            if (lane < pw) vi = v[p + lane];
+#pragma unroll
+            for (int jj = 0; jj < 32; ++jj) {
+                const int j = BACK ? 31 - jj : jj;
+                if (j < pw) {
+                    const double wj = __shfl_sync(0xffffffffu, vi, j);
+                    if (BACK ? lane < j : lane > j) vi = fma(-Lr[j], wj, vi);
+                }
+            }
+            if (lane < pw) v[p + lane] = BACK ? vi : vi * dinv[p + lane];
+        }
+        __syncthreads();
+        if (!BACK) {
+            const int rend = min(nb, p + pw + L.kd);
+            for (int r = p + pw + threadIdx.x; r < rend; r += kThreads) {
+                double s0 = v[r], s1 = 0.0;
+                int l = 0;
+                for (; l + 1 < pw; l += 2) {
+                    s0 = fma(-L.at(r, p + l), v[p + l], s0);
+                    s1 = fma(-L.at(r, p + l + 1), v[p + l + 1], s1);
+                }
+                if (l < pw) s0 = fma(-L.at(r, p + l), v[p + l], s0);
+                v[r] = s0 + s1;
+            }
+        } else {
+            for (int c = max(0, p - L.kd) + threadIdx.x; c < p; c += kThreads) {
+                double s0 = 0.0, s1 = 0.0;
+                int l = 0;
+                for (; l + 1 < pw; l += 2) {
+                    s0 = fma(L.at(p + l, c), v[p + l], s0);
+                    s1 = fma(L.at(p + l + 1, c), v[p + l + 1], s1);
+                }
+                if (l < pw) s0 = fma(L.at(p + l, c), v[p + l], s0);
+                v[c] = fma(-(s0 + s1), dinv[c], v[c]);
+            }
+        }
+        __syncthreads();
+    }
+}
+
 __global__ void __launch_bounds__(kThreads, 1) solve_kernel(SolveArgs a) {
-    extern __shared__ double smem[];
-    double* Ls = smem;                             // diagonal tile, L(r,c) at r + c*kLdc
+    extern __shared__ __align__(16) double smem[];
+    double* Dsm = smem;                            // diagonal tile (banded: storage layout, by TMA;
+                                                   // dense: column-major, ld nb + 1)
     __shared__ double acc[kSolveWarps * kNbMax];   // per-warp partial sums
     __shared__ double v[kNbMax];                   // block right-hand side / solution
     __shared__ double ysm[kNbMax];                 // the y (or z) block an off-diagonal tile multiplies
     __shared__ double sdinv[kNbMax];               // 1 / L_jj of the diagonal tile
+    __shared__ __align__(8) unsigned long long bar;
     __shared__ long long s_slot;
     __shared__ int s_ok;
     const long long total = 2LL * a.nt * a.chains;
     const int nb = a.nb, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    unsigned parity = 0;
     for (;;) {
         if (threadIdx.x == 0) s_slot = (long long)atomicAdd(&a.hdr->head, 1ULL);
         __syncthreads();
@@ -1098,35 +1215,39 @@ __global__ void __launch_bounds__(kThreads, 1) solve_kernel(SolveArgs a) {
         const bool fwd = ti < a.nt;
         const int k = fwd ? ti : a.nt - 1 - (ti - a.nt);
         const DTile D = a.tiles[a.diag[k]];
+        const bool band = D.kind == TILE_DIAG_BAND;
+        const DiagView Lv{Dsm, band ? D.kd : min(D.kd, nb - 1), band ? 0 : nb + 1, band};
         if (threadIdx.x == 0) {
             s_ok = (*(volatile int*)&a.hdr->status == STC_OK);
+            if (band) {
+                // the banded tile is contiguous: bulk copies into shared memory, issued before
+                // any wait (the previous step's readers have passed the barriers above)
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                const unsigned bytes = (unsigned)((D.kd + 1) * nb * sizeof(double));
+                mbar_expect_tx(&bar, bytes);
+                for (unsigned o = 0; o < bytes; o += 32768u)
+                    tma_load_1d((char*)Dsm + o, (const char*)(F + D.off) + o, min(32768u, bytes - o), &bar);
+            }
             if (s_ok && !fwd) s_ok = wait_counter(done + k, 1, a.spin, &a.hdr->status);
         }
         __syncthreads();
         if (s_ok) {
             for (int i = threadIdx.x; i < kSolveWarps * nb; i += kThreads) acc[i] = 0.0;
-            for_rc(nb, nb, [&](int r, int c) { Ls[r + c * kLdc] = 0.0; });
-            __syncthreads();
-            read_diag_rows(F + D.off, D, nb, 0, nb, [&](int r, int c, double v) { Ls[r + c * kLdc] = v; });
+            if (!band)
+                for_rc(nb, nb, [&](int r, int c) {
+                    if (r >= c) Dsm[r + c * (nb + 1)] = __ldcg(F + D.off + r + (size_t)c * nb);
+                });
             for (int r = threadIdx.x; r < nb; r += kThreads) {
                 const long long g = (long long)k * nb + r;
                 v[r] = fwd ? (g < a.n ? a.b[ch * a.n + a.perm[g]] : 0.0) : __ldcg(y + g);
             }
             __syncthreads();
-            // L_kk = M diag(L_kk): scale the columns to M (unit diagonal) before any wait
-            for (int c = threadIdx.x; c < nb; c += kThreads) sdinv[c] = 1.0 / Ls[c * (kLdc + 1)];
-            __syncthreads();
-            for_rc(nb, nb, [&](int r, int c) { if (r > c) Ls[r + c * kLdc] *= sdinv[c]; });
-            if (!fwd)
-                for (int r = threadIdx.x; r < nb; r += kThreads) v[r] *= sdinv[r];
-            __syncthreads();
             if (fwd) {
                 // acc -= L_kn y_n over the off-diagonal tiles of block row k (oldest n first):
                 // y_n's stored-column entries go to shared memory, then each thread owns one
-                // row and a residue class of columns, with four independent loads in flight
+                // row and a residue class of columns, with four independent accumulators; the
+                // tile's entries are loaded to registers before the wait for y_n
                 const int G = min(kThreads / nb, kSolveWarps), gr = threadIdx.x % nb, gq = threadIdx.x / nb;
-                // (the tile's entries go to registers before the wait for y_n, so only the
-                // multiply-adds remain once y_n is there)
                 for (int q = a.rowstart[k]; q < a.rowstart[k + 1]; ++q) {
                     const DTile T = a.tiles[a.rowtiles[q]];
                     const bool act = gq < G && gr >= T.r0 && gr < T.r1;
@@ -1159,13 +1280,13 @@ __global__ void __launch_bounds__(kThreads, 1) solve_kernel(SolveArgs a) {
                 }
             } else {
                 // acc -= L_mk^T z_m over the tiles below the diagonal in block column k (oldest
-                // m first): z_m goes to shared memory, then each warp reduces four stored
-                // columns at a time over the rows, lanes striding the rows
+                // m first): each warp owns 16 stored columns (c = 32 g + 4 warp + j), its
+                // lanes stride the rows; the 16 partial sums of a lane are reduced over the
+                // warp by a reduce-scatter butterfly (16 shuffles and adds per lane, after
+                // which lane pair 2v, 2v+1 holds column v's total)
                 for (int q = a.colstart[k + 1] - 1; q >= a.colstart[k]; --q) {
                     const DTile T = a.tiles[q];
                     if (T.I == T.J) continue;
-                    // this warp's columns c = 32 g + 4 warp + j and rows r = r0 + lane + 32 i,
-                    // loaded before the wait for z_m
                     double pre[4][4][4];
 #pragma unroll
                     for (int g = 0; g < 4; ++g)
@@ -1188,41 +1309,62 @@ __global__ void __launch_bounds__(kThreads, 1) solve_kernel(SolveArgs a) {
                         const int r = T.r0 + lane + 32 * i;
                         zr[i] = r < T.r1 ? ysm[r] : 0.0;
                     }
+                    double d[16];
 #pragma unroll
                     for (int g = 0; g < 4; ++g)
 #pragma unroll
                         for (int j = 0; j < 4; ++j) {
-                            const int c = 32 * g + warp * 4 + j;
-                            double d = 0.0;
+                            double s = 0.0;
 #pragma unroll
-                            for (int i = 0; i < 4; ++i) d = fma(pre[g][j][i], zr[i], d);
-#pragma unroll
-                            for (int o = 16; o > 0; o >>= 1) d += __shfl_down_sync(0xffffffffu, d, o);
-                            if (lane == 0 && c < T.sw) acc[warp * nb + logical_col(T, a.saind, c)] -= d;
+                            for (int i = 0; i < 4; ++i) s = fma(pre[g][j][i], zr[i], s);
+                            d[4 * g + j] = s;
                         }
+#pragma unroll
+                    for (int st = 0; st < 4; ++st) {
+                        const int h = 8 >> st, m = 16 >> st;
+                        const bool up = (lane & m) != 0;
+#pragma unroll
+                        for (int t = 0; t < h; ++t) {
+                            const double send = up ? d[t] : d[t + h];
+                            const double keep = up ? d[t + h] : d[t];
+                            d[t] = keep + __shfl_xor_sync(0xffffffffu, send, m);
+                        }
+                    }
+                    d[0] += __shfl_xor_sync(0xffffffffu, d[0], 1);
+                    if ((lane & 1) == 0) {
+                        const int vi = lane >> 1;
+                        const int c = 32 * (vi >> 2) + warp * 4 + (vi & 3);
+                        if (c < T.sw) acc[warp * nb + logical_col(T, a.saind, c)] -= d[0];
+                    }
                     __syncthreads();
                 }
             }
-            // backward: the products enter scaled by 1/L_kk like the block itself
             for (int r = threadIdx.x; r < nb; r += kThreads) {
                 double sacc = 0.0;
                 for (int w2 = 0; w2 < kSolveWarps; ++w2) sacc += acc[w2 * nb + r];
-                v[r] = fwd ? v[r] + sacc : fma(sacc, sdinv[r], v[r]);
+                v[r] += sacc;
             }
+        }
+        // the diagonal tile: wait for its bulk copy (issued whatever the status, so always
+        // awaited before the buffer is reused or the kernel ends)
+        if (band) {
+            if (!mbar_wait(&bar, parity, a.spin)) {
+                if (threadIdx.x == 0) atomicCAS(&a.hdr->status, STC_OK, STC_ERR_TIMEOUT);
+                mbar_wait(&bar, parity, a.spin);
+                s_ok = 0;
+            }
+            parity ^= 1u;
+        }
+        __syncthreads();
+        if (s_ok) {
+            for (int c = threadIdx.x; c < nb; c += kThreads) sdinv[c] = 1.0 / Lv.at(c, c);
             __syncthreads();
-            if (s_ok) {
-                if (fwd) {
-                    diag_solve<false>(v, Ls, D, nb, nb);
-                    for (int i = threadIdx.x; i < nb; i += kThreads) v[i] *= sdinv[i];
-                    __syncthreads();
-                } else {
-                    diag_solve<true>(v, Ls, D, nb, nb);
-                }
-                for (int i = threadIdx.x; i < nb; i += kThreads) {
-                    __stcg(y + (long long)k * nb + i, v[i]);
-                    const long long g = (long long)k * nb + i;
-                    if (!fwd && g < a.n) a.x[ch * a.n + a.perm[g]] = v[i];
-                }
+            if (fwd) diag_solve_tile<false>(v, Lv, nb, sdinv);
+            else diag_solve_tile<true>(v, Lv, nb, sdinv);
+            for (int i = threadIdx.x; i < nb; i += kThreads) {
+                __stcg(y + (long long)k * nb + i, v[i]);
+                const long long g = (long long)k * nb + i;
+                if (!fwd && g < a.n) a.x[ch * a.n + a.perm[g]] = v[i];
             }
         }
         __threadfence();
