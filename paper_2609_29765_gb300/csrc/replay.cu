@@ -1003,7 +1003,8 @@ struct SolveArgs {
 constexpr int kSolveWarps = kThreads / 32;
 constexpr int kSolvePre = kNbMax / 2;  // tile entries per thread held across a wait (forward)
 static_assert(kNbMax <= 128 && kThreads == 256, "the solve's register prefetch covers 128 x 128 tiles");
-constexpr size_t kSolveSmem = (size_t)kLdc * kNbMax * sizeof(double);  // >= (nb + 1) nb and (kd + 1) nb
+// diagonal tile (>= (nb + 1) nb and (kd + 1) nb doubles) + four 32 x 33 panel triangles
+constexpr size_t kSolveSmem = ((size_t)kLdc * kNbMax + 4 * 32 * 33) * sizeof(double);
 
 // Diagonal-block substitution with the unit lower triangular M = L diag(L)^{-1} (Ls
 // holds M, its columns scaled beforehand, off the dependency chain), panels of 32: warp 0
@@ -1116,11 +1117,27 @@ struct DiagView {
 
 // v <- L^{-1} v (forward) or v <- L^{-T} v (backward) for a diagonal tile held in shared
 // memory, panels of 32.  Inside a panel warp 0 solves with the unit triangle
-// M = L diag(L)^{-1} (its entries scaled as they are loaded into registers, so a step of
-// the dependency chain is one shuffle and one FMA); the rows below (forward) or columns
-// above (backward) are then updated by one thread each with the true L.
+// M = L diag(L)^{-1} of the panel's 32 x 32 diagonal block, prepared in Mp by
+// prepare_panels (so a step of the dependency chain is one shuffle and one FMA); the
+// rows below (forward) or columns above (backward) are then updated by one thread each
+// with the true L.
+// Strict lower part of M = L diag(L)^{-1} on the 32 x 32 diagonal block of every panel,
+// panel q at Mp + q kMpStride, entry (i, l) at i + 33 l (zero elsewhere), and 1 / L_jj in
+// dinv: off the dependency chain of the solve (it needs only the diagonal tile).
+constexpr int kMpStride = 32 * 33;
+__device__ void prepare_panels(double* Mp, double* dinv, const DiagView& L, int nb) {
+    for (int c = threadIdx.x; c < nb; c += kThreads) dinv[c] = 1.0 / L.at(c, c);
+    __syncthreads();
+    const int np = (nb + 31) / 32;
+    for (int idx = threadIdx.x; idx < np * 1024; idx += kThreads) {
+        const int q = idx >> 10, i = idx & 31, l = (idx >> 5) & 31;
+        const int p = q * 32, pw = min(32, nb - p);
+        Mp[q * kMpStride + i + 33 * l] = (i < pw && l < i) ? L.at(p + i, p + l) * dinv[p + l] : 0.0;
+    }
+}
+
 template <bool BACK>
-__device__ void diag_solve_tile(double* v, const DiagView& L, int nb, const double* dinv) {
+__device__ void diag_solve_tile(double* v, const DiagView& L, int nb, const double* dinv, const double* Mp) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int np = (nb + 31) / 32;
     if (BACK) {
@@ -1136,10 +1153,8 @@ __device__ void diag_solve_tile(double* v, const DiagView& L, int nb, const doub
 #pragma unroll
             for (int l = 0; l < 32; ++l) {
                 // forward: row p+lane, columns p+l < row; backward: column p+lane, rows p+l > it
-                double x = 0.0;
-                if (lane < pw && l < pw && (BACK ? l > lane : l < lane))
-                    x = BACK ? L.at(p + l, p + lane) * dinv[p + lane] : L.at(p + lane, p + l) * dinv[p + l];
-                Lr[l] = x;
+                const double* M = Mp + (p / 32) * kMpStride;
+                Lr[l] = BACK ? M[l + lane * 33] : M[lane + l * 33];
             }
             if (lane < pw) vi = v[p + lane];
 #pragma unroll
@@ -1185,6 +1200,7 @@ __global__ void __launch_bounds__(kThreads, 1) solve_kernel(SolveArgs a) {
     extern __shared__ __align__(16) double smem[];
     double* Dsm = smem;                            // diagonal tile (banded: storage layout, by TMA;
                                                    // dense: column-major, ld nb + 1)
+    double* Mp = smem + kLdc * kNbMax;             // unit panel triangles (prepare_panels)
     __shared__ double acc[kSolveWarps * kNbMax];   // per-warp partial sums
     __shared__ double v[kNbMax];                   // block right-hand side / solution
     __shared__ double ysm[kNbMax];                 // the y (or z) block an off-diagonal tile multiplies
@@ -1241,6 +1257,21 @@ __global__ void __launch_bounds__(kThreads, 1) solve_kernel(SolveArgs a) {
                 const long long g = (long long)k * nb + r;
                 v[r] = fwd ? (g < a.n ? a.b[ch * a.n + a.perm[g]] : 0.0) : __ldcg(y + g);
             }
+        }
+        // the diagonal tile: wait for its bulk copy (issued whatever the status, so always
+        // awaited before the buffer is reused or the kernel ends), then prepare the panel
+        // triangles of the solve, all before the waits on the other chains' blocks
+        if (band) {
+            if (!mbar_wait(&bar, parity, a.spin)) {
+                if (threadIdx.x == 0) atomicCAS(&a.hdr->status, STC_OK, STC_ERR_TIMEOUT);
+                mbar_wait(&bar, parity, a.spin);
+                s_ok = 0;
+            }
+            parity ^= 1u;
+        }
+        __syncthreads();
+        if (s_ok) {
+            prepare_panels(Mp, sdinv, Lv, nb);
             __syncthreads();
             if (fwd) {
                 // acc -= L_kn y_n over the off-diagonal tiles of block row k (oldest n first):
@@ -1345,22 +1376,10 @@ __global__ void __launch_bounds__(kThreads, 1) solve_kernel(SolveArgs a) {
                 v[r] += sacc;
             }
         }
-        // the diagonal tile: wait for its bulk copy (issued whatever the status, so always
-        // awaited before the buffer is reused or the kernel ends)
-        if (band) {
-            if (!mbar_wait(&bar, parity, a.spin)) {
-                if (threadIdx.x == 0) atomicCAS(&a.hdr->status, STC_OK, STC_ERR_TIMEOUT);
-                mbar_wait(&bar, parity, a.spin);
-                s_ok = 0;
-            }
-            parity ^= 1u;
-        }
         __syncthreads();
         if (s_ok) {
-            for (int c = threadIdx.x; c < nb; c += kThreads) sdinv[c] = 1.0 / Lv.at(c, c);
-            __syncthreads();
-            if (fwd) diag_solve_tile<false>(v, Lv, nb, sdinv);
-            else diag_solve_tile<true>(v, Lv, nb, sdinv);
+            if (fwd) diag_solve_tile<false>(v, Lv, nb, sdinv, Mp);
+            else diag_solve_tile<true>(v, Lv, nb, sdinv, Mp);
             for (int i = threadIdx.x; i < nb; i += kThreads) {
                 __stcg(y + (long long)k * nb + i, v[i]);
                 const long long g = (long long)k * nb + i;
