@@ -178,6 +178,19 @@ typedef struct stc_plan_info {
 #define STC_EXPORT_SN_DEV_MAPS 17   /* the row / column position maps (int16 widened)     */
 #define STC_EXPORT_SN_VALUE_MAP 18  /* [nnzA] arena offset of each entry of A             */
 #define STC_EXPORT_SN_CSC_MAP 19    /* [nnzL] arena offset of each structural entry of L  */
+/* The supernodal selected inverse (Takahashi's recurrence over the supernodes, in
+ * reverse): an off-diagonal task computes rows [rs0, rs1) of Sigma(K,J) = -(sum over J's
+ * cells (K',J) of Sigma(rows of (K,J), rows of (K',J)) L(K',J)) L_JJ^{-1}, reading Sigma
+ * from the diagonal cell of K (mode 0, K' = K), from the cell (K,K') of supernode K'
+ * (mode 1, K' < K) or transposed from the cell (K',K) of K (mode 2, K' > K); a diagonal
+ * task sums Sigma(K',J)^T L(K',J) over J's cells (mode 3) and runs the element recurrence
+ * in the diagonal block. */
+#define STC_EXPORT_SN_SEL_TASKS 20  /* [ntasks][7]: kind (0 off-diagonal, 1 diagonal), cell,
+                                       diagonal cell, contributions [cbeg, cend), rows
+                                       [rs0, rs1)                                       */
+#define STC_EXPORT_SN_SEL_CONS 21   /* [ncons][3]: L cell (K',J), Sigma cell read, mode     */
+#define STC_EXPORT_SN_CELL_ROWOFF 22 /* [ncells] offset in STC_EXPORT_SN_ROWS of each cell's
+                                       first row                                        */
 
 /* Fill *opt with defaults (nb 128, auto route, auto ordering, ND leaf 64; selector gates
  * of Table 5: rho_dense 0.90, phi 2.0, rho_semi 0.15, sigma 20). */

@@ -30,7 +30,8 @@ STC_ORDER_AUTO, STC_ORDER_NATURAL, STC_ORDER_GIVEN, STC_ORDER_ND, STC_ORDER_RCM 
  STC_EXPORT_TASKS, STC_EXPORT_VALUE_MAP, STC_EXPORT_TILE_OFFSETS, STC_EXPORT_CHUNK_EXTENTS,
  STC_EXPORT_SN_NODES, STC_EXPORT_SN_ROWS, STC_EXPORT_SN_CELLS, STC_EXPORT_SN_TASKS,
  STC_EXPORT_SN_DEV_CELLS, STC_EXPORT_SN_DEV_TASKS, STC_EXPORT_SN_DEV_UPDS, STC_EXPORT_SN_DEV_MAPS,
- STC_EXPORT_SN_VALUE_MAP, STC_EXPORT_SN_CSC_MAP) = range(20)
+ STC_EXPORT_SN_VALUE_MAP, STC_EXPORT_SN_CSC_MAP, STC_EXPORT_SN_SEL_TASKS, STC_EXPORT_SN_SEL_CONS,
+ STC_EXPORT_SN_CELL_ROWOFF) = range(23)
 
 # every symbol include/stc.h declares
 EXPORTED = [

@@ -93,7 +93,9 @@ class Plan:
                 "sn_cells": L.STC_EXPORT_SN_CELLS, "sn_tasks": L.STC_EXPORT_SN_TASKS,
                 "sn_dev_cells": L.STC_EXPORT_SN_DEV_CELLS, "sn_dev_tasks": L.STC_EXPORT_SN_DEV_TASKS,
                 "sn_dev_upds": L.STC_EXPORT_SN_DEV_UPDS, "sn_dev_maps": L.STC_EXPORT_SN_DEV_MAPS,
-                "sn_value_map": L.STC_EXPORT_SN_VALUE_MAP, "sn_csc_map": L.STC_EXPORT_SN_CSC_MAP}[what]
+                "sn_value_map": L.STC_EXPORT_SN_VALUE_MAP, "sn_csc_map": L.STC_EXPORT_SN_CSC_MAP,
+                "sn_sel_tasks": L.STC_EXPORT_SN_SEL_TASKS, "sn_sel_cons": L.STC_EXPORT_SN_SEL_CONS,
+                "sn_cell_rowoff": L.STC_EXPORT_SN_CELL_ROWOFF}[what]
         a = L.stc_plan_export(self.h, code)
         if what == "tiles":
             return a.reshape(-1, 9)
@@ -101,8 +103,10 @@ class Plan:
             return a.reshape(-1, 8, 2)
         if what in ("tasks", "sn_nodes", "sn_cells", "sn_tasks"):
             return a.reshape(-1, 4)
-        if what in ("sn_dev_cells", "sn_dev_upds"):
+        if what in ("sn_dev_cells", "sn_dev_upds", "sn_sel_tasks"):
             return a.reshape(-1, 7)
+        if what == "sn_sel_cons":
+            return a.reshape(-1, 3)
         if what == "sn_dev_tasks":
             return a.reshape(-1, 8)
         return a

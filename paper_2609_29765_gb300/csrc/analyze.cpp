@@ -1394,7 +1394,10 @@ static int plan_export_impl(const stc_plan* P, int what, void* buf, size_t* byte
         case STC_EXPORT_SN_DEV_UPDS:
         case STC_EXPORT_SN_DEV_MAPS:
         case STC_EXPORT_SN_VALUE_MAP:
-        case STC_EXPORT_SN_CSC_MAP: {
+        case STC_EXPORT_SN_CSC_MAP:
+        case STC_EXPORT_SN_SEL_TASKS:
+        case STC_EXPORT_SN_SEL_CONS:
+        case STC_EXPORT_SN_CELL_ROWOFF: {
             const stc::SnPlan& S = P->supernodal();
             const int64_t nsn = (int64_t)S.first.size() - 1;
             if (what == STC_EXPORT_SN_NODES) {
@@ -1427,6 +1430,18 @@ static int plan_export_impl(const stc_plan* P, int what, void* buf, size_t* byte
                 tmp.assign(S.maps.begin(), S.maps.end());
             } else if (what == STC_EXPORT_SN_VALUE_MAP) {
                 tmp.assign(S.value_map.begin(), S.value_map.end());
+            } else if (what == STC_EXPORT_SN_SEL_TASKS) {
+                for (const stc::SnSTask& t : S.stasks) {
+                    const int64_t f[7] = {t.kind, t.cell, t.diag, t.cbeg, t.cend, t.rs0, t.rs1};
+                    tmp.insert(tmp.end(), f, f + 7);
+                }
+            } else if (what == STC_EXPORT_SN_SEL_CONS) {
+                for (const stc::SnSCon& c : S.scons) {
+                    const int64_t f[3] = {c.lcell, c.scell, c.mode};
+                    tmp.insert(tmp.end(), f, f + 3);
+                }
+            } else if (what == STC_EXPORT_SN_CELL_ROWOFF) {
+                tmp.assign(S.cell_rowoff.begin(), S.cell_rowoff.end());
             } else {
                 tmp.assign(S.csc_map.begin(), S.csc_map.end());
             }

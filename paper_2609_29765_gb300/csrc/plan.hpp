@@ -204,6 +204,30 @@ struct SnDevUpd {
     int32_t klen;      // inner length (columns of supernode I)
     int32_t pad;
 };
+// Selected inverse on the supernodal layout (Takahashi's recurrence walked over the
+// supernodes in reverse): an off-diagonal task computes rows [rs0, rs1) of
+// Sigma(K,J) = -(sum over J's cells (K',J) of Sigma(rows of (K,J), rows of (K',J))
+// L(K',J)) L_JJ^{-1}; the Sigma block comes from the diagonal cell of K (K' = K), from
+// the cell (K,K') of supernode K' (K' < K) or transposed from the cell (K',K) of K
+// (K' > K), rows located by searching the source cell's row list.  A diagonal task forms
+// Z = sum over J's cells of Sigma(K',J)^T L(K',J) and runs the element recurrence inside
+// the diagonal block.
+enum : int32_t { SN_S_OFF = 0, SN_S_DIAG = 1 };
+enum : int32_t { SN_SC_SAME = 0, SN_SC_LOWER = 1, SN_SC_UPPER = 2, SN_SC_OWN = 3 };
+struct SnSTask {
+    int32_t kind;      // SN_S_OFF or SN_S_DIAG
+    int32_t cell;      // target cell
+    int32_t diag;      // diagonal cell of J
+    int32_t cbeg, cend;
+    int32_t rs0, rs1;  // rows of the target cell written
+    int32_t pad;
+};
+struct SnSCon {
+    int32_t lcell;     // L cell (K',J)
+    int32_t scell;     // Sigma cell read
+    int32_t mode;      // SN_SC_*
+    int32_t pad;
+};
 struct SnPlan {
     std::vector<int32_t> first;
     std::vector<int64_t> rptr;
@@ -235,6 +259,9 @@ struct SnPlan {
                                      // its row supernode (-1 for diagonal cells)
     std::vector<int32_t> rptr_cells, row_cells;  // per row supernode J: cells (J, I), I < J
     double fma_exec = 0.0;           // FMAs of the device form (updates, POTRF, TRSM)
+    std::vector<SnSTask> stasks;     // selected inverse, reverse supernode order
+    std::vector<SnSCon> scons;
+    std::vector<int32_t> cell_rowoff;  // per cell: offset in rows of its first row
     int32_t nsn() const { return (int32_t)first.size() - 1; }
     // item layout of the supernodal route: the arena, then one logdet partial per supernode
     int64_t poff() const { return (arena + 31) / 32 * 32; }
@@ -254,6 +281,10 @@ struct SnDev {
     int32_t* row_cells = nullptr;
     int64_t* value_map = nullptr;
     int64_t* csc_map = nullptr;
+    SnSTask* stasks = nullptr;
+    SnSCon* scons = nullptr;
+    int32_t* rows = nullptr;        // the supernodes' row lists (permuted indices)
+    int32_t* cell_rowoff = nullptr;
     int device = -1;
 };
 

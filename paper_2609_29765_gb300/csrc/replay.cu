@@ -2037,6 +2037,208 @@ __global__ void __launch_bounds__(kThreads, 1) selinv_kernel(SelinvArgs a) {
     }
 }
 
+// ---------------------------------------------------------------------------
+// Selected inverse on the supernodal layout (Takahashi's recurrence over the supernodes,
+// walked in reverse; not in the paper, which leaves selected inversion to separate work).
+// Off-diagonal task, rows [rs0, rs1) of cell (K,J):
+//   Sigma(K,J) = -(sum over J's cells (K',J) of Sigma(rows_K, rows_K') L(K',J)) L_JJ^{-1}
+// with Sigma(rows_K, rows_K') read from the diagonal cell of K (K' = K), from the cell
+// (K,K') of supernode K' (K' < K) or transposed from the cell (K',K) of K (K' > K), each
+// row located by a search of the source cell's row list.  Diagonal task: C = -Z,
+// Z = sum over J's cells of Sigma(K',J)^T L(K',J), then the element recurrence inside the
+// diagonal block (as for a diagonal tile).
+// ---------------------------------------------------------------------------
+struct SnSelinvArgs {
+    const SnDevCell* cells;
+    const SnSTask* tasks;
+    const SnSCon* cons;
+    const int32_t* rows;       // the supernodes' row lists
+    const int32_t* rowoff;     // per cell: offset of its first row in rows
+    const int32_t* first;      // first column of each supernode
+    const double* factor;
+    double* sigma;
+    long long fstride;
+    int* counters;             // [batch][ncells]
+    int ncells;
+    WorkHeader* hdr;
+    int ntasks;
+    long long batch;
+    long long spin;
+};
+
+__global__ void __launch_bounds__(kThreads, 1) sn_selinv_kernel(SnSelinvArgs a) {
+    extern __shared__ double smem[];
+    double* C = smem;
+    double* S0 = C + kCbuf;
+    double* S1 = S0 + kStage;
+    double* sv = S1 + kStage;
+    __shared__ long long s_slot;
+    __shared__ int s_ok;
+    __shared__ int ia[kNbMax], ja[kNbMax], srow[kNbMax];
+    constexpr int LDS = kNbMax + 9;
+    const long long total = (long long)a.ntasks * a.batch;
+    for (;;) {
+        if (threadIdx.x == 0) s_slot = (long long)atomicAdd(&a.hdr->head, 1ULL);
+        __syncthreads();
+        const long long slot = s_slot;
+        __syncthreads();
+        if (slot >= total) break;
+        const int ti = (int)(slot / a.batch);
+        const long long item = slot % a.batch;
+        const SnSTask t = a.tasks[ti];
+        const double* Lf = a.factor + item * a.fstride;
+        double* Sg = a.sigma + item * a.fstride;
+        int* cnt = a.counters + item * a.ncells;
+        const SnDevCell O = a.cells[t.cell];
+        const SnDevCell D = a.cells[t.diag];
+        const int w = D.w;
+        const double* DL = Lf + D.off;  // L_JJ(r, c) = DL[r + c * D.ld], r >= c
+        if (threadIdx.x == 0) s_ok = (*(volatile int*)&a.hdr->status == STC_OK);
+        __syncthreads();
+        if (t.kind == SN_S_OFF && s_ok) {
+            const int R = t.rs1 - t.rs0;
+            const int K = O.J;
+            for_rc(R, w, [&](int r, int c) { C[r + c * kLdc] = 0.0; });
+            __syncthreads();
+            for (int ci = t.cbeg; ci < t.cend; ++ci) {
+                const SnSCon q = a.cons[ci];
+                const SnDevCell Lc = a.cells[q.lcell];
+                const SnDevCell Sc = a.cells[q.scell];
+                const int Kp = Lc.J, h = Lc.h;
+                if (threadIdx.x == 0) s_ok = wait_counter(cnt + q.scell, Sc.nslices, a.spin, &a.hdr->status);
+                // row lists: the source cell's (for the searches) and the index maps of the
+                // gathered block G(i, j) = Sigma(row i of the target slice, row j of (K',J))
+                for (int i = threadIdx.x; i < Sc.h; i += kThreads) srow[i] = a.rows[a.rowoff[q.scell] + i];
+                __syncthreads();
+                if (!s_ok) break;
+                const int* rt = a.rows + a.rowoff[t.cell] + t.rs0;
+                const int* rp = a.rows + a.rowoff[q.lcell];
+                auto find = [&](int r) {  // position of global row r in the source cell's rows
+                    int lo = 0, hi = Sc.h;
+                    while (lo < hi) {
+                        const int mid = (lo + hi) >> 1;
+                        if (srow[mid] < r) lo = mid + 1; else hi = mid;
+                    }
+                    return lo;
+                };
+                for (int i = threadIdx.x; i < R; i += kThreads)
+                    ia[i] = q.mode == SN_SC_LOWER ? find(rt[i]) : rt[i] - a.first[K];
+                for (int j = threadIdx.x; j < h; j += kThreads)
+                    ja[j] = q.mode == SN_SC_UPPER ? find(rp[j]) : rp[j] - a.first[q.mode == SN_SC_SAME ? K : Kp];
+                __syncthreads();
+                const double* ST = Sg + Sc.off;
+                const double* LT = Lf + Lc.off;
+                for (int j0 = 0; j0 < h; j0 += kKc) {
+                    const int Kc = min(kKc, h - j0);
+                    const int Rp = ((R + 3) & ~3) + 4, Cp = ((w + 3) & ~3) + 4;
+                    stage_gather<true>(S0, LDS, R, Rp, Kc, [&](int r, int k) {
+                        const int x = ia[r], y = ja[j0 + k];
+                        if (q.mode == SN_SC_SAME)
+                            return __ldcg(ST + max(x, y) + (size_t)min(x, y) * Sc.ld);
+                        if (q.mode == SN_SC_LOWER) return __ldcg(ST + x + (size_t)y * Sc.ld);
+                        return __ldcg(ST + y + (size_t)x * Sc.ld);
+                    });
+                    // L(K',J) rows j0.. (contiguous along the inner index)
+                    stage_gather<false>(S1, LDS, w, Cp, Kc,
+                                        [&](int c, int k) { return __ldcg(LT + (j0 + k) + (size_t)c * Lc.ld); });
+                    __syncthreads();
+                    mma_sub<false>(C, kLdc, R, w, S0, LDS, S1, LDS, Kc);  // C = -sum G L
+                    __syncthreads();
+                }
+            }
+            if (s_ok) {
+                // X L_JJ = C, panels from the right (backward)
+                for (int p = ((w - 1) / kPb) * kPb; p >= 0; p -= kPb) {
+                    const int pw = min(kPb, w - p);
+                    for (int k0 = p + pw; k0 < w; k0 += kKc) {
+                        const int Kc = min(kKc, w - k0);
+                        const int Cp = ((pw + 3) & ~3) + 4;
+                        for_rc(Cp, Kc, [&](int c, int kk) {
+                            S1[c + kk * LDS] = c < pw ? __ldcg(DL + (k0 + kk) + (size_t)(p + c) * D.ld) : 0.0;
+                        });
+                        __syncthreads();
+                        mma_sub<false>(C + p * kLdc, kLdc, R, pw, C + k0 * kLdc, kLdc, S1, LDS, Kc);
+                        __syncthreads();
+                    }
+                    for (int idx = threadIdx.x; idx < kPb * kPb; idx += kThreads) {
+                        const int i = idx & (kPb - 1), j = idx / kPb;
+                        S0[i + j * (kPb + 1)] =
+                            (i < pw && j < pw && i >= j) ? __ldcg(DL + (p + i) + (size_t)(p + j) * D.ld) : 0.0;
+                    }
+                    __syncthreads();
+                    if (threadIdx.x < pw) sv[threadIdx.x] = 1.0 / S0[threadIdx.x * (kPb + 2)];
+                    __syncthreads();
+                    trsm_rows_dir<true>(C + p * kLdc, kLdc, R, pw, S0, kPb + 1, sv);
+                    __syncthreads();
+                }
+                double* T = Sg + O.off + t.rs0;
+                for_rc(R, w, [&](int r, int c) { __stcg(T + r + (size_t)c * O.ld, C[r + c * kLdc]); });
+            }
+        } else if (t.kind == SN_S_DIAG && s_ok) {
+            for_rc(w, w, [&](int r, int c) { C[r + c * kLdc] = 0.0; });
+            __syncthreads();
+            for (int ci = t.cbeg; ci < t.cend; ++ci) {
+                const SnSCon q = a.cons[ci];
+                const SnDevCell Lc = a.cells[q.lcell];
+                if (threadIdx.x == 0) s_ok = wait_counter(cnt + q.scell, Lc.nslices, a.spin, &a.hdr->status);
+                __syncthreads();
+                if (!s_ok) break;
+                const double* ST = Sg + Lc.off;
+                const double* LT = Lf + Lc.off;
+                for (int i0 = 0; i0 < Lc.h; i0 += kKc) {
+                    const int Kc = min(kKc, Lc.h - i0);
+                    const int Mp = ((w + 3) & ~3) + 4;
+                    stage_gather<false>(S0, LDS, w, Mp, Kc,
+                                        [&](int r, int k) { return __ldcg(ST + (i0 + k) + (size_t)r * Lc.ld); });
+                    stage_gather<false>(S1, LDS, w, Mp, Kc,
+                                        [&](int r, int k) { return __ldcg(LT + (i0 + k) + (size_t)r * Lc.ld); });
+                    __syncthreads();
+                    mma_sub<true>(C, kLdc, w, w, S0, LDS, S1, LDS, Kc);  // C = -Z (lower)
+                    __syncthreads();
+                }
+            }
+            if (s_ok) {
+                // packed lower triangle of L_JJ: (r, c) at c*w - c(c-1)/2 + r - c
+                double* Lp = S0;
+                for_rc(w, w, [&](int r, int c) {
+                    if (r >= c) Lp[c * w - c * (c - 1) / 2 + (r - c)] = __ldcg(DL + r + (size_t)c * D.ld);
+                });
+                __syncthreads();
+                for (int c = w - 1; c >= 0; --c) {
+                    const double* Lcol = Lp + c * w - c * (c - 1) / 2 - c;  // Lcol[i] = L[i][c]
+                    const double inv = 1.0 / Lcol[c];
+                    for (int r = c + 1 + threadIdx.x; r < w; r += kThreads) {
+                        double s0 = C[r + c * kLdc], s1 = 0.0;
+                        int i = c + 1;
+                        for (; i + 1 < w; i += 2) {
+                            s0 = fma(-Lcol[i], i >= r ? C[i + r * kLdc] : C[r + i * kLdc], s0);
+                            s1 = fma(-Lcol[i + 1], i + 1 >= r ? C[i + 1 + r * kLdc] : C[r + (i + 1) * kLdc], s1);
+                        }
+                        if (i < w) s0 = fma(-Lcol[i], i >= r ? C[i + r * kLdc] : C[r + i * kLdc], s0);
+                        C[r + c * kLdc] = (s0 + s1) * inv;
+                    }
+                    __syncthreads();
+                    if (threadIdx.x < 32) {
+                        double sacc = 0.0;
+                        for (int i = c + 1 + threadIdx.x; i < w; i += 32) sacc = fma(Lcol[i], C[i + c * kLdc], sacc);
+#pragma unroll
+                        for (int o = 16; o > 0; o >>= 1) sacc += __shfl_down_sync(0xffffffffu, sacc, o);
+                        if (threadIdx.x == 0) C[c + c * kLdc] = inv * inv + (C[c + c * kLdc] - sacc) * inv;
+                    }
+                    __syncthreads();
+                }
+                double* T = Sg + D.off;
+                for_rc(w, w, [&](int r, int c) {
+                    if (r >= c) __stcg(T + r + (size_t)c * D.ld, C[r + c * kLdc]);
+                });
+            }
+        }
+        __threadfence();
+        __syncthreads();
+        if (threadIdx.x == 0) red_release_add(cnt + t.cell, 1);
+    }
+}
+
 // d logdet / d a_e = gout_b (2 - delta_e) Sigma_e, gathered through the value map.
 __global__ void grad_gather_kernel(const double* __restrict__ Sg, long long fstride, long long batch,
                                    const int64_t* __restrict__ map, const int8_t* __restrict__ vdiag, long long nnz,
@@ -2125,6 +2327,9 @@ int device_info(int* dev, int* sms) {
         if (cudaFuncSetAttribute(sn_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSolveSmem) !=
             cudaSuccess)
             return STC_ERR_CUDA;
+        if (cudaFuncSetAttribute(sn_selinv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes) !=
+            cudaSuccess)
+            return STC_ERR_CUDA;
         d.attr_set = true;
     }
     *sms = d.sms;
@@ -2151,7 +2356,7 @@ void free_dev(stc_plan* P) {
     d = DevPlanArrays{};
     SnDev& q = P->sndev;
     void* sptrs[] = {q.cells, q.tasks, q.upds, q.maps, q.first, q.cell_cmap, q.cptr, q.rptr_cells, q.row_cells,
-                     q.value_map, q.csc_map};
+                     q.value_map, q.csc_map, q.stasks, q.scons, q.rows, q.cell_rowoff};
     for (void* p : sptrs)
         if (p) cudaFree(p);
     q = SnDev{};
@@ -2273,6 +2478,12 @@ int ensure_sn_impl(stc_plan* P, int dev) {
     if ((rc = upload(&d.row_cells, rc_list))) return rc;
     if ((rc = upload(&d.value_map, S.value_map))) return rc;
     if ((rc = upload(&d.csc_map, S.csc_map))) return rc;
+    std::vector<SnSCon> scons = S.scons;
+    if (scons.empty()) scons.push_back(SnSCon{});
+    if ((rc = upload(&d.stasks, S.stasks))) return rc;
+    if ((rc = upload(&d.scons, scons))) return rc;
+    if ((rc = upload(&d.rows, S.rows))) return rc;
+    if ((rc = upload(&d.cell_rowoff, S.cell_rowoff))) return rc;
     d.device = dev;
     return STC_OK;
 }
@@ -2414,6 +2625,28 @@ int sn_solve(stc_plan* P, const void* d_factor, int64_t batch, int64_t nrhs, con
     const long long total = 2LL * a.nsn * chains;
     const int grid = grid_of(P, sms, total);
     sn_solve_kernel<<<grid, kThreads, kSolveSmem, st>>>(a);
+    return cudaGetLastError() == cudaSuccess ? STC_OK : STC_ERR_CUDA;
+}
+
+// Supernodal selected inverse: the persistent kernel over (task, item) slots.
+int sn_selinv(stc_plan* P, const void* d_factor, int64_t batch, void* d_sigma, void* d_work, void* stream, int dev,
+              int sms) {
+    int rc;
+    if ((rc = ensure_sn(P, dev))) return rc;
+    const SnPlan& Sp = P->supernodal();
+    cudaStream_t st = S(stream);
+    if (cudaMemsetAsync(d_sigma, 0, stc_factor_bytes(P, batch), st) != cudaSuccess) return STC_ERR_CUDA;
+    if (cudaMemsetAsync(d_work, 0, factorize_ws(P, batch), st) != cudaSuccess) return STC_ERR_CUDA;
+    SnSelinvArgs a{};
+    a.cells = P->sndev.cells; a.tasks = P->sndev.stasks; a.cons = P->sndev.scons; a.rows = P->sndev.rows;
+    a.rowoff = P->sndev.cell_rowoff; a.first = P->sndev.first; a.factor = (const double*)d_factor;
+    a.sigma = (double*)d_sigma; a.fstride = Sp.item_doubles(); a.hdr = (WorkHeader*)d_work;
+    a.counters = (int*)((char*)d_work + sizeof(WorkHeader)); a.ncells = (int)Sp.dcells.size();
+    a.ntasks = (int)Sp.stasks.size(); a.batch = batch;
+    a.spin = P->opt.spin_limit > 0 ? P->opt.spin_limit : kDefaultSpin;
+    const long long total = (long long)a.ntasks * batch;
+    const int grid = grid_of(P, sms, total);
+    sn_selinv_kernel<<<grid, kThreads, kSmemBytes, st>>>(a);
     return cudaGetLastError() == cudaSuccess ? STC_OK : STC_ERR_CUDA;
 }
 
@@ -2663,11 +2896,11 @@ extern "C" int stc_selinv(const stc_plan* Pc, const void* d_factor, int64_t batc
                           void* stream) {
     stc_plan* P = const_cast<stc_plan*>(Pc);
     if (!P || !d_factor || !d_sigma || batch <= 0 || d_factor == d_sigma) return STC_ERR_INVALID_ARG;
-    if (is_sn(P)) return STC_ERR_UNSUPPORTED;  // selected inverse on the tile routes only
     int dev, sms, rc;
     if ((rc = device_info(&dev, &sms))) return rc;
     if ((rc = ensure_plan(P, dev))) return rc;
     if (!d_work && (rc = own_buffer(P, false, stc_workspace_bytes(P, batch), &d_work))) return rc;
+    if (is_sn(P)) return sn_selinv(P, d_factor, batch, d_sigma, d_work, stream, dev, sms);
     TaskSet* ts = nullptr;
     if ((rc = get_taskset(P, 1, false, &ts))) return rc;
     if ((rc = ensure_taskset(P, ts, dev))) return rc;
@@ -2701,9 +2934,9 @@ extern "C" int stc_logdet_backward(const stc_plan* Pc, const void* d_factor, int
     if ((rc = stc_selinv(P, d_factor, batch, d_sigma, d_work, stream))) return rc;
     int sms = g_dev[P->dev.device].sms;
     const int blocks = std::max(1, std::min<int>(sms * 8, (int)((P->nnzA + 255) / 256)));
-    grad_gather_kernel<<<blocks, 256, 0, S(stream)>>>((const double*)d_sigma, P->factor_doubles, batch,
-                                                       P->dev.value_map, P->dev.vdiag, P->nnzA, d_gout, d_gvalues,
-                                                       accumulate);
+    grad_gather_kernel<<<blocks, 256, 0, S(stream)>>>((const double*)d_sigma, P->item_doubles(), batch,
+                                                       is_sn(P) ? P->sndev.value_map : P->dev.value_map, P->dev.vdiag,
+                                                       P->nnzA, d_gout, d_gvalues, accumulate);
     return cudaGetLastError() == cudaSuccess ? STC_OK : STC_ERR_CUDA;
 }
 

@@ -289,6 +289,45 @@ void stc_plan::build_device_form(stc::SnPlan& S, const vector<int32_t>& snof,
         fma += t.kind == stc::SN_T_DIAG ? w * (w + 1) * (w + 2) / 6 : double(t.rs1 - t.rs0) * w * (w + 1) / 2;
     }
     S.fma_exec = fma;
+    // selected inverse tasks: supernodes in reverse order, for each its off-diagonal cells
+    // (row slices as in the factorization) with one contribution per cell (K', J) of J,
+    // then its diagonal cell with its own cells as contributions
+    S.cell_rowoff.resize(ncell);
+    for (int32_t c = 0; c < ncell; ++c) S.cell_rowoff[c] = (int32_t)(S.rptr[S.cells[4 * c]] + S.cells[4 * c + 2]);
+    for (int32_t J = nsn - 1; J >= 0; --J) {
+        const int32_t c0 = S.cptr[J], c1 = S.cptr[J + 1];
+        for (int32_t T = c0 + 1; T < c1; ++T) {
+            const int32_t K = S.cells[4 * T + 1];
+            for (int32_t sl = 0; sl < S.dcells[T].nslices; ++sl) {
+                stc::SnSTask t{};
+                t.kind = stc::SN_S_OFF; t.cell = T; t.diag = c0;
+                t.rs0 = sl * stc::kSnSliceH; t.rs1 = std::min(height(T), t.rs0 + stc::kSnSliceH);
+                t.cbeg = (int32_t)S.scons.size();
+                for (int32_t c2 = c0 + 1; c2 < c1; ++c2) {
+                    const int32_t K2 = S.cells[4 * c2 + 1];
+                    stc::SnSCon q{};
+                    q.lcell = c2;
+                    if (K2 == K) { q.mode = stc::SN_SC_SAME; q.scell = S.cptr[K]; }
+                    else if (K2 < K) { q.mode = stc::SN_SC_LOWER; q.scell = cell_of(K2, K); }
+                    else { q.mode = stc::SN_SC_UPPER; q.scell = cell_of(K, K2); }
+                    if (q.scell < 0) throw std::logic_error("selected inverse: source cell missing");
+                    S.scons.push_back(q);
+                }
+                t.cend = (int32_t)S.scons.size();
+                S.stasks.push_back(t);
+            }
+        }
+        stc::SnSTask d{};
+        d.kind = stc::SN_S_DIAG; d.cell = c0; d.diag = c0; d.rs0 = 0; d.rs1 = width(J);
+        d.cbeg = (int32_t)S.scons.size();
+        for (int32_t c2 = c0 + 1; c2 < c1; ++c2) {
+            stc::SnSCon q{};
+            q.lcell = c2; q.scell = c2; q.mode = stc::SN_SC_OWN;
+            S.scons.push_back(q);
+        }
+        d.cend = (int32_t)S.scons.size();
+        S.stasks.push_back(d);
+    }
     // value and CSC maps into the arena
     vector<int64_t> iperm(n);
     for (int64_t k = 0; k < n; ++k) iperm[perm[k]] = k;

@@ -117,11 +117,33 @@ def test_supernodal_refuses_tile_only_calls():
     P = Plan(200, Ap, Ai, route="supernodal", ordering="natural")
     P.upload()
     fac = torch.zeros(P.factor_bytes(1) // 8, dtype=torch.float64, device="cuda")
-    ws = P.workspace(1)
-    sig = torch.zeros_like(fac)
-    assert L.stc_selinv(P.h, fac, 1, sig, ws) == L.STC_ERR_UNSUPPORTED
     v = torch.zeros(1, P.nnzA, dtype=torch.float64, device="cuda")
     info = torch.zeros(1, dtype=torch.int32, device="cuda")
     assert L.stc_factorize_noalloc(P.h, v, 1, fac, info) == L.STC_ERR_UNSUPPORTED
     rc, g = L.stc_group_create([P.h], [1])
     assert rc == L.STC_ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("case", [c for c in CASES if c[0] != "dense_300"], ids=lambda c: c[0])
+def test_supernodal_selinv_and_logdet_gradient(case):
+    # Sigma on every structural entry and d logdet / d a against the oracle (Takahashi),
+    # with the tolerances of test_gpu_adjoint.py
+    from test_gpu_adjoint import _selinv_case
+    name, Ap, Ai, Ax, kw = case
+    n = len(Ap) - 1
+    P = Plan(n, Ap, Ai, route="supernodal", **kw)
+    _selinv_case(P, Ap, Ai, _batch(Ap, Ai, Ax, 2, 5))
+
+
+def test_supernodal_selinv_spatio_temporal_and_serial_replay():
+    from test_gpu_adjoint import _selinv_case
+    Ap, Ai, coords = I.stcov_pattern(14, 12, 8, 6)
+    vals = np.stack([I.stcov_values(t, 14, 12, 8, 6) for t in I.stcov_thetas(3, 9)])
+    n = len(Ap) - 1
+    _selinv_case(Plan(n, Ap, Ai, coords=coords, route="supernodal"), Ap, Ai, vals)
+    out = []
+    for ctas in (1, 0):
+        P = Plan(n, Ap, Ai, coords=coords, route="supernodal", replay_ctas=ctas)
+        fac = P.factorize(dev(vals))
+        out.append((fac.selinv().data.clone(), fac.logdet_backward().clone()))
+    assert torch.equal(out[0][0], out[1][0]) and torch.equal(out[0][1], out[1][1])

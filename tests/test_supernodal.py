@@ -305,3 +305,119 @@ def test_supernodal_device_form_reproduces_oracle(case):
     assert np.all(cells[:, 2] <= 128) and np.all(cells[:, 3] <= 128)
     # one task per diagonal cell and per slice of each off-diagonal cell
     assert len(tasks) == cells[:, 6].sum()
+
+
+def _arena_factor(n, P, values):
+    """The supernodal factor in its arena (the device form run in numpy)."""
+    cells = P.export("sn_dev_cells")
+    tasks = P.export("sn_dev_tasks")
+    upds = P.export("sn_dev_upds")
+    maps = P.export("sn_dev_maps")
+    nodes = P.export("sn_nodes")
+    arena = np.zeros(int(nodes[-1, 3] + nodes[-1, 1] * nodes[-1, 2]) + 4)
+    arena[P.export("sn_value_map")] = values
+
+    def view(c):
+        off, ld, h, w = cells[c, :4]
+        return np.lib.stride_tricks.as_strided(arena[off:], shape=(h, w), strides=(8, 8 * ld))
+
+    for kind, c, d, ub, ue, rs0, rs1, _ in tasks:
+        X = view(c)[rs0:rs1].copy()
+        for a, b, ar0, ar1, rmap, cmap, klen in upds[ub:ue]:
+            U = view(a)[ar0:ar1] @ view(b).T
+            rr = maps[rmap + ar0:rmap + ar1] - rs0
+            cc = maps[cmap:cmap + cells[b, 2]]
+            if kind == 0:
+                U = np.where(rr[:, None] >= cc[None, :], U, 0.0)
+            np.subtract.at(X, (rr[:, None], cc[None, :]), U)
+        if kind == 0:
+            S = np.tril(X)
+            X = np.linalg.cholesky(S + np.tril(S, -1).T)
+        else:
+            X = np.linalg.solve(np.tril(view(d)), X.T).T
+        view(c)[rs0:rs1] = X
+    return arena, view
+
+
+def _execute_selinv_form(n, P, arena):
+    """Run the supernodal selected-inverse task list (STC_EXPORT_SN_SEL_*) with numpy, as
+    the device kernel does: gather the Sigma blocks of each contribution by mode, locate
+    rows by searching the source cell's row list, multiply by L's cell, solve with L_JJ,
+    and the element recurrence in each diagonal block from the lower part of Z."""
+    cells = P.export("sn_dev_cells")
+    nodes = P.export("sn_nodes")
+    rows = P.export("sn_rows")
+    rowoff = P.export("sn_cell_rowoff")
+    stasks = P.export("sn_sel_tasks")
+    scons = P.export("sn_sel_cons")
+    sig = np.zeros_like(arena)
+
+    def view(A, c):
+        off, ld, h, w = cells[c, :4]
+        return np.lib.stride_tricks.as_strided(A[off:], shape=(h, w), strides=(8, 8 * ld))
+
+    def crow(c):
+        return rows[rowoff[c]:rowoff[c] + cells[c, 2]]
+
+    for kind, T, d, cb, ce, rs0, rs1 in stasks:
+        J = cells[T, 4]
+        w = cells[d, 3]
+        Ljj = np.tril(view(arena, d))
+        if kind == 0:
+            K = cells[T, 5]
+            rt = crow(T)[rs0:rs1]
+            C = np.zeros((rs1 - rs0, w))
+            for lc, sc, mode in scons[cb:ce]:
+                Kp = cells[lc, 5]
+                rp = crow(lc)
+                Sv = view(sig, sc)
+                if mode == 0:
+                    a = rt - nodes[K, 0]
+                    b = rp - nodes[K, 0]
+                    G = Sv[np.maximum.outer(a, b), np.minimum.outer(a, b)]
+                elif mode == 1:
+                    pos = np.searchsorted(crow(sc), rt)
+                    assert np.array_equal(crow(sc)[pos], rt)
+                    G = Sv[pos[:, None], (rp - nodes[Kp, 0])[None, :]]
+                else:
+                    pos = np.searchsorted(crow(sc), rp)
+                    assert np.array_equal(crow(sc)[pos], rp)
+                    G = Sv[pos[None, :], (rt - nodes[K, 0])[:, None]]
+                C -= G @ view(arena, lc)
+            view(sig, T)[rs0:rs1] = np.linalg.solve(Ljj.T, C.T).T
+        else:
+            Z = np.zeros((w, w))
+            for lc, sc, mode in scons[cb:ce]:
+                assert mode == 3 and lc == sc
+                Z += view(sig, sc).T @ view(arena, lc)
+            Sg = np.zeros((w, w))
+            for c in range(w - 1, -1, -1):
+                for r in range(w - 1, c, -1):
+                    acc = -Z[r, c]
+                    for i in range(c + 1, w):
+                        acc -= Ljj[i, c] * (Sg[max(r, i), min(r, i)])
+                    Sg[r, c] = acc / Ljj[c, c]
+                acc = -Z[c, c]
+                for i in range(c + 1, w):
+                    acc -= Ljj[i, c] * Sg[i, c]
+                Sg[c, c] = 1.0 / Ljj[c, c] ** 2 + acc / Ljj[c, c]
+            view(sig, d)[:] = np.tril(Sg)
+    return sig[P.export("sn_csc_map")]
+
+
+@pytest.mark.parametrize("case", [c for c in CASES if c[0] != "dense_300"], ids=lambda c: c[0])
+def test_supernodal_selinv_form_reproduces_oracle(case):
+    # every structural entry of Sigma = A_p^{-1} from the supernodal selected-inverse task
+    # list, against the oracle's Takahashi recurrence; a dropped contribution or a wrong
+    # mode (transposed source) fails it
+    name, Ap, Ai, Ax, kw = case
+    n, P = _plan(case)
+    arena, _ = _arena_factor(n, P, Ax)
+    got = _execute_selinv_form(n, P, arena)
+    F = O.OracleFactor(n, Ap, Ai, P.export("perm"))
+    Lx, info = F.factor(Ax)
+    So = F.selinv(Lx)
+    assert np.max(np.abs(got - So)) <= 1e-11 * np.max(np.abs(So)), name
+    modes = P.export("sn_sel_cons")[:, 2]
+    if name in ("stcov_nd", "fem3d_nd", "laplace_bordered_nd"):
+        assert set(modes.tolist()) >= {0, 1, 2, 3}
