@@ -64,10 +64,7 @@ const char* stc_strerror(int code);
 #define STC_ROUTE_AUTO (-1)
 #define STC_ROUTE_DENSE 0       /* every active tile stored as a full n_b x n_b block  */
 #define STC_ROUTE_SEMISPARSE 1  /* active-column tiles + banded-packed diagonal tiles */
-#define STC_ROUTE_SUPERNODAL 2  /* non-uniform supernodal panels (Sec. 5.4).  Executed
-                                   when asked for with force_route; a plan whose selector
-                                   picks it under STC_ROUTE_AUTO executes on the
-                                   semisparse route (route_executed says which)        */
+#define STC_ROUTE_SUPERNODAL 2  /* non-uniform supernodal panels (Sec. 5.4)           */
 
 /* ---- orderings (Sec. 3) ------------------------------------------------ */
 #define STC_ORDER_AUTO 0     /* ND when coordinates are given, else best of RCM/natural */

@@ -1160,11 +1160,7 @@ static int analyze_impl(int64_t n, const int64_t* Ap, const int64_t* Ai, const d
         else if (P->rho >= opt.gate_rho_semi || P->sigma >= opt.gate_sigma_skew) sel = STC_ROUTE_SEMISPARSE;
         else sel = STC_ROUTE_SUPERNODAL;
         P->route_selected = sel;
-        int ex = opt.force_route != STC_ROUTE_AUTO ? opt.force_route : sel;
-        // the selector's supernodal choice executes on the semisparse tile route unless the
-        // supernodal route is asked for explicitly
-        if (ex == STC_ROUTE_SUPERNODAL && opt.force_route != STC_ROUTE_SUPERNODAL) ex = STC_ROUTE_SEMISPARSE;
-        P->route_exec = ex;
+        P->route_exec = opt.force_route != STC_ROUTE_AUTO ? opt.force_route : sel;
     }
     if (P->route_exec == STC_ROUTE_DENSE) {  // rebuild storage as full tiles
         P->tiles.clear(); P->nact.clear(); P->aoff_struct.clear(); P->aind_struct.clear();

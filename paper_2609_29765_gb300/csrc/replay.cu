@@ -306,6 +306,28 @@ __device__ __forceinline__ void trsm_rows(double* X, int ldx, int R, int pw, con
     trsm_rows_dir<false>(X, ldx, R, pw, D, ldd, dinv);
 }
 
+struct SnArgs {
+    const SnDevCell* cells;
+    const SnDevTask* tasks;
+    const SnDevUpd* upds;
+    const int16_t* maps;
+    const int32_t* first;    // first column of each supernode
+    double* factor;          // item 0
+    long long fstride;       // doubles per item
+    long long poff;          // offset of the logdet partials (one per supernode)
+    int* counters;           // [batch][ncells]
+    int ncells;
+    int* info;
+    WorkHeader* hdr;
+    int ntasks;
+    long long batch;
+    long long spin;
+};
+
+// One supernodal task; defined with the supernodal route below.
+__device__ __forceinline__ void sn_task(const SnArgs& a, int ti, long long item, double* C, double* S0, double* S1,
+                                        double* sv, int* s_rm, int* s_cm, int& s_ok);
+
 struct ReplayArgs {        // one job: a plan and a batch of value sets
     const DTile* tiles;
     const int16_t* saind;
@@ -325,6 +347,7 @@ struct ReplayArgs {        // one job: a plan and a batch of value sets
     int nb;
     int slice_h;             // rows per row slice of an off-diagonal tile
     long long spin;
+    int sn;                  // != 0: a supernodal plan, executed from the launch's snj[job]
 };
 
 // One launch of the replay kernel: up to kMaxJobs jobs (plans) in one persistent grid.
@@ -333,6 +356,7 @@ struct ReplayArgs {        // one job: a plan and a batch of value sets
 constexpr int kMaxJobs = 8;
 struct ReplayLaunch {
     ReplayArgs job[kMaxJobs];
+    SnArgs snj[kMaxJobs];    // the supernodal jobs' arguments (mixed-route groups)
     int njobs;
     const uint64_t* queue;
     long long total;
@@ -661,7 +685,11 @@ __device__ void potrf_packed(double* P, int nb, int w, int kd, double* S, int* b
     __syncthreads();
 }
 
-__global__ void __launch_bounds__(kThreads, 2) replay_kernel(const __grid_constant__ ReplayLaunch Lc) {
+// WITH_SN: the launch may hold supernodal jobs (a mixed-route group); their tasks run
+// through sn_task.  The tile-only instantiation is the one every single-plan factorization
+// of a tile route uses.
+template <bool WITH_SN>
+__global__ void __launch_bounds__(kThreads, 2) replay_kernel_t(const __grid_constant__ ReplayLaunch Lc) {
     extern __shared__ double smem[];
     double* C = smem;              // row-slice buffer (ld kRLd) or packed diagonal tile
     double* S0 = C + kRCbuf;       // staging, kRKc columns of ld kRStLd
@@ -687,6 +715,13 @@ __global__ void __launch_bounds__(kThreads, 2) replay_kernel(const __grid_consta
             jb = 0;
             ti = (int)(slot / Lc.job[0].batch);
             item = slot % Lc.job[0].batch;
+        }
+        if constexpr (WITH_SN) {
+            if (Lc.job[jb].sn) {
+                __shared__ int s_rm[kNbMax], s_cm[kNbMax];
+                sn_task(Lc.snj[jb], ti, item, C, S0, S1, sv, s_rm, s_cm, s_ok);
+                continue;
+            }
         }
         const ReplayArgs& a = Lc.job[jb];
         const int nb = a.nb;
@@ -1404,23 +1439,6 @@ __global__ void __launch_bounds__(kThreads, 1) solve_kernel(SolveArgs a) {
 // (each row of A lands on one target row, each row of B on one target column).  A
 // cell's completion counter counts its finished slices.
 // ---------------------------------------------------------------------------
-struct SnArgs {
-    const SnDevCell* cells;
-    const SnDevTask* tasks;
-    const SnDevUpd* upds;
-    const int16_t* maps;
-    const int32_t* first;    // first column of each supernode
-    double* factor;          // item 0
-    long long fstride;       // doubles per item
-    long long poff;          // offset of the logdet partials (one per supernode)
-    int* counters;           // [batch][ncells]
-    int ncells;
-    int* info;
-    WorkHeader* hdr;
-    int ntasks;
-    long long batch;
-    long long spin;
-};
 
 // C(rm[r], cm[c]) -= sum_k A(r,k) B(c,k) for r < R, c < Cn: the tile product of
 // mma_tiles with the result scattered through row and column maps (shared memory, each
@@ -1501,6 +1519,122 @@ __device__ __forceinline__ void sn_stage(double* S, int ld, const double* F, con
     for_rc(Rp, K, [&](int r, int k) { S[r + k * ld] = r < R ? __ldcg(base + r + (size_t)k * c.ld) : 0.0; });
 }
 
+// One supernodal task (a diagonal cell or a row slice of an off-diagonal cell) of item
+// `item`, executed by the whole CTA: its updates, then POTRF or TRSM, then publication.
+// C, S0, S1, sv: the replay kernel's shared buffers; s_rm, s_cm: kNbMax ints of shared
+// memory; s_ok: the CTA's shared status flag.
+__device__ __forceinline__ void sn_task(const SnArgs& a, int ti, long long item, double* C, double* S0, double* S1,
+                                        double* sv, int* s_rm, int* s_cm, int& s_ok) {
+    const SnDevTask t = a.tasks[ti];
+    const SnDevCell O = a.cells[t.cell];
+    double* F = a.factor + item * a.fstride;
+    int* cnt = a.counters + item * a.ncells;
+    if (threadIdx.x == 0) s_ok = (*(volatile int*)&a.hdr->status == STC_OK);
+    __syncthreads();
+    if (t.kind == SN_T_DIAG) {
+        const int w = O.w;
+        if (s_ok) {
+            // lower triangle of the diagonal cell -> packed triangle of width w
+            for_rc(w, w, [&](int r, int c) {
+                if (r >= c) C[pk(w, r, c)] = __ldcg(F + O.off + r + (size_t)c * O.ld);
+            });
+            __syncthreads();
+            for (int ui = t.ubeg; ui < t.uend && s_ok; ++ui) {
+                const SnDevUpd u = a.upds[ui];
+                const SnDevCell A = a.cells[u.a];
+                if (threadIdx.x == 0) s_ok = wait_counter(cnt + u.a, A.nslices, a.spin, &a.hdr->status);
+                for (int i = threadIdx.x; i < A.h; i += kThreads) s_rm[i] = a.maps[u.rmap + i];
+                __syncthreads();
+                if (!s_ok) break;
+                for (int k0 = 0; k0 < u.klen; k0 += kRKc) {
+                    const int K = min(kRKc, u.klen - k0);
+                    sn_stage(S0, kRStLd, F, A, 0, A.h, k0, K);
+                    __syncthreads();
+                    mma_scatter<true, true>(C, 0, A.h, A.h, S0, kRStLd, S0, kRStLd, K, s_rm, s_rm, w);
+                    __syncthreads();
+                }
+            }
+            if (s_ok) {
+                int bad;
+                double ls;
+                potrf_packed(C, w, w, w - 1, S0, &bad, &ls, [](int) {});
+                for_rc(w, w, [&](int r, int c) {
+                    if (r >= c) __stcg(F + O.off + r + (size_t)c * O.ld, C[pk(w, r, c)]);
+                });
+                if (threadIdx.x == 0) {
+                    if (bad >= 0) record_info(a.info + item, a.first[O.I] + bad + 1);
+                    F[a.poff + O.I] = bad >= 0 ? __longlong_as_double(0x7ff8000000000000LL) : ls;
+                }
+            }
+        }
+    } else {
+        const int R = t.rs1 - t.rs0, w = O.w;
+        if (s_ok) {
+            for_rc(R, w, [&](int r, int c) { C[r + c * kRLd] = __ldcg(F + O.off + t.rs0 + r + (size_t)c * O.ld); });
+            __syncthreads();
+            for (int ui = t.ubeg; ui < t.uend && s_ok; ++ui) {
+                const SnDevUpd u = a.upds[ui];
+                const SnDevCell A = a.cells[u.a];
+                const SnDevCell B = a.cells[u.b];
+                const int Ra = u.ar1 - u.ar0;
+                if (threadIdx.x == 0)
+                    s_ok = wait_counter(cnt + u.a, A.nslices, a.spin, &a.hdr->status) &&
+                           wait_counter(cnt + u.b, B.nslices, a.spin, &a.hdr->status);
+                for (int i = threadIdx.x; i < Ra; i += kThreads) s_rm[i] = a.maps[u.rmap + u.ar0 + i] - t.rs0;
+                for (int j = threadIdx.x; j < B.h; j += kThreads) s_cm[j] = a.maps[u.cmap + j];
+                __syncthreads();
+                if (!s_ok) break;
+                for (int k0 = 0; k0 < u.klen; k0 += kRKc) {
+                    const int K = min(kRKc, u.klen - k0);
+                    sn_stage(S0, kRStLd, F, A, u.ar0, Ra, k0, K);
+                    sn_stage(S1, kRStLd, F, B, 0, B.h, k0, K);
+                    __syncthreads();
+                    mma_scatter<false, false>(C, kRLd, Ra, B.h, S0, kRStLd, S1, kRStLd, K, s_rm, s_cm, 0);
+                    __syncthreads();
+                }
+            }
+            if (s_ok) {
+                const SnDevCell D = a.cells[t.diag];
+                if (threadIdx.x == 0) s_ok = wait_counter(cnt + t.diag, 1, a.spin, &a.hdr->status);
+                __syncthreads();
+                if (s_ok) {
+                    // X <- X L_JJ^{-T}, right-looking by panels of kPb columns
+                    const double* DT = F + D.off;
+                    for (int p = 0; p < w; p += kPb) {
+                        const int pw = min(kPb, w - p);
+                        for (int idx = threadIdx.x; idx < kPb * kPb; idx += kThreads) {
+                            const int i = idx & (kPb - 1), j = idx / kPb;
+                            S0[i + j * (kPb + 1)] =
+                                (i < pw && j < pw && i >= j) ? __ldcg(DT + p + i + (size_t)(p + j) * D.ld) : 0.0;
+                        }
+                        __syncthreads();
+                        if (threadIdx.x < pw) sv[threadIdx.x] = 1.0 / S0[threadIdx.x * (kPb + 2)];
+                        __syncthreads();
+                        trsm_rows(C + p * kRLd, kRLd, R, pw, S0, kPb + 1, sv);
+                        __syncthreads();
+                        const int pn = p + pw, Cn = w - pn;
+                        if (Cn <= 0) continue;
+                        for (int k0 = p; k0 < pn; k0 += kRKc) {
+                            const int K = min(kRKc, pn - k0);
+                            const int Cp = ((Cn + 3) & ~3) + 4;
+                            for_rc(Cp, K, [&](int c, int k) {
+                                S1[c + k * kRStLd] = c < Cn ? __ldcg(DT + pn + c + (size_t)(k0 + k) * D.ld) : 0.0;
+                            });
+                            __syncthreads();
+                            mma_sub<false>(C + pn * kRLd, kRLd, R, Cn, C + k0 * kRLd, kRLd, S1, kRStLd, K);
+                            __syncthreads();
+                        }
+                    }
+                    for_rc(R, w, [&](int r, int c) { __stcg(F + O.off + t.rs0 + r + (size_t)c * O.ld, C[r + c * kRLd]); });
+                }
+            }
+        }
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) red_release_add(cnt + t.cell, 1);
+}
+
 __global__ void __launch_bounds__(kThreads, 2) sn_replay_kernel(const __grid_constant__ SnArgs a) {
     extern __shared__ double smem[];
     double* C = smem;              // row-slice buffer (ld kRLd) or packed diagonal cell
@@ -1517,116 +1651,7 @@ __global__ void __launch_bounds__(kThreads, 2) sn_replay_kernel(const __grid_con
         const long long slot = s_slot;
         __syncthreads();
         if (slot >= total) break;
-        const int ti = (int)(slot / a.batch);
-        const long long item = slot % a.batch;
-        const SnDevTask t = a.tasks[ti];
-        const SnDevCell O = a.cells[t.cell];
-        double* F = a.factor + item * a.fstride;
-        int* cnt = a.counters + item * a.ncells;
-        if (threadIdx.x == 0) s_ok = (*(volatile int*)&a.hdr->status == STC_OK);
-        __syncthreads();
-        if (t.kind == SN_T_DIAG) {
-            const int w = O.w;
-            if (s_ok) {
-                // lower triangle of the diagonal cell -> packed triangle of width w
-                for_rc(w, w, [&](int r, int c) {
-                    if (r >= c) C[pk(w, r, c)] = __ldcg(F + O.off + r + (size_t)c * O.ld);
-                });
-                __syncthreads();
-                for (int ui = t.ubeg; ui < t.uend && s_ok; ++ui) {
-                    const SnDevUpd u = a.upds[ui];
-                    const SnDevCell A = a.cells[u.a];
-                    if (threadIdx.x == 0) s_ok = wait_counter(cnt + u.a, A.nslices, a.spin, &a.hdr->status);
-                    for (int i = threadIdx.x; i < A.h; i += kThreads) s_rm[i] = a.maps[u.rmap + i];
-                    __syncthreads();
-                    if (!s_ok) break;
-                    for (int k0 = 0; k0 < u.klen; k0 += kRKc) {
-                        const int K = min(kRKc, u.klen - k0);
-                        sn_stage(S0, kRStLd, F, A, 0, A.h, k0, K);
-                        __syncthreads();
-                        mma_scatter<true, true>(C, 0, A.h, A.h, S0, kRStLd, S0, kRStLd, K, s_rm, s_rm, w);
-                        __syncthreads();
-                    }
-                }
-                if (s_ok) {
-                    int bad;
-                    double ls;
-                    potrf_packed(C, w, w, w - 1, S0, &bad, &ls, [](int) {});
-                    for_rc(w, w, [&](int r, int c) {
-                        if (r >= c) __stcg(F + O.off + r + (size_t)c * O.ld, C[pk(w, r, c)]);
-                    });
-                    if (threadIdx.x == 0) {
-                        if (bad >= 0) record_info(a.info + item, a.first[O.I] + bad + 1);
-                        F[a.poff + O.I] = bad >= 0 ? __longlong_as_double(0x7ff8000000000000LL) : ls;
-                    }
-                }
-            }
-        } else {
-            const int R = t.rs1 - t.rs0, w = O.w;
-            if (s_ok) {
-                for_rc(R, w, [&](int r, int c) { C[r + c * kRLd] = __ldcg(F + O.off + t.rs0 + r + (size_t)c * O.ld); });
-                __syncthreads();
-                for (int ui = t.ubeg; ui < t.uend && s_ok; ++ui) {
-                    const SnDevUpd u = a.upds[ui];
-                    const SnDevCell A = a.cells[u.a];
-                    const SnDevCell B = a.cells[u.b];
-                    const int Ra = u.ar1 - u.ar0;
-                    if (threadIdx.x == 0)
-                        s_ok = wait_counter(cnt + u.a, A.nslices, a.spin, &a.hdr->status) &&
-                               wait_counter(cnt + u.b, B.nslices, a.spin, &a.hdr->status);
-                    for (int i = threadIdx.x; i < Ra; i += kThreads) s_rm[i] = a.maps[u.rmap + u.ar0 + i] - t.rs0;
-                    for (int j = threadIdx.x; j < B.h; j += kThreads) s_cm[j] = a.maps[u.cmap + j];
-                    __syncthreads();
-                    if (!s_ok) break;
-                    for (int k0 = 0; k0 < u.klen; k0 += kRKc) {
-                        const int K = min(kRKc, u.klen - k0);
-                        sn_stage(S0, kRStLd, F, A, u.ar0, Ra, k0, K);
-                        sn_stage(S1, kRStLd, F, B, 0, B.h, k0, K);
-                        __syncthreads();
-                        mma_scatter<false, false>(C, kRLd, Ra, B.h, S0, kRStLd, S1, kRStLd, K, s_rm, s_cm, 0);
-                        __syncthreads();
-                    }
-                }
-                if (s_ok) {
-                    const SnDevCell D = a.cells[t.diag];
-                    if (threadIdx.x == 0) s_ok = wait_counter(cnt + t.diag, 1, a.spin, &a.hdr->status);
-                    __syncthreads();
-                    if (s_ok) {
-                        // X <- X L_JJ^{-T}, right-looking by panels of kPb columns
-                        const double* DT = F + D.off;
-                        for (int p = 0; p < w; p += kPb) {
-                            const int pw = min(kPb, w - p);
-                            for (int idx = threadIdx.x; idx < kPb * kPb; idx += kThreads) {
-                                const int i = idx & (kPb - 1), j = idx / kPb;
-                                S0[i + j * (kPb + 1)] =
-                                    (i < pw && j < pw && i >= j) ? __ldcg(DT + p + i + (size_t)(p + j) * D.ld) : 0.0;
-                            }
-                            __syncthreads();
-                            if (threadIdx.x < pw) sv[threadIdx.x] = 1.0 / S0[threadIdx.x * (kPb + 2)];
-                            __syncthreads();
-                            trsm_rows(C + p * kRLd, kRLd, R, pw, S0, kPb + 1, sv);
-                            __syncthreads();
-                            const int pn = p + pw, Cn = w - pn;
-                            if (Cn <= 0) continue;
-                            for (int k0 = p; k0 < pn; k0 += kRKc) {
-                                const int K = min(kRKc, pn - k0);
-                                const int Cp = ((Cn + 3) & ~3) + 4;
-                                for_rc(Cp, K, [&](int c, int k) {
-                                    S1[c + k * kRStLd] = c < Cn ? __ldcg(DT + pn + c + (size_t)(k0 + k) * D.ld) : 0.0;
-                                });
-                                __syncthreads();
-                                mma_sub<false>(C + pn * kRLd, kRLd, R, Cn, C + k0 * kRLd, kRLd, S1, kRStLd, K);
-                                __syncthreads();
-                            }
-                        }
-                        for_rc(R, w, [&](int r, int c) { __stcg(F + O.off + t.rs0 + r + (size_t)c * O.ld, C[r + c * kRLd]); });
-                    }
-                }
-            }
-        }
-        __threadfence();
-        __syncthreads();
-        if (threadIdx.x == 0) red_release_add(cnt + t.cell, 1);
+        sn_task(a, (int)(slot / a.batch), slot % a.batch, C, S0, S1, sv, s_rm, s_cm, s_ok);
     }
 }
 
@@ -2315,7 +2340,11 @@ int device_info(int* dev, int* sms) {
     DevInfo& d = g_dev[*dev];
     if (!d.attr_set) {
         if (cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, *dev) != cudaSuccess) return STC_ERR_CUDA;
-        if (cudaFuncSetAttribute(replay_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRSmemBytes) != cudaSuccess)
+        if (cudaFuncSetAttribute(replay_kernel_t<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)kRSmemBytes) != cudaSuccess)
+            return STC_ERR_CUDA;
+        if (cudaFuncSetAttribute(replay_kernel_t<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)kRSmemBytes) != cudaSuccess)
             return STC_ERR_CUDA;
         if (cudaFuncSetAttribute(selinv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes) != cudaSuccess)
             return STC_ERR_CUDA;
@@ -2582,22 +2611,28 @@ int pick_taskset(stc_plan* P, int64_t batch, int sms, bool bl_order, TaskSet** o
 
 inline cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 
+// Arguments of a supernodal job (the plan's device copies must be resident).
+void fill_sn(SnArgs& a, const stc_plan* P, void* d_factor, int* counters, int32_t* d_info, int64_t batch,
+             WorkHeader* hdr) {
+    const SnPlan& Sp = P->supernodal();
+    a.cells = P->sndev.cells; a.tasks = P->sndev.tasks; a.upds = P->sndev.upds; a.maps = P->sndev.maps;
+    a.first = P->sndev.first; a.factor = (double*)d_factor; a.fstride = Sp.item_doubles(); a.poff = Sp.poff();
+    a.hdr = hdr; a.counters = counters; a.ncells = (int)Sp.dcells.size(); a.info = d_info;
+    a.ntasks = (int)Sp.dtasks.size(); a.batch = batch;
+    a.spin = P->opt.spin_limit > 0 ? P->opt.spin_limit : kDefaultSpin;
+}
+
 // Supernodal factorization: the persistent kernel over (task, item) slots, every item of
 // a task in lockstep (the left-looking task order is topological).
 int sn_factorize_scattered(stc_plan* P, int64_t batch, void* d_factor, void* d_work, int32_t* d_info, void* stream,
                            int dev, int sms) {
     int rc;
     if ((rc = ensure_sn(P, dev))) return rc;
-    const SnPlan& Sp = P->supernodal();
     cudaStream_t st = S(stream);
     if (cudaMemsetAsync(d_work, 0, factorize_ws(P, batch), st) != cudaSuccess) return STC_ERR_CUDA;
     if (cudaMemsetAsync(d_info, 0, (size_t)batch * sizeof(int32_t), st) != cudaSuccess) return STC_ERR_CUDA;
     SnArgs a{};
-    a.cells = P->sndev.cells; a.tasks = P->sndev.tasks; a.upds = P->sndev.upds; a.maps = P->sndev.maps;
-    a.first = P->sndev.first; a.factor = (double*)d_factor; a.fstride = Sp.item_doubles(); a.poff = Sp.poff();
-    a.hdr = (WorkHeader*)d_work; a.counters = (int*)((char*)d_work + sizeof(WorkHeader));
-    a.ncells = (int)Sp.dcells.size(); a.info = d_info; a.ntasks = (int)Sp.dtasks.size(); a.batch = batch;
-    a.spin = P->opt.spin_limit > 0 ? P->opt.spin_limit : kDefaultSpin;
+    fill_sn(a, P, d_factor, (int*)((char*)d_work + sizeof(WorkHeader)), d_info, batch, (WorkHeader*)d_work);
     const long long total = (long long)a.ntasks * batch;
     const int grid = grid_of(P, default_ctas(sms, batch), total);
     sn_replay_kernel<<<grid, kThreads, kRSmemBytes, st>>>(a);
@@ -2769,7 +2804,7 @@ extern "C" int stc_factorize_scattered(const stc_plan* Pc, int64_t batch, void* 
     Lc.hdr = (WorkHeader*)d_work;
     Lc.total = (long long)ts->tasks.size() * batch;
     const int grid = grid_of(P, default_ctas(sms, batch_total(Lc)), Lc.total);
-    replay_kernel<<<grid, kThreads, kRSmemBytes, st>>>(Lc);
+    replay_kernel_t<false><<<grid, kThreads, kRSmemBytes, st>>>(Lc);
     return cudaGetLastError() == cudaSuccess ? STC_OK : STC_ERR_CUDA;
 }
 
@@ -2977,6 +3012,7 @@ struct stc_group {
     uint64_t* d_queue = nullptr;
     long long total = 0;
     int device = -1;
+    bool has_sn = false;      // a supernodal plan among the jobs (the mixed-route kernel runs)
 };
 
 extern "C" int stc_group_create(int32_t nplans, const stc_plan* const* plans, const int64_t* batch,
@@ -2991,7 +3027,6 @@ extern "C" int stc_group_create(int32_t nplans, const stc_plan* const* plans, co
     int64_t btot = 0;
     for (int p = 0; p < nplans; ++p) {
         if (!plans[p] || batch[p] <= 0 || batch[p] >= (1LL << 28)) return STC_ERR_INVALID_ARG;
-        if (is_sn(plans[p])) return STC_ERR_UNSUPPORTED;  // mixed batches of tile-route plans
         btot += batch[p];
     }
     size_t off = sizeof(WorkHeader);
@@ -2999,32 +3034,47 @@ extern "C" int stc_group_create(int32_t nplans, const stc_plan* const* plans, co
         stc_plan* P = const_cast<stc_plan*>(plans[p]);
         if ((rc = ensure_plan(P, dev))) return rc;
         TaskSet* ts = nullptr;
-        if ((rc = pick_taskset(P, btot, sms, false, &ts))) return rc;
-        if ((rc = ensure_taskset(P, ts, dev))) return rc;
+        if (is_sn(P)) {
+            if ((rc = ensure_sn(P, dev))) return rc;
+            g->has_sn = true;
+        } else {
+            if ((rc = pick_taskset(P, btot, sms, false, &ts))) return rc;
+            if ((rc = ensure_taskset(P, ts, dev))) return rc;
+        }
         g->plans.push_back(P);
         g->batch.push_back(batch[p]);
         g->ts.push_back(ts);
         g->cnt_off.push_back(off);
-        off += ((size_t)batch[p] * P->tiles.size() * sizeof(int) + 255) / 256 * 256;
+        off += ((size_t)batch[p] * counters_per_item(P) * sizeof(int) + 255) / 256 * 256;
     }
     g->ws_bytes = off;
+    // queue keys: the tile plans' modelled earliest starts; a supernodal plan's tasks (in
+    // their left-looking order) spread evenly over the longest tile plan's span
+    double span = 0.0;
+    for (int p = 0; p < nplans; ++p)
+        if (g->ts[p] && !g->ts[p]->qkey.empty()) span = std::max(span, g->ts[p]->qkey.back());
+    if (!(span > 0.0)) span = 1.0;
+    auto ntasks = [&](int p) { return g->ts[p] ? g->ts[p]->tasks.size() : g->plans[p]->supernodal().dtasks.size(); };
+    auto key = [&](int p, size_t t) {
+        return g->ts[p] ? g->ts[p]->qkey[t] : span * double(t + 1) / double(ntasks(p));
+    };
     // merged queue: plans' task lists in earliest-start order, each task expanded to its
     // plan's batch items in lockstep
     std::vector<uint64_t> q;
     size_t nslots = 0;
-    for (int p = 0; p < nplans; ++p) nslots += g->ts[p]->tasks.size() * (size_t)batch[p];
+    for (int p = 0; p < nplans; ++p) nslots += ntasks(p) * (size_t)batch[p];
     q.reserve(nslots);
     typedef std::pair<double, int> E;
     std::priority_queue<E, std::vector<E>, std::greater<E>> h;
     std::vector<size_t> pos(nplans, 0);
     for (int p = 0; p < nplans; ++p)
-        if (!g->ts[p]->tasks.empty()) h.push(E(g->ts[p]->qkey[0], p));
+        if (ntasks(p) > 0) h.push(E(key(p, 0), p));
     while (!h.empty()) {
         const int p = h.top().second;
         h.pop();
         const size_t t = pos[p];
         for (int64_t b = 0; b < batch[p]; ++b) q.push_back(qpack(p, (int)t, b));
-        if (++pos[p] < g->ts[p]->tasks.size()) h.push(E(g->ts[p]->qkey[pos[p]], p));
+        if (++pos[p] < ntasks(p)) h.push(E(key(p, pos[p]), p));
     }
     g->total = (long long)q.size();
     if (cudaMalloc((void**)&g->d_queue, std::max<size_t>(1, q.size()) * sizeof(uint64_t)) != cudaSuccess)
@@ -3057,15 +3107,25 @@ extern "C" int stc_factorize_group(stc_group* g, const double* const* d_values, 
     for (int p = 0; p < np; ++p) {
         if (cudaMemsetAsync(d_info[p], 0, (size_t)g->batch[p] * sizeof(int32_t), st) != cudaSuccess)
             return STC_ERR_CUDA;
-        fill_job(Lc.job[p], g->plans[p], g->ts[p], d_factor[p], (int*)((char*)d_work + g->cnt_off[p]), d_info[p],
-                 g->batch[p], (WorkHeader*)d_work);
+        int* counters = (int*)((char*)d_work + g->cnt_off[p]);
+        if (g->ts[p]) {
+            fill_job(Lc.job[p], g->plans[p], g->ts[p], d_factor[p], counters, d_info[p], g->batch[p],
+                     (WorkHeader*)d_work);
+        } else {
+            fill_sn(Lc.snj[p], g->plans[p], d_factor[p], counters, d_info[p], g->batch[p], (WorkHeader*)d_work);
+            Lc.job[p].sn = 1;
+            Lc.job[p].batch = g->batch[p];
+        }
     }
     Lc.njobs = np;
     Lc.queue = g->d_queue;
     Lc.hdr = (WorkHeader*)d_work;
     Lc.total = g->total;
     const int grid = grid_of(g->plans[0], default_ctas(sms, batch_total(Lc)), Lc.total);
-    replay_kernel<<<grid, kThreads, kRSmemBytes, st>>>(Lc);
+    if (g->has_sn)
+        replay_kernel_t<true><<<grid, kThreads, kRSmemBytes, st>>>(Lc);
+    else
+        replay_kernel_t<false><<<grid, kThreads, kRSmemBytes, st>>>(Lc);
     return cudaGetLastError() == cudaSuccess ? STC_OK : STC_ERR_CUDA;
 }
 
@@ -3112,7 +3172,7 @@ extern "C" int stc_factorize_noalloc(const stc_plan* Pc, const double* d_values,
     Lc.hdr = (WorkHeader*)scratch;
     Lc.total = (long long)ts->tasks.size() * batch;
     const int grid = grid_of(P, default_ctas(sms, batch_total(Lc)), Lc.total);
-    replay_kernel<<<grid, kThreads, kRSmemBytes, st>>>(Lc);
+    replay_kernel_t<false><<<grid, kThreads, kRSmemBytes, st>>>(Lc);
     if (cudaGetLastError() != cudaSuccess) return STC_ERR_CUDA;
     if (d_status && cudaMemcpyAsync(d_status, &Lc.hdr->status, sizeof(int32_t), cudaMemcpyDeviceToDevice, st) !=
                         cudaSuccess)

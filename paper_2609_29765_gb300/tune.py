@@ -1,4 +1,4 @@
-"""Autotuner: pick the tile size n_b and the row-slice count for a pattern and batch.
+"""Autotuner: pick the route, the tile size n_b and the row-slice count for a pattern and batch.
 
 Grid search, measured on the device: for every candidate n_b the pattern is analysed on
 the host (ordering and symbolic factor are shared by construction of the inputs), and
@@ -16,15 +16,23 @@ from .api import Plan
 
 def autotune(n, colptr, rowind, values, coords=None, nbs=(32, 64, 96, 128), slices=(1, 2, 4, 8),
              route="auto", ordering="auto", reps=2, nd_leaf=64):
+    """route="auto" also tries the three routes (the supernodal layout once: n_b and the
+    row slices do not change it); a named route tunes n_b and the slices of that route."""
     import torch
     if values.dim() == 1:
         values = values.unsqueeze(0)
     values = values.contiguous()
     batch = values.shape[0]
     table = []
-    for nb in nbs:
-        for s in slices:
-            P = Plan(n, colptr, rowind, coords=coords, nb=nb, route=route, ordering=ordering,
+    configs = []
+    for r in (("semisparse", "dense", "supernodal") if route == "auto" else (route,)):
+        if r == "supernodal":
+            configs.append((r, nbs[0], slices[0]))
+        else:
+            configs += [(r, nb, s) for nb in nbs for s in slices]
+    for r, nb, s in configs:
+        if True:
+            P = Plan(n, colptr, rowind, coords=coords, nb=nb, route=r, ordering=ordering,
                      row_slices=s, nd_leaf=nd_leaf)
             fac = torch.empty(P.factor_bytes(batch) // 8, dtype=torch.float64, device=values.device)
             info = torch.empty(batch, dtype=torch.int32, device=values.device)

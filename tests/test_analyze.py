@@ -138,7 +138,7 @@ def test_dense_route_stores_full_tiles():
 
 def test_value_map_is_injective_and_inside_factor():
     Ap, Ai, _ = I.random_spd(200, 0.02, 3)
-    P = Plan(200, Ap, Ai, nb=16, ordering="rcm")
+    P = Plan(200, Ap, Ai, nb=16, ordering="rcm", route="semisparse")
     vm = P.export("value_map")
     assert len(np.unique(vm)) == len(vm)
     assert vm.min() >= 0 and vm.max() < P.info["factor_doubles"]

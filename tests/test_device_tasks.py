@@ -208,14 +208,14 @@ def _cases():
     yield "bordered_nd_nb16", Ap, Ai, Ax, dict(coords=coords, nb=16, route="semisparse", nd_leaf=16)
     yield "bordered_nd_dense_nb32", Ap, Ai, Ax, dict(coords=coords, nb=32, route="dense", nd_leaf=16)
     Ap, Ai, Ax = I.band(700, 40, 1)
-    yield "band_nb32", Ap, Ai, Ax, dict(nb=32, ordering="natural")
-    yield "band_nb128", Ap, Ai, Ax, dict(nb=128, ordering="natural")
+    yield "band_nb32", Ap, Ai, Ax, dict(nb=32, ordering="natural", route="semisparse")
+    yield "band_nb128", Ap, Ai, Ax, dict(nb=128, ordering="natural", route="semisparse")
     Ap, Ai, coords = I.stcov_pattern(7, 6, 5, 3)
     Ax = I.stcov_values((2.0, 0.7, 0.5), 7, 6, 5, 3)
-    yield "stcov_nd_nb16", Ap, Ai, Ax, dict(coords=coords, nb=16, nd_leaf=20)
+    yield "stcov_nd_nb16", Ap, Ai, Ax, dict(coords=coords, nb=16, nd_leaf=20, route="semisparse")
     Ap, Ai, Ax = I.random_spd(400, 0.008, 5)
-    yield "random_rcm_nb8", Ap, Ai, Ax, dict(nb=8, ordering="rcm")
-    yield "random_rcm_nb24", Ap, Ai, Ax, dict(nb=24, ordering="rcm")
+    yield "random_rcm_nb8", Ap, Ai, Ax, dict(nb=8, ordering="rcm", route="semisparse")
+    yield "random_rcm_nb24", Ap, Ai, Ax, dict(nb=24, ordering="rcm", route="semisparse")
     Ap, Ai, Ax, coords = I.fem3d(7, 6, 6)
     yield "fem_dense_nb16", Ap, Ai, Ax, dict(coords=coords, nb=16, route="dense", nd_leaf=20)
 

@@ -16,16 +16,19 @@ def dev(a):
     return torch.as_tensor(np.ascontiguousarray(a), device="cuda")
 
 
-@pytest.mark.parametrize("route", ["dense", "semisparse"])
+@pytest.mark.parametrize("route", ["dense", "semisparse", "supernodal", "mixed"])
 def test_group_mixed_patterns_match_single_launch_and_oracle(route):
+    # "mixed": one plan per route in the same launch (the kernel that also runs
+    # supernodal tasks)
     plans, vals, pats = [], [], []
-    for m, b in ((8, 2), (10, 3), (12, 2)):   # 8^3, 10^3, 12^3 grids, uneven batches
+    for i, (m, b) in enumerate(((8, 2), (10, 3), (12, 2))):   # 8^3, 10^3, 12^3 grids, uneven batches
         vs = []
         for s in range(b):
             Ap, Ai, Ax, coords = I.fem3d(m, m, m, seed=s)
             vs.append(Ax)
         pats.append((len(Ap) - 1, Ap, Ai))
-        plans.append(Plan(len(Ap) - 1, Ap, Ai, coords=coords, nb=32, route=route, nd_leaf=32))
+        r = ("dense", "supernodal", "semisparse")[i] if route == "mixed" else route
+        plans.append(Plan(len(Ap) - 1, Ap, Ai, coords=coords, nb=32, route=r, nd_leaf=32))
         vals.append(dev(np.stack(vs)))
     G = Group(plans, [v.shape[0] for v in vals])
     facs = G.factorize(vals)
@@ -60,9 +63,10 @@ def test_autotuner_picks_a_valid_configuration():
     n = len(Ap) - 1
     v = dev(np.stack([I.laplace2d_bordered(seed=s)[2] for s in range(8)]))
     best, table = autotune(n, Ap, Ai, v, coords=coords, nbs=(32, 64), slices=(1, 2), reps=1)
-    assert len(table) == 4 and all(r["ok"] for r in table)
+    assert len(table) == 9 and all(r["ok"] for r in table)   # 2 tile routes x 4, supernodal once
+    assert {r["route"] for r in table} == {"semisparse", "dense", "supernodal"}
     assert best["ms"] == min(r["ms"] for r in table)
-    P = Plan(n, Ap, Ai, coords=coords, nb=best["nb"], row_slices=best["row_slices"])
+    P = Plan(n, Ap, Ai, coords=coords, nb=best["nb"], row_slices=best["row_slices"], route=best["route"])
     F = O.OracleFactor(n, Ap, Ai, P.export("perm"))
     Lo, _ = F.factor(v[3].cpu().numpy())
     ld = P.factorize(v).logdet().cpu().numpy()[3]

@@ -56,7 +56,7 @@ def test_noalloc_matches_workspace_factorize_twice():
 def test_noalloc_rejects_oversized_batch_and_unuploaded_plan():
     n = 100_000
     Ap, Ai, Ax = I.tridiag(n, 0)
-    P = Plan(n, Ap, Ai, nb=8, ordering="natural")
+    P = Plan(n, Ap, Ai, nb=8, ordering="natural", route="semisparse")
     ntiles = P.info["ntiles"]
     too_big = (L.STC_NOALLOC_SCRATCH_BYTES - 64) // (4 * ntiles) + 1
     v = torch.zeros(1, P.nnzA, dtype=torch.float64, device="cuda")
