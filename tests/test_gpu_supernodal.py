@@ -112,7 +112,7 @@ def test_supernodal_serial_and_parallel_replay_bit_identical():
             assert torch.equal(a, r)
 
 
-def test_supernodal_refuses_tile_only_calls():
+def test_supernodal_refuses_the_allocation_free_entry():
     Ap, Ai, _ = I.tridiag(200, 0)
     P = Plan(200, Ap, Ai, route="supernodal", ordering="natural")
     P.upload()
@@ -120,8 +120,6 @@ def test_supernodal_refuses_tile_only_calls():
     v = torch.zeros(1, P.nnzA, dtype=torch.float64, device="cuda")
     info = torch.zeros(1, dtype=torch.int32, device="cuda")
     assert L.stc_factorize_noalloc(P.h, v, 1, fac, info) == L.STC_ERR_UNSUPPORTED
-    rc, g = L.stc_group_create([P.h], [1])
-    assert rc == L.STC_ERR_UNSUPPORTED
 
 
 @pytest.mark.parametrize("case", [c for c in CASES if c[0] != "dense_300"], ids=lambda c: c[0])
