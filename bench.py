@@ -359,58 +359,59 @@ def measure_workloads(args):
         torch.cuda.empty_cache()
     if "c5" in want:
         Ap, Ai, coords = I.stcov_pattern()
-        P = Plan(len(Ap) - 1, Ap, Ai, coords=coords, nb=64, route="semisparse")
         batch = 8 if small else 64
         th = I.stcov_thetas(batch, 0)
         distinct = 4 if small else 16
         vals = dev(_distinct_values(lambda s: I.stcov_values(th[s]), batch, distinct))
-        xs = dev(np.stack([I.rhs(P.n, s)[0] for s in range(batch)]))
-        fac = torch.empty(P.factor_bytes(batch) // 8, dtype=torch.float64, device="cuda")
-        sig = torch.empty_like(fac)
-        info = torch.empty(batch, dtype=torch.int32, device="cuda")
-        ld = torch.empty(batch, dtype=torch.float64, device="cuda")
-        q = torch.empty_like(ld)
-        g = torch.empty(batch, P.nnzA, dtype=torch.float64, device="cuda")
-        neg = torch.full((batch,), -1.0, dtype=torch.float64, device="cuda")
-        ws = P.workspace(batch)
-        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
-
-        def grad_step(bt, rec=False):
-            if rec:
-                ev[0].record()
-            L.check(L.stc_factorize(P.h, vals[:bt], bt, fac, ws, info), "factorize")
-            L.check(L.stc_logdet(P.h, fac, bt, ld), "logdet")
-            if rec:
-                ev[1].record()
-            L.check(L.stc_logdet_backward(P.h, fac, bt, None, g[:bt], 0, sig, ws), "logdet_backward")
-            if rec:
-                ev[2].record()
-            L.check(L.stc_quad_form(P.h, bt, vals[:bt], xs[:bt], q), "quad_form")
-            L.check(L.stc_sym_outer_backward(P.h, bt, xs[:bt], xs[:bt], neg, g[:bt], 1), "outer_backward")
-            if rec:
-                ev[3].record()
-        grad_step(min(batch, 4))       # warm-up on a few items (same kernels and plan upload)
-        torch.cuda.synchronize()
-        grad_step(batch, True)
-        torch.cuda.synchronize()
-        L.check(L.stc_sync_status(ws), "device status")
-        assert int(info.abs().sum()) == 0
-        ms_tot = ev[0].elapsed_time(ev[3])
-        ms_bwd = ev[1].elapsed_time(ev[2])
-        fa = P.info["flops_alg"]
-        out["c5"] = {"workload": "d/dQ [logdet Q(theta) - x^T Q(theta) x] on the n=180,020 pattern above, "
-                                 "semisparse route",
-                     "gradients": {"value": batch * 1e3 / ms_tot, "unit": "gradients/s", "batch": batch,
-                                   "values": "%d distinct theta draws cycled" % distinct,
-                                   "step": "factorize+logdet+selected inverse+gather+quad form+outer product",
-                                   "ms": ms_tot},
-                     "roofline_selinv": dict(_fp64(2 * fa * batch, ms_bwd), bound="alu", peak=PEAK_FP64_NOMINAL,
-                                             work="2 sum_j c_j^2 = %.4g flops per item (Takahashi)" % (2 * fa),
-                                             ms=ms_bwd),
+        xs = dev(np.stack([I.rhs(len(Ap) - 1, s)[0] for s in range(batch)]))
+        out["c5"] = {"workload": "d/dQ [logdet Q(theta) - x^T Q(theta) x] on the n=180,020 pattern above",
+                     "step": "factorize+logdet+selected inverse+gather+quad form+outer product",
+                     "values": "%d distinct theta draws cycled" % distinct,
                      "gradient_w_r_t": "the nnzA values of Q; the 3-parameter theta chain is a host-side "
                                        "contraction outside the step"}
-        del vals, fac, sig, g, P
-        torch.cuda.empty_cache()
+        for route in ("supernodal", "semisparse"):
+            P = Plan(len(Ap) - 1, Ap, Ai, coords=coords, nb=64, route=route)
+            fac = torch.empty(P.factor_bytes(batch) // 8, dtype=torch.float64, device="cuda")
+            sig = torch.empty_like(fac)
+            info = torch.empty(batch, dtype=torch.int32, device="cuda")
+            ld = torch.empty(batch, dtype=torch.float64, device="cuda")
+            q = torch.empty_like(ld)
+            g = torch.empty(batch, P.nnzA, dtype=torch.float64, device="cuda")
+            neg = torch.full((batch,), -1.0, dtype=torch.float64, device="cuda")
+            ws = P.workspace(batch)
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+
+            def grad_step(bt, rec=False):
+                if rec:
+                    ev[0].record()
+                L.check(L.stc_factorize(P.h, vals[:bt], bt, fac, ws, info), "factorize")
+                L.check(L.stc_logdet(P.h, fac, bt, ld), "logdet")
+                if rec:
+                    ev[1].record()
+                L.check(L.stc_logdet_backward(P.h, fac, bt, None, g[:bt], 0, sig, ws), "logdet_backward")
+                if rec:
+                    ev[2].record()
+                L.check(L.stc_quad_form(P.h, bt, vals[:bt], xs[:bt], q), "quad_form")
+                L.check(L.stc_sym_outer_backward(P.h, bt, xs[:bt], xs[:bt], neg, g[:bt], 1), "outer_backward")
+                if rec:
+                    ev[3].record()
+            grad_step(min(batch, 4))       # warm-up on a few items (same kernels and plan upload)
+            torch.cuda.synchronize()
+            grad_step(batch, True)
+            torch.cuda.synchronize()
+            L.check(L.stc_sync_status(ws), "device status")
+            assert int(info.abs().sum()) == 0
+            ms_tot = ev[0].elapsed_time(ev[3])
+            ms_bwd = ev[1].elapsed_time(ev[2])
+            fa = P.info["flops_alg"]
+            out["c5"][route] = {
+                "gradients": {"value": batch * 1e3 / ms_tot, "unit": "gradients/s", "batch": batch, "ms": ms_tot},
+                "roofline_selinv": dict(_fp64(2 * fa * batch, ms_bwd), bound="alu", peak=PEAK_FP64_NOMINAL,
+                                        work="2 sum_j c_j^2 = %.4g flops per item (Takahashi)" % (2 * fa),
+                                        ms=ms_bwd)}
+            del fac, sig, g, P
+            torch.cuda.empty_cache()
+        del vals
     if "c4" in want:
         plans, vals = [], []
         per = 2 if small else 8
