@@ -136,6 +136,8 @@ struct DevPlanArrays {          // device pointers of one plan's metadata
     int64_t* value_map = nullptr;
     int64_t* pad_diag = nullptr;   // offsets set to 1.0 (padding of the ragged tile)
     int64_t* csc_map = nullptr;    // nnzL: offset of each structural L entry
+    int32_t* fill_src = nullptr;   // per factor double: the A entry stored there, -1 (zero)
+                                   // or -2 (padding diagonal, 1.0)
     int32_t* perm = nullptr;
     int32_t* srow_beg = nullptr;   // solve: per block row, tiles (k,n) n<k: [beg,end)
     int32_t* srow_tiles = nullptr;
@@ -281,6 +283,7 @@ struct SnDev {
     int32_t* row_cells = nullptr;
     int64_t* value_map = nullptr;
     int64_t* csc_map = nullptr;
+    int32_t* fill_src = nullptr;    // per arena double: the A entry stored there or -1
     SnSTask* stasks = nullptr;
     SnSCon* scons = nullptr;
     int32_t* rows = nullptr;        // the supernodes' row lists (permuted indices)

@@ -964,20 +964,22 @@ __global__ void __launch_bounds__(kThreads, 2) replay_kernel_t(const __grid_cons
 }
 
 // ---------------------------------------------------------------------------
-// a1: value scatter.  factor[b][map[e]] = values[b][e]; padding diagonal = 1.
-// ---------------------------------------------------------------------------
-__global__ void scatter_kernel(const double* __restrict__ vals, long long nnz, long long batch,
-                               const int64_t* __restrict__ map, double* __restrict__ F,
-                               long long fstride, const int64_t* __restrict__ pad, int npad) {
+// a1: value scatter, in gather form: every double of every item's factor written once, in order:
+// F[b][f] = values[b][src[f]] (src >= 0), 1 (src == -2, padding diagonal) or 0.  Replaces
+// the zero-fill plus scattered writes by one coalesced pass over the factor; the source
+// map is read once for the whole batch.
+__global__ void fill_kernel(const double* __restrict__ vals, long long nnz, long long batch,
+                            const int32_t* __restrict__ src, double* __restrict__ F, long long fstride) {
     const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long e = tid; e < nnz; e += stride) {
-        const int64_t m = __ldg(map + e);
-        for (long long b = 0; b < batch; ++b) F[b * fstride + m] = __ldcs(vals + b * nnz + e);
-    }
-    for (long long i = tid; i < (long long)npad * batch; i += stride) {
-        const long long b = i / npad;
-        F[b * fstride + pad[i % npad]] = 1.0;
+    for (long long f = tid; f < fstride; f += stride) {
+        const int e = __ldg(src + f);
+        const double c = e == -2 ? 1.0 : 0.0;
+        if (e >= 0) {
+            for (long long b = 0; b < batch; ++b) __stcs(F + b * fstride + f, __ldcs(vals + b * nnz + e));
+        } else {
+            for (long long b = 0; b < batch; ++b) __stcs(F + b * fstride + f, c);
+        }
     }
 }
 
@@ -2377,7 +2379,7 @@ int upload(T** dst, const std::vector<T>& src) {
 
 void free_dev(stc_plan* P) {
     DevPlanArrays& d = P->dev;
-    void* ptrs[] = {d.saind, d.cext, d.value_map, d.pad_diag, d.csc_map, d.perm, d.srow_beg,
+    void* ptrs[] = {d.saind, d.cext, d.value_map, d.pad_diag, d.csc_map, d.fill_src, d.perm, d.srow_beg,
                     d.srow_tiles, d.scol_beg, d.diag_tile, d.sinv, d.stasks, d.scons, d.vdiag,
                     d.arow, d.acol};
     for (void* p : ptrs)
@@ -2385,7 +2387,7 @@ void free_dev(stc_plan* P) {
     d = DevPlanArrays{};
     SnDev& q = P->sndev;
     void* sptrs[] = {q.cells, q.tasks, q.upds, q.maps, q.first, q.cell_cmap, q.cptr, q.rptr_cells, q.row_cells,
-                     q.value_map, q.csc_map, q.stasks, q.scons, q.rows, q.cell_rowoff};
+                     q.value_map, q.csc_map, q.fill_src, q.stasks, q.scons, q.rows, q.cell_rowoff};
     for (void* p : sptrs)
         if (p) cudaFree(p);
     q = SnDev{};
@@ -2447,6 +2449,12 @@ int ensure_plan_impl(stc_plan* P, int dev) {
     if ((rc = upload(&d.cext, P->cext))) return rc;
     if ((rc = upload(&d.value_map, P->value_map))) return rc;
     if ((rc = upload(&d.pad_diag, P->pad_diag))) return rc;
+    {
+        std::vector<int32_t> src((size_t)P->factor_doubles, -1);
+        for (int64_t e = 0; e < P->nnzA; ++e) src[P->value_map[e]] = (int32_t)e;
+        for (int64_t f : P->pad_diag) src[f] = -2;
+        if ((rc = upload(&d.fill_src, src))) return rc;
+    }
     if ((rc = upload(&d.csc_map, P->csc_map))) return rc;
     if ((rc = upload(&d.perm, perm32))) return rc;
     if ((rc = upload(&d.srow_beg, P->rowstart))) return rc;
@@ -2507,6 +2515,11 @@ int ensure_sn_impl(stc_plan* P, int dev) {
     if ((rc = upload(&d.row_cells, rc_list))) return rc;
     if ((rc = upload(&d.value_map, S.value_map))) return rc;
     if ((rc = upload(&d.csc_map, S.csc_map))) return rc;
+    {
+        std::vector<int32_t> src((size_t)S.item_doubles(), -1);
+        for (int64_t e = 0; e < P->nnzA; ++e) src[S.value_map[e]] = (int32_t)e;
+        if ((rc = upload(&d.fill_src, src))) return rc;
+    }
     std::vector<SnSCon> scons = S.scons;
     if (scons.empty()) scons.push_back(SnSCon{});
     if ((rc = upload(&d.stasks, S.stasks))) return rc;
@@ -2769,14 +2782,10 @@ extern "C" int stc_scatter_values(const stc_plan* Pc, const double* d_values, in
     if ((rc = ensure_plan(P, dev))) return rc;
     if (is_sn(P) && (rc = ensure_sn(P, dev))) return rc;
     cudaStream_t st = S(stream);
-    if (cudaMemsetAsync(d_factor, 0, stc_factor_bytes(P, batch), st) != cudaSuccess) return STC_ERR_CUDA;
-    const int blocks = std::max(1, std::min<int>(sms * 8, (int)((P->nnzA + 255) / 256)));
-    if (is_sn(P))  // the supernodal arena has no padding
-        scatter_kernel<<<blocks, 256, 0, st>>>(d_values, P->nnzA, batch, P->sndev.value_map, (double*)d_factor,
-                                               P->item_doubles(), nullptr, 0);
-    else
-        scatter_kernel<<<blocks, 256, 0, st>>>(d_values, P->nnzA, batch, P->dev.value_map, (double*)d_factor,
-                                               P->factor_doubles, P->dev.pad_diag, (int)P->pad_diag.size());
+    const long long fd = P->item_doubles();
+    const int blocks = (int)std::max<long long>(1, std::min<long long>((long long)sms * 16, (fd + 255) / 256));
+    fill_kernel<<<blocks, 256, 0, st>>>(d_values, P->nnzA, batch, is_sn(P) ? P->sndev.fill_src : P->dev.fill_src,
+                                        (double*)d_factor, fd);
     return cudaGetLastError() == cudaSuccess ? STC_OK : STC_ERR_CUDA;
 }
 
