@@ -69,6 +69,9 @@ def parse():
                    help="other workloads measured after the headline, comma list or 'none'")
     p.add_argument("--small-workloads", action="store_true",
                    help="the other workloads at reduced batch sizes (a quick check, not the configured sizes)")
+    p.add_argument("--c3-grid", default="60,60,50",
+                   help="grid nx,ny,nt of the spatio-temporal workloads (configs 3 and 5); a smaller one "
+                        "is for profiling captures only")
     return p.parse_args()
 
 
@@ -320,15 +323,16 @@ def measure_workloads(args):
                                 "plain": {"value": 1e3 / ms_p, "unit": UNIT, "us_per_call": 1e3 * ms_p},
                                 "batched": {"value": batch * 1e3 / ms_b, "unit": UNIT, "batch": batch}}
         del vals
+    gx, gy, gt = (int(v) for v in args.c3_grid.split(","))
     if "c3" in want:
-        Ap, Ai, coords = I.stcov_pattern()
+        Ap, Ai, coords = I.stcov_pattern(gx, gy, gt)
         n = len(Ap) - 1
         batch = 16 if small else 256
         th = I.stcov_thetas(batch, 0)
         distinct = 4 if small else 16
-        vals = dev(_distinct_values(lambda s: I.stcov_values(th[s]), batch, distinct))
-        out["c3"] = {"workload": "tau AR1(rho) x SPDE 9-point 60x60, 50 steps, + 20 border rows, n=180,020, "
-                                 "ND; factor+logdet", "values": "%d distinct theta draws cycled" % distinct}
+        vals = dev(_distinct_values(lambda s: I.stcov_values(th[s], gx, gy, gt), batch, distinct))
+        out["c3"] = {"workload": "tau AR1(rho) x SPDE 9-point %dx%d, %d steps, + 20 border rows, n=%d, "
+                                 "ND; factor+logdet" % (gx, gy, gt, n), "values": "%d distinct theta draws cycled" % distinct}
         # the supernodal route (the selector's choice) holds all 256 theta sets in one launch
         P = Plan(n, Ap, Ai, coords=coords, nb=64, route="supernodal")
         ms_b, ms_f, ms_p = plain_and_batched(P, vals, 1, 2, False)
@@ -358,13 +362,14 @@ def measure_workloads(args):
         del vals, P
         torch.cuda.empty_cache()
     if "c5" in want:
-        Ap, Ai, coords = I.stcov_pattern()
+        Ap, Ai, coords = I.stcov_pattern(gx, gy, gt)
         batch = 8 if small else 64
         th = I.stcov_thetas(batch, 0)
         distinct = 4 if small else 16
-        vals = dev(_distinct_values(lambda s: I.stcov_values(th[s]), batch, distinct))
+        vals = dev(_distinct_values(lambda s: I.stcov_values(th[s], gx, gy, gt), batch, distinct))
         xs = dev(np.stack([I.rhs(len(Ap) - 1, s)[0] for s in range(batch)]))
-        out["c5"] = {"workload": "d/dQ [logdet Q(theta) - x^T Q(theta) x] on the n=180,020 pattern above",
+        out["c5"] = {"workload": "d/dQ [logdet Q(theta) - x^T Q(theta) x] on the spatio-temporal pattern of config 3 "
+                                 "(%dx%dx%d + 20 border rows)" % (gx, gy, gt),
                      "step": "factorize+logdet+selected inverse+gather+quad form+outer product",
                      "values": "%d distinct theta draws cycled" % distinct,
                      "gradient_w_r_t": "the nnzA values of Q; the 3-parameter theta chain is a host-side "
