@@ -66,7 +66,8 @@ def parse():
     p.add_argument("--row-slices", type=int, default=0,
                    help="row slices per off-diagonal tile (0: the library's choice)")
     p.add_argument("--workloads", default="c1,c3,c4,c5",
-                   help="other workloads measured after the headline, comma list or 'none'")
+                   help="other workloads measured after the headline, comma list or 'none' "
+                        "('forced': the selector's route against every forced route)")
     p.add_argument("--small-workloads", action="store_true",
                    help="the other workloads at reduced batch sizes (a quick check, not the configured sizes)")
     p.add_argument("--c3-grid", default="60,60,50",
@@ -458,6 +459,46 @@ def measure_workloads(args):
                                            "ms": ms_g, **_fp64(fl, ms_g),
                                            "tile_tflops": ft / (ms_g * 1e-3) / 1e12}}
         del G, vals
+    if "forced" in want:
+        # the selector's choice against each forced route (Table 4's comparison on the
+        # synthetic classes): factorize (scatter + task-DAG kernel), best of 3 after a warm-up
+        cases = []
+        Ap, Ai, _, coords = I.laplace2d_bordered(seed=0)
+        cases.append(("config 1, 64 copies", Ap, Ai, coords, 64,
+                      np.stack([I.laplace2d_bordered(seed=s % 16)[2] for s in range(64)])))
+        Ap, Ai = I.band_pattern(N, BW)
+        cases.append(("config 2, 8 value sets", Ap, Ai, None, 128,
+                      np.stack([I.band_values(N, BW, s, Ap, Ai) for s in range(8)])))
+        Ap, Ai, coords = I.stcov_pattern(gx, gy, gt)
+        th = I.stcov_thetas(4, 0)
+        cases.append(("config 3, 4 theta sets", Ap, Ai, coords, 64,
+                      np.stack([I.stcov_values(t, gx, gy, gt) for t in th])))
+        Ap, Ai, Ax, coords = I.fem3d(64, 64, 64, seed=0)
+        cases.append(("config 4 64^3, 1 value set", Ap, Ai, coords, 64, Ax[None]))
+        out["forced"] = {"note": "factorize (scatter + task-DAG kernel) per route, best of 3 after a warm-up; "
+                                 "ms per launch"}
+        for name, Ap, Ai, coords, nb, vals in cases:
+            v = dev(vals)
+            row = {}
+            for route in ("auto", "semisparse", "dense", "supernodal"):
+                P = Plan(len(Ap) - 1, Ap, Ai, coords=coords, nb=nb, route=route,
+                         ordering="natural" if coords is None else "auto")
+                bt = vals.shape[0]
+                fac = torch.empty(P.factor_bytes(bt) // 8, dtype=torch.float64, device="cuda")
+                info = torch.empty(bt, dtype=torch.int32, device="cuda")
+                ws = P.workspace(bt)
+                run = lambda: L.check(L.stc_factorize(P.h, v, bt, fac, ws, info), "factorize")
+                run()
+                torch.cuda.synchronize()
+                best = min(_events_ms(run, 1, 0) for _ in range(3))
+                L.check(L.stc_sync_status(ws), "device status")
+                row[route] = {"ms": best, "route_executed": P.route, "factor_GB": P.factor_bytes(bt) / 1e9}
+                if route == "auto":
+                    row["selected"] = P.route_selected
+                del fac, P
+                torch.cuda.empty_cache()
+            out["forced"][name] = row
+            del v
     torch.cuda.empty_cache()
     return out
 
