@@ -1156,8 +1156,10 @@ struct DiagView {
 // memory, panels of 32.  Inside a panel warp 0 solves with the unit triangle
 // M = L diag(L)^{-1} of the panel's 32 x 32 diagonal block, prepared in Mp by
 // prepare_panels (so a step of the dependency chain is one shuffle and one FMA); the
-// rows below (forward) or columns above (backward) are then updated by one thread each
-// with the true L.
+// panel's final entries are stored to ypub and published (one count on *done per panel,
+// in the order the panels are solved: first to last forward, last to first backward);
+// the rows below (forward) or columns above (backward) are then updated by one thread
+// each with the true L.
 // Strict lower part of M = L diag(L)^{-1} on the 32 x 32 diagonal block of every panel,
 // panel q at Mp + q kMpStride, entry (i, l) at i + 33 l (zero elsewhere), and 1 / L_jj in
 // dinv: off the dependency chain of the solve (it needs only the diagonal tile).
@@ -1174,7 +1176,8 @@ __device__ void prepare_panels(double* Mp, double* dinv, const DiagView& L, int 
 }
 
 template <bool BACK>
-__device__ void diag_solve_tile(double* v, const DiagView& L, int nb, const double* dinv, const double* Mp) {
+__device__ void diag_solve_tile(double* v, const DiagView& L, int nb, const double* dinv, const double* Mp,
+                                double* ypub, int* done) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int np = (nb + 31) / 32;
     if (BACK) {
@@ -1202,7 +1205,15 @@ __device__ void diag_solve_tile(double* v, const DiagView& L, int nb, const doub
                     if (BACK ? lane < j : lane > j) vi = fma(-Lr[j], wj, vi);
                 }
             }
-            if (lane < pw) v[p + lane] = BACK ? vi : vi * dinv[p + lane];
+            // the panel's entries are final: store and publish them (one count per panel)
+            const double val = BACK ? vi : vi * dinv[p + lane];
+            if (lane < pw) {
+                v[p + lane] = val;
+                __stcg(ypub + p + lane, val);
+            }
+            __threadfence();
+            __syncwarp();
+            if (lane == 0) red_release_add(done, 1);
         }
         __syncthreads();
         if (!BACK) {
@@ -1247,6 +1258,8 @@ __global__ void __launch_bounds__(kThreads, 1) solve_kernel(SolveArgs a) {
     __shared__ int s_ok;
     const long long total = 2LL * a.nt * a.chains;
     const int nb = a.nb, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int np = (nb + 31) / 32;                 // panels of a block: its completion count
+    __shared__ int s_pb[kNbMax / 32 + 1];          // stored-column start of each panel (forward)
     if (threadIdx.x == 0) {
         mbar_init(&bar);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -1281,9 +1294,10 @@ __global__ void __launch_bounds__(kThreads, 1) solve_kernel(SolveArgs a) {
                 for (unsigned o = 0; o < bytes; o += 32768u)
                     tma_load_1d((char*)Dsm + o, (const char*)(F + D.off) + o, min(32768u, bytes - o), &bar);
             }
-            if (s_ok && !fwd) s_ok = wait_counter(done + k, 1, a.spin, &a.hdr->status);
+            if (s_ok && !fwd) s_ok = wait_counter(done + k, np, a.spin, &a.hdr->status);
         }
         __syncthreads();
+        bool solved = false;
         if (s_ok) {
             for (int i = threadIdx.x; i < kSolveWarps * nb; i += kThreads) acc[i] = 0.0;
             if (!band)
@@ -1311,47 +1325,67 @@ __global__ void __launch_bounds__(kThreads, 1) solve_kernel(SolveArgs a) {
             prepare_panels(Mp, sdinv, Lv, nb);
             __syncthreads();
             if (fwd) {
-                // acc -= L_kn y_n over the off-diagonal tiles of block row k (oldest n first):
-                // y_n's stored-column entries go to shared memory, then each thread owns one
-                // row and a residue class of columns, with four independent accumulators; the
-                // tile's entries are loaded to registers before the wait for y_n
+                // acc -= L_kn y_n over the off-diagonal tiles of block row k (oldest n first),
+                // 32 columns of y_n at a time as y_n's panels are published: each thread owns
+                // one row and, in every panel, a residue class of the tile's stored columns
+                // (s_pb: the stored-column range of each panel), with four accumulators; the
+                // tile's entries are loaded to registers before the first wait
                 const int G = min(kThreads / nb, kSolveWarps), gr = threadIdx.x % nb, gq = threadIdx.x / nb;
+                constexpr int kPer = kSolvePre / 4;  // stored columns per thread and panel
                 for (int q = a.rowstart[k]; q < a.rowstart[k + 1]; ++q) {
                     const DTile T = a.tiles[a.rowtiles[q]];
                     const bool act = gq < G && gr >= T.r0 && gr < T.r1;
+                    if (threadIdx.x <= np) s_pb[threadIdx.x] = T.sw;
+                    __syncthreads();
+                    for (int c = threadIdx.x; c < T.sw; c += kThreads) {
+                        const int qc = logical_col(T, a.saind, c) >> 5;
+                        const int qp = c > 0 ? logical_col(T, a.saind, c - 1) >> 5 : -1;
+                        for (int z = qp + 1; z <= qc; ++z) s_pb[z] = c;
+                    }
+                    __syncthreads();
                     const double* base = F + T.off + gr;
-                    double pre[kSolvePre];
+                    double pre[4][kPer];
 #pragma unroll
-                    for (int i = 0; i < kSolvePre; ++i) {
-                        const int c = gq + i * G;
-                        pre[i] = (act && c < T.sw) ? __ldcg(base + (size_t)c * nb) : 0.0;
-                    }
-                    if (threadIdx.x == 0) s_ok = wait_counter(done + T.J, 1, a.spin, &a.hdr->status);
-                    __syncthreads();
-                    if (!s_ok) break;
-                    const double* yn = y + (long long)T.J * nb;
-                    for (int c = threadIdx.x; c < T.sw; c += kThreads) ysm[c] = __ldcg(yn + logical_col(T, a.saind, c));
-                    __syncthreads();
-                    if (act) {
-                        double p0 = 0.0, p1 = 0.0, p2 = 0.0, p3 = 0.0;
+                    for (int z = 0; z < 4; ++z)
 #pragma unroll
-                        for (int i = 0; i < kSolvePre; i += 4) {
-                            const int c = gq + i * G;
-                            if (c < T.sw) p0 = fma(-pre[i], ysm[c], p0);
-                            if (c + G < T.sw) p1 = fma(-pre[i + 1], ysm[c + G], p1);
-                            if (c + 2 * G < T.sw) p2 = fma(-pre[i + 2], ysm[c + 2 * G], p2);
-                            if (c + 3 * G < T.sw) p3 = fma(-pre[i + 3], ysm[c + 3 * G], p3);
+                        for (int j = 0; j < kPer; ++j) {
+                            const int c = (z < np ? s_pb[z] : T.sw) + gq + j * G;
+                            pre[z][j] = (act && z < np && c < s_pb[z + 1]) ? __ldcg(base + (size_t)c * nb) : 0.0;
                         }
-                        acc[gq * nb + gr] += (p0 + p1) + (p2 + p3);
+                    const double* yn = y + (long long)T.J * nb;
+                    double p0 = 0.0, p1 = 0.0, p2 = 0.0, p3 = 0.0;
+#pragma unroll
+                    for (int z = 0; z < 4; ++z) {
+                        if (z >= np) break;
+                        const int b0 = s_pb[z], b1 = s_pb[z + 1];
+                        if (b0 >= b1) continue;  // no stored column in this panel of y_n
+                        if (threadIdx.x == 0) s_ok = wait_counter(done + T.J, z + 1, a.spin, &a.hdr->status);
+                        __syncthreads();
+                        if (!s_ok) break;
+                        for (int c = b0 + threadIdx.x; c < b1; c += kThreads) ysm[c] = __ldcg(yn + logical_col(T, a.saind, c));
+                        __syncthreads();
+                        if (act) {
+#pragma unroll
+                            for (int j = 0; j < kPer; j += 4) {
+                                const int c = b0 + gq + j * G;
+                                if (c < b1) p0 = fma(-pre[z][j], ysm[c], p0);
+                                if (c + G < b1) p1 = fma(-pre[z][j + 1], ysm[c + G], p1);
+                                if (c + 2 * G < b1) p2 = fma(-pre[z][j + 2], ysm[c + 2 * G], p2);
+                                if (c + 3 * G < b1) p3 = fma(-pre[z][j + 3], ysm[c + 3 * G], p3);
+                            }
+                        }
                     }
+                    if (!s_ok) break;
+                    if (act) acc[gq * nb + gr] += (p0 + p1) + (p2 + p3);
                     __syncthreads();
                 }
             } else {
                 // acc -= L_mk^T z_m over the tiles below the diagonal in block column k (oldest
-                // m first): each warp owns 16 stored columns (c = 32 g + 4 warp + j), its
-                // lanes stride the rows; the 16 partial sums of a lane are reduced over the
-                // warp by a reduce-scatter butterfly (16 shuffles and adds per lane, after
-                // which lane pair 2v, 2v+1 holds column v's total)
+                // m first), 32 rows of z_m at a time as z_m's panels are published (last panel
+                // first): each warp owns 16 stored columns (c = 32 g + 4 warp + j), lane l the
+                // rows l + 32 i; the 16 partial sums of a lane are reduced over the warp by a
+                // reduce-scatter butterfly (16 shuffles and adds per lane, after which lane
+                // pair 2v, 2v+1 holds column v's total)
                 for (int q = a.colstart[k + 1] - 1; q >= a.colstart[k]; --q) {
                     const DTile T = a.tiles[q];
                     if (T.I == T.J) continue;
@@ -1362,31 +1396,30 @@ __global__ void __launch_bounds__(kThreads, 1) solve_kernel(SolveArgs a) {
                         for (int j = 0; j < 4; ++j)
 #pragma unroll
                             for (int i = 0; i < 4; ++i) {
-                                const int c = 32 * g + warp * 4 + j, r = T.r0 + lane + 32 * i;
-                                pre[g][j][i] = (c < T.sw && r < T.r1) ? __ldcg(F + T.off + (size_t)c * nb + r) : 0.0;
+                                const int c = 32 * g + warp * 4 + j, r = lane + 32 * i;
+                                pre[g][j][i] = (c < T.sw && r >= T.r0 && r < T.r1)
+                                                   ? __ldcg(F + T.off + (size_t)c * nb + r) : 0.0;
                             }
-                    if (threadIdx.x == 0) s_ok = wait_counter(done + a.nt + T.I, 1, a.spin, &a.hdr->status);
-                    __syncthreads();
-                    if (!s_ok) break;
                     const double* zm = y + (long long)T.I * nb;
-                    for (int r = threadIdx.x; r < nb; r += kThreads) ysm[r] = __ldcg(zm + r);
-                    __syncthreads();
-                    double zr[4];
-#pragma unroll
-                    for (int i = 0; i < 4; ++i) {
-                        const int r = T.r0 + lane + 32 * i;
-                        zr[i] = r < T.r1 ? ysm[r] : 0.0;
-                    }
                     double d[16];
 #pragma unroll
-                    for (int g = 0; g < 4; ++g)
+                    for (int v2 = 0; v2 < 16; ++v2) d[v2] = 0.0;
 #pragma unroll
-                        for (int j = 0; j < 4; ++j) {
-                            double s = 0.0;
+                    for (int ii = 0; ii < 4; ++ii) {
+                        const int i = 3 - ii;
+                        // rows [32 i, 32 i + 32) of z_m: published once np - i panels are
+                        if (i >= np || 32 * i >= T.r1 || 32 * i + 32 <= T.r0) continue;
+                        if (threadIdx.x == 0) s_ok = wait_counter(done + a.nt + T.I, np - i, a.spin, &a.hdr->status);
+                        __syncthreads();
+                        if (!s_ok) break;
+                        const int r = lane + 32 * i;
+                        const double zr = (r >= T.r0 && r < T.r1) ? __ldcg(zm + r) : 0.0;
 #pragma unroll
-                            for (int i = 0; i < 4; ++i) s = fma(pre[g][j][i], zr[i], s);
-                            d[4 * g + j] = s;
-                        }
+                        for (int g = 0; g < 4; ++g)
+#pragma unroll
+                            for (int j = 0; j < 4; ++j) d[4 * g + j] = fma(pre[g][j][i], zr, d[4 * g + j]);
+                    }
+                    if (!s_ok) break;
 #pragma unroll
                     for (int st = 0; st < 4; ++st) {
                         const int h = 8 >> st, m = 16 >> st;
@@ -1415,17 +1448,21 @@ __global__ void __launch_bounds__(kThreads, 1) solve_kernel(SolveArgs a) {
         }
         __syncthreads();
         if (s_ok) {
-            if (fwd) diag_solve_tile<false>(v, Lv, nb, sdinv, Mp);
-            else diag_solve_tile<true>(v, Lv, nb, sdinv, Mp);
-            for (int i = threadIdx.x; i < nb; i += kThreads) {
-                __stcg(y + (long long)k * nb + i, v[i]);
-                const long long g = (long long)k * nb + i;
-                if (!fwd && g < a.n) a.x[ch * a.n + a.perm[g]] = v[i];
-            }
+            int* dk = done + (fwd ? k : a.nt + k);
+            if (fwd) diag_solve_tile<false>(v, Lv, nb, sdinv, Mp, y + (long long)k * nb, dk);
+            else diag_solve_tile<true>(v, Lv, nb, sdinv, Mp, y + (long long)k * nb, dk);
+            solved = true;
+            if (!fwd)
+                for (int i = threadIdx.x; i < nb; i += kThreads) {
+                    const long long g = (long long)k * nb + i;
+                    if (g < a.n) a.x[ch * a.n + a.perm[g]] = v[i];
+                }
         }
+        // a step that did not solve (a failed wait) still completes its count, so that
+        // no later wait depends on it
         __threadfence();
         __syncthreads();
-        if (threadIdx.x == 0) red_release_add(done + (fwd ? k : a.nt + k), 1);
+        if (threadIdx.x == 0 && !solved) red_release_add(done + (fwd ? k : a.nt + k), np);
     }
 }
 
