@@ -2,7 +2,7 @@
 
 Degenerate sizes and structures (n = 1, n < n_b: a single ragged tile, n a multiple of
 n_b, a diagonal matrix, a dense matrix, an arrowhead with its dense rows last,
-disconnected blocks) on both tile routes, with the tolerances of test_gpu_factor.py.
+disconnected blocks) on the three routes, with the tolerances of test_gpu_factor.py.
 
 Race check: the persistent kernels walk a topological task queue, so one CTA executing
 it in queue order (replay_ctas = 1) is a schedule with no concurrency at all.  Every
@@ -47,7 +47,7 @@ def _edge_cases():
 EDGES = list(_edge_cases())
 
 
-@pytest.mark.parametrize("route", ["semisparse", "dense"])
+@pytest.mark.parametrize("route", ["semisparse", "dense", "supernodal"])
 @pytest.mark.parametrize("nb", [8, 32])
 @pytest.mark.parametrize("case", EDGES, ids=lambda c: c[0])
 def test_edge_case_parity(case, nb, route):
@@ -101,3 +101,13 @@ def test_parallel_replay_matches_serial_bit_for_bit(case):
     for ctas in (0, 3 * 152):
         for what, a, r in zip(("factor", "logdet", "solve", "selected inverse"), out[ctas], ref):
             assert torch.equal(a, r), "%s: %s differs from the serial replay (grid %d)" % (name, what, ctas)
+
+
+@pytest.mark.parametrize("case", EDGES, ids=lambda c: c[0])
+def test_edge_case_selected_inverse(case):
+    # Sigma and d logdet / d a on the degenerate cases, both layouts
+    from test_gpu_adjoint import _selinv_case
+    name, Ap, Ai, Ax = case
+    n = len(Ap) - 1
+    for route in ("semisparse", "supernodal"):
+        _selinv_case(Plan(n, Ap, Ai, nb=8, route=route, ordering="natural"), Ap, Ai, Ax[None])
