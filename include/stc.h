@@ -224,10 +224,11 @@ int stc_plan_export(const stc_plan* plan, int what, void* buf, size_t* bytes);
  * so that host-side checks can execute it.  Every entry is widened to int64.  The set is
  * built on first request, as on the first factorization that uses it. */
 #define STC_TASKSET_TASKS 0     /* [ntasks][12] in queue order: kind (0 DIAG = SYRKs + POTRF,
-                                   1 OFF = GEMMs + TRSM of a row slice, 2 SYRK row slice,
-                                   3 POTRF), output tile, diagonal tile, update range
-                                   [ubeg, uend), row slice [rs0, rs1), TRSM rows [tr0, tr1),
-                                   POTRF's wait count, slice index, slice height          */
+                                   1 OFF = GEMMs + TRSM of a row slice, 2 SYRK = SYRKs into
+                                   a row slice of (k,k) + the factorization of its rows),
+                                   output tile, diagonal tile, update range [ubeg, uend),
+                                   row slice [rs0, rs1), TRSM rows [tr0, tr1), 0, slice
+                                   index, slice height of the off-diagonal tiles           */
 #define STC_TASKSET_UPDS 1      /* [nupds][10]: a, b (operand tiles), kmap (pair offset in
                                    the imap, -1 = contiguous inner range), klen, ka0, kb0
                                    (first stored column of a / b when contiguous), ra0, ra1
@@ -238,7 +239,10 @@ int stc_plan_export(const stc_plan* plan, int what, void* buf, size_t* bytes);
                                    diagonal, 2 banded diagonal), stored width, first
                                    logical column if contiguous else -1, offset in the
                                    stored-column list, storage kd, row extent r0, r1,
-                                   completion target, logdet slot, extent-pair offset    */
+                                   completion word once final (off-diagonal: bit
+                                   q*8 + s per TRSM panel q of row slice s; diagonal: bit
+                                   g*4 + s per 16-column group g of row slice s), logdet
+                                   slot, extent-pair offset                              */
 #define STC_TASKSET_SAIND 4     /* stored-column lists of indexed tiles                      */
 #define STC_TASKSET_CEXT 5      /* (lo, hi) row extent per 16 stored columns                 */
 #define STC_TASKSET_CSC_MAP 6   /* [nnzL] factor offset of each structural entry of L        */
@@ -316,7 +320,8 @@ int stc_factorize_scattered(const stc_plan* plan, int64_t batch, void* d_factor,
  * task lists in earliest-start order (up to STC_GROUP_MAX_PLANS plans).  No counterpart
  * in the paper beyond its motivation: INLA factorizes many matrices per fit (Sec. 1, 2),
  * and Algorithm 2's executor takes any ready task, whichever matrix it belongs to.
- * Tile-route plans only (a supernodal plan gives STC_ERR_UNSUPPORTED).
+ * Plans of every executable route mix freely (a group holding a supernodal plan runs the
+ * kernel variant that also executes supernodal tasks).
  *   stc_group_create: host + device set-up (synchronous; uploads the plans and the merged
  *     queue); plans must outlive the group; batch[p] in 1 .. 2^28-1.
  *   stc_factorize_group: d_values[p], d_factor[p], d_info[p] are host arrays of device
@@ -379,7 +384,8 @@ int stc_factor_to_csc(const stc_plan* plan, const void* d_factor, int64_t batch,
  *   d_factor: a factor from stc_factorize; d_sigma: stc_factor_bytes(plan,batch) bytes
  *   (written, same layout as the factor, must not alias it); d_work:
  *   stc_workspace_bytes(plan,batch) bytes or NULL (see above).
- * Tile routes only: a supernodal plan gives STC_ERR_UNSUPPORTED. */
+ * On the supernodal route the same recurrence runs over the supernodes (the task form
+ * of stc_plan_export's SN_SEL_TASKS / SN_SEL_CONS), in the supernodal layout. */
 int stc_selinv(const stc_plan* plan, const void* d_factor, int64_t batch, void* d_sigma,
                void* d_work, void* stream);
 

@@ -715,8 +715,10 @@ stc::TaskSet* stc_plan::taskset(int32_t slices, bool bl_order) {
         }
         return c;
     };
-    // the factored diagonal tile is published kPanel columns at a time (one count each)
-    auto diag_groups = [&](const stc::DTile& D) { return (D.sw + kPanel - 1) / kPanel; };
+    // completion bit of column group g of row slice s of a diagonal tile
+    constexpr int DG = stc::kDiagGroupW;
+    auto dbit = [](int g, int s) { return (int32_t)(1u << (g * stc::kMaxDiagSlices + s)); };
+    const double kSliceSync = 3000.0;  // modelled cost of one more slice of a diagonal tile
     auto potrf_cost = [&](const stc::DTile& D) {
         double w = D.sw, kd = std::min<double>(D.kd, w - 1);
         return (D.kind == stc::TILE_DIAG_BAND) ? w * (kd + 1) * (kd + 1) / 2 : w * w * w / 6;
@@ -735,6 +737,7 @@ stc::TaskSet* stc_plan::taskset(int32_t slices, bool bl_order) {
         const int32_t dk = diag_tile[k];
         const stc::DTile& D = tiles[dk];
         const bool has_syrk = rowstart[k + 1] > rowstart[k];
+        const int G = (D.sw + DG - 1) / DG;  // column groups of the diagonal tile
         if (eff == 1 || !has_syrk) {
             // TASK_DIAG: every SYRK from (k,n), n < k, then POTRF
             stc::DTask t{};
@@ -753,38 +756,66 @@ stc::TaskSet* stc_plan::taskset(int32_t slices, bool bl_order) {
             t.uend = (int32_t)Lk.upds.size();
             t.rs0 = 0; t.rs1 = NB; t.tr0 = 0; t.tr1 = NB;
             mt.fcost = potrf_cost(D);
-            mt.npub = diag_groups(D);
-                        Lk.tasks.push_back(t);
+            mt.npub = G;
+            Lk.tasks.push_back(t);
             Lk.meta.push_back(mt);
-            ts->nfinal[dk] = diag_groups(D);
+            for (int g = 0; g < G; ++g) ts->nfinal[dk] |= dbit(g, 0);
         } else {
-            // TASK_SYRK row slices of (k,k), then TASK_POTRF.  Row r of the lower
-            // triangle costs ~(r+1): slices are cut (on 8-row boundaries, at most 64 rows)
-            // so that each carries about 1/eff of the triangle's work.
-            vector<int> cuts{0};
-            {
-                const double target = double(D.sw) * (D.sw + 1) / 2.0 / eff;
-                double accum = 0.0;
-                int start = 0;
-                for (int r = 0; r < D.sw; ++r) {
-                    accum += r + 1;
-                    const int len = r + 1 - start;
-                    if (r + 1 < D.sw && (len % 8 == 0) && (accum >= target || len >= 64)) {
-                        cuts.push_back(r + 1);
-                        start = r + 1;
-                        accum = 0.0;
-                    }
+            // TASK_SYRK row slices of (k,k): each applies every SYRK into its rows, then
+            // factors them against the columns the earlier slices publish (a row-partitioned
+            // POTRF), so the factorization of (k,k) is spread over the slices' CTAs.  Cuts lie
+            // on kDiagGroupW-row boundaries, slices hold at most 64 rows, and the cut set
+            // minimises the largest slice's modelled work (its SYRK products plus its rows'
+            // share of the POTRF), plus a synchronisation cost per extra slice.
+            vector<double> wb(G, 0.0);
+            for (int b = 0; b < G; ++b) {
+                const int r0 = b * DG, r1 = std::min(D.sw, r0 + DG);
+                for (int32_t a = rowstart[k]; a < rowstart[k + 1]; ++a) {
+                    const stc::DTile& A = tiles[rowtiles[a]];
+                    const int ra = std::max(r0, A.r0), rb = std::min(r1, A.r1);
+                    if (ra >= rb) continue;
+                    stc::DUpd u{};
+                    u.a = rowtiles[a]; u.b = u.a; u.kmap = -1; u.klen = A.sw;
+                    wb[b] += syrk_cost(Lk.imap, u, A.r0, ra, rb);
                 }
-                cuts.push_back(D.sw);
+                for (int r = r0; r < r1; ++r) {
+                    const double m = std::min(r, D.kd);
+                    wb[b] += m * (m + 1) / 2;
+                }
             }
-            int nsl = 0;
-            for (size_t ci = 0; ci + 1 < cuts.size(); ++ci) {
-                const int rs0 = cuts[ci];
-                const int rs1 = cuts[ci + 1];
-                if (rs1 <= rs0) continue;
+            unsigned best_mask = 0;
+            double best = std::numeric_limits<double>::infinity();
+            for (unsigned mask = 0; mask < (1u << std::max(0, G - 1)); ++mask) {
+                // bit b - 1 of mask: a cut before group b
+                int runs = 0, len = 0;
+                double cur = 0.0, worst = 0.0;
+                bool ok = true;
+                for (int b = 0; b < G && ok; ++b) {
+                    if (b > 0 && (mask >> (b - 1) & 1u)) {
+                        worst = std::max(worst, cur);
+                        cur = 0.0;
+                        len = 0;
+                        ++runs;
+                    }
+                    cur += wb[b];
+                    ok = ++len * DG <= 64;
+                }
+                ++runs;
+                worst = std::max(worst, cur);
+                if (!ok || runs > stc::kMaxDiagSlices) continue;
+                const double obj = worst + kSliceSync * (runs - 1);
+                if (obj < best) { best = obj; best_mask = mask; }
+            }
+            vector<int> cuts{0};
+            for (int b = 1; b < G; ++b)
+                if (best_mask >> (b - 1) & 1u) cuts.push_back(b * DG);
+            cuts.push_back(D.sw);
+            const int kd = D.kd;
+            for (size_t s = 0; s + 1 < cuts.size(); ++s) {
+                const int rs0 = cuts[s], rs1 = cuts[s + 1], R = rs1 - rs0;
                 stc::DTask t{};
                 Meta mt;
-                t.kind = stc::TASK_SYRK; t.tile = dk; t.diag = dk;
+                t.kind = stc::TASK_SYRK; t.tile = dk; t.diag = dk; t.slice = (int32_t)s;
                 t.rs0 = rs0; t.rs1 = rs1; t.tr0 = rs0; t.tr1 = rs1;
                 t.ubeg = (int32_t)Lk.upds.size();
                 for (int32_t a = rowstart[k]; a < rowstart[k + 1]; ++a) {
@@ -800,21 +831,39 @@ stc::TaskSet* stc_plan::taskset(int32_t slices, bool bl_order) {
                     mt.ucost.push_back(syrk_cost(Lk.imap, u, A.r0, ra, rb));
                 }
                 t.uend = (int32_t)Lk.upds.size();
-                if (t.uend == t.ubeg) continue;  // rows untouched by any SYRK
-                                Lk.tasks.push_back(t);
+                // the factorization of the rows, as the kernel executes it: per group of the
+                // earlier slices' columns (skipped where it lies outside the band of every
+                // row of the slice) a TRSM of the rows and the rank-kDiagGroupW update of
+                // their later columns; then the POTRF of the slice's own diagonal block
+                double fc = 0.0;
+                int npub = 0;
+                for (int g0 = 0; g0 < rs0; g0 += DG) {
+                    if (g0 + DG <= rs0 - kd) continue;
+                    fc += double(R) * DG * (DG - 1) / 2 + double(R) * (rs0 - g0 - DG) * DG +
+                          double(R) * (R + 1) / 2 * DG;
+                    ts->nfinal[dk] |= dbit(g0 / DG, (int)s);
+                    ++npub;
+                }
+                {
+                    const int64_t kdd = std::min(kd, R - 1);
+                    for (int64_t j = 0; j < R; ++j) {
+                        const double m = double(std::min<int64_t>(kdd, R - 1 - j));
+                        fc += m * (m + 1) / 2 + m;
+                    }
+                }
+                for (int g = rs0 / DG; g < (rs1 + DG - 1) / DG; ++g) {
+                    ts->nfinal[dk] |= dbit(g, (int)s);
+                    ++npub;
+                }
+                mt.fcost = fc;
+                mt.npub = npub;
+                if (s > 0) {  // follows the earlier slices' published groups
+                    mt.final_tile = dk;
+                    mt.trsm = true;
+                }
+                Lk.tasks.push_back(t);
                 Lk.meta.push_back(mt);
-                ++nsl;
             }
-            stc::DTask p{};
-            Meta mp;
-            p.kind = stc::TASK_POTRF; p.tile = dk; p.diag = dk; p.ubeg = p.uend = (int32_t)Lk.upds.size();
-            p.rs0 = 0; p.rs1 = NB; p.tr0 = 0; p.tr1 = NB; p.own_wait = nsl;
-            mp.final_tile = nsl > 0 ? dk : -1;
-            mp.fcost = potrf_cost(D);
-            mp.npub = diag_groups(D);
-                        Lk.tasks.push_back(p);
-            Lk.meta.push_back(mp);
-            ts->nfinal[dk] = nsl + diag_groups(D);
         }
         // OFF(m,k) row slices: GEMM from every n in N(k) & N(m), n < k, then TRSM
         for (int32_t o = colstart[k]; o < colstart[k + 1]; ++o) {
@@ -924,7 +973,7 @@ stc::TaskSet* stc_plan::taskset(int32_t slices, bool bl_order) {
         Lk = Local();
     }
     // Queue order: earliest start on unbounded workers.  Tiles are published in steps
-    // (an off-diagonal slice per TRSM panel, a diagonal tile per kPanel factored
+    // (an off-diagonal slice per TRSM panel, a diagonal tile per kDiagGroupW factored
     // columns), so a consumer can start on a tile's first published part ("avail") and
     // finishes its use of it a fraction of its own work after the tile is final ("fin").
     // A task starts when its first input is available and runs its updates in order;
@@ -974,12 +1023,25 @@ stc::TaskSet* stc_plan::taskset(int32_t slices, bool bl_order) {
         t += kSync;
         fin[i] = t;
         key[i] = std::max(first, kdep + 1e-6);
-        ts->fma += std::accumulate(mt.ucost.begin(), mt.ucost.end(), 0.0) + mt.fcost;
+        {
+            // algorithmic count: a row slice's share of POTRF(k) is sum_r m (m+1) / 2 over its
+            // rows r, m = min(r, kd) (its fcost is what the kernel executes)
+            double fa = mt.fcost;
+            if (tasks[i].kind == stc::TASK_SYRK) {
+                const stc::DTile& Dt = tiles[tasks[i].tile];
+                fa = 0.0;
+                for (int r = tasks[i].rs0; r < tasks[i].rs1; ++r) {
+                    const double m = std::min(r, Dt.kd);
+                    fa += m * (m + 1) / 2;
+                }
+            }
+            ts->fma += std::accumulate(mt.ucost.begin(), mt.ucost.end(), 0.0) + fa;
+        }
         {
             // the POTRF cost of the model is the banded-Cholesky estimate w (kd+1)^2 / 2;
             // the kernel updates, after column j, the min(kd, w-1-j) rows below it
             double fc = mt.fcost;
-            if (tasks[i].kind == stc::TASK_DIAG || tasks[i].kind == stc::TASK_POTRF) {
+            if (tasks[i].kind == stc::TASK_DIAG) {
                 const stc::DTile& Dt = tiles[tasks[i].tile];
                 const int64_t kdd = std::min<int64_t>(Dt.kd, Dt.sw - 1);
                 fc = 0.0;
@@ -1005,8 +1067,10 @@ stc::TaskSet* stc_plan::taskset(int32_t slices, bool bl_order) {
             cost[i] = bl[i] = std::accumulate(meta[i].ucost.begin(), meta[i].ucost.end(), 0.0) + meta[i].fcost + kSync;
         for (size_t ii = T; ii-- > 0;) {
             auto pull = [&](int32_t tile) {
+                // producers built before ii (a row slice of (k,k) reads only the slices
+                // of its own tile that precede it)
                 for (int32_t d : producers[tile])
-                    if ((size_t)d != ii) bl[d] = std::max(bl[d], cost[d] + bl[ii]);
+                    if ((size_t)d < ii) bl[d] = std::max(bl[d], cost[d] + bl[ii]);
             };
             for (int32_t s2 : meta[ii].srcs) pull(s2);
             if (meta[ii].final_tile >= 0) pull(meta[ii].final_tile);

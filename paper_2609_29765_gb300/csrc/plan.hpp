@@ -65,17 +65,26 @@ constexpr int kMaxNb = 128;  // largest tile size n_b
 constexpr int kPanelW = 32;
 // Completion word of an off-diagonal tile: bit q * kMaxSlices + s is set once row slice
 // s has finished TRSM panel q (columns [q kPanelW, (q+1) kPanelW) of its rows are final),
-// so a consumer can wait for exactly the rows and columns it reads.  Diagonal tiles keep
-// a count (SYRK slices, then one per published kPanelW columns).
+// so a consumer can wait for exactly the rows and columns it reads.
 constexpr int kMaxSlices = 8;
 static_assert((kMaxNb / kPanelW) * kMaxSlices <= 32, "completion word holds every (panel, slice) bit");
+// Completion word of a diagonal tile: its rows are factored in up to kMaxDiagSlices row
+// slices (cut on multiples of kDiagGroupW rows); bit g * kMaxDiagSlices + s is set once
+// slice s has made final the columns [g kDiagGroupW, (g+1) kDiagGroupW) of its rows.  The
+// tile's nfinal holds every bit that will be set (a banded tile skips groups that lie
+// wholly outside the band of a slice's rows).
+constexpr int kDiagGroupW = 16;
+constexpr int kMaxDiagSlices = 4;
+static_assert((kMaxNb / kDiagGroupW) * kMaxDiagSlices <= 32, "completion word holds every (group, slice) bit");
 
-enum : int32_t { TASK_DIAG = 0, TASK_OFF = 1, TASK_SYRK = 2, TASK_POTRF = 3 };
+enum : int32_t { TASK_DIAG = 0, TASK_OFF = 1, TASK_SYRK = 2 };
 
 // One device task, the cases of Algorithm 1 grouped by output tile (row slice):
 //   TASK_DIAG  every SYRK into (k,k), then POTRF(k)                 (unsliced)
-//   TASK_SYRK  every SYRK into rows [rs0,rs1) of (k,k)              (row slice)
-//   TASK_POTRF POTRF(k) once `own_wait` SYRK slices have finished
+//   TASK_SYRK  every SYRK into rows [rs0,rs1) of (k,k), then the factorization of those
+//              rows: solved against the columns [0, rs0) that the earlier slices
+//              publish group by group, then the Cholesky factor of the slice's own
+//              diagonal block (a row-partitioned POTRF(k))          (row slice)
 //   TASK_OFF   every GEMM into rows [rs0,rs1) of (m,k), then the TRSM of those rows
 struct DTask {
     int32_t kind;
@@ -84,8 +93,8 @@ struct DTask {
     int32_t ubeg, uend;  // range in the update array
     int32_t rs0, rs1;    // row slice of the output tile
     int32_t tr0, tr1;    // rows of the slice the TRSM touches (slice cut to r-extent)
-    int32_t own_wait;    // TASK_POTRF: completions of (k,k) to wait for
-    int32_t slice;       // TASK_OFF: index of the row slice (rs0 / slice height)
+    int32_t own_wait;    // unused (0)
+    int32_t slice;       // TASK_OFF, TASK_SYRK: index of the row slice in its tile
     int32_t pad;
 };
 

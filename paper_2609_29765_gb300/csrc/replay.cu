@@ -636,10 +636,12 @@ __device__ void potrf_diag8(double* P, int nb, int p, int pw, const double* S, i
 // the staging buffer S for the next step.  Rows more than kd below the diagonal are
 // structurally zero and skipped.  *bad receives the first non-positive pivot column (or
 // -1); *logsum = sum_j log L_jj, one log per diagonal entry reduced in a fixed order.
-// pub(c) is called by every thread (after a barrier) each time columns [c - kPb, c) have
-// become final, for c < w a multiple of kPb.
+// pub(c) is called by every thread (after a barrier) each time columns [c - pubw, c) have
+// become final, for c < w a multiple of pubw (a multiple of 8).  *bad and *logsum are
+// valid in thread 0 only.
 template <class Pub>
-__device__ void potrf_packed(double* P, int nb, int w, int kd, double* S, int* bad, double* logsum, Pub pub) {
+__device__ void potrf_packed(double* P, int nb, int w, int kd, double* S, int* bad, double* logsum, int pubw,
+                             Pub pub) {
     __shared__ PotrfShared<8> sh;
     if (threadIdx.x == 0) sh.bad = -1;
     __syncthreads();
@@ -667,7 +669,7 @@ __device__ void potrf_packed(double* P, int nb, int w, int kd, double* S, int* b
         __syncthreads();
         potrf_rows_below<8>(P, nb, pn, pwn, min(w, pn + pwn + kd), S, sh);
         __syncthreads();
-        if (pn + pwn < w && (pn + pwn) % kPb == 0) pub(pn + pwn);
+        if (pn + pwn < w && (pn + pwn) % pubw == 0) pub(pn + pwn);
     }
     __shared__ double s_red[kThreads / 32];
     double lg = 0.0;
@@ -683,6 +685,130 @@ __device__ void potrf_packed(double* P, int nb, int w, int kd, double* S, int* b
         *logsum = t;
     }
     __syncthreads();
+}
+
+// Completion bits of a diagonal tile: the column groups covering [c0, c1) of row slice s
+// (c0 a multiple of kDiagGroupW), every group of a set of slices, and every slice's bits
+// of the groups [0, g].
+__device__ __forceinline__ unsigned diag_bits(int c0, int c1, int s) {
+    unsigned m = 0u;
+    for (int g = c0 / kDiagGroupW; g * kDiagGroupW < c1; ++g) m |= 1u << (g * kMaxDiagSlices + s);
+    return m;
+}
+__device__ __forceinline__ unsigned slice_bits(unsigned slices) {
+    unsigned m = 0u;
+    for (int g = 0; g < kMaxNb / kDiagGroupW; ++g) m |= slices << (g * kMaxDiagSlices);
+    return m;
+}
+__device__ __forceinline__ unsigned diag_prefix(int g) {
+    const int nbits = (g + 1) * kMaxDiagSlices;
+    return nbits >= 32 ? ~0u : (1u << nbits) - 1u;
+}
+
+// Sum of v over the CTA in a fixed order (per-thread values, then warps, then warp sums).
+__device__ double cta_sum_fixed(double v) {
+    __shared__ double s_part[kThreads / 32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) s_part[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double t = 0.0;
+    for (int q = 0; q < kThreads / 32; ++q) t += s_part[q];
+    __syncthreads();
+    return t;
+}
+
+// Factorization of rows [a0, b0) of a diagonal tile (the second half of TASK_SYRK, after
+// its SYRKs; POTRF(k) of Algorithm 1 partitioned by rows).  C holds the rows,
+// C[(r - a0) + c * kRLd] for columns [0, b0).  Columns [0, a0) belong to the earlier
+// slices: group by group (kDiagGroupW columns) the rows [g0, a0) of L that they published
+// are staged, this slice's rows are solved against the group's diagonal block and
+// published, and the rank-kDiagGroupW update from them is applied to their later columns;
+// a group wholly outside the band of these rows is zero in them and skipped.  The slice's
+// own diagonal block is then factored (potrf_packed) and published group by group.  The
+// last slice writes the tile's logdet partial from every L_jj.  s_ok turns 0 when a wait
+// fails (timeout or an earlier error).
+__device__ void slice_factor(const ReplayArgs& a, const DTask& t, const DTile& O, double* F, int* cnt,
+                             long long item, double* C, double* S0, double* S1, double* sv, int& s_ok) {
+    const int nb = a.nb, a0 = t.rs0, b0 = t.rs1, R = b0 - a0, sl = t.slice;
+    double* T = F + O.off;
+    const unsigned nf = (unsigned)O.nfinal;
+    const unsigned below = (1u << sl) - 1u;  // the slices before this one, in a group's bits
+    for (int g0 = 0; g0 < a0; g0 += kDiagGroupW) {
+        if (g0 + kDiagGroupW <= a0 - O.kd) continue;
+        const int g = g0 / kDiagGroupW;
+        if (threadIdx.x == 0)
+            s_ok = wait_bits(cnt + t.tile, nf & (below << (g * kMaxDiagSlices)), a.spin, &a.hdr->status);
+        __syncthreads();
+        if (!s_ok) return;
+        // rows [g0, a0) of the group's columns into S0 (row r - g0, column c - g0): zero above
+        // the diagonal, outside the band and on the padding rows the products read
+        const int Rs = a0 - g0, Rsp = ((Rs + 3) & ~3) + 4;
+        if (O.kind == TILE_DIAG_BAND) {
+            // consecutive threads along a stored row
+            for (int idx = threadIdx.x; idx < Rsp * kDiagGroupW; idx += kThreads) {
+                const int r = idx / kDiagGroupW, c = idx % kDiagGroupW;
+                S0[r + c * kRStLd] = (r < Rs && r >= c) ? diag_at(T, O, nb, g0 + r, g0 + c) : 0.0;
+            }
+        } else {
+            for_rc(Rsp, kDiagGroupW, [&](int r, int c) {
+                S0[r + c * kRStLd] = (r < Rs && r >= c) ? diag_at(T, O, nb, g0 + r, g0 + c) : 0.0;
+            });
+        }
+        __syncthreads();
+        if (threadIdx.x < kDiagGroupW) sv[threadIdx.x] = 1.0 / S0[threadIdx.x * (kRStLd + 1)];
+        __syncthreads();
+        double* X = C + g0 * kRLd;
+        trsm_rows(X, kRLd, R, kDiagGroupW, S0, kRStLd, sv);
+        __syncthreads();
+        write_diag_rows(T, O, nb, a0, b0, g0, g0 + kDiagGroupW, [&](int r, int c) { return C[(r - a0) + c * kRLd]; });
+        __threadfence();
+        __syncthreads();
+        if (threadIdx.x == 0) red_release_or(cnt + t.tile, 1u << (g * kMaxDiagSlices + sl));
+        // later columns of the rows: [g0 + kDiagGroupW, a0) against the staged rows, the
+        // slice's own triangle [a0, b0) against the rows themselves
+        const int cn = a0 - g0 - kDiagGroupW;
+        if (cn > 0)
+            mma_sub<false>(X + kDiagGroupW * kRLd, kRLd, R, cn, X, kRLd, S0 + kDiagGroupW, kRStLd, kDiagGroupW);
+        mma_sub<true>(C + a0 * kRLd, kRLd, R, R, X, kRLd, X, kRLd, kDiagGroupW);
+        __syncthreads();
+    }
+    // the slice's own diagonal block, as a packed triangle in S0 (R (R+1) / 2 <= kRStage)
+    double* P = S0;
+    for (int idx = threadIdx.x; idx < R * R; idx += kThreads) {
+        const int i = idx % R, j = idx / R;
+        if (i >= j) P[pk(R, i, j)] = C[i + (a0 + j) * kRLd];
+    }
+    __syncthreads();
+    int bad = -1, done = 0;
+    double ls;
+    auto own = [&](int r, int c) { return P[pk(R, r - a0, c - a0)]; };
+    potrf_packed(P, R, R, min(O.kd, R - 1), S1, &bad, &ls, kDiagGroupW, [&](int c1) {
+        write_diag_rows(T, O, nb, a0 + done, b0, a0 + done, a0 + c1, own);
+        __threadfence();
+        __syncthreads();
+        if (threadIdx.x == 0) red_release_or(cnt + t.tile, diag_bits(a0 + done, a0 + c1, sl));
+        done = c1;
+    });
+    write_diag_rows(T, O, nb, a0 + done, b0, a0 + done, b0, own);
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (bad >= 0) record_info(a.info + item, O.J * nb + a0 + bad + 1);
+        red_release_or(cnt + t.tile, diag_bits(a0 + done, b0, sl));
+    }
+    if (b0 == O.sw) {
+        // the last slice: logdet partial of the tile once every earlier slice is final
+        if (threadIdx.x == 0 && sl > 0)
+            s_ok = wait_bits(cnt + t.tile, nf & slice_bits(below), a.spin, &a.hdr->status);
+        __syncthreads();
+        if (!s_ok) return;
+        double lg = 0.0;
+        for (int j = threadIdx.x; j < O.sw; j += kThreads)
+            lg += log(j < a0 ? diag_at(T, O, nb, j, j) : P[pk(R, j - a0, j - a0)]);
+        lg = cta_sum_fixed(lg);
+        if (threadIdx.x == 0) F[a.poff + O.pd_slot] = bad >= 0 ? __longlong_as_double(0x7ff8000000000000LL) : lg;
+    }
 }
 
 // WITH_SN: the launch may hold supernodal jobs (a mixed-route group); their tasks run
@@ -731,12 +857,8 @@ __global__ void __launch_bounds__(kThreads, 2) replay_kernel_t(const __grid_cons
         const DTile O = a.tiles[t.tile];
         if (threadIdx.x == 0) s_ok = (*(volatile int*)&a.hdr->status == STC_OK);
         __syncthreads();
-        if (t.kind == TASK_DIAG || t.kind == TASK_POTRF) {
-            // (fused SYRKs +) POTRF on the whole diagonal tile, held as a packed triangle
-            if (s_ok && t.kind == TASK_POTRF && t.own_wait > 0) {
-                if (threadIdx.x == 0) s_ok = wait_counter(cnt + t.tile, t.own_wait, a.spin, &a.hdr->status);
-                __syncthreads();
-            }
+        if (t.kind == TASK_DIAG) {
+            // SYRKs + POTRF on the whole diagonal tile, held as a packed triangle
             if (s_ok) {
                 load_diag_packed(C, F + O.off, O, nb);
                 __syncthreads();
@@ -765,26 +887,31 @@ __global__ void __launch_bounds__(kThreads, 2) replay_kernel_t(const __grid_cons
                     }
                 }
                 if (s_ok) {
-                    // columns are published kPb at a time as they become final, so the TRSMs
-                    // of this block column can start before the whole tile is factored
+                    // columns are published kDiagGroupW at a time as they become final (one
+                    // slice holds every row), so the TRSMs of this block column can start
+                    // before the whole tile is factored
                     int bad, done = 0;
                     double ls;
-                    potrf_packed(C, nb, O.sw, min(O.kd, nb - 1), S0, &bad, &ls, [&](int c1) {
+                    potrf_packed(C, nb, O.sw, min(O.kd, nb - 1), S0, &bad, &ls, kDiagGroupW, [&](int c1) {
                         store_diag_cols(C, F + O.off, O, nb, done, c1);
-                        done = c1;
                         __threadfence();
                         __syncthreads();
-                        if (threadIdx.x == 0) red_release_add(cnt + t.tile, 1);
+                        if (threadIdx.x == 0) red_release_or(cnt + t.tile, diag_bits(done, c1, 0));
+                        done = c1;
                     });
                     if (threadIdx.x == 0) {
                         if (bad >= 0) record_info(a.info + item, O.J * nb + bad + 1);
                         F[a.poff + O.pd_slot] = bad >= 0 ? __longlong_as_double(0x7ff8000000000000LL) : ls;
                     }
                     store_diag_cols(C, F + O.off, O, nb, done, nb);
+                    __threadfence();
+                    __syncthreads();
+                    if (threadIdx.x == 0) red_release_or(cnt + t.tile, diag_bits(done, O.sw, 0));
                 }
             }
         } else if (t.kind == TASK_SYRK) {
-            // rows [rs0, rs1) of (k,k): every SYRK update, lower part only
+            // rows [rs0, rs1) of (k,k): every SYRK update, lower part only, then their
+            // factorization
             const int R = t.rs1 - t.rs0;
             if (s_ok) {
                 const double* T = F + O.off;
@@ -823,10 +950,7 @@ __global__ void __launch_bounds__(kThreads, 2) replay_kernel_t(const __grid_cons
                         __syncthreads();
                     }
                 }
-                if (s_ok) {
-                    write_diag_rows(F + O.off, O, nb, t.rs0, t.rs1, 0, t.rs1,
-                                    [&](int r, int c) { return C[(r - t.rs0) + c * kRLd]; });
-                }
+                if (s_ok) slice_factor(a, t, O, F, cnt, item, C, S0, S1, sv, s_ok);
             }
         } else {
             const int R = t.rs1 - t.rs0;
@@ -874,10 +998,8 @@ __global__ void __launch_bounds__(kThreads, 2) replay_kernel_t(const __grid_cons
                     }
                 }
                 // TRSM of rows [tr0, tr1) against L_kk restricted to the stored columns
-                // L_kk arrives kPb columns at a time: its counter ends at nfinal and reaches
-                // nfinal - ng + q + 1 once columns [0, (q+1) kPb) are final
+                // L_kk arrives kDiagGroupW columns at a time (per row slice of (k,k))
                 const DTile D = a.tiles[t.diag];
-                const int dbase = D.nfinal - (D.sw + kPb - 1) / kPb;
                 if (s_ok) {
                     // rows of X outside a column group's extent are zero there and stay zero
                     const double* DT = F + D.off;
@@ -886,9 +1008,11 @@ __global__ void __launch_bounds__(kThreads, 2) replay_kernel_t(const __grid_cons
                     // it, so the work left after the last columns of L_kk arrive is small
                     for (int p = 0; p < sw; p += kPb) {
                         const int pw = min(kPb, sw - p);
-                        if (threadIdx.x == 0)
-                            s_ok = wait_counter(cnt + t.diag, dbase + logical_col(O, a.saind, p + pw - 1) / kPb + 1,
-                                                a.spin, &a.hdr->status);
+                        if (threadIdx.x == 0) {
+                            const int gl = logical_col(O, a.saind, p + pw - 1) / kDiagGroupW;
+                            s_ok = wait_bits(cnt + t.diag, (unsigned)D.nfinal & diag_prefix(gl), a.spin,
+                                             &a.hdr->status);
+                        }
                         __syncthreads();
                         if (!s_ok) break;
                         int lo, hi;
@@ -955,11 +1079,8 @@ __global__ void __launch_bounds__(kThreads, 2) replay_kernel_t(const __grid_cons
                 }
             }
         }
-        // publish: every thread's stores are fenced before the counter moves (off-diagonal
-        // tiles have published each panel already)
-        __threadfence();
+        // every task has published its tile's parts itself (completion bits)
         __syncthreads();
-        if (threadIdx.x == 0 && t.kind != TASK_OFF) red_release_add(cnt + t.tile, 1);
     }
 }
 
@@ -1596,7 +1717,7 @@ __device__ __forceinline__ void sn_task(const SnArgs& a, int ti, long long item,
             if (s_ok) {
                 int bad;
                 double ls;
-                potrf_packed(C, w, w, w - 1, S0, &bad, &ls, [](int) {});
+                potrf_packed(C, w, w, w - 1, S0, &bad, &ls, kPb, [](int) {});
                 for_rc(w, w, [&](int r, int c) {
                     if (r >= c) __stcg(F + O.off + r + (size_t)c * O.ld, C[pk(w, r, c)]);
                 });

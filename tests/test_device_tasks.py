@@ -6,17 +6,21 @@ the tiles with their stored columns and 16-column row extents.  This file runs t
 with numpy, one task after another in queue order (a topological order of the DAG), the
 way the kernel does it: SYRK / GEMM products chunked by 16 inner columns and cut to the
 chunk's row extents, the TRSM of a row slice by 32-column panels cut to the panel's row
-extents.  It checks that
+extents, a row slice of a diagonal tile factored against the rows of the slices before
+it.  It checks that
 
 * the result equals the oracle's factor on every structural entry of L (so the update
   lists are complete and the inner-dimension maps pair the right columns), and
 * every row or column the extents let the kernel skip is exactly zero in the operand
-  (so skipping is exact, reading 13).
+  (so skipping is exact, reading 13), and
+* the completion word of every diagonal tile (its nfinal) holds exactly the (column
+  group, row slice) bits its tasks set, groups outside a slice's band skipped.
 
 Row slices 1, 2, 4 and 8 and both queue orders are covered.
 """
 import numpy as np
 import pytest
+from scipy.linalg import solve_triangular
 
 from oracle import oracle as O
 from paper_2609_29765_gb300 import _lib as L
@@ -26,7 +30,8 @@ from paper_2609_29765_gb300.api import Plan
 
 KC = 16      # inner chunk of the tile products
 PANEL = 32   # TRSM panel width
-DIAG, OFF, SYRK, POTRF = 0, 1, 2, 3
+DIAG, OFF, SYRK = 0, 1, 2
+DG, DSL = 16, 4   # column group width and slices per word of a diagonal tile's completion bits
 T_OFF, T_DENSE, T_BAND = 0, 1, 2
 
 
@@ -177,6 +182,10 @@ class Replay:
         Ot[rs0:rs1] = X
 
     def run(self, values):
+        self.dbits = {}
+        for t in range(len(self.tiles)):
+            if self.tiles[t, 3] != T_OFF:
+                self.dbits[t] = 0
         F = np.zeros(self.fdoubles)
         F[self.value_map] = values
         F[self.pad] = 1.0
@@ -184,22 +193,44 @@ class Replay:
         for tk in self.tasks:
             kind, t = tk[0], tk[1]
             if kind == DIAG:
+                for g in range((self.tiles[t, 4] + DG - 1) // DG):
+                    self.dbits[t] |= 1 << (g * DSL)
                 D = self.diag_full(F, t)
                 for u in self.upds[tk[3]:tk[4]]:
                     self.syrk_into(F, D, u, u[8], u[6], u[7])
                 self.diag_store(F, t, D)
                 self.potrf(F, t)
             elif kind == SYRK:
-                rs0, rs1 = tk[5], tk[6]
+                rs0, rs1, sl = tk[5], tk[6], tk[10]
+                assert rs0 % DG == 0 and rs1 - rs0 <= 64 and sl < DSL
                 D = self.diag_full(F, t)
                 for u in self.upds[tk[3]:tk[4]]:
                     assert rs0 <= u[6] and u[7] <= rs1
                     self.syrk_into(F, D, u, u[8], u[6], u[7])
+                # the rows' factorization: columns [0, rs0) against the earlier slices' rows
+                # (final: they come earlier in the queue), then the own diagonal block
+                kd = self.tiles[t, 7]
+                if rs0 > 0:
+                    X = solve_triangular(D[:rs0, :rs0], D[rs0:rs1, :rs0].T, lower=True).T
+                    for g0 in range(0, rs0, DG):
+                        if g0 + DG <= rs0 - kd:   # skipped by the kernel: zero in these rows
+                            assert np.all(X[:, g0:g0 + DG] == 0.0), "skipped group not zero"
+                            self.skipped_checks += 1
+                        else:
+                            self.dbits[t] |= 1 << ((g0 // DG) * DSL + sl)
+                    D[rs0:rs1, :rs0] = X
+                    S = D[rs0:rs1, rs0:rs1] - X @ X.T
+                else:
+                    S = D[rs0:rs1, rs0:rs1]
+                S = np.tril(S)
+                D[rs0:rs1, rs0:rs1] = np.linalg.cholesky(S + np.tril(S, -1).T)
+                for g in range(rs0 // DG, (rs1 + DG - 1) // DG):
+                    self.dbits[t] |= 1 << (g * DSL + sl)
                 self.diag_store(F, t, D, rows=range(rs0, rs1))
-            elif kind == POTRF:
-                self.potrf(F, t)
             else:
                 self.off_task(F, tk)
+        for t, bits in self.dbits.items():
+            assert bits == (self.tiles[t, 10] & 0xffffffff), "completion bits of diagonal tile %d" % t
         return F[self.csc_map]
 
 
@@ -242,8 +273,8 @@ def test_device_task_list_reproduces_oracle(case, slices, bl):
 
 def test_queue_order_is_topological():
     # every tile a task reads (update operands, the diagonal tile of a TRSM) is complete,
-    # i.e. all of its producing tasks come earlier in the queue; a POTRF comes after the
-    # SYRK slices of its tile
+    # i.e. all of its producing tasks come earlier in the queue (a row slice of a diagonal
+    # tile after the slices before it)
     Ap, Ai, Ax, coords = I.laplace2d_bordered(16, 16, 2)
     P = Plan(len(Ap) - 1, Ap, Ai, coords=coords, nb=16)
     for slices, bl in ((1, False), (2, False), (4, True), (8, False)):
@@ -256,9 +287,12 @@ def test_queue_order_is_topological():
                 assert last[u[0]] < i and last[u[1]] < i, (slices, bl, i)
             if tk[0] == OFF:
                 assert last[tk[2]] < i
-            if tk[0] == POTRF:
-                slices_of_tile = [j for j, t2 in enumerate(R.tasks) if t2[1] == tk[1] and t2[0] == SYRK]
-                assert len(slices_of_tile) == tk[9] and all(j < i for j in slices_of_tile)
+        # the row slices of a diagonal tile: in row order, contiguous, covering its width
+        for t in {tk[1] for tk in R.tasks if tk[0] == SYRK}:
+            rows = [(tk[5], tk[6], tk[10]) for tk in R.tasks if tk[0] == SYRK and tk[1] == t]
+            assert [r[2] for r in rows] == list(range(len(rows)))
+            assert rows[0][0] == 0 and rows[-1][1] == R.tiles[t, 4]
+            assert all(rows[j][1] == rows[j + 1][0] for j in range(len(rows) - 1))
 
 
 def _spd_from_pattern(n, rows, cols, seed):
