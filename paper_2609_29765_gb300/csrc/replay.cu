@@ -275,6 +275,10 @@ __device__ void trsm_rows_t(double* X, int ldx, int R, int pw, const double* D, 
                 if (q == j % TPR) b[j / TPR] = xj;
 #pragma unroll
                 for (int s = 0; s < NJ; ++s) {
+                    // s and j are compile-time here: register groups whose columns all lie on
+                    // the finished side of j issue no instruction (a masked DFMA still takes a
+                    // slot of the FP64 pipe)
+                    if (BACK ? s * TPR >= j : s * TPR + TPR - 1 <= j) continue;
                     const int k = s * TPR + q;
                     if (!BACK && k > j && k < pw) b[s] = fma(-xj, D[k + j * ldd], b[s]);
                     if (BACK && k < j) b[s] = fma(-xj, D[j + k * ldd], b[s]);
@@ -1097,7 +1101,7 @@ __global__ void fill_kernel(const double* __restrict__ vals, long long nnz, long
         const int e = __ldg(src + f);
         const double c = e == -2 ? 1.0 : 0.0;
         if (e >= 0) {
-            for (long long b = 0; b < batch; ++b) __stcs(F + b * fstride + f, __ldcs(vals + b * nnz + e));
+            for (long long b = 0; b < batch; ++b) __stcs(F + b * fstride + f, __ldg(vals + b * nnz + e));
         } else {
             for (long long b = 0; b < batch; ++b) __stcs(F + b * fstride + f, c);
         }
