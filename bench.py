@@ -81,7 +81,8 @@ def workload_config(args, batch):
                         % (args.n, BW, NB, batch),
             "n": args.n, "half_bandwidth": BW, "nb": NB, "batch_per_gpu": batch,
             "route": "semisparse", "ordering": "natural",
-            "step": "scatter+factorize+logdet+solve(1 rhs)",
+            "step": "scatter+factorize(with the forward substitution in its launch)+logdet+backward "
+                    "substitution (1 rhs)",
             "l2": "inputs larger than L2 (values %.1f GB, factor %.1f GB per step)"}
 
 
@@ -546,7 +547,8 @@ def run_ours(args):
     dv = hv.to("cuda")
     db = hb.to("cuda")
     fac = torch.empty(P.factor_bytes(batch) // 8, dtype=torch.float64, device="cuda")
-    ws = torch.empty(max(P.workspace_bytes(batch), 64), dtype=torch.uint8, device="cuda")
+    ws = torch.empty(max(P.workspace_bytes(batch), L.stc_factorize_solve_workspace_bytes(P.h, batch, 1), 64),
+                     dtype=torch.uint8, device="cuda")
     info = torch.empty(batch, dtype=torch.int32, device="cuda")
     ld = torch.empty(batch, dtype=torch.float64, device="cuda")
     dx = torch.empty_like(db)
@@ -561,13 +563,15 @@ def run_ours(args):
         L.check(L.stc_scatter_values(P.h, vals, batch, fac), "scatter")
         if rp is not None:
             rp[1].record(st)
-        L.check(L.stc_factorize_scattered(P.h, batch, fac, ws, info), "factorize")
+        # the factorization with the forward substitution in the same launch, then the
+        # backward substitution (stc_factorize_solve's two halves)
+        L.check(L.stc_factorize_forward(P.h, batch, 1, bvec, fac, ws, info), "factorize+forward")
         if rp is not None:
             rp[2].record(st)
         L.check(L.stc_logdet(P.h, fac, batch, ld), "logdet")
         if rp is not None:
             rp[3].record(st)
-        L.check(L.stc_solve(P.h, fac, batch, 1, bvec, xout, ws), "solve")
+        L.check(L.stc_solve_backward(P.h, fac, batch, 1, xout, ws), "backward solve")
         if rp is not None:
             rp[4].record(st)
 
@@ -618,9 +622,9 @@ def run_ours(args):
 
         def step_io(vals, bvec, xout, ldout):
             L.check(L.stc_scatter_values(P.h, vals, batch, fac), "scatter")
-            L.check(L.stc_factorize_scattered(P.h, batch, fac, ws, info), "factorize")
+            L.check(L.stc_factorize_forward(P.h, batch, 1, bvec, fac, ws, info), "factorize+forward")
             L.check(L.stc_logdet(P.h, fac, batch, ldout), "logdet")
-            L.check(L.stc_solve(P.h, fac, batch, 1, bvec, xout, ws), "solve")
+            L.check(L.stc_solve_backward(P.h, fac, batch, 1, xout, ws), "backward solve")
 
         def run_e2e(steps):
             with torch.cuda.stream(cs):
@@ -666,9 +670,8 @@ def run_ours(args):
     x1 = torch.empty(1, 1, n, dtype=torch.float64, device="cuda")
 
     def step1():
-        L.check(L.stc_factorize(P.h, dv[0:1], 1, fac1, ws, info1), "factorize1")
+        L.check(L.stc_factorize_solve(P.h, dv[0:1], 1, 1, db[0:1], fac1, x1, ws, info1), "factorize+solve1")
         L.check(L.stc_logdet(P.h, fac1, 1, ld1), "logdet1")
-        L.check(L.stc_solve(P.h, fac1, 1, 1, db[0:1], x1, ws), "solve1")
 
     for _ in range(2):
         step1()
@@ -696,7 +699,7 @@ def run_ours(args):
         return
     stored = P.info["stored_entries"]
     scat_bytes = P.factor_bytes(batch) + batch * nnz * 8 + P.factor_bytes(1) // 2
-    solve_bytes = batch * (2 * stored * 8 + 2 * n * 8)
+    solve_bytes = batch * (stored * 8 + 2 * n * 8)
     total_items = batch * world
     value = total_items / (ms_step * 1e-3)
     flops_alg = P.info["flops_alg"]
@@ -710,11 +713,13 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": cfg,
         "plain": {"value": 1e3 / ms_plain, "unit": UNIT, "ms_per_factorization": ms_plain,
-                  "note": "batch 1, one launch per factorization (+logdet+solve)"},
+                  "note": "batch 1, one stc_factorize_solve per factorization (+logdet)"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": replay_traffic(args.n, batch),
-                     "kernel": "replay_kernel (persistent task-DAG factorization)",
-                     "work": "algorithmic flops sum_j c_j^2 = %.4g per factorization x %d" % (flops_alg, batch),
+                     "kernel": "replay_kernel (persistent task-DAG factorization, with the forward "
+                               "substitution's tasks)",
+                     "work": "algorithmic flops sum_j c_j^2 = %.4g per factorization x %d (the forward "
+                             "substitution's 2 flops per stored entry not counted)" % (flops_alg, batch),
                      "peak_source": "nominal FP64 ALU: 152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz",
                      "peak_measured_dfma_tflops": dfma_gflops / 1e3,
                      "frac_of_measured_dfma": achieved / (dfma_gflops / 1e3),
@@ -731,7 +736,7 @@ def run_ours(args):
                              "achieved": solve_bytes / (ms_solve * 1e-3) / 1e9,
                              "peak": HBM_GBS, "peak_source": HBM_SOURCE,
                              "frac": solve_bytes / (ms_solve * 1e-3) / 1e9 / HBM_GBS,
-                             "work": "factor tiles read twice (forward + backward) + b, x"},
+                             "work": "backward substitution: factor tiles read once + y, x"},
             "logdet_kernel": {"ms": ms_logdet},
         },
         "gpu_launches": 4 * args.steps,

@@ -220,12 +220,14 @@ int stc_plan_export(const stc_plan* plan, int what, void* buf, size_t* bytes);
 
 /* Copy one array of the device task list that stc_factorize replays (Algorithm 1's tasks
  * grouped per output tile, Sec. 5.2-5.3) with `slices` row slices per off-diagonal tile
- * (1, 2, 4 or 8; bl_order != 0: queued by bottom level, as for one or two value sets),
- * so that host-side checks can execute it.  Every entry is widened to int64.  The set is
+ * (1, 2, 4 or 8; bit 0 of bl_order: queued by bottom level, as for one or two value
+ * sets; bit 1: the set of stc_factorize_solve, with its forward-substitution tasks), so
+ * that host-side checks can execute it.  Every entry is widened to int64.  The set is
  * built on first request, as on the first factorization that uses it. */
 #define STC_TASKSET_TASKS 0     /* [ntasks][12] in queue order: kind (0 DIAG = SYRKs + POTRF,
                                    1 OFF = GEMMs + TRSM of a row slice, 2 SYRK = SYRKs into
-                                   a row slice of (k,k) + the factorization of its rows),
+                                   a row slice of (k,k) + the factorization of its rows,
+                                   3 FWD = forward substitution of block row k),
                                    output tile, diagonal tile, update range [ubeg, uend),
                                    row slice [rs0, rs1), TRSM rows [tr0, tr1), 0, slice
                                    index, slice height of the off-diagonal tiles           */
@@ -368,6 +370,32 @@ int stc_logdet(const stc_plan* plan, const void* d_factor, int64_t batch,
  * batch*nrhs) bytes or NULL (see above). */
 int stc_solve(const stc_plan* plan, const void* d_factor, int64_t batch, int64_t nrhs,
               const double* d_b, double* d_x, void* d_work, void* stream);
+
+/* Factorization and solve in one call: stc_factorize followed by stc_solve's result,
+ * with the forward substitution L y = P b (Sec. 6.7: the solves consume the factor where
+ * it sits on the device) run inside the factorization's persistent launch, one task per
+ * (item, block row) queued behind the factorization wavefront, so only the backward
+ * substitution runs after it.  Same arguments as stc_factorize and stc_solve: d_values
+ * [batch][nnzA]; d_b, d_x [batch][nrhs][n] FP64 (original ordering; d_x written, may not
+ * alias d_b); d_factor and d_info written as by stc_factorize (the factor is the same to
+ * the bit); d_work stc_factorize_solve_workspace_bytes(plan, batch, nrhs) bytes or NULL
+ * (see above).  Status as for stc_factorize (stc_sync_status on d_work).  On the
+ * supernodal route it runs the two calls one after the other. */
+size_t stc_factorize_solve_workspace_bytes(const stc_plan* plan, int64_t batch, int64_t nrhs);
+int stc_factorize_solve(const stc_plan* plan, const double* d_values, int64_t batch, int64_t nrhs,
+                        const double* d_b, void* d_factor, double* d_x, void* d_work, int32_t* d_info,
+                        void* stream);
+/* Its halves after stc_scatter_values, for callers that time or overlap them separately
+ * (tile routes only; a supernodal plan gives STC_ERR_UNSUPPORTED; d_work is required):
+ *   stc_factorize_forward -- the factorization with the forward substitution (d_b as above)
+ *                            on a factor that stc_scatter_values filled; y stays in d_work;
+ *   stc_solve_backward    -- the backward substitution L^T z = y, x = P^T z, from the y
+ *                            that stc_factorize_forward left in the same d_work (same
+ *                            batch and nrhs). */
+int stc_factorize_forward(const stc_plan* plan, int64_t batch, int64_t nrhs, const double* d_b,
+                          void* d_factor, void* d_work, int32_t* d_info, void* stream);
+int stc_solve_backward(const stc_plan* plan, const void* d_factor, int64_t batch, int64_t nrhs,
+                       double* d_x, void* d_work, void* stream);
 
 /* Copy L's values out of the factor storage into CSC order (STC_EXPORT_LP / LI layout),
  * the "factor returned" form of Sec. 6.7 (Table 6 reports the factor kept on the device

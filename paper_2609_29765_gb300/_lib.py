@@ -42,7 +42,8 @@ EXPORTED = [
     "stc_selinv", "stc_logdet_backward", "stc_sym_outer_backward", "stc_quad_form",
     "stc_group_create", "stc_group_workspace_bytes", "stc_factorize_group", "stc_group_destroy",
     "stc_strerror", "stc_factorize_mixed", "stc_quad_backward", "stc_plan_save", "stc_plan_load",
-    "stc_plan_export_taskset", "stc_plan_sync_status",
+    "stc_plan_export_taskset", "stc_plan_sync_status", "stc_factorize_solve",
+    "stc_factorize_solve_workspace_bytes", "stc_factorize_forward", "stc_solve_backward",
 ]
 (STC_TASKSET_TASKS, STC_TASKSET_UPDS, STC_TASKSET_IMAP, STC_TASKSET_TILES, STC_TASKSET_SAIND,
  STC_TASKSET_CEXT, STC_TASKSET_CSC_MAP, STC_TASKSET_PAD_DIAG) = range(8)
@@ -130,6 +131,14 @@ def lib():
         L.stc_logdet.restype = C.c_int
         L.stc_solve.argtypes = [_vp, _vp, C.c_int64, C.c_int64, _vp, _vp, _vp, _vp]
         L.stc_solve.restype = C.c_int
+        L.stc_factorize_solve.argtypes = [_vp, _vp, C.c_int64, C.c_int64, _vp, _vp, _vp, _vp, _vp, _vp]
+        L.stc_factorize_solve.restype = C.c_int
+        L.stc_factorize_solve_workspace_bytes.argtypes = [_vp, C.c_int64, C.c_int64]
+        L.stc_factorize_solve_workspace_bytes.restype = C.c_size_t
+        L.stc_factorize_forward.argtypes = [_vp, C.c_int64, C.c_int64, _vp, _vp, _vp, _vp, _vp]
+        L.stc_factorize_forward.restype = C.c_int
+        L.stc_solve_backward.argtypes = [_vp, _vp, C.c_int64, C.c_int64, _vp, _vp, _vp]
+        L.stc_solve_backward.restype = C.c_int
         L.stc_factor_to_csc.argtypes = [_vp, _vp, C.c_int64, _vp, _vp]
         L.stc_factor_to_csc.restype = C.c_int
         L.stc_group_create.argtypes = [C.c_int32, C.POINTER(_vp), C.POINTER(C.c_int64), C.POINTER(_vp)]
@@ -292,6 +301,26 @@ def stc_logdet(plan, d_factor, batch, d_logdet, stream=None):
 def stc_solve(plan, d_factor, batch, nrhs, d_b, d_x, d_work, stream=None):
     return lib().stc_solve(plan, _dev_ptr(d_factor), int(batch), int(nrhs), _dev_ptr(d_b), _dev_ptr(d_x),
                            _dev_ptr(d_work), _stream(stream))
+
+
+def stc_factorize_solve(plan, d_values, batch, nrhs, d_b, d_factor, d_x, d_work, d_info, stream=None):
+    return lib().stc_factorize_solve(plan, _dev_ptr(d_values), int(batch), int(nrhs), _dev_ptr(d_b),
+                                     _dev_ptr(d_factor), _dev_ptr(d_x), _dev_ptr(d_work), _dev_ptr(d_info),
+                                     _stream(stream))
+
+
+def stc_factorize_solve_workspace_bytes(plan, batch, nrhs) -> int:
+    return int(lib().stc_factorize_solve_workspace_bytes(plan, int(batch), int(nrhs)))
+
+
+def stc_factorize_forward(plan, batch, nrhs, d_b, d_factor, d_work, d_info, stream=None):
+    return lib().stc_factorize_forward(plan, int(batch), int(nrhs), _dev_ptr(d_b), _dev_ptr(d_factor),
+                                       _dev_ptr(d_work), _dev_ptr(d_info), _stream(stream))
+
+
+def stc_solve_backward(plan, d_factor, batch, nrhs, d_x, d_work, stream=None):
+    return lib().stc_solve_backward(plan, _dev_ptr(d_factor), int(batch), int(nrhs), _dev_ptr(d_x),
+                                    _dev_ptr(d_work), _stream(stream))
 
 
 def stc_factor_to_csc(plan, d_factor, batch, d_Lx, stream=None):

@@ -120,9 +120,9 @@ class Plan:
     def upload(self):
         L.check(L.stc_plan_upload(self.h), "stc_plan_upload")
 
-    def workspace(self, batch: int, device=None):
+    def workspace(self, batch: int, device=None, nbytes=None):
         torch = _torch()
-        nbytes = self.workspace_bytes(batch)
+        nbytes = self.workspace_bytes(batch) if nbytes is None else max(int(nbytes), self.workspace_bytes(batch))
         dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
         w = self._ws.get(dev)
         if w is None or w.numel() < nbytes:
@@ -149,6 +149,34 @@ class Plan:
         if check_status:
             L.check(L.stc_sync_status(ws), "stc_factorize (device status)")
         return Factor(self, fac, info, batch)
+
+
+    def factorize_solve(self, values, b, check_status=False):
+        """Factorize and solve in one call (the forward substitution runs inside the
+        factorization's launch): values [batch, nnzA], b [batch, nrhs, n] (or [batch, n]),
+        CUDA float64.  Returns (Factor, x); the factor is the one factorize() gives."""
+        torch = _torch()
+        if values.dim() == 1:
+            values = values.unsqueeze(0)
+        if values.dtype != torch.float64 or values.shape[1] != self.nnzA:
+            raise ValueError("values must be float64 [batch, nnzA=%d]" % self.nnzA)
+        values = values.contiguous()
+        batch = values.shape[0]
+        squeeze = b.dim() == 2
+        if squeeze:
+            b = b.unsqueeze(1)
+        b = b.contiguous()
+        if b.shape[0] != batch or b.shape[2] != self.n or b.dtype != torch.float64:
+            raise ValueError("b must be float64 [batch, nrhs, n]")
+        nrhs = b.shape[1]
+        fac = torch.empty(self.factor_bytes(batch) // 8, dtype=torch.float64, device=values.device)
+        info = torch.empty(batch, dtype=torch.int32, device=values.device)
+        x = torch.empty_like(b)
+        ws = self.workspace(batch, values.device, L.stc_factorize_solve_workspace_bytes(self.h, batch, nrhs))
+        L.check(L.stc_factorize_solve(self.h, values, batch, nrhs, b, fac, x, ws, info), "stc_factorize_solve")
+        if check_status:
+            L.check(L.stc_sync_status(ws), "stc_factorize_solve (device status)")
+        return Factor(self, fac, info, batch), (x.squeeze(1) if squeeze else x)
 
 
 class Factor:

@@ -615,9 +615,9 @@ void stored_cols(const stc_plan& P, const stc::DTile& t, vector<int>& out) {
 constexpr int kChunk = stc::kExtW;
 constexpr int kPanel = stc::kPanelW;
 
-stc::TaskSet* stc_plan::taskset(int32_t slices, bool bl_order) {
+stc::TaskSet* stc_plan::taskset(int32_t slices, bool bl_order, bool fwd) {
     std::lock_guard<std::mutex> g(mu);
-    auto it = tasksets.find(taskset_key(slices, bl_order));
+    auto it = tasksets.find(taskset_key(slices, bl_order, fwd));
     if (it != tasksets.end()) return it->second.get();
     auto ts = std::make_unique<stc::TaskSet>();
     const int64_t NT = nt;
@@ -972,6 +972,17 @@ stc::TaskSet* stc_plan::taskset(int32_t slices, bool bl_order) {
         ts->imap.insert(ts->imap.end(), Lk.imap.begin(), Lk.imap.end());
         Lk = Local();
     }
+    // TASK_FWD (fused forward substitution): one per block, after every factorization
+    // task; they produce nothing another factorization task reads
+    const size_t nfact = tasks.size();
+    if (fwd)
+        for (int64_t k = 0; k < NT; ++k) {
+            stc::DTask f{};
+            f.kind = stc::TASK_FWD; f.tile = diag_tile[k]; f.diag = diag_tile[k];
+            f.rs0 = 0; f.rs1 = NB; f.tr0 = 0; f.tr1 = NB;
+            tasks.push_back(f);
+            meta.emplace_back();
+        }
     // Queue order: earliest start on unbounded workers.  Tiles are published in steps
     // (an off-diagonal slice per TRSM panel, a diagonal tile per kDiagGroupW factored
     // columns), so a consumer can start on a tile's first published part ("avail") and
@@ -985,7 +996,7 @@ stc::TaskSet* stc_plan::taskset(int32_t slices, bool bl_order) {
     vector<double> key(T, 0.0), fin(T, 0.0), tile_fin(tiles.size(), 0.0), tile_key(tiles.size(), 0.0);
     vector<double> tile_avail(tiles.size(), kInf);
     auto avail = [&](int32_t tl) { return tile_avail[tl] < kInf ? tile_avail[tl] : tile_fin[tl]; };
-    for (size_t i = 0; i < T; ++i) {
+    for (size_t i = 0; i < nfact; ++i) {
         const Meta& mt = meta[i];
         double kdep = 0.0;
         for (int32_t s : mt.srcs) kdep = std::max(kdep, tile_key[s]);
@@ -1065,7 +1076,7 @@ stc::TaskSet* stc_plan::taskset(int32_t slices, bool bl_order) {
         vector<double> cost(T), bl(T);
         for (size_t i = 0; i < T; ++i)
             cost[i] = bl[i] = std::accumulate(meta[i].ucost.begin(), meta[i].ucost.end(), 0.0) + meta[i].fcost + kSync;
-        for (size_t ii = T; ii-- > 0;) {
+        for (size_t ii = nfact; ii-- > 0;) {
             auto pull = [&](int32_t tile) {
                 // producers built before ii (a row slice of (k,k) reads only the slices
                 // of its own tile that precede it)
@@ -1076,6 +1087,21 @@ stc::TaskSet* stc_plan::taskset(int32_t slices, bool bl_order) {
             if (meta[ii].final_tile >= 0) pull(meta[ii].final_tile);
         }
         for (size_t i = 0; i < T; ++i) key[i] = -bl[i];
+    }
+    if (fwd) {
+        // TASK_FWD k after the tasks of every tile it reads ((k,k), the tiles of block row k)
+        // and after FWD k-1; and no earlier than the tasks of (k+2,k+2), so that a CTA that
+        // takes it finds its inputs final instead of waiting for them
+        vector<double> tkey(tiles.size(), -std::numeric_limits<double>::infinity());
+        for (size_t i = 0; i < nfact; ++i) tkey[tasks[i].tile] = std::max(tkey[tasks[i].tile], key[i]);
+        double prev = -std::numeric_limits<double>::infinity();
+        for (int64_t k = 0; k < NT; ++k) {
+            double kk = std::max(prev, std::max(tkey[diag_tile[k]], tkey[diag_tile[std::min<int64_t>(NT - 1, k + 2)]]));
+            for (int32_t a = rowstart[k]; a < rowstart[k + 1]; ++a) kk = std::max(kk, tkey[rowtiles[a]]);
+            kk += 1e-6 * (std::abs(kk) + 1.0);
+            key[nfact + k] = kk;
+            prev = kk;
+        }
     }
     vector<int32_t> order(T);
     std::iota(order.begin(), order.end(), 0);
@@ -1090,7 +1116,7 @@ stc::TaskSet* stc_plan::taskset(int32_t slices, bool bl_order) {
     const double makespan = T ? *std::max_element(fin.begin(), fin.end()) : 0.0;
     ts->par = makespan > 0.0 ? ts->fma / makespan : 1.0;
     stc::TaskSet* raw = ts.get();
-    tasksets[taskset_key(slices, bl_order)] = std::move(ts);
+    tasksets[taskset_key(slices, bl_order, fwd)] = std::move(ts);
     return raw;
 }
 
@@ -1522,7 +1548,7 @@ static int taskset_export_impl(const stc_plan* P, int32_t slices, int bl_order, 
     if (!P || !bytes) return STC_ERR_INVALID_ARG;
     if (slices != 1 && slices != 2 && slices != 4 && slices != 8) return STC_ERR_INVALID_ARG;
     // task sets are built on demand under the plan's lock, as on the first factorization
-    const stc::TaskSet* ts = const_cast<stc_plan*>(P)->taskset(slices, bl_order != 0);
+    const stc::TaskSet* ts = const_cast<stc_plan*>(P)->taskset(slices, (bl_order & 1) != 0, (bl_order & 2) != 0);
     vector<int64_t> tmp;
     switch (what) {
         case STC_TASKSET_TASKS:

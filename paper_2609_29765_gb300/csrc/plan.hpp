@@ -77,7 +77,7 @@ constexpr int kDiagGroupW = 16;
 constexpr int kMaxDiagSlices = 4;
 static_assert((kMaxNb / kDiagGroupW) * kMaxDiagSlices <= 32, "completion word holds every (group, slice) bit");
 
-enum : int32_t { TASK_DIAG = 0, TASK_OFF = 1, TASK_SYRK = 2 };
+enum : int32_t { TASK_DIAG = 0, TASK_OFF = 1, TASK_SYRK = 2, TASK_FWD = 3 };
 
 // One device task, the cases of Algorithm 1 grouped by output tile (row slice):
 //   TASK_DIAG  every SYRK into (k,k), then POTRF(k)                 (unsliced)
@@ -86,6 +86,9 @@ enum : int32_t { TASK_DIAG = 0, TASK_OFF = 1, TASK_SYRK = 2 };
 //              publish group by group, then the Cholesky factor of the slice's own
 //              diagonal block (a row-partitioned POTRF(k))          (row slice)
 //   TASK_OFF   every GEMM into rows [rs0,rs1) of (m,k), then the TRSM of those rows
+//   TASK_FWD   forward substitution of block row k (tile = diag = (k,k)): y_k from the
+//              right-hand sides, L_kn y_n and L_kk, once they are final (only in the task
+//              sets of the fused factorization + solve)
 struct DTask {
     int32_t kind;
     int32_t tile;        // output tile
@@ -370,6 +373,9 @@ struct stc_plan {
     int tile_id(int64_t I, int64_t J) const;  // -1 if not active
     // built on demand (host); bl_order: queue by bottom level (longest path to the end of
     // the item's DAG) instead of modelled earliest start
-    stc::TaskSet* taskset(int32_t slices, bool bl_order = false);
-    static int32_t taskset_key(int32_t slices, bool bl_order) { return slices * 2 + (bl_order ? 1 : 0); }
+    // fwd: with one TASK_FWD per block (the fused factorization + forward substitution)
+    stc::TaskSet* taskset(int32_t slices, bool bl_order = false, bool fwd = false);
+    static int32_t taskset_key(int32_t slices, bool bl_order, bool fwd = false) {
+        return (slices * 2 + (bl_order ? 1 : 0)) * 2 + (fwd ? 1 : 0);
+    }
 };

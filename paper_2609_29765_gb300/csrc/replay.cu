@@ -352,6 +352,16 @@ struct ReplayArgs {        // one job: a plan and a batch of value sets
     int slice_h;             // rows per row slice of an off-diagonal tile
     long long spin;
     int sn;                  // != 0: a supernodal plan, executed from the launch's snj[job]
+    // TASK_FWD (fused factorization + forward substitution; null otherwise)
+    const double* rhs;       // [batch][nrhs][n]
+    double* y;               // [batch * nrhs][nt * nb]: forward results, read by the backward solve
+    int* sdone;              // [batch * nrhs][2 nt]: the solve's step flags (forward half set here)
+    const int32_t* perm;     // permuted position -> original index
+    const int32_t* rowstart; // per block row k: its off-diagonal tiles (k,n) in rowtiles
+    const int32_t* rowtiles;
+    long long n;
+    int nrhs;
+    int nt;
 };
 
 // One launch of the replay kernel: up to kMaxJobs jobs (plans) in one persistent grid.
@@ -815,6 +825,103 @@ __device__ void slice_factor(const ReplayArgs& a, const DTask& t, const DTile& O
     }
 }
 
+// a10 inside the factorization launch (TASK_FWD): forward substitution of block row k for
+// every right-hand side of one item, y_k = L_kk^{-1} (b_k - sum_n L_kn y_n), once L_kk, the
+// tiles L_kn of block row k and the y_n are final.  The products take a row per thread
+// (threads kThreads / nb apart share a row, over stored columns taken in turn, four
+// accumulators, partial sums added in a fixed order).  The substitution runs on the unit
+// triangle M = L_kk diag(L_kk)^{-1} (scaled in place in the packed copy in C), so a column
+// step is one FMA per later row: the owner of row j publishes u_j, the warps that own rows
+// meet at a named barrier, and every later row takes its term; y = diag(L_kk)^{-1} u.  y_k
+// goes to the solve's y array and its step flag is set to the panel count, as the solve's
+// own forward step would leave it, so that the backward solve can follow.  A step whose
+// waits fail still sets its flags (with the status word set, later steps stop early).
+__device__ void fwd_task(const ReplayArgs& a, const DTask& t, long long item, double* F, int* cnt, double* C,
+                         double* S0, double* S1, double* sv, int& s_ok) {
+    const int nb = a.nb, nt = a.nt, np = (nb + 31) / 32;
+    const DTile O = a.tiles[t.tile];
+    const int k = O.J, sw = O.sw, kd = min(O.kd, nb - 1);
+    if (threadIdx.x == 0) {
+        bool ok = s_ok && wait_bits(cnt + t.tile, (unsigned)O.nfinal, a.spin, &a.hdr->status);
+        for (int q = a.rowstart[k]; ok && q < a.rowstart[k + 1]; ++q) {
+            const int tt = a.rowtiles[q];
+            ok = wait_bits(cnt + tt, (unsigned)a.tiles[tt].nfinal, a.spin, &a.hdr->status);
+            for (int r = 0; ok && r < a.nrhs; ++r)
+                ok = wait_counter(a.sdone + (item * a.nrhs + r) * 2LL * nt + a.tiles[tt].J, np, a.spin,
+                                  &a.hdr->status);
+        }
+        s_ok = ok;
+    }
+    __syncthreads();
+    if (s_ok) {
+        load_diag_packed(C, F + O.off, O, nb);
+        __syncthreads();
+        for (int j = threadIdx.x; j < sw; j += kThreads) sv[j] = 1.0 / C[pk(nb, j, j)];
+        __syncthreads();
+        {
+            // M = L diag(L)^{-1} below the diagonal, a warp per column
+            const int lane = threadIdx.x & 31;
+            for (int j = threadIdx.x >> 5; j < sw; j += kThreads / 32)
+                for (int i = j + 1 + lane; i < min(sw, j + kd + 1); i += 32) C[pk(nb, i, j)] *= sv[j];
+        }
+        __syncthreads();
+        const int G = kThreads / nb, row = threadIdx.x % nb, part = threadIdx.x / nb;
+        const int nrow = (sw + 31) & ~31;  // threads of the warps that own rows
+        double* vb = S1;        // the block's right-hand side after the products
+        double* us = S1 + nb;   // u = diag(L) y
+        for (int r = 0; r < a.nrhs; ++r) {
+            const long long ch = item * a.nrhs + r;
+            const double* ych = a.y + ch * (long long)nt * nb;
+            if (part < G) {
+                double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+                for (int q = a.rowstart[k]; q < a.rowstart[k + 1]; ++q) {
+                    const DTile T = a.tiles[a.rowtiles[q]];
+                    if (row < T.r0 || row >= T.r1) continue;
+                    const double* Tc = F + T.off + row;
+                    const double* yn = ych + (long long)T.J * nb;
+                    int c = part;
+                    for (; c + 3 * G < T.sw; c += 4 * G) {
+                        s0 = fma(__ldcg(Tc + (size_t)c * nb), __ldcg(yn + logical_col(T, a.saind, c)), s0);
+                        s1 = fma(__ldcg(Tc + (size_t)(c + G) * nb), __ldcg(yn + logical_col(T, a.saind, c + G)), s1);
+                        s2 = fma(__ldcg(Tc + (size_t)(c + 2 * G) * nb), __ldcg(yn + logical_col(T, a.saind, c + 2 * G)),
+                                 s2);
+                        s3 = fma(__ldcg(Tc + (size_t)(c + 3 * G) * nb), __ldcg(yn + logical_col(T, a.saind, c + 3 * G)),
+                                 s3);
+                    }
+                    for (; c < T.sw; c += G)
+                        s0 = fma(__ldcg(Tc + (size_t)c * nb), __ldcg(yn + logical_col(T, a.saind, c)), s0);
+                }
+                S0[part * nb + row] = (s0 + s1) + (s2 + s3);
+            }
+            __syncthreads();
+            if (threadIdx.x < nb) {
+                const long long g = (long long)k * nb + threadIdx.x;
+                double s2 = 0.0;
+                for (int p2 = 0; p2 < G; ++p2) s2 += S0[p2 * nb + threadIdx.x];
+                vb[threadIdx.x] = (g < a.n ? a.rhs[ch * a.n + a.perm[g]] : 0.0) - s2;
+            }
+            __syncthreads();
+            if ((int)threadIdx.x < nrow) {
+                const int i = threadIdx.x;
+                double ur = i < sw ? vb[i] : 0.0;
+                for (int j = 0; j < sw; ++j) {
+                    if (i == j) us[j] = ur;
+                    asm volatile("bar.sync 1, %0;" ::"r"(nrow) : "memory");
+                    if (i > j && i < sw && i - j <= kd) ur = fma(-C[pk(nb, i, j)], us[j], ur);
+                }
+            }
+            __syncthreads();
+            double* yk = a.y + ch * (long long)nt * nb + (long long)k * nb;
+            for (int i = threadIdx.x; i < nb; i += kThreads) __stcg(yk + i, i < sw ? us[i] * sv[i] : 0.0);
+            __syncthreads();
+        }
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0)
+        for (int r = 0; r < a.nrhs; ++r) red_release_add(a.sdone + (item * a.nrhs + r) * 2LL * nt + k, np);
+}
+
 // WITH_SN: the launch may hold supernodal jobs (a mixed-route group); their tasks run
 // through sn_task.  The tile-only instantiation is the one every single-plan factorization
 // of a tile route uses.
@@ -913,6 +1020,8 @@ __global__ void __launch_bounds__(kThreads, 2) replay_kernel_t(const __grid_cons
                     if (threadIdx.x == 0) red_release_or(cnt + t.tile, diag_bits(done, O.sw, 0));
                 }
             }
+        } else if (t.kind == TASK_FWD) {
+            fwd_task(a, t, item, F, cnt, C, S0, S1, sv, s_ok);
         } else if (t.kind == TASK_SYRK) {
             // rows [rs0, rs1) of (k,k): every SYRK update, lower part only, then their
             // factorization
@@ -1160,6 +1269,7 @@ struct SolveArgs {
     int nt, nb;
     long long n;
     long long spin;
+    int ti0;                   // first step: 0 (forward + backward) or nt (backward only)
 };
 
 constexpr int kSolveWarps = kThreads / 32;
@@ -1381,7 +1491,7 @@ __global__ void __launch_bounds__(kThreads, 1) solve_kernel(SolveArgs a) {
     __shared__ __align__(8) unsigned long long bar;
     __shared__ long long s_slot;
     __shared__ int s_ok;
-    const long long total = 2LL * a.nt * a.chains;
+    const long long total = (2LL * a.nt - a.ti0) * a.chains;
     const int nb = a.nb, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int np = (nb + 31) / 32;                 // panels of a block: its completion count
     __shared__ int s_pb[kNbMax / 32 + 1];          // stored-column start of each panel (forward)
@@ -1397,7 +1507,7 @@ __global__ void __launch_bounds__(kThreads, 1) solve_kernel(SolveArgs a) {
         const long long slot = s_slot;
         __syncthreads();
         if (slot >= total) break;
-        const int ti = (int)(slot / a.chains);
+        const int ti = (int)(slot / a.chains) + a.ti0;
         const long long ch = slot % a.chains;
         const long long item = ch / a.nrhs;
         const double* F = a.factor + item * a.fstride;
@@ -2587,10 +2697,10 @@ int no_throw(F&& f) {
 }
 
 // The plan's device task list for `slices` row slices (built on the host on first use).
-int get_taskset(stc_plan* P, int32_t slices, bool bl_order, TaskSet** out) {
+int get_taskset(stc_plan* P, int32_t slices, bool bl_order, TaskSet** out, bool fwd = false) {
     *out = nullptr;
     return no_throw([&] {
-        *out = P->taskset(slices, bl_order);
+        *out = P->taskset(slices, bl_order, fwd);
         return STC_OK;
     });
 }
@@ -2776,10 +2886,10 @@ int32_t pick_slices_impl(stc_plan* P, int64_t batch, int sms) {
 
 // The task set a factorization of `batch` value sets replays (slice count from the batch,
 // bottom-level order for one or two value sets).
-int pick_taskset(stc_plan* P, int64_t batch, int sms, bool bl_order, TaskSet** out) {
+int pick_taskset(stc_plan* P, int64_t batch, int sms, bool bl_order, TaskSet** out, bool fwd = false) {
     *out = nullptr;
     return no_throw([&] {
-        *out = P->taskset(pick_slices_impl(P, batch, sms), bl_order);
+        *out = P->taskset(pick_slices_impl(P, batch, sms), bl_order, fwd);
         return STC_OK;
     });
 }
@@ -3070,6 +3180,103 @@ extern "C" int stc_solve(const stc_plan* Pc, const void* d_factor, int64_t batch
     const int grid = grid_of(P, sms, total);
     solve_kernel<<<grid, kThreads, kSolveSmem, st>>>(a);
     return cudaGetLastError() == cudaSuccess ? STC_OK : STC_ERR_CUDA;
+}
+
+// Fused factorization + solve: [header | completion counters], then (256-byte aligned)
+// the solve's step flags and y vectors.
+size_t fused_solve_off(const stc_plan* P, int64_t batch) { return (factorize_ws(P, batch) + 255) / 256 * 256; }
+
+extern "C" size_t stc_factorize_solve_workspace_bytes(const stc_plan* P, int64_t batch, int64_t nrhs) {
+    if (!P || batch < 0 || nrhs < 0) return 0;
+    if (is_sn(P)) return std::max(factorize_ws(P, batch), solve_ws(P, batch * nrhs));
+    return fused_solve_off(P, batch) + solve_ws(P, batch * nrhs) - sizeof(WorkHeader);
+}
+
+extern "C" int stc_factorize_forward(const stc_plan* Pc, int64_t batch, int64_t nrhs, const double* d_b,
+                                     void* d_factor, void* d_work, int32_t* d_info, void* stream) {
+    stc_plan* P = const_cast<stc_plan*>(Pc);
+    if (!P || !d_factor || !d_info || !d_b || !d_work || batch <= 0 || nrhs <= 0) return STC_ERR_INVALID_ARG;
+    if (is_sn(P)) return STC_ERR_UNSUPPORTED;
+    int dev, sms, rc;
+    if ((rc = device_info(&dev, &sms))) return rc;
+    if ((rc = ensure_plan(P, dev))) return rc;
+    TaskSet* ts = nullptr;
+    if ((rc = pick_taskset(P, batch, sms, batch <= 2, &ts, true))) return rc;
+    if ((rc = ensure_taskset(P, ts, dev))) return rc;
+    const long long chains = batch * nrhs;
+    cudaStream_t st = S(stream);
+    const size_t off = fused_solve_off(P, batch), flags = solve_flags(P, chains);
+    if (cudaMemsetAsync(d_work, 0, off + flags, st) != cudaSuccess) return STC_ERR_CUDA;
+    if (cudaMemsetAsync(d_info, 0, (size_t)batch * sizeof(int32_t), st) != cudaSuccess) return STC_ERR_CUDA;
+    WorkHeader* hdr = (WorkHeader*)d_work;
+    ReplayLaunch Lc{};
+    fill_job(Lc.job[0], P, ts, d_factor, (int*)((char*)d_work + sizeof(WorkHeader)), d_info, batch, hdr);
+    ReplayArgs& j = Lc.job[0];
+    j.rhs = d_b;
+    j.sdone = (int*)((char*)d_work + off);
+    j.y = (double*)((char*)d_work + off + flags);
+    j.perm = P->dev.perm; j.rowstart = P->dev.srow_beg; j.rowtiles = P->dev.srow_tiles;
+    j.n = P->n; j.nrhs = (int)nrhs; j.nt = (int)P->nt;
+    Lc.njobs = 1;
+    Lc.queue = nullptr;
+    Lc.hdr = hdr;
+    Lc.total = (long long)ts->tasks.size() * batch;
+    replay_kernel_t<false><<<grid_of(P, default_ctas(sms, batch_total(Lc)), Lc.total), kThreads, kRSmemBytes, st>>>(Lc);
+    return cudaGetLastError() == cudaSuccess ? STC_OK : STC_ERR_CUDA;
+}
+
+extern "C" int stc_solve_backward(const stc_plan* Pc, const void* d_factor, int64_t batch, int64_t nrhs,
+                                  double* d_x, void* d_work, void* stream) {
+    stc_plan* P = const_cast<stc_plan*>(Pc);
+    if (!P || !d_factor || !d_x || !d_work || batch <= 0 || nrhs <= 0) return STC_ERR_INVALID_ARG;
+    if (is_sn(P)) return STC_ERR_UNSUPPORTED;
+    int dev, sms, rc;
+    if ((rc = device_info(&dev, &sms))) return rc;
+    if ((rc = ensure_plan(P, dev))) return rc;
+    TaskSet* ts = nullptr;
+    if ((rc = pick_taskset(P, batch, sms, batch <= 2, &ts, true))) return rc;
+    if ((rc = ensure_taskset(P, ts, dev))) return rc;
+    const long long chains = batch * nrhs;
+    cudaStream_t st = S(stream);
+    const size_t off = fused_solve_off(P, batch), flags = solve_flags(P, chains);
+    WorkHeader* hdr = (WorkHeader*)d_work;
+    // the solve kernel's backward steps; its slot counter restarted, the status word keeps
+    // the factorization's outcome
+    if (cudaMemsetAsync(&hdr->head, 0, sizeof(hdr->head), st) != cudaSuccess) return STC_ERR_CUDA;
+    SolveArgs a{};
+    a.tiles = ts->d_tiles; a.saind = P->dev.saind; a.rowstart = P->dev.srow_beg; a.rowtiles = P->dev.srow_tiles;
+    a.colstart = P->dev.scol_beg; a.diag = P->dev.diag_tile; a.perm = P->dev.perm;
+    a.factor = (const double*)d_factor; a.fstride = P->factor_doubles; a.b = nullptr; a.x = d_x;
+    a.hdr = hdr;
+    a.done = (int*)((char*)d_work + off);
+    a.y = (double*)((char*)d_work + off + flags);
+    a.chains = chains; a.nrhs = nrhs; a.nt = (int)P->nt; a.nb = (int)P->nb; a.n = P->n;
+    a.spin = P->opt.spin_limit > 0 ? P->opt.spin_limit : kDefaultSpin;
+    a.ti0 = (int)P->nt;
+    const long long total = P->nt * chains;
+    solve_kernel<<<grid_of(P, sms, total), kThreads, kSolveSmem, st>>>(a);
+    return cudaGetLastError() == cudaSuccess ? STC_OK : STC_ERR_CUDA;
+}
+
+extern "C" int stc_factorize_solve(const stc_plan* Pc, const double* d_values, int64_t batch, int64_t nrhs,
+                                   const double* d_b, void* d_factor, double* d_x, void* d_work, int32_t* d_info,
+                                   void* stream) {
+    stc_plan* P = const_cast<stc_plan*>(Pc);
+    if (!P || !d_values || !d_factor || !d_info || !d_b || !d_x || batch <= 0 || nrhs <= 0 || d_b == d_x)
+        return STC_ERR_INVALID_ARG;
+    int dev, sms, rc;
+    if ((rc = device_info(&dev, &sms))) return rc;
+    if ((rc = ensure_plan(P, dev))) return rc;
+    if (!d_work && (rc = own_buffer(P, false, stc_factorize_solve_workspace_bytes(P, batch, nrhs), &d_work)))
+        return rc;
+    if (is_sn(P)) {
+        // supernodal route: the factorization, then the solve, on the same stream
+        if ((rc = stc_factorize(P, d_values, batch, d_factor, d_work, d_info, stream))) return rc;
+        return stc_solve(P, d_factor, batch, nrhs, d_b, d_x, d_work, stream);
+    }
+    if ((rc = stc_scatter_values(P, d_values, batch, d_factor, stream))) return rc;
+    if ((rc = stc_factorize_forward(P, batch, nrhs, d_b, d_factor, d_work, d_info, stream))) return rc;
+    return stc_solve_backward(P, d_factor, batch, nrhs, d_x, d_work, stream);
 }
 
 extern "C" int stc_fp64_peak_probe(double* d_scratch, int64_t scratch_doubles, int64_t iters, double* gflops) {

@@ -30,7 +30,7 @@ from paper_2609_29765_gb300.api import Plan
 
 KC = 16      # inner chunk of the tile products
 PANEL = 32   # TRSM panel width
-DIAG, OFF, SYRK = 0, 1, 2
+DIAG, OFF, SYRK, FWD = 0, 1, 2, 3
 DG, DSL = 16, 4   # column group width and slices per word of a diagonal tile's completion bits
 T_OFF, T_DENSE, T_BAND = 0, 1, 2
 
@@ -43,8 +43,8 @@ def _built():
 
 
 class Replay:
-    def __init__(self, P, slices, bl):
-        ex = lambda w: L.stc_plan_export_taskset(P.h, slices, bl, w)
+    def __init__(self, P, slices, bl, fwd=False):
+        ex = lambda w: L.stc_plan_export_taskset(P.h, slices, int(bl) | (2 if fwd else 0), w)
         self.nb = P.info["nb"]
         self.tasks = ex(L.STC_TASKSET_TASKS).reshape(-1, 12)
         self.upds = ex(L.STC_TASKSET_UPDS).reshape(-1, 10)
@@ -55,6 +55,7 @@ class Replay:
         self.csc_map = ex(L.STC_TASKSET_CSC_MAP)
         self.pad = ex(L.STC_TASKSET_PAD_DIAG)
         self.value_map = P.export("value_map")
+        self.perm = P.export("perm")
         self.fdoubles = P.factor_bytes(1) // 8
         self.skipped_checks = 0
 
@@ -181,8 +182,27 @@ class Replay:
                     X[x0 - rs0:x1 - rs0, pn:] -= X[x0 - rs0:x1 - rs0, k0:k0 + K] @ Ls[pn:, k0:k0 + K].T
         Ot[rs0:rs1] = X
 
-    def run(self, values):
+    def fwd_task(self, F, tk, bp, Y):
+        # y_k = L_kk^{-1} (b_k - sum_n L_kn y_n) with the tiles as they stand at this point
+        # of the queue (a tile that is not final yet gives a wrong y)
+        t, nb = tk[1], self.nb
+        k = self.tiles[t, 2]
+        v = bp[k * nb:(k + 1) * nb].copy()
+        for o in np.nonzero((self.tiles[:, 3] == T_OFF) & (self.tiles[:, 1] == k))[0]:
+            lc = self.logical(o, np.arange(self.tiles[o, 4]))
+            v -= self.off_view(F, o) @ Y[self.tiles[o, 2] * nb + lc]
+        D = self.diag_full(F, t)
+        sw = self.tiles[t, 4]
+        Y[k * nb:k * nb + sw] = solve_triangular(D[:sw, :sw], v[:sw], lower=True)
+
+    def run(self, values, rhs=None):
         self.dbits = {}
+        nb, n = self.nb, len(self.perm)
+        nt = (n + nb - 1) // nb
+        bp = np.zeros(nt * nb)
+        if rhs is not None:
+            bp[:n] = rhs[self.perm]
+        self.y = np.zeros(nt * nb)
         for t in range(len(self.tiles)):
             if self.tiles[t, 3] != T_OFF:
                 self.dbits[t] = 0
@@ -227,6 +247,8 @@ class Replay:
                 for g in range(rs0 // DG, (rs1 + DG - 1) // DG):
                     self.dbits[t] |= 1 << (g * DSL + sl)
                 self.diag_store(F, t, D, rows=range(rs0, rs1))
+            elif kind == FWD:
+                self.fwd_task(F, tk, bp, self.y)
             else:
                 self.off_task(F, tk)
         for t, bits in self.dbits.items():
@@ -269,6 +291,30 @@ def test_device_task_list_reproduces_oracle(case, slices, bl):
     scale = np.maximum.reduceat(np.abs(Lo), F.Lp[:-1])[col]
     assert np.max(np.abs(got - Lo) / scale) <= 1e-12, name
     assert R.skipped_checks > 0
+
+
+@pytest.mark.parametrize("slices,bl", [(2, False), (8, True)])
+@pytest.mark.parametrize("case", [c for c in CASES if c[0] in ("band_nb128", "bordered_nd_nb16", "fem_dense_nb16")],
+                         ids=lambda c: c[0])
+def test_forward_substitution_tasks(case, slices, bl):
+    # the task set of the fused factorization + solve: its factor is the plain set's, and
+    # each forward-substitution task, executed where it sits in the queue, gives
+    # y = L^{-1} P b (so every tile it reads is final there)
+    from scipy.sparse.linalg import spsolve_triangular
+    import scipy.sparse as sp
+    name, Ap, Ai, Ax, kw = case
+    n = len(Ap) - 1
+    P = Plan(n, Ap, Ai, **kw)
+    b = np.random.default_rng(3).standard_normal(n)
+    R = Replay(P, slices, bl, fwd=True)
+    assert (R.tasks[:, 0] == FWD).sum() == (n + P.info["nb"] - 1) // P.info["nb"]
+    got = R.run(Ax, b)
+    F = O.OracleFactor(n, Ap, Ai, P.export("perm"))
+    Lo, info = F.factor(Ax)
+    assert np.array_equal(got, Replay(P, slices, bl).run(Ax))
+    Lm = sp.csr_matrix(sp.csc_matrix((Lo, F.Li, F.Lp), shape=(n, n)))
+    y = spsolve_triangular(Lm, b[F.perm], lower=True)
+    assert np.max(np.abs(R.y[:n] - y)) <= 1e-12 * np.max(np.abs(y)), name
 
 
 def test_queue_order_is_topological():

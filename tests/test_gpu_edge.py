@@ -100,10 +100,12 @@ def test_parallel_replay_matches_serial_bit_for_bit(case):
         x = fac.solve(b)
         sig = fac.selinv()
         assert sig.status() == L.STC_OK
-        out[ctas] = (fac.data.clone(), ld.clone(), x.clone(), sig.data.clone())
+        fac2, x2 = P.factorize_solve(v, b, check_status=True)
+        out[ctas] = (fac.data.clone(), ld.clone(), x.clone(), sig.data.clone(), fac2.data.clone(), x2.clone())
     ref = out[1]
     for ctas in (0, 3 * 152):
-        for what, a, r in zip(("factor", "logdet", "solve", "selected inverse"), out[ctas], ref):
+        for what, a, r in zip(("factor", "logdet", "solve", "selected inverse", "fused factor", "fused solve"),
+                              out[ctas], ref):
             assert torch.equal(a, r), "%s: %s differs from the serial replay (grid %d)" % (name, what, ctas)
 
 

@@ -252,3 +252,44 @@ def test_null_workspace_uses_the_plans_own():
     assert L.stc_logdet_backward(P.h, fac, 3, None, g, 0, None, None) == L.STC_OK
     assert L.stc_plan_sync_status(P.h) == L.STC_OK
     assert torch.equal(g, ref.logdet_backward())
+
+
+def _fused_cases():
+    n, bw = 5000, 200
+    Ap, Ai = I.band_pattern(n, bw)
+    vals = np.stack([I.band_values(n, bw, s, Ap, Ai) for s in range(3)])
+    yield "band n=5000 bw 200", (n, Ap, Ai), dict(nb=128, ordering="natural", route="semisparse"), vals
+    n2, bw2 = 3000, 40
+    Ap2, Ai2 = I.band_pattern(n2, bw2)
+    vals2 = np.stack([I.band_values(n2, bw2, s, Ap2, Ai2) for s in range(20)])
+    yield "band n=3000 bw 40, 20 value sets", (n2, Ap2, Ai2), dict(nb=128, ordering="natural", route="semisparse"), vals2
+    Ap3, Ai3, coords, vals3 = c1_batch(2)
+    yield "config 1, dense route", (len(Ap3) - 1, Ap3, Ai3), dict(coords=coords, nb=64, route="dense"), vals3
+    n4 = 517
+    Ap4, Ai4, Ax4 = I.random_spd(n4, 0.006, 1)
+    yield "random indexed, n_b 16", (n4, Ap4, Ai4), dict(nb=16, ordering="rcm", route="semisparse"), Ax4[None]
+    yield "config 1, supernodal route", (len(Ap3) - 1, Ap3, Ai3), dict(coords=coords, nb=64, route="supernodal"), vals3
+
+
+@pytest.mark.parametrize("case", list(_fused_cases()), ids=lambda c: c[0])
+def test_factorize_solve_fused(case):
+    # factorization + solve in one call (the forward substitution inside the factorization
+    # launch): the factor equals stc_factorize's to the bit, x matches the oracle's solve
+    name, (n, Ap, Ai), kw, vals = case
+    batch = vals.shape[0]
+    P = Plan(n, Ap, Ai, **kw)
+    rhs = np.stack([I.rhs(n, 30 + b, 2) for b in range(batch)])
+    fac1 = P.factorize(dev(vals))
+    fac2, x = P.factorize_solve(dev(vals), dev(rhs), check_status=True)
+    assert int(fac2.info.abs().sum()) == 0
+    assert torch.equal(fac1.data, fac2.data), name
+    x = x.cpu().numpy()
+    F = O.OracleFactor(n, Ap, Ai, P.export("perm"))
+    for b in sorted({0, batch - 1}):
+        Lo, _ = F.factor(vals[b])
+        for r in range(2):
+            xo = F.solve(Lo, rhs[b, r])
+            assert np.linalg.norm(x[b, r] - xo) <= TOL_X * np.linalg.norm(xo), (name, b, r)
+    # a second call on the same workspace gives the same x
+    _, x2 = P.factorize_solve(dev(vals), dev(rhs))
+    assert np.array_equal(x2.cpu().numpy(), x)
