@@ -718,7 +718,13 @@ stc::TaskSet* stc_plan::taskset(int32_t slices, bool bl_order, bool fwd) {
     // completion bit of column group g of row slice s of a diagonal tile
     constexpr int DG = stc::kDiagGroupW;
     auto dbit = [](int g, int s) { return (int32_t)(1u << (g * stc::kMaxDiagSlices + s)); };
-    const double kSliceSync = 3000.0;  // modelled cost of one more slice of a diagonal tile
+    // modelled cost of one more slice of a diagonal tile: with two slices per off-diagonal
+    // tile (the choice for wide batches, whose replay is bound by the SMs' FP64 throughput)
+    // an extra slice's staging and synchronisation weigh more than a shorter chain; with
+    // more slices (few items, the chain bounds) they weigh little.  Measured on the
+    // n = 200,000 band: 64 value sets 739 ms with four slices of (k,k), 720 ms with three;
+    // one value set 270 ms with four, 287 ms with three.
+    const double kSliceSync = eff <= 2 ? 150000.0 : 3000.0;
     auto potrf_cost = [&](const stc::DTile& D) {
         double w = D.sw, kd = std::min<double>(D.kd, w - 1);
         return (D.kind == stc::TILE_DIAG_BAND) ? w * (kd + 1) * (kd + 1) / 2 : w * w * w / 6;
@@ -1106,13 +1112,60 @@ stc::TaskSet* stc_plan::taskset(int32_t slices, bool bl_order, bool fwd) {
     vector<int32_t> order(T);
     std::iota(order.begin(), order.end(), 0);
     std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return key[a] < key[b]; });
-    ts->tasks.reserve(T);
-    ts->qkey.reserve(T);
+    if (fwd) {
+        // Forward substitution of block k hosted by a factorization task that usually starts
+        // by waiting (slice 0 of a diagonal tile, or an unsliced one), so that it fills the
+        // host's wait instead of taking a CTA slot of its own: the second such task, in queue
+        // order, after every task of (k,k) and of the tiles of block row k and after the host
+        // of block k-1.  The host runs it first (DTask.own_wait = diagonal tile of k, plus 1).
+        // A block with no host left keeps its own TASK_FWD.
+        vector<int32_t> pos(T);
+        for (size_t q = 0; q < T; ++q) pos[order[q]] = (int32_t)q;
+        vector<int32_t> dep(NT, -1);
+        for (size_t i = 0; i < nfact; ++i) {
+            const int64_t row = tiles[tasks[i].tile].I;  // block row of the task's tile
+            dep[row] = std::max(dep[row], pos[i]);
+        }
+        int32_t prev = -1;
+        std::vector<char> drop(T, 0);
+        auto eligible = [&](int32_t q) {
+            const stc::DTask& h = tasks[order[q]];
+            return h.kind == stc::TASK_DIAG || (h.kind == stc::TASK_SYRK && h.slice == 0);
+        };
+        for (int64_t k = 0; k < NT; ++k) {
+            // the second eligible position after the block's inputs, or the first free eligible
+            // task after it and after the previous block's host
+            int32_t from = -1, seen = 0, host = -1;
+            for (int32_t q = dep[k] + 1; q < (int32_t)T; ++q)
+                if (eligible(q) && ++seen == 2) { from = q; break; }
+            if (from >= 0)
+                for (int32_t q = std::max(from, prev + 1); q < (int32_t)T; ++q)
+                    if (eligible(q) && tasks[order[q]].own_wait == 0) { host = q; break; }
+            if (host < 0) break;  // this block and the later ones keep their TASK_FWD
+            tasks[order[host]].own_wait = diag_tile[k] + 1;
+            drop[nfact + k] = 1;
+            prev = host;
+        }
+        // the blocks without a host last, in block order (after every host)
+        vector<int32_t> kept;
+        kept.reserve(T);
+        for (int32_t i : order)
+            if ((size_t)i < nfact) kept.push_back(i);
+        double klast = kept.empty() ? 0.0 : key[kept.back()];
+        for (int64_t k = 0; k < NT; ++k)
+            if (!drop[nfact + k]) {
+                key[nfact + k] = klast += 1.0;
+                kept.push_back((int32_t)(nfact + k));
+            }
+        order.swap(kept);
+    }
+    ts->tasks.reserve(order.size());
+    ts->qkey.reserve(order.size());
     for (int32_t i : order) {
         ts->tasks.push_back(tasks[i]);
         ts->qkey.push_back(key[i]);
     }
-    ts->period = T ? key[order[T - 1]] / double(std::max<int64_t>(1, NT)) : 0.0;
+    ts->period = T ? key[order.back()] / double(std::max<int64_t>(1, NT)) : 0.0;
     const double makespan = T ? *std::max_element(fin.begin(), fin.end()) : 0.0;
     ts->par = makespan > 0.0 ? ts->fma / makespan : 1.0;
     stc::TaskSet* raw = ts.get();

@@ -88,7 +88,8 @@ enum : int32_t { TASK_DIAG = 0, TASK_OFF = 1, TASK_SYRK = 2, TASK_FWD = 3 };
 //   TASK_OFF   every GEMM into rows [rs0,rs1) of (m,k), then the TRSM of those rows
 //   TASK_FWD   forward substitution of block row k (tile = diag = (k,k)): y_k from the
 //              right-hand sides, L_kn y_n and L_kk, once they are final (only in the task
-//              sets of the fused factorization + solve)
+//              sets of the fused factorization + solve, for blocks no waiting diagonal task
+//              hosts; see own_wait)
 struct DTask {
     int32_t kind;
     int32_t tile;        // output tile
@@ -96,7 +97,9 @@ struct DTask {
     int32_t ubeg, uend;  // range in the update array
     int32_t rs0, rs1;    // row slice of the output tile
     int32_t tr0, tr1;    // rows of the slice the TRSM touches (slice cut to r-extent)
-    int32_t own_wait;    // unused (0)
+    int32_t own_wait;    // fused task sets: on a TASK_DIAG or slice-0 TASK_SYRK, 1 + the
+                         // diagonal tile of the block whose forward substitution it runs
+                         // first (0: none)
     int32_t slice;       // TASK_OFF, TASK_SYRK: index of the row slice in its tile
     int32_t pad;
 };

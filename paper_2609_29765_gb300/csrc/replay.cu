@@ -836,13 +836,13 @@ __device__ void slice_factor(const ReplayArgs& a, const DTask& t, const DTile& O
 // goes to the solve's y array and its step flag is set to the panel count, as the solve's
 // own forward step would leave it, so that the backward solve can follow.  A step whose
 // waits fail still sets its flags (with the status word set, later steps stop early).
-__device__ void fwd_task(const ReplayArgs& a, const DTask& t, long long item, double* F, int* cnt, double* C,
+__device__ void fwd_task(const ReplayArgs& a, int dtile, long long item, double* F, int* cnt, double* C,
                          double* S0, double* S1, double* sv, int& s_ok) {
     const int nb = a.nb, nt = a.nt, np = (nb + 31) / 32;
-    const DTile O = a.tiles[t.tile];
+    const DTile O = a.tiles[dtile];
     const int k = O.J, sw = O.sw, kd = min(O.kd, nb - 1);
     if (threadIdx.x == 0) {
-        bool ok = s_ok && wait_bits(cnt + t.tile, (unsigned)O.nfinal, a.spin, &a.hdr->status);
+        bool ok = s_ok && wait_bits(cnt + dtile, (unsigned)O.nfinal, a.spin, &a.hdr->status);
         for (int q = a.rowstart[k]; ok && q < a.rowstart[k + 1]; ++q) {
             const int tt = a.rowtiles[q];
             ok = wait_bits(cnt + tt, (unsigned)a.tiles[tt].nfinal, a.spin, &a.hdr->status);
@@ -968,6 +968,11 @@ __global__ void __launch_bounds__(kThreads, 2) replay_kernel_t(const __grid_cons
         const DTile O = a.tiles[t.tile];
         if (threadIdx.x == 0) s_ok = (*(volatile int*)&a.hdr->status == STC_OK);
         __syncthreads();
+        if (t.own_wait > 0 && a.y) {
+            // fused task sets: a forward-substitution step hosted by this task, run first
+            fwd_task(a, t.own_wait - 1, item, F, cnt, C, S0, S1, sv, s_ok);
+            __syncthreads();
+        }
         if (t.kind == TASK_DIAG) {
             // SYRKs + POTRF on the whole diagonal tile, held as a packed triangle
             if (s_ok) {
@@ -1021,7 +1026,7 @@ __global__ void __launch_bounds__(kThreads, 2) replay_kernel_t(const __grid_cons
                 }
             }
         } else if (t.kind == TASK_FWD) {
-            fwd_task(a, t, item, F, cnt, C, S0, S1, sv, s_ok);
+            fwd_task(a, t.tile, item, F, cnt, C, S0, S1, sv, s_ok);
         } else if (t.kind == TASK_SYRK) {
             // rows [rs0, rs1) of (k,k): every SYRK update, lower part only, then their
             // factorization

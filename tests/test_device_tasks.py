@@ -212,6 +212,9 @@ class Replay:
         nb = self.nb
         for tk in self.tasks:
             kind, t = tk[0], tk[1]
+            if tk[9] > 0:   # a hosted forward-substitution step, run first
+                assert kind == DIAG or (kind == SYRK and tk[10] == 0)
+                self.fwd_task(F, (FWD, tk[9] - 1), bp, self.y)
             if kind == DIAG:
                 for g in range((self.tiles[t, 4] + DG - 1) // DG):
                     self.dbits[t] |= 1 << (g * DSL)
@@ -307,7 +310,11 @@ def test_forward_substitution_tasks(case, slices, bl):
     P = Plan(n, Ap, Ai, **kw)
     b = np.random.default_rng(3).standard_normal(n)
     R = Replay(P, slices, bl, fwd=True)
-    assert (R.tasks[:, 0] == FWD).sum() == (n + P.info["nb"] - 1) // P.info["nb"]
+    # every block's forward step exactly once: hosted by a waiting diagonal task or its own
+    hosted = R.tiles[R.tasks[R.tasks[:, 9] > 0, 9] - 1, 2]
+    own = R.tiles[R.tasks[R.tasks[:, 0] == FWD, 1], 2]
+    assert sorted(np.concatenate([hosted, own])) == list(range((n + P.info["nb"] - 1) // P.info["nb"]))
+    assert len(hosted) > 0
     got = R.run(Ax, b)
     F = O.OracleFactor(n, Ap, Ai, P.export("perm"))
     Lo, info = F.factor(Ax)

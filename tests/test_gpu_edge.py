@@ -71,7 +71,7 @@ def _race_cases():
     n2, bw2 = 3000, 40   # banded diagonal tiles whose later slices skip groups outside the band
     Ap2, Ai2 = I.band_pattern(n2, bw2)
     vals2 = np.stack([I.band_values(n2, bw2, s, Ap2, Ai2) for s in range(3)])
-    yield "band n=3000 bw 40, 2 slices", (n2, Ap2, Ai2), dict(nb=128, ordering="natural", row_slices=2), vals2
+    yield "band n=3000 bw 40, 8 slices", (n2, Ap2, Ai2), dict(nb=128, ordering="natural", row_slices=8), vals2
     Ap, Ai, Ax, coords = I.laplace2d_bordered(seed=0)
     vals = np.stack([I.laplace2d_bordered(seed=s)[2] for s in range(3)])
     yield "config 1 (bordered 2-D), ND", (len(Ap) - 1, Ap, Ai), dict(coords=coords, nb=64), vals

@@ -110,17 +110,18 @@ def test_band_row_slices(slices):
     check_against_oracle(P, Ap, Ai, vals, np.stack([I.rhs(n, s, 1) for s in range(2)]))
 
 
-@pytest.mark.parametrize("n,bw,nb", [(3000, 40, 128), (2001, 70, 128), (1500, 14, 64), (999, 200, 64)])
-def test_row_sliced_diagonal_factorization(n, bw, nb):
+@pytest.mark.parametrize("n,bw,nb,slices", [(3000, 40, 128, 8), (2001, 70, 128, 8), (1500, 14, 64, 8),
+                                             (999, 200, 64, 8), (5000, 200, 128, 2)])
+def test_row_sliced_diagonal_factorization(n, bw, nb, slices):
     # POTRF(k) partitioned over the row slices of (k,k): each slice solves its rows against
     # the column groups the earlier slices publish, then factors its own block.  Bands
     # narrower than n_b make banded diagonal tiles in which a slice skips the groups lying
     # wholly outside its rows' band; the exported task list shows that this happens.
     Ap, Ai = I.band_pattern(n, bw)
     vals = np.stack([I.band_values(n, bw, s, Ap, Ai) for s in range(2)])
-    P = Plan(n, Ap, Ai, nb=nb, ordering="natural", route="semisparse", row_slices=2)
-    T = L.stc_plan_export_taskset(P.h, 2, False, L.STC_TASKSET_TASKS).reshape(-1, 12)
-    tiles = L.stc_plan_export_taskset(P.h, 2, False, L.STC_TASKSET_TILES).reshape(-1, 13)
+    P = Plan(n, Ap, Ai, nb=nb, ordering="natural", route="semisparse", row_slices=slices)
+    T = L.stc_plan_export_taskset(P.h, slices, False, L.STC_TASKSET_TASKS).reshape(-1, 12)
+    tiles = L.stc_plan_export_taskset(P.h, slices, False, L.STC_TASKSET_TILES).reshape(-1, 13)
     sy = T[T[:, 0] == 2]
     assert len(sy) and (sy[:, 10] > 0).any(), "no diagonal tile factored by several slices"
     if bw + 16 < nb:
