@@ -224,13 +224,16 @@ int stc_plan_export(const stc_plan* plan, int what, void* buf, size_t* bytes);
  * sets; bit 1: the set of stc_factorize_solve, with its forward-substitution tasks), so
  * that host-side checks can execute it.  Every entry is widened to int64.  The set is
  * built on first request, as on the first factorization that uses it. */
-#define STC_TASKSET_TASKS 0     /* [ntasks][12] in queue order: kind (0 DIAG = SYRKs + POTRF,
+#define STC_TASKSET_TASKS 0     /* [ntasks][13] in queue order: kind (0 DIAG = SYRKs + POTRF,
                                    1 OFF = GEMMs + TRSM of a row slice, 2 SYRK = SYRKs into
                                    a row slice of (k,k) + the factorization of its rows,
-                                   3 FWD = forward substitution of block row k),
+                                   3 FWD = forward substitution of block row k, 4 FILL =
+                                   value upload of block column k),
                                    output tile, diagonal tile, update range [ubeg, uend),
-                                   row slice [rs0, rs1), TRSM rows [tr0, tr1), 0, slice
-                                   index, slice height of the off-diagonal tiles           */
+                                   row slice [rs0, rs1), TRSM rows [tr0, tr1), hosted
+                                   forward step (1 + its diagonal tile; 0: none), slice
+                                   index, slice height of the off-diagonal tiles, hosted
+                                   value upload (1 + its block column; 0: none)           */
 #define STC_TASKSET_UPDS 1      /* [nupds][10]: a, b (operand tiles), kmap (pair offset in
                                    the imap, -1 = contiguous inner range), klen, ka0, kb0
                                    (first stored column of a / b when contiguous), ra0, ra1
@@ -385,17 +388,25 @@ size_t stc_factorize_solve_workspace_bytes(const stc_plan* plan, int64_t batch, 
 int stc_factorize_solve(const stc_plan* plan, const double* d_values, int64_t batch, int64_t nrhs,
                         const double* d_b, void* d_factor, double* d_x, void* d_work, int32_t* d_info,
                         void* stream);
-/* Its halves after stc_scatter_values, for callers that time or overlap them separately
- * (tile routes only; a supernodal plan gives STC_ERR_UNSUPPORTED; d_work is required):
- *   stc_factorize_forward -- the factorization with the forward substitution (d_b as above)
- *                            on a factor that stc_scatter_values filled; y stays in d_work;
+/* Its two halves, for callers that time or overlap them separately (tile routes only; a
+ * supernodal plan gives STC_ERR_UNSUPPORTED; d_work is required):
+ *   stc_factorize_forward -- the value upload of Sec. 6.7 (d_values as for stc_factorize;
+ *                            where the plan's task set has enough waiting tasks to host it,
+ *                            each block column's values are placed inside the same launch,
+ *                            ahead of that column's tasks; else by stc_scatter_values
+ *                            first), the factorization and the forward substitution (d_b as
+ *                            above); y stays in d_work;
  *   stc_solve_backward    -- the backward substitution L^T z = y, x = P^T z, from the y
  *                            that stc_factorize_forward left in the same d_work (same
  *                            batch and nrhs). */
-int stc_factorize_forward(const stc_plan* plan, int64_t batch, int64_t nrhs, const double* d_b,
-                          void* d_factor, void* d_work, int32_t* d_info, void* stream);
+int stc_factorize_forward(const stc_plan* plan, const double* d_values, int64_t batch, int64_t nrhs,
+                          const double* d_b, void* d_factor, void* d_work, int32_t* d_info, void* stream);
 int stc_solve_backward(const stc_plan* plan, const void* d_factor, int64_t batch, int64_t nrhs,
                        double* d_x, void* d_work, void* stream);
+/* 1 if stc_factorize_forward of `batch` value sets places the values inside its launch
+ * (no separate scatter kernel), 0 if it runs stc_scatter_values first (and on the
+ * supernodal route); a negative STC_ERR_* on error.  Builds the task set on first use. */
+int stc_factorize_forward_fills(const stc_plan* plan, int64_t batch);
 
 /* Copy L's values out of the factor storage into CSC order (STC_EXPORT_LP / LI layout),
  * the "factor returned" form of Sec. 6.7 (Table 6 reports the factor kept on the device

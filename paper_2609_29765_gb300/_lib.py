@@ -44,6 +44,7 @@ EXPORTED = [
     "stc_strerror", "stc_factorize_mixed", "stc_quad_backward", "stc_plan_save", "stc_plan_load",
     "stc_plan_export_taskset", "stc_plan_sync_status", "stc_factorize_solve",
     "stc_factorize_solve_workspace_bytes", "stc_factorize_forward", "stc_solve_backward",
+    "stc_factorize_forward_fills",
 ]
 (STC_TASKSET_TASKS, STC_TASKSET_UPDS, STC_TASKSET_IMAP, STC_TASKSET_TILES, STC_TASKSET_SAIND,
  STC_TASKSET_CEXT, STC_TASKSET_CSC_MAP, STC_TASKSET_PAD_DIAG) = range(8)
@@ -135,10 +136,12 @@ def lib():
         L.stc_factorize_solve.restype = C.c_int
         L.stc_factorize_solve_workspace_bytes.argtypes = [_vp, C.c_int64, C.c_int64]
         L.stc_factorize_solve_workspace_bytes.restype = C.c_size_t
-        L.stc_factorize_forward.argtypes = [_vp, C.c_int64, C.c_int64, _vp, _vp, _vp, _vp, _vp]
+        L.stc_factorize_forward.argtypes = [_vp, _vp, C.c_int64, C.c_int64, _vp, _vp, _vp, _vp, _vp]
         L.stc_factorize_forward.restype = C.c_int
         L.stc_solve_backward.argtypes = [_vp, _vp, C.c_int64, C.c_int64, _vp, _vp, _vp]
         L.stc_solve_backward.restype = C.c_int
+        L.stc_factorize_forward_fills.argtypes = [_vp, C.c_int64]
+        L.stc_factorize_forward_fills.restype = C.c_int
         L.stc_factor_to_csc.argtypes = [_vp, _vp, C.c_int64, _vp, _vp]
         L.stc_factor_to_csc.restype = C.c_int
         L.stc_group_create.argtypes = [C.c_int32, C.POINTER(_vp), C.POINTER(C.c_int64), C.POINTER(_vp)]
@@ -313,9 +316,9 @@ def stc_factorize_solve_workspace_bytes(plan, batch, nrhs) -> int:
     return int(lib().stc_factorize_solve_workspace_bytes(plan, int(batch), int(nrhs)))
 
 
-def stc_factorize_forward(plan, batch, nrhs, d_b, d_factor, d_work, d_info, stream=None):
-    return lib().stc_factorize_forward(plan, int(batch), int(nrhs), _dev_ptr(d_b), _dev_ptr(d_factor),
-                                       _dev_ptr(d_work), _dev_ptr(d_info), _stream(stream))
+def stc_factorize_forward(plan, d_values, batch, nrhs, d_b, d_factor, d_work, d_info, stream=None):
+    return lib().stc_factorize_forward(plan, _dev_ptr(d_values), int(batch), int(nrhs), _dev_ptr(d_b),
+                                       _dev_ptr(d_factor), _dev_ptr(d_work), _dev_ptr(d_info), _stream(stream))
 
 
 def stc_solve_backward(plan, d_factor, batch, nrhs, d_x, d_work, stream=None):

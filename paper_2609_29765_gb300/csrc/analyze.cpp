@@ -1158,6 +1158,54 @@ stc::TaskSet* stc_plan::taskset(int32_t slices, bool bl_order, bool fwd) {
                 kept.push_back((int32_t)(nfact + k));
             }
         order.swap(kept);
+        // Value scatter of block column k inside the launch, hosted by a task that usually
+        // waits at its start (slice 1 of a diagonal tile waits for slice 0's first groups):
+        // the second such position before the first task of column k (or the nearest free
+        // one before it).  Every task of column k waits for the column's fill flag, so a
+        // host must come earlier in the queue.  Columns without a host get a TASK_FILL at
+        // the head of the queue; when fewer than half the columns find a host the set
+        // keeps the separate scatter kernel.
+        const size_t Q = order.size();
+        vector<int32_t> firstq(NT, (int32_t)Q);
+        for (size_t q = 0; q < Q; ++q) {
+            const int64_t col = tiles[tasks[order[q]].tile].J;
+            firstq[col] = std::min<int32_t>(firstq[col], (int32_t)q);
+        }
+        auto fhost = [&](int32_t q) {
+            const stc::DTask& h = tasks[order[q]];
+            return h.kind == stc::TASK_SYRK && h.slice == 1;
+        };
+        vector<int32_t> host(NT, -1);
+        int64_t nhost = 0;
+        for (int64_t k = 0; k < NT; ++k) {
+            int32_t from = -1, seen = 0;
+            for (int32_t q = firstq[k] - 1; q >= 0; --q)
+                if (fhost(q) && ++seen == 2) { from = q; break; }
+            for (int32_t q = from; q >= 0; --q)
+                if (fhost(q) && tasks[order[q]].fill == 0) {
+                    tasks[order[q]].fill = (int32_t)k + 1;
+                    host[k] = q;
+                    ++nhost;
+                    break;
+                }
+        }
+        if (2 * nhost < NT) {
+            for (int64_t k = 0; k < NT; ++k)
+                if (host[k] >= 0) tasks[order[host[k]]].fill = 0;
+        } else {
+            ts->fill_inside = true;
+            vector<int32_t> head;
+            for (int64_t k = 0; k < NT; ++k)
+                if (host[k] < 0) {
+                    stc::DTask f{};
+                    f.kind = stc::TASK_FILL; f.tile = diag_tile[k]; f.diag = diag_tile[k];
+                    tasks.push_back(f);
+                    key.push_back(-1.0);
+                    head.push_back((int32_t)(tasks.size() - 1));
+                }
+            head.insert(head.end(), order.begin(), order.end());
+            order.swap(head);
+        }
     }
     ts->tasks.reserve(order.size());
     ts->qkey.reserve(order.size());
@@ -1606,9 +1654,9 @@ static int taskset_export_impl(const stc_plan* P, int32_t slices, int bl_order, 
     switch (what) {
         case STC_TASKSET_TASKS:
             for (const stc::DTask& t : ts->tasks) {
-                const int64_t f[12] = {t.kind, t.tile, t.diag, t.ubeg, t.uend, t.rs0, t.rs1,
-                                       t.tr0, t.tr1, t.own_wait, t.slice, ts->slice_h};
-                tmp.insert(tmp.end(), f, f + 12);
+                const int64_t f[13] = {t.kind, t.tile, t.diag, t.ubeg, t.uend, t.rs0, t.rs1,
+                                       t.tr0, t.tr1, t.own_wait, t.slice, ts->slice_h, t.fill};
+                tmp.insert(tmp.end(), f, f + 13);
             }
             break;
         case STC_TASKSET_UPDS:

@@ -77,7 +77,7 @@ constexpr int kDiagGroupW = 16;
 constexpr int kMaxDiagSlices = 4;
 static_assert((kMaxNb / kDiagGroupW) * kMaxDiagSlices <= 32, "completion word holds every (group, slice) bit");
 
-enum : int32_t { TASK_DIAG = 0, TASK_OFF = 1, TASK_SYRK = 2, TASK_FWD = 3 };
+enum : int32_t { TASK_DIAG = 0, TASK_OFF = 1, TASK_SYRK = 2, TASK_FWD = 3, TASK_FILL = 4 };
 
 // One device task, the cases of Algorithm 1 grouped by output tile (row slice):
 //   TASK_DIAG  every SYRK into (k,k), then POTRF(k)                 (unsliced)
@@ -90,6 +90,9 @@ enum : int32_t { TASK_DIAG = 0, TASK_OFF = 1, TASK_SYRK = 2, TASK_FWD = 3 };
 //              right-hand sides, L_kn y_n and L_kk, once they are final (only in the task
 //              sets of the fused factorization + solve, for blocks no waiting diagonal task
 //              hosts; see own_wait)
+//   TASK_FILL  value scatter of block column k (tile = (k,k)): the column's range of the
+//              factor from the values through the fill map (fused task sets that fill
+//              inside the launch, for columns no waiting task hosts; see fill)
 struct DTask {
     int32_t kind;
     int32_t tile;        // output tile
@@ -101,7 +104,9 @@ struct DTask {
                          // diagonal tile of the block whose forward substitution it runs
                          // first (0: none)
     int32_t slice;       // TASK_OFF, TASK_SYRK: index of the row slice in its tile
-    int32_t pad;
+    int32_t fill;        // fused task sets that fill inside the launch: on a slice-1
+                         // TASK_SYRK, 1 + the block column whose value scatter it runs
+                         // first (0: none)
 };
 
 // One SYRK (a == b) or GEMM source of a task: out -= A(rows, inner) * B(cols, inner)^T.
@@ -176,6 +181,7 @@ struct TaskSet {
     std::vector<DUpd> upds;
     std::vector<int16_t> imap;
     int32_t slice_h = 0;          // rows per slice of an off-diagonal tile
+    bool fill_inside = false;     // fused set: the value scatter runs inside the launch
     std::vector<int32_t> nfinal;  // per tile completion target (count, or bit mask)
     std::vector<double> qkey;     // modelled start of each task (queue order)
     double period = 0.0;          // modelled time per block column

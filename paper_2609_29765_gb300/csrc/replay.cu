@@ -362,6 +362,12 @@ struct ReplayArgs {        // one job: a plan and a batch of value sets
     long long n;
     int nrhs;
     int nt;
+    // value scatter inside the launch (fused sets with fill_inside; null otherwise)
+    const double* vals;      // [batch][nnzA]
+    long long nnz;
+    const int32_t* fill_src; // per factor double: the A entry stored there, -1 (zero), -2 (1.0)
+    int* fillflag;           // [batch][nt]: block column k of the item filled
+    const int32_t* colstart; // per block column: its first tile (the diagonal), tiles in order
 };
 
 // One launch of the replay kernel: up to kMaxJobs jobs (plans) in one persistent grid.
@@ -825,6 +831,39 @@ __device__ void slice_factor(const ReplayArgs& a, const DTask& t, const DTile& O
     }
 }
 
+// a1 inside the factorization launch (TASK_FILL, or a slice-1 TASK_SYRK hosting it): the
+// value scatter of block column k for one item, every double of the column's tiles (they
+// are contiguous in the factor, up to the logdet partials) from the values through the
+// fill map, eight entries per thread in flight (the last column also zeroes the item's
+// tail after the partials); then the column's fill flag is set.
+__device__ void fill_col(const ReplayArgs& a, int k, long long item, double* F) {
+    const long long b = a.tiles[a.colstart[k]].off;
+    const long long e = k + 1 < a.nt ? a.tiles[a.colstart[k + 1]].off : a.poff;
+    const double* v = a.vals + item * a.nnz;
+    constexpr int U = 8;
+    for (long long f0 = b + threadIdx.x; f0 < e; f0 += (long long)kThreads * U) {
+        int src[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const long long f = f0 + (long long)u * kThreads;
+            src[u] = f < e ? __ldg(a.fill_src + f) : -1;
+        }
+        double x[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) x[u] = src[u] >= 0 ? __ldg(v + src[u]) : (src[u] == -2 ? 1.0 : 0.0);
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const long long f = f0 + (long long)u * kThreads;
+            if (f < e) __stcg(F + f, x[u]);
+        }
+    }
+    if (k == a.nt - 1)  // the item's tail after the logdet partials (which the diagonal tasks write)
+        for (long long f = a.poff + a.nt + threadIdx.x; f < a.fstride; f += kThreads) __stcg(F + f, 0.0);
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) red_release_add(a.fillflag + item * a.nt + k, 1);
+}
+
 // a10 inside the factorization launch (TASK_FWD): forward substitution of block row k for
 // every right-hand side of one item, y_k = L_kk^{-1} (b_k - sum_n L_kn y_n), once L_kk, the
 // tiles L_kn of block row k and the y_n are final.  The products take a row per thread
@@ -968,6 +1007,17 @@ __global__ void __launch_bounds__(kThreads, 2) replay_kernel_t(const __grid_cons
         const DTile O = a.tiles[t.tile];
         if (threadIdx.x == 0) s_ok = (*(volatile int*)&a.hdr->status == STC_OK);
         __syncthreads();
+        if (a.vals) {
+            // value scatter inside the launch: a hosted or explicit column fill first, and
+            // no work on a column before its values are in place
+            if (t.fill > 0 || t.kind == TASK_FILL) {
+                fill_col(a, t.kind == TASK_FILL ? O.J : t.fill - 1, item, F);
+                if (t.kind == TASK_FILL) continue;
+            }
+            if (threadIdx.x == 0 && s_ok)
+                s_ok = wait_counter(a.fillflag + item * a.nt + O.J, 1, a.spin, &a.hdr->status);
+            __syncthreads();
+        }
         if (t.own_wait > 0 && a.y) {
             // fused task sets: a forward-substitution step hosted by this task, run first
             fwd_task(a, t.own_wait - 1, item, F, cnt, C, S0, S1, sv, s_ok);
@@ -3187,9 +3237,11 @@ extern "C" int stc_solve(const stc_plan* Pc, const void* d_factor, int64_t batch
     return cudaGetLastError() == cudaSuccess ? STC_OK : STC_ERR_CUDA;
 }
 
-// Fused factorization + solve: [header | completion counters], then (256-byte aligned)
-// the solve's step flags and y vectors.
-size_t fused_solve_off(const stc_plan* P, int64_t batch) { return (factorize_ws(P, batch) + 255) / 256 * 256; }
+// Fused factorization + solve: [header | completion counters | fill flags (one per item
+// and block column)], then (256-byte aligned) the solve's step flags and y vectors.
+size_t fused_solve_off(const stc_plan* P, int64_t batch) {
+    return (factorize_ws(P, batch) + (size_t)batch * P->nt * sizeof(int) + 255) / 256 * 256;
+}
 
 extern "C" size_t stc_factorize_solve_workspace_bytes(const stc_plan* P, int64_t batch, int64_t nrhs) {
     if (!P || batch < 0 || nrhs < 0) return 0;
@@ -3197,10 +3249,12 @@ extern "C" size_t stc_factorize_solve_workspace_bytes(const stc_plan* P, int64_t
     return fused_solve_off(P, batch) + solve_ws(P, batch * nrhs) - sizeof(WorkHeader);
 }
 
-extern "C" int stc_factorize_forward(const stc_plan* Pc, int64_t batch, int64_t nrhs, const double* d_b,
-                                     void* d_factor, void* d_work, int32_t* d_info, void* stream) {
+extern "C" int stc_factorize_forward(const stc_plan* Pc, const double* d_values, int64_t batch, int64_t nrhs,
+                                     const double* d_b, void* d_factor, void* d_work, int32_t* d_info,
+                                     void* stream) {
     stc_plan* P = const_cast<stc_plan*>(Pc);
-    if (!P || !d_factor || !d_info || !d_b || !d_work || batch <= 0 || nrhs <= 0) return STC_ERR_INVALID_ARG;
+    if (!P || !d_values || !d_factor || !d_info || !d_b || !d_work || batch <= 0 || nrhs <= 0)
+        return STC_ERR_INVALID_ARG;
     if (is_sn(P)) return STC_ERR_UNSUPPORTED;
     int dev, sms, rc;
     if ((rc = device_info(&dev, &sms))) return rc;
@@ -3208,6 +3262,9 @@ extern "C" int stc_factorize_forward(const stc_plan* Pc, int64_t batch, int64_t 
     TaskSet* ts = nullptr;
     if ((rc = pick_taskset(P, batch, sms, batch <= 2, &ts, true))) return rc;
     if ((rc = ensure_taskset(P, ts, dev))) return rc;
+    // the value scatter: inside the launch (hosted by waiting tasks) or, for task sets
+    // with too few hosts, the scatter kernel first
+    if (!ts->fill_inside && (rc = stc_scatter_values(P, d_values, batch, d_factor, stream))) return rc;
     const long long chains = batch * nrhs;
     cudaStream_t st = S(stream);
     const size_t off = fused_solve_off(P, batch), flags = solve_flags(P, chains);
@@ -3222,12 +3279,28 @@ extern "C" int stc_factorize_forward(const stc_plan* Pc, int64_t batch, int64_t 
     j.y = (double*)((char*)d_work + off + flags);
     j.perm = P->dev.perm; j.rowstart = P->dev.srow_beg; j.rowtiles = P->dev.srow_tiles;
     j.n = P->n; j.nrhs = (int)nrhs; j.nt = (int)P->nt;
+    if (ts->fill_inside) {
+        j.vals = d_values; j.nnz = P->nnzA; j.fill_src = P->dev.fill_src;
+        j.fillflag = (int*)((char*)d_work + factorize_ws(P, batch));
+        j.colstart = P->dev.scol_beg;
+    }
     Lc.njobs = 1;
     Lc.queue = nullptr;
     Lc.hdr = hdr;
     Lc.total = (long long)ts->tasks.size() * batch;
     replay_kernel_t<false><<<grid_of(P, default_ctas(sms, batch_total(Lc)), Lc.total), kThreads, kRSmemBytes, st>>>(Lc);
     return cudaGetLastError() == cudaSuccess ? STC_OK : STC_ERR_CUDA;
+}
+
+extern "C" int stc_factorize_forward_fills(const stc_plan* Pc, int64_t batch) {
+    stc_plan* P = const_cast<stc_plan*>(Pc);
+    if (!P || batch <= 0) return STC_ERR_INVALID_ARG;
+    if (is_sn(P)) return 0;
+    int dev, sms, rc;
+    if ((rc = device_info(&dev, &sms))) return rc;
+    TaskSet* ts = nullptr;
+    if ((rc = pick_taskset(P, batch, sms, batch <= 2, &ts, true))) return rc;
+    return ts->fill_inside ? 1 : 0;
 }
 
 extern "C" int stc_solve_backward(const stc_plan* Pc, const void* d_factor, int64_t batch, int64_t nrhs,
@@ -3279,8 +3352,7 @@ extern "C" int stc_factorize_solve(const stc_plan* Pc, const double* d_values, i
         if ((rc = stc_factorize(P, d_values, batch, d_factor, d_work, d_info, stream))) return rc;
         return stc_solve(P, d_factor, batch, nrhs, d_b, d_x, d_work, stream);
     }
-    if ((rc = stc_scatter_values(P, d_values, batch, d_factor, stream))) return rc;
-    if ((rc = stc_factorize_forward(P, batch, nrhs, d_b, d_factor, d_work, d_info, stream))) return rc;
+    if ((rc = stc_factorize_forward(P, d_values, batch, nrhs, d_b, d_factor, d_work, d_info, stream))) return rc;
     return stc_solve_backward(P, d_factor, batch, nrhs, d_x, d_work, stream);
 }
 

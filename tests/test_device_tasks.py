@@ -30,7 +30,7 @@ from paper_2609_29765_gb300.api import Plan
 
 KC = 16      # inner chunk of the tile products
 PANEL = 32   # TRSM panel width
-DIAG, OFF, SYRK, FWD = 0, 1, 2, 3
+DIAG, OFF, SYRK, FWD, FILL = 0, 1, 2, 3, 4
 DG, DSL = 16, 4   # column group width and slices per word of a diagonal tile's completion bits
 T_OFF, T_DENSE, T_BAND = 0, 1, 2
 
@@ -46,7 +46,7 @@ class Replay:
     def __init__(self, P, slices, bl, fwd=False):
         ex = lambda w: L.stc_plan_export_taskset(P.h, slices, int(bl) | (2 if fwd else 0), w)
         self.nb = P.info["nb"]
-        self.tasks = ex(L.STC_TASKSET_TASKS).reshape(-1, 12)
+        self.tasks = ex(L.STC_TASKSET_TASKS).reshape(-1, 13)
         self.upds = ex(L.STC_TASKSET_UPDS).reshape(-1, 10)
         self.imap = ex(L.STC_TASKSET_IMAP).reshape(-1, 2)
         self.tiles = ex(L.STC_TASKSET_TILES).reshape(-1, 13)
@@ -195,6 +195,24 @@ class Replay:
         sw = self.tiles[t, 4]
         Y[k * nb:k * nb + sw] = solve_triangular(D[:sw, :sw], v[:sw], lower=True)
 
+    def col_range(self, k):
+        # a block column's tiles are contiguous in the factor, up to the logdet partials
+        nb = self.nb
+        size = lambda t: nb * t[4] if t[3] == T_OFF else (nb * nb if t[3] == T_DENSE else (t[7] + 1) * nb)
+        ends = {}
+        for t in self.tiles:
+            b, e = ends.get(t[2], (t[0], t[0]))
+            ends[t[2]] = (min(b, t[0]), max(e, t[0] + size(t)))
+        return ends[k]
+
+    def fill_col(self, F, k, values):
+        b, e = self.col_range(k)
+        F[b:e] = 0.0
+        m = (self.value_map >= b) & (self.value_map < e)
+        F[self.value_map[m]] = values[m]
+        p = self.pad[(self.pad >= b) & (self.pad < e)]
+        F[p] = 1.0
+
     def run(self, values, rhs=None):
         self.dbits = {}
         nb, n = self.nb, len(self.perm)
@@ -206,12 +224,24 @@ class Replay:
         for t in range(len(self.tiles)):
             if self.tiles[t, 3] != T_OFF:
                 self.dbits[t] = 0
-        F = np.zeros(self.fdoubles)
-        F[self.value_map] = values
-        F[self.pad] = 1.0
+        inside = bool((self.tasks[:, 0] == FILL).any() or (self.tasks[:, 12] > 0).any())
+        if inside:
+            # the values arrive column by column inside the launch: anything a task reads
+            # before its column is filled is NaN and shows in the result
+            F = np.full(self.fdoubles, np.nan)
+        else:
+            F = np.zeros(self.fdoubles)
+            F[self.value_map] = values
+            F[self.pad] = 1.0
         nb = self.nb
         for tk in self.tasks:
             kind, t = tk[0], tk[1]
+            if tk[12] > 0:  # a hosted value upload of a later block column, run first
+                assert kind == SYRK and tk[10] == 1
+                self.fill_col(F, tk[12] - 1, values)
+            if kind == FILL:
+                self.fill_col(F, self.tiles[t, 2], values)
+                continue
             if tk[9] > 0:   # a hosted forward-substitution step, run first
                 assert kind == DIAG or (kind == SYRK and tk[10] == 0)
                 self.fwd_task(F, (FWD, tk[9] - 1), bp, self.y)
@@ -315,7 +345,10 @@ def test_forward_substitution_tasks(case, slices, bl):
     own = R.tiles[R.tasks[R.tasks[:, 0] == FWD, 1], 2]
     assert sorted(np.concatenate([hosted, own])) == list(range((n + P.info["nb"] - 1) // P.info["nb"]))
     assert len(hosted) > 0
+    if name == "band_nb128":
+        assert (R.tasks[:, 12] > 0).sum() >= len(hosted) // 2, "value upload not hosted"
     got = R.run(Ax, b)
+    assert not np.isnan(got).any()
     F = O.OracleFactor(n, Ap, Ai, P.export("perm"))
     Lo, info = F.factor(Ax)
     assert np.array_equal(got, Replay(P, slices, bl).run(Ax))

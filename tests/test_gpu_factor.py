@@ -120,7 +120,7 @@ def test_row_sliced_diagonal_factorization(n, bw, nb, slices):
     Ap, Ai = I.band_pattern(n, bw)
     vals = np.stack([I.band_values(n, bw, s, Ap, Ai) for s in range(2)])
     P = Plan(n, Ap, Ai, nb=nb, ordering="natural", route="semisparse", row_slices=slices)
-    T = L.stc_plan_export_taskset(P.h, slices, False, L.STC_TASKSET_TASKS).reshape(-1, 12)
+    T = L.stc_plan_export_taskset(P.h, slices, False, L.STC_TASKSET_TASKS).reshape(-1, 13)
     tiles = L.stc_plan_export_taskset(P.h, slices, False, L.STC_TASKSET_TILES).reshape(-1, 13)
     sy = T[T[:, 0] == 2]
     assert len(sy) and (sy[:, 10] > 0).any(), "no diagonal tile factored by several slices"
