@@ -609,12 +609,47 @@ def run_ours(args):
     # the scatter kernel on its own (outside the timed region): in the step the value
     # upload runs inside the factorization's launch when the task set hosts it
     ms_scatter = _events_ms(lambda: L.check(L.stc_scatter_values(P.h, dv, batch, fac), "scatter"), 3, 1)
-    # ---- e2e: host buffers in, logdet + x back out, every step.  The copies run on a
-    # second stream, double-buffered: step k+1's values and right-hand sides go up while
-    # step k factorizes, step k's logdet and x come back while step k+1 runs.
-    e2e_ms = 0.0
+    # ---- e2e: inputs in pinned host memory, logdet + x back out, every step.  (1) the
+    # kernels read the values and right-hand sides in place from pinned host memory (the
+    # value upload runs inside the factorization's launch, over NVLink-C2C); (2) the same
+    # with explicit copies on a second stream, double-buffered: step k+1's inputs go up
+    # while step k factorizes.  Both copy logdet and x back on a second stream while the
+    # next step runs.
+    e2e_ms = e2e_copy_ms = 0.0
     if not args.no_e2e:
         cs = torch.cuda.Stream()
+        xb = [dx, torch.empty_like(dx)]
+        lb = [ld, torch.empty_like(ld)]
+        zdone = [ev(), ev()]
+        zout = [ev(), ev()]
+
+        def run_zc(steps):
+            for k in range(steps):
+                j = k % 2
+                if k >= 2:
+                    st.wait_event(zout[j])        # step k-2's results have left this buffer
+                L.check(L.stc_factorize_forward(P.h, hv, batch, 1, hb, fac, ws, info), "factorize+forward")
+                L.check(L.stc_logdet(P.h, fac, batch, lb[j]), "logdet")
+                L.check(L.stc_solve_backward(P.h, fac, batch, 1, xb[j], ws), "backward solve")
+                zdone[j].record(st)
+                with torch.cuda.stream(cs):
+                    cs.wait_event(zdone[j])
+                    hld.copy_(lb[j], non_blocking=True)
+                    hx.copy_(xb[j], non_blocking=True)
+                    zout[j].record(cs)
+            st.wait_stream(cs)
+
+        run_zc(2)
+        barrier()
+        t0, t1 = ev(), ev()
+        t0.record(st)
+        cs.wait_stream(st)
+        run_zc(args.steps)
+        t1.record(st)
+        barrier()
+        e2e_ms = t0.elapsed_time(t1) / args.steps
+        L.check(L.stc_sync_status(ws), "device status")
+        del xb, lb
         bufs = [(dv, db, dx, ld),
                 (torch.empty_like(dv), torch.empty_like(db), torch.empty_like(dx), torch.empty_like(ld))]
         ev_in = [ev(), ev()]
@@ -661,7 +696,7 @@ def run_ours(args):
         run_e2e(args.steps)
         t1.record(st)
         barrier()
-        e2e_ms = t0.elapsed_time(t1) / args.steps
+        e2e_copy_ms = t0.elapsed_time(t1) / args.steps
         del bufs
     # ---- plain: one factorization per launch (batch 1)
     fac1 = torch.empty(P.factor_bytes(1) // 8, dtype=torch.float64, device="cuda")
@@ -686,7 +721,8 @@ def run_ours(args):
     L.check(L.stc_sync_status(ws), "device status")
 
     # ---- max over ranks
-    ms_step, ms_replay, e2e_ms, ms_plain = max_over_ranks([ms_step, ms_replay, e2e_ms, ms_plain], dist, "cuda")
+    ms_step, ms_replay, e2e_ms, e2e_copy_ms, ms_plain = max_over_ranks(
+        [ms_step, ms_replay, e2e_ms, e2e_copy_ms, ms_plain], dist, "cuda")
     # ---- the other workloads (rank 0, after the headline; free the headline's buffers first)
     workloads = None
     if rank == 0 and args.workloads != "none":
@@ -753,8 +789,16 @@ def run_ours(args):
         line["e2e"] = {"value": total_items / (e2e_ms * 1e-3), "unit": UNIT,
                        "h2d_bytes_per_step": batch * (nnz + n) * 8,
                        "d2h_bytes_per_step": batch * (1 + n) * 8,
-                       "note": "pinned host buffers; every step's values and RHS copied in and logdet + x "
-                               "copied out on a second stream, double-buffered against the factorization"}
+                       "note": "every step's values and RHS start in pinned host memory and are read in place "
+                               "by the kernels (the value upload runs inside the factorization's launch, over "
+                               "NVLink-C2C; stc_factorize_forward given the host buffers); logdet + x copied "
+                               "out on a second stream while the next step runs"}
+        line["e2e_copies"] = {"value": total_items / (e2e_copy_ms * 1e-3), "unit": UNIT,
+                              "h2d_bytes_per_step": batch * (nnz + n) * 8,
+                              "d2h_bytes_per_step": batch * (1 + n) * 8,
+                              "note": "the same with explicit copies: every step's values and RHS copied in "
+                                      "(cudaMemcpyAsync from pinned memory) on a second stream, double-buffered "
+                                      "against the factorization; the first step's copy is not hidden"}
     if workloads:
         line["workloads"] = workloads
     print(json.dumps(line), flush=True)

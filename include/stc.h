@@ -383,7 +383,12 @@ int stc_solve(const stc_plan* plan, const void* d_factor, int64_t batch, int64_t
  * alias d_b); d_factor and d_info written as by stc_factorize (the factor is the same to
  * the bit); d_work stc_factorize_solve_workspace_bytes(plan, batch, nrhs) bytes or NULL
  * (see above).  Status as for stc_factorize (stc_sync_status on d_work).  On the
- * supernodal route it runs the two calls one after the other. */
+ * supernodal route it runs the two calls one after the other.  d_values and d_b (here, in
+ * stc_factorize_forward, stc_factorize and stc_scatter_values) may also point to pinned
+ * host memory that the device can address (cudaHostAlloc'ed memory under unified
+ * addressing): the kernels then read the inputs in place, the upload overlapping the
+ * factorization, with no separate copy (on a GB300 with NVLink-C2C: the same step time
+ * as with inputs in HBM); pageable host memory is not supported. */
 size_t stc_factorize_solve_workspace_bytes(const stc_plan* plan, int64_t batch, int64_t nrhs);
 int stc_factorize_solve(const stc_plan* plan, const double* d_values, int64_t batch, int64_t nrhs,
                         const double* d_b, void* d_factor, double* d_x, void* d_work, int32_t* d_info,

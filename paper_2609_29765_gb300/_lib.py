@@ -193,6 +193,18 @@ def _dev_ptr(t):
     return C.c_void_p(t.data_ptr())
 
 
+def _in_ptr(t):
+    """An input the kernels read: a CUDA tensor, or a pinned host tensor (read by the
+    kernels in place where the platform maps pinned host memory for the device)."""
+    if t is not None and not t.is_cuda:
+        if not t.is_pinned():
+            raise ValueError("expected a CUDA tensor or a pinned host tensor")
+        if not t.is_contiguous():
+            raise ValueError("expected a contiguous tensor")
+        return C.c_void_p(t.data_ptr())
+    return _dev_ptr(t)
+
+
 def _stream(stream):
     if stream is None:
         import torch
@@ -276,12 +288,12 @@ def stc_workspace_bytes(plan, batch):
 
 
 def stc_factorize(plan, d_values, batch, d_factor, d_work, d_info, stream=None):
-    return lib().stc_factorize(plan, _dev_ptr(d_values), int(batch), _dev_ptr(d_factor), _dev_ptr(d_work),
+    return lib().stc_factorize(plan, _in_ptr(d_values), int(batch), _dev_ptr(d_factor), _dev_ptr(d_work),
                                _dev_ptr(d_info), _stream(stream))
 
 
 def stc_scatter_values(plan, d_values, batch, d_factor, stream=None):
-    return lib().stc_scatter_values(plan, _dev_ptr(d_values), int(batch), _dev_ptr(d_factor), _stream(stream))
+    return lib().stc_scatter_values(plan, _in_ptr(d_values), int(batch), _dev_ptr(d_factor), _stream(stream))
 
 
 def stc_factorize_scattered(plan, batch, d_factor, d_work, d_info, stream=None):
@@ -307,7 +319,7 @@ def stc_solve(plan, d_factor, batch, nrhs, d_b, d_x, d_work, stream=None):
 
 
 def stc_factorize_solve(plan, d_values, batch, nrhs, d_b, d_factor, d_x, d_work, d_info, stream=None):
-    return lib().stc_factorize_solve(plan, _dev_ptr(d_values), int(batch), int(nrhs), _dev_ptr(d_b),
+    return lib().stc_factorize_solve(plan, _in_ptr(d_values), int(batch), int(nrhs), _in_ptr(d_b),
                                      _dev_ptr(d_factor), _dev_ptr(d_x), _dev_ptr(d_work), _dev_ptr(d_info),
                                      _stream(stream))
 
@@ -317,7 +329,7 @@ def stc_factorize_solve_workspace_bytes(plan, batch, nrhs) -> int:
 
 
 def stc_factorize_forward(plan, d_values, batch, nrhs, d_b, d_factor, d_work, d_info, stream=None):
-    return lib().stc_factorize_forward(plan, _dev_ptr(d_values), int(batch), int(nrhs), _dev_ptr(d_b),
+    return lib().stc_factorize_forward(plan, _in_ptr(d_values), int(batch), int(nrhs), _in_ptr(d_b),
                                        _dev_ptr(d_factor), _dev_ptr(d_work), _dev_ptr(d_info), _stream(stream))
 
 

@@ -152,9 +152,12 @@ class Plan:
 
 
     def factorize_solve(self, values, b, check_status=False):
-        """Factorize and solve in one call (the forward substitution runs inside the
-        factorization's launch): values [batch, nnzA], b [batch, nrhs, n] (or [batch, n]),
-        CUDA float64.  Returns (Factor, x); the factor is the one factorize() gives."""
+        """Factorize and solve in one call (the value upload and the forward substitution
+        run inside the factorization's launch): values [batch, nnzA], b [batch, nrhs, n]
+        (or [batch, n]), float64 on the GPU or in pinned host memory (read by the kernels
+        in place, where the platform maps pinned host memory for the device, as over
+        NVLink-C2C).  Returns (Factor, x) with x on the GPU; the factor is the one
+        factorize() gives."""
         torch = _torch()
         if values.dim() == 1:
             values = values.unsqueeze(0)
@@ -169,10 +172,12 @@ class Plan:
         if b.shape[0] != batch or b.shape[2] != self.n or b.dtype != torch.float64:
             raise ValueError("b must be float64 [batch, nrhs, n]")
         nrhs = b.shape[1]
-        fac = torch.empty(self.factor_bytes(batch) // 8, dtype=torch.float64, device=values.device)
-        info = torch.empty(batch, dtype=torch.int32, device=values.device)
-        x = torch.empty_like(b)
-        ws = self.workspace(batch, values.device, L.stc_factorize_solve_workspace_bytes(self.h, batch, nrhs))
+        # values and b may be pinned host tensors: the kernels then read them in place
+        dev = values.device if values.is_cuda else torch.device("cuda", torch.cuda.current_device())
+        fac = torch.empty(self.factor_bytes(batch) // 8, dtype=torch.float64, device=dev)
+        info = torch.empty(batch, dtype=torch.int32, device=dev)
+        x = torch.empty(b.shape, dtype=torch.float64, device=dev)
+        ws = self.workspace(batch, dev, L.stc_factorize_solve_workspace_bytes(self.h, batch, nrhs))
         L.check(L.stc_factorize_solve(self.h, values, batch, nrhs, b, fac, x, ws, info), "stc_factorize_solve")
         if check_status:
             L.check(L.stc_sync_status(ws), "stc_factorize_solve (device status)")

@@ -294,3 +294,21 @@ def test_factorize_solve_fused(case):
     # a second call on the same workspace gives the same x
     _, x2 = P.factorize_solve(dev(vals), dev(rhs))
     assert np.array_equal(x2.cpu().numpy(), x)
+
+
+@pytest.mark.parametrize("case", [c for c in _fused_cases() if c[0] in (
+    "band n=5000 bw 200", "random indexed, n_b 16", "config 1, supernodal route")], ids=lambda c: c[0])
+def test_factorize_solve_pinned_host_inputs(case):
+    # values and right-hand sides left in pinned host memory and read in place by the
+    # kernels (value upload inside the launch, the scatter kernel, or the supernodal
+    # route's separate calls): the same factor and solution, to the bit, as from HBM
+    name, (n, Ap, Ai), kw, vals = case
+    P = Plan(n, Ap, Ai, **kw)
+    rhs = np.stack([I.rhs(n, 60 + b, 2) for b in range(vals.shape[0])])
+    fac1, x1 = P.factorize_solve(dev(vals), dev(rhs))
+    hv = torch.from_numpy(np.ascontiguousarray(vals)).pin_memory()
+    hb = torch.from_numpy(np.ascontiguousarray(rhs)).pin_memory()
+    fac2, x2 = P.factorize_solve(hv, hb, check_status=True)
+    assert int(fac2.info.abs().sum()) == 0
+    assert torch.equal(fac1.data, fac2.data), name
+    assert torch.equal(x1, x2), name
