@@ -35,6 +35,17 @@ def test_library_exports_every_header_symbol():
     assert sorted(L.EXPORTED) == declared
 
 
+def test_binding_refuses_pageable_host_inputs():
+    # inputs the kernels read may be device tensors or pinned host tensors (read in place);
+    # pageable host memory is refused before any call, outputs must be device tensors
+    torch = pytest.importorskip("torch")
+    x = torch.zeros(3, dtype=torch.float64)
+    with pytest.raises(ValueError):
+        L._in_ptr(x)
+    with pytest.raises(ValueError):
+        L._dev_ptr(x)
+
+
 def _cases():
     Ap, Ai, Ax, coords = I.laplace2d_bordered()
     yield "c1_nd_nb64", len(Ap) - 1, Ap, Ai, coords, dict(nb=64, ordering="nd"), None
