@@ -417,3 +417,32 @@ def test_edge_patterns(edge, nb):
             for slices, bl in ((1, False), (2, False), (8, True)):
                 got = Replay(P, slices, bl).run(Ax)
                 assert np.max(np.abs(got - Lo)) <= 1e-12 * np.max(np.abs(Lo)), (name, route, ordering, slices)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_fused_task_sets_on_random_patterns(seed):
+    # random patterns, tile sizes, orderings and slice counts: the fused task set executed
+    # in queue order from a NaN factor (value uploads and forward steps where the queue
+    # puts them) gives the oracle's factor and y = L^{-1} P b, so every task comes after
+    # what it reads
+    from scipy.sparse.linalg import spsolve_triangular
+    import scipy.sparse as sp
+    rng = np.random.default_rng(100 + seed)
+    n = int(rng.integers(150, 700))
+    Ap, Ai, Ax = I.random_spd(n, float(rng.uniform(0.004, 0.03)), seed)
+    nb = int(rng.choice([8, 16, 32, 64]))
+    P = Plan(n, Ap, Ai, nb=nb, ordering=str(rng.choice(["rcm", "natural"])), route="semisparse")
+    F = O.OracleFactor(n, Ap, Ai, P.export("perm"))
+    Lo, info = F.factor(Ax)
+    assert info == 0
+    b = rng.standard_normal(n)
+    Lm = sp.csr_matrix(sp.csc_matrix((Lo, F.Li, F.Lp), shape=(n, n)))
+    y = spsolve_triangular(Lm, b[F.perm], lower=True)
+    col = np.repeat(np.arange(n), np.diff(F.Lp))
+    scale = np.maximum.reduceat(np.abs(Lo), F.Lp[:-1])[col]
+    for slices, bl in ((1, False), (2, False), (4, True), (8, False)):
+        R = Replay(P, slices, bl, fwd=True)
+        got = R.run(Ax, b)
+        assert not np.isnan(got).any()
+        assert np.max(np.abs(got - Lo) / scale) <= 1e-12, (seed, slices, bl)
+        assert np.max(np.abs(R.y[:n] - y)) <= 1e-11 * np.max(np.abs(y)), (seed, slices, bl)
